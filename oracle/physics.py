@@ -1,0 +1,75 @@
+"""Scalar formulas of arXiv:1410.1921, FP64, one function per equation.
+
+Test infrastructure (part of the oracle).  SI units unless a name says
+otherwise.
+"""
+import math
+
+R_GAS = 8.314462618  # J / (mol K)
+
+
+def knudsen_diffusivity(d_m, T_K, M_kg_per_mol):
+    """Eq. 11: D_K = (d_p / 3) sqrt(8 R T / (pi M))."""
+    return (d_m / 3.0) * math.sqrt(8.0 * R_GAS * T_K / (math.pi * M_kg_per_mol))
+
+
+def tau_knudsen(d_nm, d_ref_nm=60.0, tau_ref=1.0):
+    """Eq. 12: tau_g = (d_p / d_p,ref)(tau_g,ref - 1/2) + 1/2."""
+    return (d_nm / d_ref_nm) * (tau_ref - 0.5) + 0.5
+
+
+def d3q7_lattice_diffusivity(tau):
+    """BGK diffusion on D3Q7 with rest weight 1/4: c_s^2 = 1/4, D_L = (tau - 1/2)/4."""
+    return (tau - 0.5) * 0.25
+
+
+def d3q19_viscosity(tau):
+    """Eq. 8 with c_s^2 = 1/3: nu = (tau - 1/2)/3 (lattice units)."""
+    return (tau - 0.5) / 3.0
+
+
+def permeability_physical(k_lattice, dx_m):
+    """Eq. 15: k_P / l_P^2 = k_L / l_L^2 with one lattice length = dx."""
+    return k_lattice * dx_m * dx_m
+
+
+def diffusivity_physical(D_lattice, d_ref_m, T_K, M, tau_ref=1.0):
+    """Eq. 15 with the time step fixed by the reference pore: D_L,ref maps to
+    D_K(d_ref) (Eqs. 11-12), so D_P = D_L * D_K,ref / D_L,ref."""
+    return D_lattice * knudsen_diffusivity(d_ref_m, T_K, M) / d3q7_lattice_diffusivity(tau_ref)
+
+
+def tortuosity(porosity, D_mean, D_eff):
+    """Eq. 16: D_eff = D eps / tortuosity."""
+    return porosity * D_mean / D_eff
+
+
+def bruggeman_alpha(D_eff, D_ref, porosity):
+    """Sec. 4.2: D_eff = D eps^alpha  ->  alpha = ln(D_eff/D)/ln(eps)."""
+    return math.log(D_eff / D_ref) / math.log(porosity)
+
+
+def kozeny_carman(d_m, porosity):
+    """Eq. 17 with A = d^2/180."""
+    return (d_m * d_m / 180.0) * porosity ** 3 / (1.0 - porosity) ** 2
+
+
+def apparent_permeability(k_d, D_eff, mu, p):
+    """Eq. 26: k_a = k_d f_c, f_c = 1 + D_eff mu / (k_d p).  Returns (k_a, f_c)."""
+    fc = 1.0 + D_eff * mu / (k_d * p)
+    return k_d * fc, fc
+
+
+def cylinder_permeability(d_m):
+    """Eq. 27: k_d = (d_p/2)^2 / 8."""
+    return (d_m / 2.0) ** 2 / 8.0
+
+
+def mean_free_path(mu, p, T_K, M):
+    """Eq. 29: lambda = (mu/p) sqrt(pi R T / (2 M))."""
+    return (mu / p) * math.sqrt(math.pi * R_GAS * T_K / (2.0 * M))
+
+
+def cylinder_fc(Kn):
+    """Eq. 28: f_c = 1 + (64 / (3 pi)) Kn."""
+    return 1.0 + 64.0 / (3.0 * math.pi) * Kn

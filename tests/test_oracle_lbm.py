@@ -1,0 +1,251 @@
+"""Oracle pins for the two lattice Boltzmann models (Secs. 3.1-3.4, App. A).
+
+MRT flow: the printed Q and Q^-1 tables, the equilibrium moments A1-A9
+against the BGK equilibrium of Eq. 3, the rates of Eq. 7, an independent
+two-relaxation-time collision, and the closed forms of plane Poiseuille
+flow (exact at the nodes), square-duct flow (Fourier series) and pipe flow
+(Eq. 27).  BGK diffusion: exactness for a straight channel, mass
+conservation, and the sphere-in-cube value printed in Sec. 3.5.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_table(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        rows.append([float(Fraction(t)) for t in line.split()])
+    return np.array(rows)
+
+
+def test_q_matches_printed_table(orc):
+    assert np.array_equal(orc.q_matrix(), _read_table("q_printed.txt"))
+
+
+def test_qinv_is_inverse_and_matches_printed_table_but_erratum(orc):
+    Q, Qi = orc.q_matrix(), orc.qinv_matrix()
+    assert np.allclose(Q @ Qi, np.eye(19), atol=1e-14)
+    printed = _read_table("qinv_printed.txt")
+    diff = np.abs(Qi - printed) > 1e-15
+    # the only disagreement: population 6 (e = -z), moments 11 and 12, where
+    # the printed -1/36, 1/36 cannot be right (Q^-1 Q = I needs -1/12, 1/12)
+    assert sorted(zip(*np.nonzero(diff))) == [(6, 11), (6, 12)]
+    assert Qi[6, 11] == pytest.approx(-1 / 12) and Qi[6, 12] == pytest.approx(1 / 12)
+    bad = printed.copy()
+    assert np.abs(bad @ Q - np.eye(19)).max() > 1e-3  # the printed table is not an inverse
+
+
+def test_velocity_set_and_weights(orc):
+    e = orc.velocities19()
+    assert len({tuple(v) for v in e}) == 19
+    s = np.abs(e).sum(axis=1)
+    assert sorted(s.tolist()) == [0] + [1] * 6 + [2] * 12
+    assert np.all(np.abs(e) <= 1)
+    w = orc.weights19()
+    gold = json.load(open(os.path.join(GOLDEN, "paper_values.json")))["weights_d3q19"]
+    assert np.allclose(w[s == 0], gold["rest"]) and np.allclose(w[s == 1], gold["axis"])
+    assert np.allclose(w[s == 2], gold["diagonal"])
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose((w[:, None, None] * e[:, :, None] * e[:, None, :]).sum(0), np.eye(3) / 3)
+    opp = orc.opposite19()
+    assert np.all(e[opp] == -e)
+
+
+def test_equilibrium_moments_equal_q_times_bgk_equilibrium(orc):
+    Q, e, w = orc.q_matrix(), orc.velocities19(), orc.weights19()
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        rho = 1 + 0.2 * rng.standard_normal()
+        j = 0.1 * rng.standard_normal(3)
+        eu = e @ j
+        feq = w * (rho + 3 * eu + 4.5 * eu ** 2 - 1.5 * j @ j)  # Eq. 3, rho0 = 1
+        assert np.allclose(Q @ feq, orc.meq(rho, *j), atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("tau", [0.55, 0.8, 1.0, 1.7, 3.0])
+def test_rates_eq7_and_magic_parameter(orc, tau):
+    s = orc.rates(tau)
+    gold = json.load(open(os.path.join(GOLDEN, "paper_values.json")))["relaxation_rates"]
+    assert np.all(s[gold["zero"]] == 0)
+    assert np.allclose(s[gold["one_over_tau"]], 1 / tau)
+    assert np.allclose(s[gold["eight_ratio"]], 8 * (2 * tau - 1) / (8 * tau - 1))
+    lam = (1 / s[1] - 0.5) * (1 / s[4] - 0.5)
+    assert lam == pytest.approx(3 / 16, rel=1e-12)
+
+
+def _trt_collide(f, tau, g, e, w, opp):
+    """Two-relaxation-time collision with omega+ = 1/tau on the symmetric and
+    omega- = 8(2 tau - 1)/(8 tau - 1) on the antisymmetric parts, half-force
+    velocity and the first-order force term -- an independent formulation."""
+    rho = f.sum()
+    j = e.T @ f
+    u = j + np.array([g / 2, 0, 0])
+    eu = e @ u
+    feq = w * (rho + 3 * eu + 4.5 * eu ** 2 - 1.5 * u @ u)
+    wp, wm = 1 / tau, 8 * (2 * tau - 1) / (8 * tau - 1)
+    fp, fm = (f + f[opp]) / 2, (f - f[opp]) / 2
+    ep, em = (feq + feq[opp]) / 2, (feq - feq[opp]) / 2
+    F = 3 * w * e[:, 0] * g
+    return f - wp * (fp - ep) - wm * (fm - em) + (1 - wm / 2) * F
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.9])
+def test_mrt_collision_equals_independent_trt(orc, tau):
+    e, w, opp = orc.velocities19(), orc.weights19(), orc.opposite19()
+    rng = np.random.default_rng(int(tau * 10))
+    for _ in range(10):
+        f = w * (1 + 0.3 * rng.standard_normal(19))
+        g = 1e-3 * rng.standard_normal()
+        out = orc.mrt_collide_node(f, tau, g)
+        assert np.allclose(out, _trt_collide(f, tau, g, e, w, opp), atol=2e-15, rtol=0)
+        assert out.sum() == pytest.approx(f.sum(), abs=1e-14)  # mass
+        assert (e.T @ out)[0] == pytest.approx((e.T @ f)[0] + g, abs=1e-14)  # momentum + g
+
+
+@pytest.mark.parametrize("tau,H", [(1.0, 8), (0.7, 11), (1.6, 6)])
+def test_plane_poiseuille_exact_at_nodes(orc, tau, H):
+    """Body-force flow between plates with halfway bounce-back: with the Eq. 7
+    rates the node values are the exact parabola u = g y (H - y) / (2 nu)
+    with the walls half a cell outside the last fluid nodes."""
+    g = 1e-6
+    m = S.slit(1, H)
+    rc, kL, sux, steps, rel, f = orc.flow_solve(m, tau=tau, g=g, tol=1e-14, K=100, max_steps=400000)
+    assert rc == 0
+    ux, uy, uz, rho = orc.flow_velocity(m, f, g)
+    nu = (tau - 0.5) / 3
+    y = np.arange(1, H + 1) - 0.5
+    exact = g * y * (H - y) / (2 * nu)
+    assert np.allclose(ux[0, 1:H + 1, 0], exact, rtol=1e-9, atol=0)
+    # Darcy: k_L = nu <u_x> / g with <.> over all voxels
+    assert kL == pytest.approx(exact.sum() / (H + 2) * nu / g, rel=1e-9)
+
+
+def _duct_series(a, yc, zc, nterms=199):
+    """Square duct |y|,|z| < a/2, lap u = -1: Fourier series (Boussinesq)."""
+    b = a / 2.0
+    u = 0.0
+    for n in range(1, nterms + 1, 2):
+        k = n * math.pi / (2 * b)
+        u += ((-1) ** ((n - 1) // 2) / n ** 3) * (1 - np.cosh(k * zc) / np.cosh(k * b)) * np.cos(k * yc)
+    return 16 * b * b / math.pi ** 3 * u
+
+
+def test_square_duct_series(orc):
+    a, g, tau = 16, 1e-6, 1.0
+    m = S.square_duct(1, a)
+    rc, kL, sux, steps, rel, f = orc.flow_solve(m, tau=tau, g=g, tol=1e-11, K=200, max_steps=200000)
+    assert rc == 0
+    ux = orc.flow_velocity(m, f, g)[0][0, 1:a + 1, 1:a + 1]
+    nu = (tau - 0.5) / 3
+    c = np.arange(a) + 0.5 - a / 2
+    Y, Z = np.meshgrid(c, c, indexing="ij")
+    exact = _duct_series(a, Y, Z) * g / nu
+    assert np.abs(ux - exact).max() / exact.max() < 4e-3
+    # mean velocity of the continuous duct: 0.0351443 a^2 g / nu (series)
+    mean_cont = (16 * (a / 2) ** 2 / math.pi ** 3) * sum(
+        (2 / (math.pi * n ** 4)) * (1 - (2 / (math.pi * n)) * math.tanh(math.pi * n / 2))
+        for n in range(1, 401, 2))
+    assert mean_cont / a ** 2 == pytest.approx(0.0351443, rel=1e-5)
+    assert ux.mean() == pytest.approx(mean_cont * g / nu, rel=5e-3)
+
+
+def test_pipe_flow_eq27(orc):
+    R, g, tau = 7.5, 1e-6, 1.0
+    m = S.tube(1, R)
+    rc, kL, sux, steps, rel, f = orc.flow_solve(m, tau=tau, g=g, tol=1e-10, K=200, max_steps=200000)
+    assert rc == 0
+    n = m.shape[1]
+    # Eq. 27 in lattice units, superficial: k = (d/2)^2/8 * (pore area)/(box area)
+    k_pore = kL * n * n / m[0].sum()
+    assert k_pore == pytest.approx(R * R / 8, rel=0.06)
+
+
+def test_flow_mass_conservation_closed_box(orc):
+    m = S.closed_box((6, 7, 5))
+    w = orc.weights19()
+    rng = np.random.default_rng(3)
+    f = w[:, None, None, None] * (1 + 0.2 * rng.random((19,) + m.shape)) * m
+    f1 = orc.flow_step(m, f, tau=0.9, g=0.0, steps=200)
+    assert f1.sum() == pytest.approx(f.sum(), rel=1e-13)
+
+
+def test_flow_momentum_gain_periodic(orc):
+    # fully periodic box without walls: the mean momentum grows by g per step
+    m = np.ones((3, 4, 5), np.uint8)
+    w = orc.weights19()
+    f = np.broadcast_to(w[:, None, None, None], (19,) + m.shape).copy()
+    g = 1e-4
+    f1 = orc.flow_step(m, f, tau=1.0, g=g, steps=10)
+    ux, _, _, rho = orc.flow_velocity(m, f1, g)
+    assert np.allclose(ux, 10 * g + g / 2, rtol=1e-12)
+    assert np.allclose(rho, 1.0, rtol=1e-14)
+
+
+# ------------------------------------------------------------------ diffusion
+def test_straight_channel_diffusion_exact(orc):
+    """Layered plane channel with a different pore size per layer: from a
+    non-linear start the steady state is linear in x in every layer, so
+    D_eff = sum of layer diffusivities / N_y, tortuosity 1 (Eq. 16)."""
+    nx, H = 10, 5
+    m, layer = S.layered_slit(nx, H)
+    dlayer = {1: 60.0, 2: 30.0, 3: 45.0, 4: 12.0, 5: 60.0}
+    d = np.zeros(m.shape)
+    for k, v in dlayer.items():
+        d[layer == k] = v
+    om = orc.omega_field(m, d)
+    g = orc.diff_init(m, 1.0, 0.0)
+    rng = np.random.default_rng(1)
+    a = np.array([0.25] + [0.125] * 6)
+    g = a[:, None, None, None] * rng.random(m.shape)[None] * m  # arbitrary start
+    for _ in range(60):
+        g = orc.diff_step(m, g, om, 1.0, 0.0, steps=500)
+    C, J = orc.diff_fields(m, g, om)
+    Dl = [(orc.tau_knudsen(v) - 0.5) / 4 for v in dlayer.values()]
+    D_eff = J.sum() / m.size * nx / 1.0
+    assert D_eff == pytest.approx(sum(Dl) / (H + 2), rel=1e-10)
+    x = np.arange(nx) + 0.5
+    assert np.allclose(C[:, 1:H + 1, 0], (1 - x / nx)[:, None], atol=1e-10)
+
+
+def test_diffusion_solve_reports_straight_channel(orc):
+    nx, H = 8, 4
+    m = S.slit(nx, H)
+    om = orc.omega_field(m, np.full(m.shape, 20.0))
+    rc, D, sj, steps, rel, sc, g = orc.diff_solve(m, om, 1.0, 0.0, tol=1e-12, K=50)
+    assert rc == 0
+    assert D == pytest.approx((orc.tau_knudsen(20.0) - 0.5) / 4 * H / (H + 2), rel=1e-12)
+
+
+def test_diffusion_mass_conservation_closed(orc):
+    m = S.closed_box((6, 6, 6))
+    rng = np.random.default_rng(2)
+    g = rng.random((7,) + m.shape) * m
+    om = orc.omega_field(m, 10 + 50 * rng.random(m.shape))
+    g1 = orc.diff_step(m, g, om, 1.0, 0.0, steps=300)
+    assert g1.sum() == pytest.approx(g.sum(), rel=1e-13)
+
+
+@pytest.mark.slow
+def test_sphere_in_cube_sec35(orc):
+    """Sec. 3.5: effective diffusivity of a cube holding a solid sphere whose
+    diameter is the side, porosity 1 - pi/6.  The paper prints 0.3317 on a
+    100^3 D3Q19 lattice; the D3Q7 oracle at 40^3 agrees within 3 %."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_values.json")))["sphere_in_cube"]
+    L = 40
+    m = S.sphere_in_cube(L)
+    assert m.mean() == pytest.approx(1 - math.pi / 6, abs=0.005)
+    om = orc.omega_field(m, np.full(m.shape, 60.0))
+    rc, D, sj, steps, rel, sc, g = orc.diff_solve(m, om, 1.0, 0.0, tol=1e-9, K=100)
+    assert rc == 0
+    assert D / 0.125 == pytest.approx(gold["D_eff_over_D"], rel=0.03)
