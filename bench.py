@@ -1,0 +1,338 @@
+"""Benchmark of the LB hot path on GB300: fluid lattice updates per second.
+
+Workload (default): the porosity sweep -- four 256^3 structures at 1 nm
+(pore spheres d ~ Normal(30, 8) nm, overlap tolerance 0.3, porosity 0.15,
+0.25, 0.35, 0.45), reconstructed, labelled and sized (13-direction pore
+size) before the timed region.  One step = for every structure one
+convergence window of the D3Q19 flow sweep (100 LB steps) and its
+convergence check, then one window of the D3Q7 Knudsen diffusion sweep and
+its check, with FP32 populations -- every row of the hot path once.
+
+value: fluid MLUPS over both models, whole job (all ranks).
+e2e:   the same metric through the host-buffer C ABI (om_solve_permeability
+       + om_solve_knudsen with a one-window step cap), host mask and pore
+       sizes copied in and the results copied out inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as S  # noqa: E402
+
+WINDOW = 100  # LB steps per convergence check
+BYTES_FLOW_F32 = 152  # 19 populations read + written, 4 B each
+BYTES_DIFF_F32 = 60  # 7 populations read + written + omega
+METRIC = "fluid MLUPS & %HBM roofline"
+UNIT = "MLUPS"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--edge", type=int, default=256, help="structure edge (default: the 256^3 sweep)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(edge, rank):
+    return [S.sweep_structure(e, seed=1 + 1000 * rank, edge=edge) for e in S.SWEEP_POROSITIES]
+
+
+def _workload_name(edge):
+    return (f"porosity sweep: 4 structures {edge}^3 @ 1 nm, d~N(30,8) nm, xi=0.3, "
+            f"eps in {{0.15,0.25,0.35,0.45}}; D3Q19 flow (tau=1, g=1e-6) + D3Q7 Knudsen diffusion, "
+            f"FP32, {WINDOW}-step windows with convergence checks")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.lines, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peak_hbm():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the D3Q19 sweep from a committed ncu summary,
+    valid only while the kernel's sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "d3q19_sweep_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in ("flow.cu", "lattice.cuh", "common.cuh", "nodeset.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1410_1921_gb300", "csrc", f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+def _oracle_sample(edge):
+    """One flow and one diffusion step of the oracle on the porosity-0.35
+    structure (the oracle's own reconstruction), cropped to 64 x-layers."""
+    import oracle
+    cfg = S.sweep_structure(0.35, seed=1, edge=edge)
+    rc, mask, *_ = oracle.reconstruct(cfg.seed, cfg.shape, cfg.dx_nm, cfg.mean_nm, cfg.sd_nm, cfg.dmin_nm,
+                                      cfg.dmax_nm, cfg.porosity, cfg.xi, cfg.p0, cfg.dist)
+    _, tr, _ = oracle.label18(mask)
+    tr = np.ascontiguousarray(tr[: min(64, edge)])
+    om_ = np.where(tr == 1, 1.0 / oracle.tau_knudsen(30.0), 0.0)  # uniform 30 nm pores (Eq. 12)
+    f = oracle.flow_init(tr)
+    g = oracle.diff_init(tr)
+    nf = int(tr.sum())
+
+    def step():
+        nonlocal f, g
+        f = oracle.flow_step(tr, f, 1.0, 1e-6, 1)
+        g = oracle.diff_step(tr, g, om_, 1.0, 0.0, 1)
+        return 2 * nf
+
+    desc = (f"oracle (FP64 C, 1 thread): 1 D3Q19 MRT + 1 D3Q7 step on the eps=0.35 {edge}^3 structure "
+            f"cropped to {tr.shape[0]} x-layers ({nf} nodes)")
+    return step, desc
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    step, desc = _oracle_sample(a.edge)
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    ups = sum(step() for _ in range(a.steps))
+    dt = time.perf_counter() - t0
+    v = ups / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_name(a.edge), "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1410_1921_gb300 import build as B
+    B.build()
+    import paper_1410_1921_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    sp = P._stream(stream)
+
+    # ---------------- setup (untimed): reconstruct, label, pore size, solvers
+    cfgs = _workload(a.edge, rank)
+    solvers, host_inputs = [], []
+    t_setup = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for cfg in cfgs:
+            dom = P.domain(cfg.shape, cfg.dx_nm)
+            N = dom.nx * dom.ny * dom.nz
+            mask = torch.empty(N, dtype=torch.uint8, device="cuda")
+            rp = P.recon_params(cfg.mean_nm, cfg.sd_nm, cfg.dmin_nm, cfg.dmax_nm, cfg.porosity, cfg.xi, cfg.p0)
+            P.om_reconstruct_dev(cfg.seed, dom, rp, mask, stream=sp)
+            tr = torch.empty(N, dtype=torch.uint8, device="cuda")
+            P.om_label_connectivity_dev(mask, dom, None, tr, stream=sp)
+            d = torch.empty(N, dtype=torch.float32, device="cuda")
+            P.om_local_pore_diameter_dev(mask, dom, P.OM_PORE_CHORD13, d, stream=sp)
+            ns = P.NodeSet(tr, dom, stream=sp)
+            if ns.n_nodes == 0:
+                continue
+            fl = P.Flow(ns, P.flow_params(precision=P.OM_F32, check_every=WINDOW), stream=sp)
+            df = P.Diffusion(ns, d, P.diff_params(precision=P.OM_F32, check_every=WINDOW), stream=sp)
+            solvers.append((cfg, ns, fl, df))
+            host_inputs.append((dom, mask.cpu().numpy(), d.cpu().numpy()))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    nodes = [ns.n_nodes for _, ns, _, _ in solvers]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in solvers]
+
+    def one_step(record):
+        for k, (cfg, ns, fl, df) in enumerate(solvers):
+            if record:
+                ev[k][0].record(stream)
+            fl.step(WINDOW, stream=sp)
+            if record:
+                ev[k][1].record(stream)
+            fl.observe(stream=sp)
+            df.step(WINDOW, stream=sp)
+            df.observe(stream=sp)
+
+    for _ in range(a.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    flow_ms = 0.0
+    t0.record(stream)
+    for _ in range(a.steps):
+        one_step(True)
+        torch.cuda.synchronize()
+        flow_ms += sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    ck = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = 2 * WINDOW * sum(nodes) * a.steps  # both models
+    total_updates = updates * world
+    value = total_updates / (ms * 1e-3) / 1e6
+
+    # dominant kernel: D3Q19 sweep, algorithmic bytes per launch / event time
+    flow_launches = WINDOW * len(solvers) * a.steps
+    flow_bytes = BYTES_FLOW_F32 * WINDOW * sum(nodes) * a.steps
+    achieved = flow_bytes / (flow_ms * 1e-3) / 1e9
+    peak, peak_kind = _peak_hbm()
+    trec = _traffic_record()
+    roofline = {"bound": "hbm", "kernel": "d3q19_sweep<float>", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "avg_launch_us": flow_ms * 1e3 / flow_launches,
+                "algorithmic_bytes_per_launch": BYTES_FLOW_F32 * sum(nodes) / len(solvers),
+                "traffic": trec["dram_bytes_per_launch"] if trec else None}
+
+    # ---------------- e2e through the host-buffer C ABI
+    fp = P.flow_params(precision=P.OM_F32, conv_tol=0.0, check_every=WINDOW, max_steps=WINDOW)
+    dp = P.diff_params(precision=P.OM_F32, conv_tol=0.0, check_every=WINDOW, max_steps=WINDOW)
+    e2e_steps = max(1, min(2, a.steps))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    e2e_updates = 0
+    for _ in range(e2e_steps):
+        for dom, m, d in host_inputs:
+            st, k, kl, info, _ = P.om_solve_permeability(m, dom, fp)
+            e2e_updates += info.n_nodes * info.steps
+            st, D, tau, info, _ = P.om_solve_knudsen(m, d, dom, dp)
+            e2e_updates += info.n_nodes * info.steps
+    te = time.perf_counter() - te
+    if world > 1:
+        t = torch.tensor([te], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": e2e_updates * world / te / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(2 * m.nbytes + d.nbytes for _, m, d in host_inputs)),
+           "d2h_bytes_per_step": int(len(host_inputs) * 2 * (2 * 8 + 48))}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": _workload_name(a.edge), "structures_per_gpu": len(solvers),
+                       "nodes_per_structure": nodes, "window": WINDOW, "precision": "f32",
+                       "layout": "fluid-node SoA, AA pattern, rank-indexed neighbours",
+                       "l2": f"no flush: populations {sum(nodes) * 4 * 26 / 1e9:.2f} GB per step > 129 MB L2",
+                       "setup_s": t_setup},
+            "flow_mlups": WINDOW * sum(nodes) * a.steps * world / (flow_ms * 1e-3) / 1e6,
+            "roofline": roofline, "clocks": ck, "e2e": e2e,
+            "gpu_launches": a.steps * len(solvers) * 2 * (WINDOW + 2)}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        try:
+            step, desc = _oracle_sample(a.edge)
+            tc = time.perf_counter()
+            ups = sum(step() for _ in range(5))
+            tc = time.perf_counter() - tc
+            desc = "5 x " + desc
+            line["cpu_baseline"] = {"value": ups / tc / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": desc}
+        except Exception as exc:  # the baseline is a report, never a reason to lose the line
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {exc}"}
+    if rank == 0:
+        print(json.dumps(line))
+    for _, ns, fl, df in solvers:
+        fl.close()
+        df.close()
+        ns.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    args = _args()
+    sys.exit(run_reference(args) if args.impl == "reference" else run_gpu(args))

@@ -1,0 +1,235 @@
+/*
+ * om.h -- C ABI of the GB300 pore-scale transport library.
+ *
+ * Method: Chen, Kang, Zhang & Tao, "Lattice Boltzmann prediction of transport
+ * properties in reconstructed nanostructures of organic matters in shales"
+ * (arXiv:1410.1921).  The library reconstructs an organic-matter nanostructure
+ * by random pore-sphere placement (Sec. 2), labels its transport pores and
+ * local pore size (Sec. 4.1), runs the D3Q19 MRT flow solve (Sec. 3.1,
+ * App. A) for the intrinsic permeability (Eq. 13) and the BGK Knudsen
+ * diffusion solve (Sec. 3.2, Eqs. 10-12) for the effective diffusivity
+ * (Eq. 14) and tortuosity (Eq. 16), and forms the apparent permeability
+ * (Eq. 26).  All heavy steps run as CUDA kernels on the current device.
+ *
+ * Conventions for every entry point
+ *  - Voxel (x, y, z) of an nx*ny*nz box is element (x*ny + y)*nz + z.  x is
+ *    the flow / diffusion direction; y and z are periodic (Sec. 3.3).
+ *  - A mask byte is 1 for pore, 0 for solid.
+ *  - Buffers are owned by the caller.  "host" buffers are ordinary CPU
+ *    memory; "device" buffers are CUDA device memory of the current device.
+ *    The library allocates its own scratch and frees it before returning,
+ *    except for the solver objects, which own their memory until
+ *    om_*_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  *_dev calls enqueue work on it; those that return host
+ *    scalars synchronise it before returning.
+ *  - Every call returns an om_status.  On anything but OM_OK the outputs are
+ *    undefined, except OM_ENOTCONVERGED (step cap reached), which fills
+ *    every output from the last convergence check.  om_last_error() gives a
+ *    message for the calling thread's most recent failure.
+ *  - Scalars are SI unless the name says otherwise (nm, lattice units).
+ */
+#ifndef OM_H
+#define OM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OM_OK = 0,
+  OM_EINVAL = 1,         /* bad argument (sizes, pointers, parameters) */
+  OM_ENOMEM = 2,         /* device or host allocation failed */
+  OM_ECUDA = 3,          /* a CUDA call failed; see om_last_error() */
+  OM_EINFEASIBLE = 4,    /* reconstruction: trial cap hit before the porosity */
+  OM_ENOPERC = 5,        /* no transport pore spans x = 0 .. nx-1 */
+  OM_ENOTCONVERGED = 6,  /* step cap hit; outputs hold the last check */
+  OM_ETIMEOUT = 7        /* a bounded device wait gave up */
+} om_status;
+
+/* Lattice box: nx*ny*nz voxels of edge dx_nm.  Limits: nx <= 1024,
+ * ny, nz <= 2048. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx_nm;
+} om_domain;
+
+/* Pore-sphere placement (Sec. 2).  dist 0: diameter ~ Normal(mean_d_nm,
+ * sd_d_nm) clipped to [dmin_nm, dmax_nm]; dist 1: Uniform(mean_d_nm -
+ * sd_d_nm, mean_d_nm + sd_d_nm), the paper's law with sd_d_nm = 15.
+ * overlap_tol is xi, p_overlap is p0; max_trials caps candidate draws. */
+typedef struct {
+  double mean_d_nm, sd_d_nm, dmin_nm, dmax_nm;
+  int32_t dist;
+  double porosity, overlap_tol, p_overlap;
+  int64_t max_trials;
+} om_recon_params;
+
+/* population storage; arithmetic is FP64 for OM_F64, FP32 otherwise */
+enum { OM_F64 = 0, OM_F32 = 1, OM_F16DEV = 2, OM_BF16DEV = 3 };
+/* local pore size definitions */
+enum { OM_PORE_CHORD13 = 0, OM_PORE_MIS = 1 };
+
+/* D3Q19 flow (Sec. 3.1): relaxation time tau (Eq. 8), body force along x in
+ * lattice units, convergence when sum|du_x| / sum|u_x| over check_every
+ * steps drops below conv_tol. */
+typedef struct {
+  double tau, body_force, conv_tol;
+  int32_t check_every;
+  int64_t max_steps;
+  int32_t precision;
+} om_flow_params;
+
+/* D3Q7 Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
+ * size and relaxation time of Eq. 12, inlet/outlet concentrations, and the
+ * convergence test of om_flow_params applied to the concentration. */
+typedef struct {
+  double T_K, M_kg_per_mol, d_ref_nm, tau_ref, c_in, c_out, conv_tol;
+  int32_t check_every;
+  int64_t max_steps;
+  int32_t precision;
+} om_diff_params;
+
+typedef struct {
+  int64_t steps;        /* LB steps taken */
+  int64_t n_nodes;      /* lattice nodes (transport voxels) updated per step */
+  double rel_change;    /* last convergence measure */
+  double mass;          /* flow: sum of (rho - 1); diffusion: sum of C */
+  double seconds;       /* wall time of the solve on the stream */
+  double mlups;         /* n_nodes * steps / seconds / 1e6 */
+} om_run_info;
+
+/* ---------------------------------------------------------------- structure */
+
+/* Sec. 2: place pore spheres with SplitMix64 stream `seed` until the pore
+ * fraction reaches params->porosity.  mask: host, N bytes, written.
+ * porosity_out: achieved porosity; n_spheres_out: accepted spheres.
+ * Returns OM_EINFEASIBLE when max_trials draws do not reach the porosity. */
+om_status om_reconstruct(uint64_t seed, om_domain d, const om_recon_params* params, uint8_t* mask,
+                         double* porosity_out, int64_t* n_spheres_out);
+/* as om_reconstruct, mask in device memory */
+om_status om_reconstruct_dev(uint64_t seed, om_domain d, const om_recon_params* params,
+                             uint8_t* mask_dev, double* porosity_out, int64_t* n_spheres_out,
+                             void* stream);
+
+/* Sec. 4.1: 18-neighbour connected-phase labelling (the D3Q19 links),
+ * periodic in y and z.  labels (nullable): int32 N, the smallest voxel index
+ * of the voxel's component, -1 in solid.  transport (nullable): uint8 N, 1 on
+ * pores of components that touch both x = 0 and x = nx-1.
+ * connectivity_out: #transport / #pore (0 when there is no pore).
+ * Host buffers. */
+om_status om_label_connectivity(const uint8_t* mask, om_domain d, int32_t* labels,
+                                uint8_t* transport, double* connectivity_out);
+om_status om_label_connectivity_dev(const uint8_t* mask_dev, om_domain d, int32_t* labels_dev,
+                                    uint8_t* transport_dev, double* connectivity_out, void* stream);
+
+/* Local pore diameter in nm, 0 in solid.
+ * mode OM_PORE_CHORD13 (Sec. 4.1): mean over 3 axis, 6 face-diagonal and 4
+ *   body-diagonal directions of the all-pore line length through the voxel
+ *   (wrapping in y, z, stopping at the x faces); witness (nullable) int32
+ *   13*N, the cell count per direction (direction-major).
+ * mode OM_PORE_MIS: diameter of the largest inscribed pore ball containing
+ *   the voxel, d = dx * max(2 sqrt(r2(c)) - 1) over centres c whose ball
+ *   (|v - c|^2 < r2(c), r2 = squared distance to the nearest solid voxel)
+ *   holds v; witness (nullable) int32 N holds r2.  OM_EINVAL if the mask
+ *   has no solid voxel.
+ * Host buffers. */
+om_status om_local_pore_diameter(const uint8_t* mask, om_domain d, int32_t mode, float* d_nm,
+                                 int32_t* witness);
+om_status om_local_pore_diameter_dev(const uint8_t* mask_dev, om_domain d, int32_t mode,
+                                     float* d_nm_dev, int32_t* witness_dev, void* stream);
+
+/* ---------------------------------------------------------------- solves */
+
+/* Intrinsic permeability (Eq. 13) of the transport pores of `mask` (host,
+ * N bytes): D3Q19 flow driven by params->body_force along x, periodic in
+ * x, y, z, halfway bounce-back at walls, to convergence.
+ * k_m2 = k_lattice * dx^2 (Eq. 15), k_lattice = nu <u_x> / g with <.> over
+ * all N voxels.  ux_out (nullable, host float N): u_x, 0 off the node set.
+ * info (nullable).  OM_ENOPERC when no pore spans the box. */
+om_status om_solve_permeability(const uint8_t* mask, om_domain d, const om_flow_params* params,
+                                double* k_m2, double* k_lattice, om_run_info* info, float* ux_out);
+
+/* Effective Knudsen diffusivity (Eq. 14) and tortuosity (Eq. 16) of the
+ * transport pores of `mask` with local pore sizes d_nm (host float N, nm):
+ * D3Q7 BGK with tau_g from Eq. 12, fixed c_in / c_out on the half links
+ * x = -1/2 and nx - 1/2, bounce-back walls, periodic y, z, to convergence.
+ * D_eff_m2s = D_eff,L * D_K(d_ref) / D_L(tau_ref) (Eqs. 11, 15);
+ * tortuosity = porosity * mean(D_K over nodes) / D_eff.  c_out (nullable,
+ * host float N): concentration, 0 off the node set.  info nullable. */
+om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om_domain d,
+                           const om_diff_params* params, double* D_eff_m2s, double* tortuosity,
+                           om_run_info* info, float* c_out);
+
+/* Eq. 26: k_app = k (1 + D_eff mu / (k p)); f_c the bracket. */
+om_status om_apparent_permeability(double k_m2, double D_eff_m2s, double mu_Pa_s, double p_Pa,
+                                   double* k_app_m2, double* f_c);
+
+/* ---------------------------------------------------------------- node set and solver objects
+ * The hot loop.  A node set holds the transport voxels in lexicographic order
+ * with a per-column bit map and prefix count, from which every neighbour's
+ * node index is computed on the fly.  Solver objects own the populations of
+ * one model on one node set and advance them with fused collide-stream
+ * kernels in the AA pattern (one read and one write per population and
+ * step).  All pointers device, all work on `stream`. */
+typedef struct om_nodeset om_nodeset;
+typedef struct om_flow om_flow;
+typedef struct om_diff om_diff;
+
+/* nodes_dev: uint8 N, 1 on lattice nodes (normally the transport mask). */
+om_status om_nodeset_create(const uint8_t* nodes_dev, om_domain d, void* stream, om_nodeset** out);
+om_status om_nodeset_count(const om_nodeset* ns, int64_t* n_nodes);
+/* voxel index of every node (int64 n_nodes, device), for gathers */
+om_status om_nodeset_voxels(const om_nodeset* ns, int64_t* voxel_dev, void* stream);
+om_status om_nodeset_destroy(om_nodeset* ns);
+
+/* f initialised to the rest state f_i = w_i (rho = 1, u = 0). */
+om_status om_flow_create(const om_nodeset* ns, const om_flow_params* params, void* stream,
+                         om_flow** out);
+/* advance nsteps LB steps (Sec. 3.1, steps 1-5 per step) */
+om_status om_flow_step(om_flow* fl, int64_t nsteps, void* stream);
+/* Observables of the current state (FP64, node order): out[0] sum u_x,
+ * out[1] sum |u_x - u_x at the previous observe|, out[2] sum |u_x|,
+ * out[3] sum (rho - 1).  Host out, synchronises. */
+om_status om_flow_observe(om_flow* fl, double* out, void* stream);
+/* run to convergence (om_flow_params) from the current state */
+om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* info, void* stream);
+/* populations at the current time in the dense layout f[i*N + voxel],
+ * i in the order of the App. A transformation matrix, 0 off the node set.
+ * f_dev: double 19*N. */
+om_status om_flow_get_populations(const om_flow* fl, double* f_dev, void* stream);
+om_status om_flow_set_populations(om_flow* fl, const double* f_dev, void* stream);
+/* velocity u = j + g/2 (Eq. 9 with the half force), float 3*N, 0 off nodes */
+om_status om_flow_get_velocity(const om_flow* fl, float* u_dev, void* stream);
+om_status om_flow_time(const om_flow* fl, int64_t* t);
+om_status om_flow_destroy(om_flow* fl);
+
+/* d_nm_dev: float N local pore size (nm) for Eq. 12; g initialised to
+ * a_i C_lin(x), the linear profile between c_in and c_out. */
+om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev, const om_diff_params* params,
+                         void* stream, om_diff** out);
+om_status om_diff_step(om_diff* df, int64_t nsteps, void* stream);
+/* out[0] sum J_x (J = (1 - omega/2) sum e_x g), out[1] sum |C - C_prev|,
+ * out[2] sum |C|, out[3] sum C, out[4] sum D_L over nodes.  Synchronises. */
+om_status om_diff_observe(om_diff* df, double* out, void* stream);
+om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_info* info, void* stream);
+/* populations in the dense layout g[i*N + voxel], order rest,+x,-x,+y,-y,+z,-z */
+om_status om_diff_get_populations(const om_diff* df, double* g_dev, void* stream);
+om_status om_diff_set_populations(om_diff* df, const double* g_dev, void* stream);
+/* concentration C (float N) and flux J_x (float N), 0 off nodes; either nullable */
+om_status om_diff_get_fields(const om_diff* df, float* c_dev, float* jx_dev, void* stream);
+om_status om_diff_time(const om_diff* df, int64_t* t);
+om_status om_diff_destroy(om_diff* df);
+
+/* ---------------------------------------------------------------- misc */
+const char* om_last_error(void);
+/* library version string */
+const char* om_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OM_H */

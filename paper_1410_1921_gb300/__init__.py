@@ -1,0 +1,386 @@
+"""Python binding of libom.so, the GB300 library of include/om.h.
+
+Argument marshalling only: every entry point below calls the C function of
+the same name, and all computation runs in the library's CUDA kernels.
+Host arrays are numpy; device arrays are torch CUDA tensors (torch is used
+for device memory and streams).  The library must have been built
+(paper_1410_1921_gb300.build.build()); there is no fallback.
+
+Method: Chen, Kang, Zhang & Tao, arXiv:1410.1921 -- pore-sphere
+reconstruction (Sec. 2), 18-neighbour labelling and pore size (Sec. 4.1),
+D3Q19 MRT flow (Sec. 3.1, App. A) and D3Q7 Knudsen diffusion (Sec. 3.2),
+permeability / diffusivity / tortuosity / apparent permeability (Eqs. 13-16,
+26).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+OM_OK, OM_EINVAL, OM_ENOMEM, OM_ECUDA, OM_EINFEASIBLE, OM_ENOPERC, OM_ENOTCONVERGED, OM_ETIMEOUT = range(8)
+OM_F64, OM_F32, OM_F16DEV, OM_BF16DEV = range(4)
+OM_PORE_CHORD13, OM_PORE_MIS = 0, 1
+STATUS_NAMES = ["OM_OK", "OM_EINVAL", "OM_ENOMEM", "OM_ECUDA", "OM_EINFEASIBLE", "OM_ENOPERC",
+                "OM_ENOTCONVERGED", "OM_ETIMEOUT"]
+
+
+class OmError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        self.status = status
+        super().__init__(f"{fn}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+class om_domain(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx_nm", C.c_double)]
+
+
+class om_recon_params(C.Structure):
+    _fields_ = [("mean_d_nm", C.c_double), ("sd_d_nm", C.c_double), ("dmin_nm", C.c_double),
+                ("dmax_nm", C.c_double), ("dist", C.c_int32), ("porosity", C.c_double),
+                ("overlap_tol", C.c_double), ("p_overlap", C.c_double), ("max_trials", C.c_int64)]
+
+
+class om_flow_params(C.Structure):
+    _fields_ = [("tau", C.c_double), ("body_force", C.c_double), ("conv_tol", C.c_double),
+                ("check_every", C.c_int32), ("max_steps", C.c_int64), ("precision", C.c_int32)]
+
+
+class om_diff_params(C.Structure):
+    _fields_ = [("T_K", C.c_double), ("M_kg_per_mol", C.c_double), ("d_ref_nm", C.c_double),
+                ("tau_ref", C.c_double), ("c_in", C.c_double), ("c_out", C.c_double),
+                ("conv_tol", C.c_double), ("check_every", C.c_int32), ("max_steps", C.c_int64),
+                ("precision", C.c_int32)]
+
+
+class om_run_info(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("n_nodes", C.c_int64), ("rel_change", C.c_double),
+                ("mass", C.c_double), ("seconds", C.c_double), ("mlups", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp, _u8p, _i32p, _f32p, _f64p, _i64p = (C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_float), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int64))
+
+# name -> argtypes (restype om_status = int)
+_SIGS = {
+    "om_reconstruct": [C.c_uint64, om_domain, C.POINTER(om_recon_params), _vp, _f64p, _i64p],
+    "om_reconstruct_dev": [C.c_uint64, om_domain, C.POINTER(om_recon_params), _vp, _f64p, _i64p, _vp],
+    "om_label_connectivity": [_vp, om_domain, _vp, _vp, _f64p],
+    "om_label_connectivity_dev": [_vp, om_domain, _vp, _vp, _f64p, _vp],
+    "om_local_pore_diameter": [_vp, om_domain, C.c_int32, _vp, _vp],
+    "om_local_pore_diameter_dev": [_vp, om_domain, C.c_int32, _vp, _vp, _vp],
+    "om_solve_permeability": [_vp, om_domain, C.POINTER(om_flow_params), _f64p, _f64p,
+                              C.POINTER(om_run_info), _vp],
+    "om_solve_knudsen": [_vp, _vp, om_domain, C.POINTER(om_diff_params), _f64p, _f64p,
+                         C.POINTER(om_run_info), _vp],
+    "om_apparent_permeability": [C.c_double, C.c_double, C.c_double, C.c_double, _f64p, _f64p],
+    "om_nodeset_create": [_vp, om_domain, _vp, C.POINTER(_vp)],
+    "om_nodeset_count": [_vp, _i64p],
+    "om_nodeset_voxels": [_vp, _vp, _vp],
+    "om_nodeset_destroy": [_vp],
+    "om_flow_create": [_vp, C.POINTER(om_flow_params), _vp, C.POINTER(_vp)],
+    "om_flow_step": [_vp, C.c_int64, _vp],
+    "om_flow_observe": [_vp, _f64p, _vp],
+    "om_flow_solve": [_vp, _f64p, C.POINTER(om_run_info), _vp],
+    "om_flow_get_populations": [_vp, _vp, _vp],
+    "om_flow_set_populations": [_vp, _vp, _vp],
+    "om_flow_get_velocity": [_vp, _vp, _vp],
+    "om_flow_time": [_vp, _i64p],
+    "om_flow_destroy": [_vp],
+    "om_diff_create": [_vp, _vp, C.POINTER(om_diff_params), _vp, C.POINTER(_vp)],
+    "om_diff_step": [_vp, C.c_int64, _vp],
+    "om_diff_observe": [_vp, _f64p, _vp],
+    "om_diff_solve": [_vp, _f64p, C.POINTER(om_run_info), _vp],
+    "om_diff_get_populations": [_vp, _vp, _vp],
+    "om_diff_set_populations": [_vp, _vp, _vp],
+    "om_diff_get_fields": [_vp, _vp, _vp, _vp],
+    "om_diff_time": [_vp, _i64p],
+    "om_diff_destroy": [_vp],
+}
+
+_lib = None
+
+
+def lib():
+    """Load libom.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_1410_1921_gb300.build.build()")
+        import torch  # noqa: F401  -- load PyTorch's CUDA runtime first so both share it
+        L = C.CDLL(LIB)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.om_last_error.restype = C.c_char_p
+        L.om_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS) + ["om_last_error", "om_version"]
+
+
+def _check(fn, st, ok=(OM_OK,)):
+    if st not in ok:
+        raise OmError(fn, st, lib().om_last_error().decode())
+    return st
+
+
+def _call(fn, *args, ok=(OM_OK,)):
+    return _check(fn, getattr(lib(), fn)(*args), ok)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "host arrays must be C-contiguous"
+        return C.c_void_p(a.ctypes.data)
+    assert a.is_contiguous(), "device tensors must be contiguous"
+    return C.c_void_p(a.data_ptr())
+
+
+def domain(shape, dx_nm=1.0):
+    nx, ny, nz = shape
+    return om_domain(nx, ny, nz, dx_nm)
+
+
+def recon_params(mean_d_nm, sd_d_nm, dmin_nm, dmax_nm, porosity, overlap_tol, p_overlap=0.5, dist=0,
+                 max_trials=20_000_000):
+    return om_recon_params(mean_d_nm, sd_d_nm, dmin_nm, dmax_nm, dist, porosity, overlap_tol, p_overlap,
+                           max_trials)
+
+
+def flow_params(tau=1.0, body_force=1e-6, conv_tol=1e-6, check_every=100, max_steps=10_000_000,
+                precision=OM_F32):
+    return om_flow_params(tau, body_force, conv_tol, check_every, max_steps, precision)
+
+
+def diff_params(T_K=300.0, M_kg_per_mol=0.016, d_ref_nm=60.0, tau_ref=1.0, c_in=1.0, c_out=0.0,
+                conv_tol=1e-6, check_every=100, max_steps=10_000_000, precision=OM_F32):
+    return om_diff_params(T_K, M_kg_per_mol, d_ref_nm, tau_ref, c_in, c_out, conv_tol, check_every,
+                          max_steps, precision)
+
+
+# ------------------------------------------------------------------ host-buffer entry points
+def om_reconstruct(seed, dom, params):
+    mask = np.zeros(dom.nx * dom.ny * dom.nz, np.uint8)
+    eps, ns = C.c_double(), C.c_int64()
+    st = _call("om_reconstruct", seed, dom, C.byref(params), _ptr(mask), C.byref(eps), C.byref(ns),
+               ok=(OM_OK, OM_EINFEASIBLE))
+    return st, mask.reshape(dom.nx, dom.ny, dom.nz), eps.value, ns.value
+
+
+def om_reconstruct_dev(seed, dom, params, mask_dev, stream=None):
+    eps, ns = C.c_double(), C.c_int64()
+    st = _call("om_reconstruct_dev", seed, dom, C.byref(params), _ptr(mask_dev), C.byref(eps), C.byref(ns),
+               _stream(stream), ok=(OM_OK, OM_EINFEASIBLE))
+    return st, eps.value, ns.value
+
+
+def om_label_connectivity(mask, dom=None):
+    mask = np.ascontiguousarray(mask, np.uint8)
+    dom = dom or domain(mask.shape)
+    labels = np.zeros(mask.shape, np.int32)
+    tr = np.zeros(mask.shape, np.uint8)
+    conn = C.c_double()
+    _call("om_label_connectivity", _ptr(mask), dom, _ptr(labels), _ptr(tr), C.byref(conn))
+    return labels, tr, conn.value
+
+
+def om_label_connectivity_dev(mask_dev, dom, labels_dev=None, transport_dev=None, stream=None):
+    conn = C.c_double()
+    _call("om_label_connectivity_dev", _ptr(mask_dev), dom, _ptr(labels_dev), _ptr(transport_dev),
+          C.byref(conn), _stream(stream))
+    return conn.value
+
+
+def om_local_pore_diameter(mask, dom=None, mode=OM_PORE_CHORD13, witness=False):
+    mask = np.ascontiguousarray(mask, np.uint8)
+    dom = dom or domain(mask.shape)
+    d = np.zeros(mask.shape, np.float32)
+    w = None
+    if witness:
+        w = np.zeros(((13,) if mode == OM_PORE_CHORD13 else ()) + mask.shape, np.int32)
+    _call("om_local_pore_diameter", _ptr(mask), dom, mode, _ptr(d), _ptr(w))
+    return d, w
+
+
+def om_local_pore_diameter_dev(mask_dev, dom, mode, d_dev, witness_dev=None, stream=None):
+    _call("om_local_pore_diameter_dev", _ptr(mask_dev), dom, mode, _ptr(d_dev), _ptr(witness_dev),
+          _stream(stream))
+
+
+def om_solve_permeability(mask, dom, params, want_ux=False):
+    mask = np.ascontiguousarray(mask, np.uint8)
+    k, kl = C.c_double(), C.c_double()
+    info = om_run_info()
+    ux = np.zeros(mask.shape, np.float32) if want_ux else None
+    st = _call("om_solve_permeability", _ptr(mask), dom, C.byref(params), C.byref(k), C.byref(kl),
+               C.byref(info), _ptr(ux), ok=(OM_OK, OM_ENOTCONVERGED))
+    return st, k.value, kl.value, info, ux
+
+
+def om_solve_knudsen(mask, d_nm, dom, params, want_c=False):
+    mask = np.ascontiguousarray(mask, np.uint8)
+    d_nm = np.ascontiguousarray(d_nm, np.float32)
+    D, tau = C.c_double(), C.c_double()
+    info = om_run_info()
+    c = np.zeros(mask.shape, np.float32) if want_c else None
+    st = _call("om_solve_knudsen", _ptr(mask), _ptr(d_nm), dom, C.byref(params), C.byref(D), C.byref(tau),
+               C.byref(info), _ptr(c), ok=(OM_OK, OM_ENOTCONVERGED))
+    return st, D.value, tau.value, info, c
+
+
+def om_apparent_permeability(k_m2, D_eff_m2s, mu_Pa_s, p_Pa):
+    ka, fc = C.c_double(), C.c_double()
+    _call("om_apparent_permeability", k_m2, D_eff_m2s, mu_Pa_s, p_Pa, C.byref(ka), C.byref(fc))
+    return ka.value, fc.value
+
+
+# ------------------------------------------------------------------ solver objects (device)
+class NodeSet:
+    """om_nodeset: the transport voxels of a device mask, numbered in voxel order."""
+
+    def __init__(self, nodes_dev, dom, stream=None):
+        self.dom = dom
+        self.h = C.c_void_p()
+        _call("om_nodeset_create", _ptr(nodes_dev), dom, _stream(stream), C.byref(self.h))
+
+    @property
+    def n_nodes(self):
+        n = C.c_int64()
+        _call("om_nodeset_count", self.h, C.byref(n))
+        return n.value
+
+    def voxels(self, out_dev, stream=None):
+        _call("om_nodeset_voxels", self.h, _ptr(out_dev), _stream(stream))
+
+    def close(self):
+        if self.h:
+            lib().om_nodeset_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Flow:
+    """om_flow: D3Q19 populations on a node set (om_flow_*)."""
+
+    def __init__(self, ns, params, stream=None):
+        self.ns, self.params = ns, params
+        self.h = C.c_void_p()
+        _call("om_flow_create", ns.h, C.byref(params), _stream(stream), C.byref(self.h))
+
+    def step(self, n, stream=None):
+        _call("om_flow_step", self.h, n, _stream(stream))
+
+    def observe(self, stream=None):
+        out = (C.c_double * 4)()
+        _call("om_flow_observe", self.h, out, _stream(stream))
+        return list(out)
+
+    def solve(self, stream=None):
+        kl = C.c_double()
+        info = om_run_info()
+        st = _call("om_flow_solve", self.h, C.byref(kl), C.byref(info), _stream(stream),
+                   ok=(OM_OK, OM_ENOTCONVERGED))
+        return st, kl.value, info
+
+    def get_populations(self, out_dev, stream=None):
+        _call("om_flow_get_populations", self.h, _ptr(out_dev), _stream(stream))
+
+    def set_populations(self, f_dev, stream=None):
+        _call("om_flow_set_populations", self.h, _ptr(f_dev), _stream(stream))
+
+    def get_velocity(self, out_dev, stream=None):
+        _call("om_flow_get_velocity", self.h, _ptr(out_dev), _stream(stream))
+
+    @property
+    def time(self):
+        t = C.c_int64()
+        _call("om_flow_time", self.h, C.byref(t))
+        return t.value
+
+    def close(self):
+        if self.h:
+            lib().om_flow_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Diffusion:
+    """om_diff: D3Q7 Knudsen-diffusion populations on a node set (om_diff_*)."""
+
+    def __init__(self, ns, d_nm_dev, params, stream=None):
+        self.ns, self.params = ns, params
+        self.h = C.c_void_p()
+        _call("om_diff_create", ns.h, _ptr(d_nm_dev), C.byref(params), _stream(stream), C.byref(self.h))
+
+    def step(self, n, stream=None):
+        _call("om_diff_step", self.h, n, _stream(stream))
+
+    def observe(self, stream=None):
+        out = (C.c_double * 5)()
+        _call("om_diff_observe", self.h, out, _stream(stream))
+        return list(out)
+
+    def solve(self, stream=None):
+        D = C.c_double()
+        info = om_run_info()
+        st = _call("om_diff_solve", self.h, C.byref(D), C.byref(info), _stream(stream),
+                   ok=(OM_OK, OM_ENOTCONVERGED))
+        return st, D.value, info
+
+    def get_populations(self, out_dev, stream=None):
+        _call("om_diff_get_populations", self.h, _ptr(out_dev), _stream(stream))
+
+    def set_populations(self, g_dev, stream=None):
+        _call("om_diff_set_populations", self.h, _ptr(g_dev), _stream(stream))
+
+    def get_fields(self, c_dev=None, jx_dev=None, stream=None):
+        _call("om_diff_get_fields", self.h, _ptr(c_dev), _ptr(jx_dev), _stream(stream))
+
+    @property
+    def time(self):
+        t = C.c_int64()
+        _call("om_diff_time", self.h, C.byref(t))
+        return t.value
+
+    def close(self):
+        if self.h:
+            lib().om_diff_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,474 @@
+// diff.cu -- D3Q7 BGK Knudsen-diffusion sweep (Sec. 3.2, Eqs. 10-12) in the
+// AA pattern on the fluid-node layout of nodeset.cu.
+//
+// g*_i = g_i - omega(x) (g_i - a_i C), C = sum g_i, a = {1/4, 1/8 x 6}, with
+// omega = 1/tau_g from the local pore size by Eq. 12.  Populations are
+// stored as deviations from a_i C_lin(x), C_lin the linear profile between
+// the two fixed concentrations, which keeps the stored values small; the
+// reference differs by a_i s e_ix (s = dC_lin/dx) between neighbours, which
+// the odd step adds when it moves a population across x.
+//
+// Boundaries: bounce-back at walls and missing neighbours (no flux), periodic
+// y and z, and fixed concentration on the half links x = -1/2 (c_in) and
+// x = nx - 1/2 (c_out) by anti-bounce-back,
+//     g_i(x_b, t+1) = -g*_opp(i)(x_b, t) + 2 a_i C_w.
+#include <algorithm>
+
+#include "lattice.cuh"
+
+namespace om {
+
+template <class T>
+struct DiffArgs {
+  T* g;
+  int64_t pitch, nf;
+  const uint2* col;
+  const uint32_t* coord;
+  const typename Stg<T>::C* omega;
+  int nx, ny, nz, W;
+  typename Stg<T>::C s;    // slope of C_lin per lattice cell, (c_out - c_in)/nx
+  typename Stg<T>::C inv;  // storage scale
+  double cin, cout;
+};
+
+// nb[i] = node of x + e_i, kNoNode for walls; x faces flagged separately
+template <class T>
+__device__ __forceinline__ void diff_neighbours(const DiffArgs<T>& a, uint32_t c, uint32_t (&nb)[7],
+                                                int& x) {
+  int y, z;
+  unpack_xyz(c, x, y, z);
+  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
+  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
+  nb[1] = x + 1 < a.nx ? node_at(a.col, a.ny, a.W, x + 1, y, z) : kNoNode;
+  nb[2] = x > 0 ? node_at(a.col, a.ny, a.W, x - 1, y, z) : kNoNode;
+  nb[3] = node_at(a.col, a.ny, a.W, x, yp, z);
+  nb[4] = node_at(a.col, a.ny, a.W, x, ym, z);
+  nb[5] = node_at(a.col, a.ny, a.W, x, y, zp);
+  nb[6] = node_at(a.col, a.ny, a.W, x, y, zm);
+}
+
+// pre-collision deviations of node n at the current time
+template <class T, bool ODD>
+__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, int64_t n, const uint32_t (&nb)[7],
+                                          int x, typename Stg<T>::C (&g)[7]) {
+  using S = Stg<T>;
+  using C = typename S::C;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    if (!ODD || i == 0) {
+      g[i] = S::ld(a.g + i * a.pitch + n, a.inv);
+    } else {
+      const int o = q7_opp(i);
+      const uint32_t src = nb[o];  // x - e_i
+      const bool inlet = (i == 1 && x == 0), outlet = (i == 2 && x == a.nx - 1);
+      if (inlet) {
+        g[i] = -S::ld(a.g + i * a.pitch + n, a.inv) - C(0.125) * a.s;
+      } else if (outlet) {
+        g[i] = -S::ld(a.g + i * a.pitch + n, a.inv) + C(0.125) * a.s;
+      } else if (src != kNoNode) {
+        g[i] = S::ld(a.g + o * a.pitch + src, a.inv) - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
+      } else {
+        g[i] = S::ld(a.g + i * a.pitch + n, a.inv);
+      }
+    }
+  }
+}
+
+template <class T, bool ODD>
+__global__ void __launch_bounds__(256) d3q7_sweep(DiffArgs<T> a) {
+  using S = Stg<T>;
+  using C = typename S::C;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  uint32_t nb[7];
+  int x = 0;
+  if (ODD) diff_neighbours(a, a.coord[n], nb, x);
+  C g[7];
+  diff_load<T, ODD>(a, n, nb, x, g);
+  const C om = a.omega[n];
+  C c = g[0];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) c += g[i];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) g[i] = g[i] - om * (g[i] - C(q7_w(i)) * c);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const int o = q7_opp(i);
+    if (!ODD) {
+      S::st(a.g + o * a.pitch + n, g[i], a.inv);
+    } else if (i == 0) {
+      S::st(a.g + n, g[0], a.inv);
+    } else {
+      const bool outlet = (i == 1 && x == a.nx - 1), inlet = (i == 2 && x == 0);
+      if (outlet) {
+        S::st(a.g + o * a.pitch + n, -g[i] + C(0.125) * a.s, a.inv);
+      } else if (inlet) {
+        S::st(a.g + o * a.pitch + n, -g[i] - C(0.125) * a.s, a.inv);
+      } else if (nb[i] != kNoNode) {
+        S::st(a.g + i * a.pitch + nb[i], g[i] - C(q7_w(i)) * C(q7_e(i, 0)) * a.s, a.inv);
+      } else {
+        S::st(a.g + o * a.pitch + n, g[i], a.inv);
+      }
+    }
+  }
+}
+
+// Observables: sum J_x, sum |C - prev|, sum |C|, sum C, sum D_L; prev <- C.
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kObsThreads) d3q7_observe(DiffArgs<T> a, double* prev,
+                                                            double* partials) {
+  using C = typename Stg<T>::C;
+  double acc[5] = {0, 0, 0, 0, 0};
+  const double s = (double)a.s;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < a.nf;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t nb[7];
+    int x, y, z;
+    unpack_xyz(a.coord[n], x, y, z);
+    if (ODD) diff_neighbours(a, a.coord[n], nb, x);
+    C g[7];
+    diff_load<T, ODD>(a, n, nb, x, g);
+    double dev = 0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) dev += (double)g[i];
+    const double cref = a.cin + s * ((double)x + 0.5);
+    const double c = dev + cref;
+    const double om = (double)a.omega[n];
+    const double jx = (1.0 - 0.5 * om) * ((double)g[1] - (double)g[2]);
+    acc[0] += jx;
+    acc[1] += fabs(c - prev[n]);
+    acc[2] += fabs(c);
+    acc[3] += c;
+    acc[4] += 0.25 * (1.0 / om - 0.5);
+    prev[n] = c;
+  }
+  block_reduce_store<5>(acc, partials);
+}
+
+template <class T, bool ODD>
+__global__ void d3q7_export(DiffArgs<T> a, const int64_t* vox, int64_t N, double* gdense,
+                            float* cdense, float* jdense) {
+  using C = typename Stg<T>::C;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  uint32_t nb[7];
+  int x, y, z;
+  unpack_xyz(a.coord[n], x, y, z);
+  if (ODD) diff_neighbours(a, a.coord[n], nb, x);
+  C g[7];
+  diff_load<T, ODD>(a, n, nb, x, g);
+  const int64_t v = vox[n];
+  const double cref = a.cin + (double)a.s * ((double)x + 0.5);
+  double dev = 0;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    dev += (double)g[i];
+    if (gdense) gdense[i * N + v] = (double)g[i] + q7_w(i) * cref;
+  }
+  if (cdense) cdense[v] = (float)(dev + cref);
+  if (jdense) jdense[v] = (float)((1.0 - 0.5 * (double)a.omega[n]) * ((double)g[1] - (double)g[2]));
+}
+
+template <class T>
+__global__ void d3q7_import(DiffArgs<T> a, const int64_t* vox, int64_t N, const double* gdense,
+                            int linear) {
+  using S = Stg<T>;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  const int64_t v = vox[n];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    // linear != 0: the linear profile itself, i.e. zero deviation
+    double val = linear ? 0.0 : gdense[i * N + v] - q7_w(i) * (a.cin + (double)a.s * ((double)(v / ((int64_t)a.ny * a.nz)) + 0.5));
+    S::st(a.g + i * a.pitch + n, (typename S::C)val, a.inv);
+  }
+}
+
+template <class T>
+__global__ void d3q7_omega(const int64_t* vox, const float* d_nm, int64_t nf, double d_ref,
+                           double tau_ref, typename Stg<T>::C* omega, int* bad) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nf) return;
+  // Eq. 12: tau_g = (d / d_ref)(tau_ref - 1/2) + 1/2
+  const double tau = ((double)d_nm[vox[n]] / d_ref) * (tau_ref - 0.5) + 0.5;
+  if (!(tau > 0.5)) atomicExch(bad, 1);
+  omega[n] = (typename Stg<T>::C)(1.0 / tau);
+}
+
+}  // namespace om
+
+using namespace om;
+
+struct om_diff {
+  const om_nodeset* ns = nullptr;
+  om_diff_params p{};
+  void* g = nullptr;
+  void* omega = nullptr;
+  double* prev = nullptr;
+  double* partials = nullptr;
+  double* obs_dev = nullptr;
+  double* obs_host = nullptr;
+  int64_t t = 0;
+  double inv = 1.0;
+};
+
+namespace {
+
+template <class T>
+DiffArgs<T> diff_args(const om_diff* df) {
+  DiffArgs<T> a;
+  const om_nodeset* ns = df->ns;
+  a.g = (T*)df->g;
+  a.pitch = ns->pitch;
+  a.nf = ns->nf;
+  a.col = ns->col;
+  a.coord = ns->coord;
+  a.omega = (const typename Stg<T>::C*)df->omega;
+  a.nx = ns->dom.nx;
+  a.ny = ns->dom.ny;
+  a.nz = ns->dom.nz;
+  a.W = ns->W;
+  a.s = (typename Stg<T>::C)((df->p.c_out - df->p.c_in) / (double)ns->dom.nx);
+  a.inv = (typename Stg<T>::C)df->inv;
+  a.cin = df->p.c_in;
+  a.cout = df->p.c_out;
+  return a;
+}
+
+inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <class T>
+om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
+  if (df->ns->nf == 0) {
+    df->t += nsteps;
+    return OM_OK;
+  }
+  DiffArgs<T> a = diff_args<T>(df);
+  const unsigned nb = blocks_for(a.nf);
+  for (int64_t k = 0; k < nsteps; ++k) {
+    if (df->t & 1) d3q7_sweep<T, true><<<nb, 256, 0, s>>>(a);
+    else d3q7_sweep<T, false><<<nb, 256, 0, s>>>(a);
+    ++df->t;
+  }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status diff_observe_t(om_diff* df, double* out, cudaStream_t s) {
+  DiffArgs<T> a = diff_args<T>(df);
+  if (df->t & 1) d3q7_observe<T, true><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
+  else d3q7_observe<T, false><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
+  launch_finalize(df->partials, kObsBlocks, 5, df->obs_dev, s);
+  OM_CUDA(cudaGetLastError());
+  OM_CUDA(cudaMemcpyAsync(df->obs_host, df->obs_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 5; ++k) out[k] = df->obs_host[k];
+  return OM_OK;
+}
+
+template <class T>
+om_status diff_export_t(const om_diff* df, double* gd, float* cd, float* jd, cudaStream_t s) {
+  const om_nodeset* ns = df->ns;
+  if (gd) OM_CUDA(cudaMemsetAsync(gd, 0, sizeof(double) * 7 * ns->N, s));
+  if (cd) OM_CUDA(cudaMemsetAsync(cd, 0, sizeof(float) * ns->N, s));
+  if (jd) OM_CUDA(cudaMemsetAsync(jd, 0, sizeof(float) * ns->N, s));
+  if (ns->nf == 0) return OM_OK;
+  DiffArgs<T> a = diff_args<T>(df);
+  if (df->t & 1) d3q7_export<T, true><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, gd, cd, jd);
+  else d3q7_export<T, false><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, gd, cd, jd);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status diff_import_t(om_diff* df, const double* gd, int linear, cudaStream_t s) {
+  if (df->ns->nf == 0) return OM_OK;
+  DiffArgs<T> a = diff_args<T>(df);
+  d3q7_import<T><<<blocks_for(a.nf), 256, 0, s>>>(a, df->ns->vox, df->ns->N, gd, linear);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status diff_omega_t(om_diff* df, const float* d_nm, cudaStream_t s) {
+  if (df->ns->nf == 0) return OM_OK;
+  DevBuf<int> bad;
+  OM_TRY(bad.alloc(1));
+  OM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  d3q7_omega<T><<<blocks_for(df->ns->nf), 256, 0, s>>>(df->ns->vox, d_nm, df->ns->nf, df->p.d_ref_nm,
+                                                       df->p.tau_ref, (typename Stg<T>::C*)df->omega,
+                                                       bad.p);
+  OM_CUDA(cudaGetLastError());
+  int hb = 0;
+  OM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  if (hb) return fail(OM_EINVAL, "om_diff_create: a node has a pore size <= 0 (tau_g <= 1/2)");
+  return OM_OK;
+}
+
+#define OM_DIFF_DISPATCH(df, fn, ...)                                        \
+  switch ((df)->p.precision) {                                               \
+    case OM_F64: return fn<double>(__VA_ARGS__);                             \
+    case OM_F32: return fn<float>(__VA_ARGS__);                              \
+    case OM_F16DEV: return fn<__half>(__VA_ARGS__);                          \
+    case OM_BF16DEV: return fn<__nv_bfloat16>(__VA_ARGS__);                  \
+    default: return fail(OM_EINVAL, "unknown precision");                    \
+  }
+
+size_t storage_bytes(int prec) { return prec == OM_F64 ? 8 : (prec == OM_F32 ? 4 : 2); }
+
+om_status diff_observe_any(om_diff* df, double* out, cudaStream_t s) {
+  OM_DIFF_DISPATCH(df, diff_observe_t, df, out, s);
+}
+
+}  // namespace
+
+extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
+                                    const om_diff_params* p, void* stream, om_diff** out) {
+  if (!ns || !d_nm_dev || !p || !out) return fail(OM_EINVAL, "om_diff_create: null pointer");
+  if (p->precision < OM_F64 || p->precision > OM_BF16DEV)
+    return fail(OM_EINVAL, "om_diff_create: unknown precision");
+  if (!(p->d_ref_nm > 0.0) || !(p->tau_ref > 0.5) || !(p->c_in != p->c_out))
+    return fail(OM_EINVAL, "om_diff_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");
+  cudaStream_t s = as_stream(stream);
+  om_diff* df = new om_diff();
+  df->ns = ns;
+  df->p = *p;
+  df->inv = p->precision == OM_F16DEV ? 1.0 / 64.0 : 1.0;
+  const size_t cb = p->precision == OM_F64 ? 8 : 4;
+  DevBuf<uint8_t> g, om;
+  DevBuf<double> prev, part, obs;
+  om_status st = g.alloc(7 * (size_t)ns->pitch * storage_bytes(p->precision));
+  if (st == OM_OK) st = om.alloc((size_t)ns->pitch * cb);
+  if (st == OM_OK) st = prev.alloc(ns->nf);
+  if (st == OM_OK) st = part.alloc((size_t)kObsBlocks * 8);
+  if (st == OM_OK) st = obs.alloc(8);
+  double* host = nullptr;
+  if (st == OM_OK && cudaMallocHost((void**)&host, 8 * sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    st = fail(OM_ENOMEM, "om_diff_create: pinned allocation failed");
+  }
+  if (st != OM_OK) {
+    delete df;
+    return st;
+  }
+  df->g = g.take();
+  df->omega = om.take();
+  df->prev = prev.take();
+  df->partials = part.take();
+  df->obs_dev = obs.take();
+  df->obs_host = host;
+  auto setup = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_omega_t, df, d_nm_dev, s); };
+  auto init = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_import_t, df, nullptr, 1, s); };
+  st = setup();
+  if (st == OM_OK) st = init();
+  if (st == OM_OK) {
+    double o[5];
+    st = diff_observe_any(df, o, s);
+  }
+  if (st != OM_OK) {
+    om_diff_destroy(df);
+    return st;
+  }
+  *out = df;
+  return OM_OK;
+}
+
+extern "C" om_status om_diff_step(om_diff* df, int64_t nsteps, void* stream) {
+  if (!df || nsteps < 0) return fail(OM_EINVAL, "om_diff_step: bad argument");
+  cudaStream_t s = as_stream(stream);
+  OM_DIFF_DISPATCH(df, diff_steps_t, df, nsteps, s);
+}
+
+extern "C" om_status om_diff_observe(om_diff* df, double* out, void* stream) {
+  if (!df || !out) return fail(OM_EINVAL, "om_diff_observe: null pointer");
+  return diff_observe_any(df, out, as_stream(stream));
+}
+
+extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_info* info,
+                                   void* stream) {
+  if (!df) return fail(OM_EINVAL, "om_diff_solve: null pointer");
+  const om_diff_params& p = df->p;
+  if (p.check_every <= 0 || (p.check_every & 1))
+    return fail(OM_EINVAL, "om_diff_solve: check_every must be a positive even number");
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0, e1;
+  OM_CUDA(cudaEventCreate(&e0));
+  OM_CUDA(cudaEventCreate(&e1));
+  double o[5];
+  OM_TRY(diff_observe_any(df, o, s));
+  const int64_t t0 = df->t;
+  OM_CUDA(cudaEventRecord(e0, s));
+  om_status rc = OM_ENOTCONVERGED;
+  double rel = 1.0;
+  while (df->t - t0 < p.max_steps) {
+    int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (df->t - t0));
+    OM_TRY(om_diff_step(df, k, stream));
+    OM_TRY(diff_observe_any(df, o, s));
+    rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+    if (rel < p.conv_tol) {
+      rc = OM_OK;
+      break;
+    }
+  }
+  OM_CUDA(cudaEventRecord(e1, s));
+  OM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  OM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const om_nodeset* ns = df->ns;
+  if (D_eff_lattice)
+    *D_eff_lattice = (o[0] / (double)ns->N) * (double)ns->dom.nx / (p.c_in - p.c_out);
+  if (info) {
+    info->steps = df->t - t0;
+    info->n_nodes = ns->nf;
+    info->rel_change = rel;
+    info->mass = o[3];
+    info->seconds = ms * 1e-3;
+    info->mlups = ms > 0 ? (double)ns->nf * (double)info->steps / (ms * 1e-3) / 1e6 : 0.0;
+  }
+  if (rc != OM_OK) set_error("om_diff_solve: step cap reached before convergence");
+  return rc;
+}
+
+extern "C" om_status om_diff_get_populations(const om_diff* df, double* g_dev, void* stream) {
+  if (!df || !g_dev) return fail(OM_EINVAL, "om_diff_get_populations: null pointer");
+  cudaStream_t s = as_stream(stream);
+  OM_DIFF_DISPATCH(df, diff_export_t, df, g_dev, (float*)nullptr, (float*)nullptr, s);
+}
+
+extern "C" om_status om_diff_get_fields(const om_diff* df, float* c_dev, float* jx_dev, void* stream) {
+  if (!df) return fail(OM_EINVAL, "om_diff_get_fields: null pointer");
+  cudaStream_t s = as_stream(stream);
+  OM_DIFF_DISPATCH(df, diff_export_t, df, (double*)nullptr, c_dev, jx_dev, s);
+}
+
+extern "C" om_status om_diff_set_populations(om_diff* df, const double* g_dev, void* stream) {
+  if (!df || !g_dev) return fail(OM_EINVAL, "om_diff_set_populations: null pointer");
+  cudaStream_t s = as_stream(stream);
+  df->t = 0;
+  auto imp = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_import_t, df, g_dev, 0, s); };
+  OM_TRY(imp());
+  double o[5];
+  return diff_observe_any(df, o, s);
+}
+
+extern "C" om_status om_diff_time(const om_diff* df, int64_t* t) {
+  if (!df || !t) return fail(OM_EINVAL, "om_diff_time: null pointer");
+  *t = df->t;
+  return OM_OK;
+}
+
+extern "C" om_status om_diff_destroy(om_diff* df) {
+  if (!df) return OM_OK;
+  cudaFree(df->g);
+  cudaFree(df->omega);
+  cudaFree(df->prev);
+  cudaFree(df->partials);
+  cudaFree(df->obs_dev);
+  if (df->obs_host) cudaFreeHost(df->obs_host);
+  delete df;
+  return OM_OK;
+}

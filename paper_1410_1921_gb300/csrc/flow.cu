@@ -1,0 +1,470 @@
+// flow.cu -- D3Q19 flow sweep (Sec. 3.1, Eqs. 1-9, App. A) in the AA
+// pattern on the fluid-node layout of nodeset.cu.
+//
+// Collision.  The moment-space MRT of Eqs. 4-7 relaxes every even
+// non-conserved moment of the App. A basis with 1/tau and every odd one with
+// s_q = 8(2 tau - 1)/(8 tau - 1); its equilibrium moments A1-A9 are the
+// moments of the incompressible BGK equilibrium of Eq. 3.  That operator is
+// the two-relaxation-time collision
+//     f*_i = f_i - w+ (f+_i - e+_i) - w- (f-_i - e-_i) + (1 - w-/2) F_i
+// with w+ = 1/tau, w- = s_q, f+-, e+- the symmetric / antisymmetric parts
+// of f and f_eq under i -> opposite(i), and the body force g along x entering
+// as j* = j + g/2 in f_eq and F_i = 3 w_i e_ix g.  Written per velocity pair
+// it costs ~200 flops per node instead of two dense 19x19 products.
+// Populations are stored as deviations f_i - w_i (rho0 = 1).
+//
+// Streaming, AA pattern.  Even steps read and write only the node's own
+// slots (post-collision f*_i goes to slot opposite(i)); odd steps read
+// slot opposite(i) of the upstream node x - e_i and write slot i of the
+// downstream node x + e_i.  Every slot is read and written by one thread
+// only, so one population array serves both steps.  A missing neighbour
+// (solid or non-transport voxel) is halfway bounce-back: the odd step reads
+// the node's own slot i and writes its own slot opposite(i).  x, y and z
+// are periodic (body-force driving).
+#include <algorithm>
+
+#include "lattice.cuh"
+
+namespace om {
+
+template <class T>
+struct FlowArgs {
+  T* f;
+  int64_t pitch, nf;
+  const uint2* col;
+  const uint32_t* coord;
+  int nx, ny, nz, W;
+  typename Stg<T>::C wp, wm, g, inv;
+};
+
+template <class T>
+__device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c, uint32_t (&nb)[19]) {
+  int x, y, z;
+  unpack_xyz(c, x, y, z);
+  const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
+  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
+  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    const int ex = q19_e(i, 0), ey = q19_e(i, 1), ez = q19_e(i, 2);
+    const int xx = ex > 0 ? xp : (ex < 0 ? xm : x);
+    const int yy = ey > 0 ? yp : (ey < 0 ? ym : y);
+    const int zz = ez > 0 ? zp : (ez < 0 ? zm : z);
+    nb[i] = node_at(a.col, a.ny, a.W, xx, yy, zz);
+  }
+}
+
+// pre-collision populations of node n at the current time
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_load(const FlowArgs<T>& a, int64_t n, const uint32_t (&nb)[19],
+                                          typename Stg<T>::C (&f)[19]) {
+  using S = Stg<T>;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    if (!ODD || i == 0) {
+      f[i] = S::ld(a.f + i * a.pitch + n, a.inv);
+    } else {
+      const uint32_t src = nb[q19_opp(i)];
+      f[i] = src != kNoNode ? S::ld(a.f + q19_opp(i) * a.pitch + src, a.inv)
+                            : S::ld(a.f + i * a.pitch + n, a.inv);
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
+  C rho = f[0];
+#pragma unroll
+  for (int i = 1; i < 19; ++i) rho += f[i];
+  C jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    if (q19_e(i, 0)) jx += q19_e(i, 0) > 0 ? f[i] : -f[i];
+    if (q19_e(i, 1)) jy += q19_e(i, 1) > 0 ? f[i] : -f[i];
+    if (q19_e(i, 2)) jz += q19_e(i, 2) > 0 ? f[i] : -f[i];
+  }
+  const C ux = jx + C(0.5) * g, uy = jy, uz = jz;
+  const C usq15 = C(1.5) * (ux * ux + uy * uy + uz * uz);
+  const C frc = (C(1) - C(0.5) * wm) * C(3) * g;
+  f[0] = f[0] - wp * (f[0] - C(1.0 / 3.0) * (rho - usq15));
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    const int o = q19_opp(i);
+    if (o < i) continue;  // each pair once, from its first member
+    const C w = C(q19_w(i));
+    const C eu = C(q19_e(i, 0)) * ux + C(q19_e(i, 1)) * uy + C(q19_e(i, 2)) * uz;
+    const C sym = w * (rho + C(4.5) * eu * eu - usq15);
+    const C asym = C(3) * w * eu;
+    const C fp = C(0.5) * (f[i] + f[o]);
+    const C fm = C(0.5) * (f[i] - f[o]);
+    const C A = wp * (fp - sym);
+    const C B = wm * (fm - asym) - w * C(q19_e(i, 0)) * frc;
+    f[i] = f[i] - A - B;
+    f[o] = f[o] - A + B;
+  }
+}
+
+template <class T, bool ODD>
+__global__ void __launch_bounds__(256) d3q19_sweep(FlowArgs<T> a) {
+  using S = Stg<T>;
+  using C = typename S::C;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  uint32_t nb[19];
+  if (ODD) flow_neighbours(a, a.coord[n], nb);
+  C f[19];
+  flow_load<T, ODD>(a, n, nb, f);
+  trt_collide(f, a.wp, a.wm, a.g);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    if (!ODD) {
+      S::st(a.f + q19_opp(i) * a.pitch + n, f[i], a.inv);
+    } else if (i == 0) {
+      S::st(a.f + n, f[0], a.inv);
+    } else {
+      const uint32_t dst = nb[i];
+      if (dst != kNoNode) S::st(a.f + i * a.pitch + dst, f[i], a.inv);
+      else S::st(a.f + q19_opp(i) * a.pitch + n, f[i], a.inv);
+    }
+  }
+}
+
+// Observables (FP64, fixed grid): sum u_x, sum |u_x - prev|, sum |u_x|,
+// sum rho-1; prev <- u_x.
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kObsThreads) d3q19_observe(FlowArgs<T> a, double* prev,
+                                                             double* partials) {
+  using C = typename Stg<T>::C;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < a.nf;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t nb[19];
+    if (ODD) flow_neighbours(a, a.coord[n], nb);
+    C f[19];
+    flow_load<T, ODD>(a, n, nb, f);
+    double rho = 0, jx = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      rho += (double)f[i];
+      jx += (double)q19_e(i, 0) * (double)f[i];
+    }
+    const double ux = jx + 0.5 * (double)a.g;
+    acc[0] += ux;
+    acc[1] += fabs(ux - prev[n]);
+    acc[2] += fabs(ux);
+    acc[3] += rho;
+    prev[n] = ux;
+  }
+  block_reduce_store<4>(acc, partials);
+}
+
+template <class T, bool ODD>
+__global__ void d3q19_export(FlowArgs<T> a, const int64_t* vox, int64_t N, double* fdense,
+                             float* udense) {
+  using C = typename Stg<T>::C;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  uint32_t nb[19];
+  if (ODD) flow_neighbours(a, a.coord[n], nb);
+  C f[19];
+  flow_load<T, ODD>(a, n, nb, f);
+  const int64_t v = vox[n];
+  if (fdense) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fdense[i * N + v] = (double)f[i] + q19_w(i);
+  }
+  if (udense) {
+    double jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      jx += (double)q19_e(i, 0) * (double)f[i];
+      jy += (double)q19_e(i, 1) * (double)f[i];
+      jz += (double)q19_e(i, 2) * (double)f[i];
+    }
+    udense[v] = (float)(jx + 0.5 * (double)a.g);
+    udense[N + v] = (float)jy;
+    udense[2 * N + v] = (float)jz;
+  }
+}
+
+template <class T>
+__global__ void d3q19_import(FlowArgs<T> a, const int64_t* vox, int64_t N, const double* fdense) {
+  using S = Stg<T>;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  const int64_t v = vox[n];
+#pragma unroll
+  for (int i = 0; i < 19; ++i)
+    S::st(a.f + i * a.pitch + n, (typename S::C)(fdense[i * N + v] - q19_w(i)), a.inv);
+}
+
+template <class T>
+__global__ void d3q19_rest(FlowArgs<T> a) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) Stg<T>::st(a.f + i * a.pitch + n, 0, a.inv);
+}
+
+}  // namespace om
+
+using namespace om;
+
+struct om_flow {
+  const om_nodeset* ns = nullptr;
+  om_flow_params p{};
+  void* f = nullptr;
+  double* prev = nullptr;
+  double* partials = nullptr;
+  double* obs_dev = nullptr;
+  double* obs_host = nullptr;  // pinned
+  int64_t t = 0;
+  double inv = 1.0;  // storage scale of reduced-precision formats
+};
+
+namespace {
+
+template <class T>
+FlowArgs<T> flow_args(const om_flow* fl) {
+  FlowArgs<T> a;
+  const om_nodeset* ns = fl->ns;
+  a.f = (T*)fl->f;
+  a.pitch = ns->pitch;
+  a.nf = ns->nf;
+  a.col = ns->col;
+  a.coord = ns->coord;
+  a.nx = ns->dom.nx;
+  a.ny = ns->dom.ny;
+  a.nz = ns->dom.nz;
+  a.W = ns->W;
+  const double tau = fl->p.tau;
+  a.wp = (typename Stg<T>::C)(1.0 / tau);
+  a.wm = (typename Stg<T>::C)(8.0 * (2.0 * tau - 1.0) / (8.0 * tau - 1.0));
+  a.g = (typename Stg<T>::C)fl->p.body_force;
+  a.inv = (typename Stg<T>::C)fl->inv;
+  return a;
+}
+
+inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <class T>
+om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
+  if (fl->ns->nf == 0) {
+    fl->t += nsteps;
+    return OM_OK;
+  }
+  FlowArgs<T> a = flow_args<T>(fl);
+  const unsigned nb = blocks_for(a.nf);
+  for (int64_t k = 0; k < nsteps; ++k) {
+    if (fl->t & 1) d3q19_sweep<T, true><<<nb, 256, 0, s>>>(a);
+    else d3q19_sweep<T, false><<<nb, 256, 0, s>>>(a);
+    ++fl->t;
+  }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status flow_observe_t(om_flow* fl, double* out, cudaStream_t s) {
+  FlowArgs<T> a = flow_args<T>(fl);
+  if (fl->t & 1) d3q19_observe<T, true><<<kObsBlocks, kObsThreads, 0, s>>>(a, fl->prev, fl->partials);
+  else d3q19_observe<T, false><<<kObsBlocks, kObsThreads, 0, s>>>(a, fl->prev, fl->partials);
+  launch_finalize(fl->partials, kObsBlocks, 4, fl->obs_dev, s);
+  OM_CUDA(cudaGetLastError());
+  OM_CUDA(cudaMemcpyAsync(fl->obs_host, fl->obs_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 4; ++k) out[k] = fl->obs_host[k];
+  return OM_OK;
+}
+
+template <class T>
+om_status flow_export_t(const om_flow* fl, double* fd, float* ud, cudaStream_t s) {
+  const om_nodeset* ns = fl->ns;
+  if (fd) OM_CUDA(cudaMemsetAsync(fd, 0, sizeof(double) * 19 * ns->N, s));
+  if (ud) OM_CUDA(cudaMemsetAsync(ud, 0, sizeof(float) * 3 * ns->N, s));
+  if (ns->nf == 0) return OM_OK;
+  FlowArgs<T> a = flow_args<T>(fl);
+  if (fl->t & 1) d3q19_export<T, true><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, fd, ud);
+  else d3q19_export<T, false><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, fd, ud);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status flow_import_t(om_flow* fl, const double* fd, cudaStream_t s) {
+  if (fl->ns->nf == 0) return OM_OK;
+  FlowArgs<T> a = flow_args<T>(fl);
+  d3q19_import<T><<<blocks_for(a.nf), 256, 0, s>>>(a, fl->ns->vox, fl->ns->N, fd);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status flow_rest_t(om_flow* fl, cudaStream_t s) {
+  if (fl->ns->nf == 0) return OM_OK;
+  FlowArgs<T> a = flow_args<T>(fl);
+  d3q19_rest<T><<<blocks_for(a.nf), 256, 0, s>>>(a);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+#define OM_FLOW_DISPATCH(fl, fn, ...)                                        \
+  switch ((fl)->p.precision) {                                               \
+    case OM_F64: return fn<double>(__VA_ARGS__);                             \
+    case OM_F32: return fn<float>(__VA_ARGS__);                              \
+    case OM_F16DEV: return fn<__half>(__VA_ARGS__);                          \
+    case OM_BF16DEV: return fn<__nv_bfloat16>(__VA_ARGS__);                  \
+    default: return fail(OM_EINVAL, "unknown precision");                    \
+  }
+
+size_t storage_bytes(int prec) {
+  return prec == OM_F64 ? 8 : (prec == OM_F32 ? 4 : 2);
+}
+
+om_status flow_observe_any(om_flow* fl, double* out, cudaStream_t s) {
+  OM_FLOW_DISPATCH(fl, flow_observe_t, fl, out, s);
+}
+
+}  // namespace
+
+extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* p, void* stream,
+                                    om_flow** out) {
+  if (!ns || !p || !out) return fail(OM_EINVAL, "om_flow_create: null pointer");
+  if (!(p->tau > 0.5)) return fail(OM_EINVAL, "om_flow_create: tau must exceed 1/2");
+  if (p->precision < OM_F64 || p->precision > OM_BF16DEV)
+    return fail(OM_EINVAL, "om_flow_create: unknown precision");
+  cudaStream_t s = as_stream(stream);
+  om_flow* fl = new om_flow();
+  fl->ns = ns;
+  fl->p = *p;
+  // reduced storage keeps deviations scaled by 2^-inv_exp (see lattice.cuh)
+  fl->inv = p->precision == OM_F16DEV ? 1.0 / 1024.0 : 1.0;
+  DevBuf<uint8_t> f;
+  DevBuf<double> prev, part, obs;
+  om_status st = f.alloc(19 * (size_t)ns->pitch * storage_bytes(p->precision));
+  if (st == OM_OK) st = prev.alloc(ns->nf);
+  if (st == OM_OK) st = part.alloc((size_t)kObsBlocks * 8);
+  if (st == OM_OK) st = obs.alloc(8);
+  double* host = nullptr;
+  if (st == OM_OK && cudaMallocHost((void**)&host, 8 * sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    st = fail(OM_ENOMEM, "om_flow_create: pinned allocation failed");
+  }
+  if (st != OM_OK) {
+    delete fl;
+    return st;
+  }
+  fl->f = f.take();
+  fl->prev = prev.take();
+  fl->partials = part.take();
+  fl->obs_dev = obs.take();
+  fl->obs_host = host;
+  auto rest = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_rest_t, fl, s); };
+  st = rest();
+  if (st == OM_OK) {
+    double o[4];
+    st = flow_observe_any(fl, o, s);  // prev <- u_x of the rest state
+  }
+  if (st != OM_OK) {
+    om_flow_destroy(fl);
+    return st;
+  }
+  *out = fl;
+  return OM_OK;
+}
+
+extern "C" om_status om_flow_step(om_flow* fl, int64_t nsteps, void* stream) {
+  if (!fl || nsteps < 0) return fail(OM_EINVAL, "om_flow_step: bad argument");
+  cudaStream_t s = as_stream(stream);
+  OM_FLOW_DISPATCH(fl, flow_steps_t, fl, nsteps, s);
+}
+
+extern "C" om_status om_flow_observe(om_flow* fl, double* out, void* stream) {
+  if (!fl || !out) return fail(OM_EINVAL, "om_flow_observe: null pointer");
+  return flow_observe_any(fl, out, as_stream(stream));
+}
+
+extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* info, void* stream) {
+  if (!fl) return fail(OM_EINVAL, "om_flow_solve: null pointer");
+  const om_flow_params& p = fl->p;
+  if (p.check_every <= 0 || (p.check_every & 1))
+    return fail(OM_EINVAL, "om_flow_solve: check_every must be a positive even number");
+  if (!(p.body_force != 0.0)) return fail(OM_EINVAL, "om_flow_solve: body_force must be nonzero");
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0, e1;
+  OM_CUDA(cudaEventCreate(&e0));
+  OM_CUDA(cudaEventCreate(&e1));
+  double o[4];
+  OM_TRY(flow_observe_any(fl, o, s));  // reference for the first check
+  const int64_t t0 = fl->t;
+  OM_CUDA(cudaEventRecord(e0, s));
+  om_status rc = OM_ENOTCONVERGED;
+  double rel = 1.0;
+  while (fl->t - t0 < p.max_steps) {
+    int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (fl->t - t0));
+    OM_TRY(om_flow_step(fl, k, stream));
+    OM_TRY(flow_observe_any(fl, o, s));
+    rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+    if (rel < p.conv_tol) {
+      rc = OM_OK;
+      break;
+    }
+  }
+  OM_CUDA(cudaEventRecord(e1, s));
+  OM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  OM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double nu = (p.tau - 0.5) / 3.0;
+  if (k_lattice) *k_lattice = nu * (o[0] / (double)fl->ns->N) / p.body_force;
+  if (info) {
+    info->steps = fl->t - t0;
+    info->n_nodes = fl->ns->nf;
+    info->rel_change = rel;
+    info->mass = o[3];
+    info->seconds = ms * 1e-3;
+    info->mlups = ms > 0 ? (double)fl->ns->nf * (double)info->steps / (ms * 1e-3) / 1e6 : 0.0;
+  }
+  if (rc != OM_OK) set_error("om_flow_solve: step cap reached before convergence");
+  return rc;
+}
+
+extern "C" om_status om_flow_get_populations(const om_flow* fl, double* f_dev, void* stream) {
+  if (!fl || !f_dev) return fail(OM_EINVAL, "om_flow_get_populations: null pointer");
+  cudaStream_t s = as_stream(stream);
+  OM_FLOW_DISPATCH(fl, flow_export_t, fl, f_dev, (float*)nullptr, s);
+}
+
+extern "C" om_status om_flow_get_velocity(const om_flow* fl, float* u_dev, void* stream) {
+  if (!fl || !u_dev) return fail(OM_EINVAL, "om_flow_get_velocity: null pointer");
+  cudaStream_t s = as_stream(stream);
+  OM_FLOW_DISPATCH(fl, flow_export_t, fl, (double*)nullptr, u_dev, s);
+}
+
+extern "C" om_status om_flow_set_populations(om_flow* fl, const double* f_dev, void* stream) {
+  if (!fl || !f_dev) return fail(OM_EINVAL, "om_flow_set_populations: null pointer");
+  cudaStream_t s = as_stream(stream);
+  fl->t = 0;
+  auto imp = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_import_t, fl, f_dev, s); };
+  OM_TRY(imp());
+  double o[4];
+  return flow_observe_any(fl, o, s);
+}
+
+extern "C" om_status om_flow_time(const om_flow* fl, int64_t* t) {
+  if (!fl || !t) return fail(OM_EINVAL, "om_flow_time: null pointer");
+  *t = fl->t;
+  return OM_OK;
+}
+
+extern "C" om_status om_flow_destroy(om_flow* fl) {
+  if (!fl) return OM_OK;
+  cudaFree(fl->f);
+  cudaFree(fl->prev);
+  cudaFree(fl->partials);
+  cudaFree(fl->obs_dev);
+  if (fl->obs_host) cudaFreeHost(fl->obs_host);
+  delete fl;
+  return OM_OK;
+}

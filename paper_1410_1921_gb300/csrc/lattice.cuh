@@ -1,0 +1,76 @@
+// lattice.cuh -- storage traits and neighbour lookups shared by the D3Q19
+// flow and D3Q7 diffusion sweeps.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace om {
+
+// Population storage.  Values are stored as deviations from a reference
+// state (w_i for flow, a_i C_lin(x) for diffusion).  Reduced-precision
+// storage also multiplies by a power-of-two scale so the deviations sit in
+// the normal range of the format.
+template <class T>
+struct Stg;
+
+template <>
+struct Stg<double> {
+  using C = double;
+  __device__ __forceinline__ static C ld(const double* p, C) { return *p; }
+  __device__ __forceinline__ static void st(double* p, C v, C) { *p = v; }
+};
+template <>
+struct Stg<float> {
+  using C = float;
+  __device__ __forceinline__ static C ld(const float* p, C) { return *p; }
+  __device__ __forceinline__ static void st(float* p, C v, C) { *p = v; }
+};
+template <>
+struct Stg<__half> {
+  using C = float;
+  __device__ __forceinline__ static C ld(const __half* p, C inv) { return __half2float(*p) * inv; }
+  __device__ __forceinline__ static void st(__half* p, C v, C inv) { *p = __float2half_rn(v / inv); }
+};
+template <>
+struct Stg<__nv_bfloat16> {
+  using C = float;
+  __device__ __forceinline__ static C ld(const __nv_bfloat16* p, C inv) {
+    return __bfloat162float(*p) * inv;
+  }
+  __device__ __forceinline__ static void st(__nv_bfloat16* p, C v, C inv) {
+    *p = __float2bfloat16_rn(v / inv);
+  }
+};
+
+// Node number of voxel (x, y, z) from its column's bit map, or kNoNode.
+__device__ __forceinline__ uint32_t node_at(const uint2* __restrict__ col, int ny, int W, int x,
+                                            int y, int z) {
+  const uint2 b = __ldg(col + ((int64_t)x * ny + y) * W + (z >> 5));
+  const uint32_t bit = 1u << (z & 31);
+  return (b.x & bit) ? b.y + __popc(b.x & (bit - 1u)) : kNoNode;
+}
+
+// Fixed-grid block reduction of NV doubles into partials[blockIdx.x][NV].
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* partials) {
+  __shared__ double sm[NV][kObsThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[k][wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double acc = 0.0;
+    for (int w = 0; w < kObsThreads / 32; ++w) acc += sm[threadIdx.x][w];
+    partials[(int64_t)blockIdx.x * NV + threadIdx.x] = acc;
+  }
+}
+
+}  // namespace om

@@ -1,0 +1,136 @@
+// solve.cu -- the host-buffer entry points that chain the steps of the
+// method: labelling (Sec. 4.1) -> node set -> LB solve (Secs. 3.1-3.2) ->
+// lattice-to-physical units (Eq. 15) -> permeability (Eq. 13), effective
+// diffusivity (Eq. 14), tortuosity (Eq. 16) and apparent permeability
+// (Eq. 26).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace om {
+om_status label_impl(const uint8_t* mask_dev, const om_domain& d, int* labels_dev, uint8_t* transport_dev,
+                     int64_t* npore, int64_t* ntrans, cudaStream_t s);
+}
+
+using namespace om;
+
+namespace {
+
+constexpr double kR = 8.314462618;  // J / (mol K), CODATA 2018
+constexpr double kPi = 3.14159265358979323846;
+
+// Eq. 11: D_K = (d / 3) sqrt(8 R T / (pi M)), d in metres
+double knudsen(double d_m, double T, double M) { return d_m / 3.0 * std::sqrt(8.0 * kR * T / (kPi * M)); }
+
+struct Scope {
+  cudaStream_t s = nullptr;
+  om_nodeset* ns = nullptr;
+  om_flow* fl = nullptr;
+  om_diff* df = nullptr;
+  ~Scope() {
+    if (fl) om_flow_destroy(fl);
+    if (df) om_diff_destroy(df);
+    if (ns) om_nodeset_destroy(ns);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+// transport mask on the device; counts of pore and transport voxels
+om_status transport_nodes(const uint8_t* mask, const om_domain& d, DevBuf<uint8_t>& tr, int64_t& np,
+                          int64_t& nt, cudaStream_t s) {
+  const int64_t N = voxels(d);
+  DevBuf<uint8_t> m;
+  DevBuf<int> lab;
+  OM_TRY(m.alloc(N));
+  OM_TRY(lab.alloc(N));
+  OM_TRY(tr.alloc(N));
+  OM_CUDA(cudaMemcpyAsync(m.p, mask, N, cudaMemcpyHostToDevice, s));
+  OM_TRY(label_impl(m.p, d, lab.p, tr.p, &np, &nt, s));
+  if (nt == 0) return fail(OM_ENOPERC, "no pore component spans x = 0 .. nx-1");
+  return OM_OK;
+}
+
+}  // namespace
+
+extern "C" om_status om_solve_permeability(const uint8_t* mask, om_domain d, const om_flow_params* params,
+                                           double* k_m2, double* k_lattice, om_run_info* info, float* ux_out) {
+  if (!mask || !params) return fail(OM_EINVAL, "om_solve_permeability: null pointer");
+  OM_TRY(check_domain(d));
+  Scope sc;
+  OM_CUDA(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking));
+  DevBuf<uint8_t> tr;
+  int64_t np = 0, nt = 0;
+  OM_TRY(transport_nodes(mask, d, tr, np, nt, sc.s));
+  OM_TRY(om_nodeset_create(tr.p, d, sc.s, &sc.ns));
+  tr.release();
+  OM_TRY(om_flow_create(sc.ns, params, sc.s, &sc.fl));
+  double kl = 0.0;
+  om_status st = om_flow_solve(sc.fl, &kl, info, sc.s);
+  if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
+  const double dx = d.dx_nm * 1e-9;
+  if (k_lattice) *k_lattice = kl;
+  if (k_m2) *k_m2 = kl * dx * dx;  // Eq. 15
+  if (ux_out) {
+    const int64_t N = voxels(d);
+    DevBuf<float> u;
+    OM_TRY(u.alloc(3 * N));
+    OM_TRY(om_flow_get_velocity(sc.fl, u.p, sc.s));
+    OM_CUDA(cudaMemcpyAsync(ux_out, u.p, N * sizeof(float), cudaMemcpyDeviceToHost, sc.s));
+    OM_CUDA(cudaStreamSynchronize(sc.s));
+  }
+  return st;
+}
+
+extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om_domain d,
+                                      const om_diff_params* params, double* D_eff_m2s, double* tortuosity,
+                                      om_run_info* info, float* c_out) {
+  if (!mask || !d_nm || !params) return fail(OM_EINVAL, "om_solve_knudsen: null pointer");
+  OM_TRY(check_domain(d));
+  if (!(params->T_K > 0.0) || !(params->M_kg_per_mol > 0.0))
+    return fail(OM_EINVAL, "om_solve_knudsen: T_K and M_kg_per_mol must be positive");
+  const int64_t N = voxels(d);
+  Scope sc;
+  OM_CUDA(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking));
+  DevBuf<uint8_t> tr;
+  int64_t np = 0, nt = 0;
+  OM_TRY(transport_nodes(mask, d, tr, np, nt, sc.s));
+  OM_TRY(om_nodeset_create(tr.p, d, sc.s, &sc.ns));
+  tr.release();
+  DevBuf<float> dd;
+  OM_TRY(dd.alloc(N));
+  OM_CUDA(cudaMemcpyAsync(dd.p, d_nm, N * sizeof(float), cudaMemcpyHostToDevice, sc.s));
+  OM_TRY(om_diff_create(sc.ns, dd.p, params, sc.s, &sc.df));
+  dd.release();
+  double Dl = 0.0;
+  om_status st = om_diff_solve(sc.df, &Dl, info, sc.s);
+  if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
+  double o[5];
+  OM_TRY(om_diff_observe(sc.df, o, sc.s));
+  // Eq. 15 with the time step set by the reference pore (Eqs. 11-12)
+  const double DL_ref = 0.25 * (params->tau_ref - 0.5);
+  const double DK_ref = knudsen(params->d_ref_nm * 1e-9, params->T_K, params->M_kg_per_mol);
+  if (D_eff_m2s) *D_eff_m2s = Dl * DK_ref / DL_ref;
+  if (tortuosity) {
+    const double porosity = (double)np / (double)N;
+    const double DL_mean = o[4] / (double)nt;
+    *tortuosity = porosity * DL_mean / Dl;  // Eq. 16
+  }
+  if (c_out) {
+    DevBuf<float> c;
+    OM_TRY(c.alloc(N));
+    OM_TRY(om_diff_get_fields(sc.df, c.p, nullptr, sc.s));
+    OM_CUDA(cudaMemcpyAsync(c_out, c.p, N * sizeof(float), cudaMemcpyDeviceToHost, sc.s));
+    OM_CUDA(cudaStreamSynchronize(sc.s));
+  }
+  return st;
+}
+
+extern "C" om_status om_apparent_permeability(double k_m2, double D_eff_m2s, double mu_Pa_s, double p_Pa,
+                                              double* k_app_m2, double* f_c) {
+  if (!(k_m2 > 0.0) || !(D_eff_m2s >= 0.0) || !(mu_Pa_s > 0.0) || !(p_Pa > 0.0))
+    return fail(OM_EINVAL, "om_apparent_permeability: need k > 0, D_eff >= 0, mu > 0, p > 0");
+  const double fc = 1.0 + D_eff_m2s * mu_Pa_s / (k_m2 * p_Pa);  // Eq. 26
+  if (f_c) *f_c = fc;
+  if (k_app_m2) *k_app_m2 = k_m2 * fc;
+  return OM_OK;
+}

@@ -18,3 +18,26 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def om():
+    """The CUDA library's binding; GPU tests fail loudly without a device."""
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a CUDA device"
+    from paper_1410_1921_gb300 import build
+    build.build()
+    import paper_1410_1921_gb300 as P
+    P.lib()
+    return P
+
+
+def recon_args(cfg):
+    """(seed, shape, ...) of a synthetic.Recon for the oracle's reconstruct."""
+    return (cfg.seed, cfg.shape, cfg.dx_nm, cfg.mean_nm, cfg.sd_nm, cfg.dmin_nm, cfg.dmax_nm,
+            cfg.porosity, cfg.xi, cfg.p0, cfg.dist, cfg.max_trials)
+
+
+def recon_params(P, cfg):
+    return P.recon_params(cfg.mean_nm, cfg.sd_nm, cfg.dmin_nm, cfg.dmax_nm, cfg.porosity, cfg.xi,
+                          cfg.p0, cfg.dist, cfg.max_trials)

@@ -1,0 +1,244 @@
+"""Parity of the CUDA LB sweeps with the oracle.
+
+Per step: populations after n = 1, 2, 3, 10, 41 steps from seeded random
+states, element by element, for both models, FP64 and FP32 storage, on
+structures with walls, ragged extents (not multiples of 32) and tiny boxes.
+At convergence: k (Eq. 13) and D_eff (Eq. 14) against the oracle, FP64 to
+1e-10 and FP32 to 1e-5 relative (the stated FP32 bound), including the
+closed-form geometries.
+
+Tolerances.  FP64 sweeps do the oracle's arithmetic in another order (the
+two-relaxation-time form of the same collision), so per step they differ by
+a few units of 2^-53 of the population scale; the bound used is
+1e-13 * n_steps (absolute, populations are O(0.3)).  FP32 storage keeps
+deviations from the rest state; each step rounds them once on store and
+~40 times in the collision, so the per-step error is below 64 u max|dev|
+with u = 2^-24, summed over the steps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda") if dtype is None else t.to("cuda", dtype)
+
+
+def _flow_run(om, node, f0, tau, g, steps, prec):
+    dom = om.domain(node.shape)
+    ns = om.NodeSet(_dev(node), dom)
+    fl = om.Flow(ns, om.flow_params(tau=tau, body_force=g, precision=prec))
+    fl.set_populations(_dev(f0))
+    fl.step(steps)
+    out = torch.empty(19 * node.size, dtype=torch.float64, device="cuda")
+    fl.get_populations(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape((19,) + node.shape)
+
+
+def _diff_run(om, node, d_nm, g0, steps, prec, cin=1.0, cout=0.0):
+    dom = om.domain(node.shape)
+    ns = om.NodeSet(_dev(node), dom)
+    df = om.Diffusion(ns, _dev(d_nm, torch.float32), om.diff_params(c_in=cin, c_out=cout, precision=prec))
+    df.set_populations(_dev(g0))
+    df.step(steps)
+    out = torch.empty(7 * node.size, dtype=torch.float64, device="cuda")
+    df.get_populations(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape((7,) + node.shape)
+
+
+GEOMS = {
+    "blobs": lambda: S.blob_mask((14, 19, 37), 11, n=7),
+    "ragged": lambda: S.random_mask((9, 33, 35), 0.7, 3),
+    "duct": lambda: S.square_duct(5, 6),
+    "tiny": lambda: S.random_mask((2, 3, 2), 0.8, 5),
+    "open": lambda: np.ones((4, 5, 3), np.uint8),
+    "line": lambda: np.ones((1, 1, 7), np.uint8),
+}
+
+
+def _rand_pops(orc, node, seed, amp=0.1):
+    w = orc.weights19()
+    r = S.random_field((19,) + node.shape, seed, -1, 1)
+    return w[:, None, None, None] * (1 + amp * r) * node
+
+
+@pytest.mark.parametrize("geom", list(GEOMS))
+@pytest.mark.parametrize("steps", [1, 2, 3, 10, 41])
+def test_flow_steps_fp64(orc, om, geom, steps):
+    node = GEOMS[geom]()
+    f0 = _rand_pops(orc, node, steps)
+    tau, g = 0.83, 3e-4
+    ref = orc.flow_step(node, f0, tau, g, steps)
+    got = _flow_run(om, node, f0, tau, g, steps, om.OM_F64)
+    assert np.abs(got - ref).max() <= 1e-13 * steps
+
+
+@pytest.mark.parametrize("geom", ["blobs", "ragged", "open"])
+@pytest.mark.parametrize("steps", [1, 2, 10])
+def test_flow_steps_fp32(orc, om, geom, steps):
+    node = GEOMS[geom]()
+    f0 = _rand_pops(orc, node, 100 + steps)
+    tau, g = 1.0, 1e-5
+    ref = orc.flow_step(node, f0, tau, g, steps)
+    got = _flow_run(om, node, f0, tau, g, steps, om.OM_F32)
+    dev = np.abs(f0 - orc.weights19()[:, None, None, None] * node).max()
+    assert np.abs(got - ref).max() <= 64 * U32 * dev * steps + 1e-12
+
+
+def _rand_diff(node, seed):
+    a = np.array([0.25] + [0.125] * 6)
+    c = S.random_field(node.shape, seed, 0.0, 1.0)
+    r = S.random_field((7,) + node.shape, seed + 1, -1, 1)
+    return a[:, None, None, None] * c[None] * (1 + 0.2 * r) * node
+
+
+def _rand_d(node, seed):
+    return (S.random_field(node.shape, seed, 3.0, 90.0) * node).astype(np.float32)
+
+
+@pytest.mark.parametrize("geom", list(GEOMS))
+@pytest.mark.parametrize("steps", [1, 2, 3, 10, 41])
+def test_diffusion_steps_fp64(orc, om, geom, steps):
+    node = GEOMS[geom]()
+    g0 = _rand_diff(node, steps)
+    d = _rand_d(node, 7 + steps)
+    om_ref = orc.omega_field(node, d)
+    ref = orc.diff_step(node, g0, om_ref, 0.9, 0.2, steps)
+    got = _diff_run(om, node, d, g0, steps, om.OM_F64, 0.9, 0.2)
+    assert np.abs(got - ref).max() <= 1e-13 * steps
+
+
+@pytest.mark.parametrize("geom", ["blobs", "ragged", "duct"])
+@pytest.mark.parametrize("steps", [1, 2, 10])
+def test_diffusion_steps_fp32(orc, om, geom, steps):
+    node = GEOMS[geom]()
+    g0 = _rand_diff(node, 50 + steps)
+    d = _rand_d(node, 60 + steps)
+    ref = orc.diff_step(node, g0, orc.omega_field(node, d), 1.0, 0.0, steps)
+    got = _diff_run(om, node, d, g0, steps, om.OM_F32)
+    assert np.abs(got - ref).max() <= 64 * U32 * np.abs(g0).max() * steps + 1e-12
+
+
+# ------------------------------------------------------------------ to convergence
+def _flow_solve_gpu(om, node, prec, tau=1.0, g=1e-6, tol=1e-10, K=100):
+    ns = om.NodeSet(_dev(node), om.domain(node.shape))
+    fl = om.Flow(ns, om.flow_params(tau=tau, body_force=g, conv_tol=tol, check_every=K, max_steps=400000,
+                                    precision=prec))
+    return fl.solve()
+
+
+@pytest.mark.parametrize("name,node,tau", [("slit", S.slit(1, 8), 1.0), ("slit_ragged", S.slit(3, 13, 5), 0.7),
+                                           ("duct", S.square_duct(1, 12), 1.0), ("tube", S.tube(2, 5.5), 1.3)])
+def test_flow_converged_permeability(orc, om, name, node, tau):
+    rc, kL, *_ = orc.flow_solve(node, tau=tau, g=1e-6, tol=1e-10, K=100, max_steps=400000)
+    assert rc == 0
+    st, k64, info = _flow_solve_gpu(om, node, om.OM_F64, tau=tau)
+    assert st == om.OM_OK and k64 == pytest.approx(kL, rel=1e-10)
+    st, k32, info = _flow_solve_gpu(om, node, om.OM_F32, tau=tau, tol=1e-7)
+    assert st == om.OM_OK and k32 == pytest.approx(kL, rel=1e-5)
+
+
+def test_flow_converged_reconstructed(orc, om):
+    cfg = S.small_structure(4).with_(shape=(20, 20, 20))
+    from conftest import recon_args
+    _, mask, *_ = orc.reconstruct(*recon_args(cfg))
+    _, tr, _ = orc.label18(mask)
+    assert tr.sum() > 0
+    rc, kL, _, steps, _, _ = orc.flow_solve(tr, tau=1.0, g=1e-6, tol=1e-8, K=100, max_steps=200000)
+    assert rc == 0
+    st, k64, _ = _flow_solve_gpu(om, tr, om.OM_F64, tol=1e-8)
+    assert k64 == pytest.approx(kL, rel=1e-9)
+    st, k32, _ = _flow_solve_gpu(om, tr, om.OM_F32, tol=1e-7)
+    assert k32 == pytest.approx(kL, rel=1e-5)
+
+
+def _diff_solve_gpu(om, node, d, prec, tol=1e-10, K=100):
+    ns = om.NodeSet(_dev(node), om.domain(node.shape))
+    df = om.Diffusion(ns, _dev(d, torch.float32), om.diff_params(conv_tol=tol, check_every=K, max_steps=2_000_000,
+                                                                 precision=prec))
+    return df.solve()
+
+
+def test_diffusion_converged_reconstructed(orc, om):
+    cfg = S.small_structure(5).with_(shape=(20, 20, 20))
+    from conftest import recon_args
+    _, mask, *_ = orc.reconstruct(*recon_args(cfg))
+    _, tr, _ = orc.label18(mask)
+    d, _ = orc.chord13(mask, cfg.dx_nm, counts=False)
+    rc, D, *_ = orc.diff_solve(tr, orc.omega_field(tr, d), 1.0, 0.0, tol=1e-9, K=100, max_steps=2_000_000)
+    assert rc == 0
+    st, D64, _ = _diff_solve_gpu(om, tr, d, om.OM_F64, tol=1e-9)
+    assert st == om.OM_OK and D64 == pytest.approx(D, rel=1e-9)
+    st, D32, _ = _diff_solve_gpu(om, tr, d, om.OM_F32, tol=1e-7)
+    assert st == om.OM_OK and D32 == pytest.approx(D, rel=1e-5)
+
+
+def test_diffusion_straight_channel_exact(om):
+    node, layer = S.layered_slit(7, 5)
+    d = np.where(node == 1, 6.0 * layer, 0).astype(np.float32)
+    st, D, info = _diff_solve_gpu(om, node, d, om.OM_F64, tol=1e-13, K=50)
+    Dl = sum((v / 60 * 0.5 + 0.5 - 0.5) / 4 for v in 6.0 * np.arange(1, 6))
+    assert D == pytest.approx(Dl / 7, rel=1e-10)
+
+
+# ------------------------------------------------------------------ host-buffer entry points
+def test_solve_permeability_entry_point(orc, om):
+    m = S.slit(4, 9, 3)
+    st, k, kl, info, ux = om.om_solve_permeability(m, om.domain(m.shape, 1.5),
+                                                   om.flow_params(conv_tol=1e-11, precision=om.OM_F64), True)
+    rc, kL, *_ = orc.flow_solve(m, tau=1.0, g=1e-6, tol=1e-11)
+    assert st == 0 and kl == pytest.approx(kL, rel=1e-10)
+    assert k == pytest.approx(kL * (1.5e-9) ** 2, rel=1e-10)
+    assert info.n_nodes == m.sum() and info.steps > 0
+    y = np.arange(1, 10) - 0.5
+    assert np.allclose(ux[0, 1:10, 0], 1e-6 * y * (9 - y) / (2 / 6), rtol=1e-6)
+
+
+def test_solve_knudsen_entry_point(orc, om):
+    from oracle import physics as PH
+    m = S.slit(6, 4, 2)
+    d = np.where(m == 1, 30.0, 0.0).astype(np.float32)
+    st, D, tau, info, c = om.om_solve_knudsen(m, d, om.domain(m.shape, 2.0),
+                                             om.diff_params(T_K=323.0, conv_tol=1e-12, precision=om.OM_F64), True)
+    assert st == 0
+    eps = 4 / 6
+    assert D == pytest.approx(eps * PH.knudsen_diffusivity(30e-9, 323.0, 0.016), rel=1e-10)
+    assert tau == pytest.approx(1.0, rel=1e-10)
+    assert np.allclose(c[:, 1:5, :], (1 - (np.arange(6) + 0.5) / 6)[:, None, None], atol=1e-6)
+
+
+def test_no_percolation_reports(om):
+    m = np.zeros((6, 6, 6), np.uint8)
+    m[:3] = 1  # touches the inlet only
+    with pytest.raises(om.OmError) as e:
+        om.om_solve_permeability(m, om.domain(m.shape), om.flow_params())
+    assert e.value.status == om.OM_ENOPERC
+
+
+def test_step_cap_reports_not_converged(om):
+    m = S.slit(2, 10)
+    st, k, kl, info, _ = om.om_solve_permeability(m, om.domain(m.shape), om.flow_params(max_steps=200))
+    assert st == om.OM_ENOTCONVERGED and info.steps == 200 and kl > 0
+
+
+def test_apparent_permeability_eq26(om):
+    from oracle import physics as PH
+    ka, fc = om.om_apparent_permeability(2e-19, 3e-7, 1.73e-5, 17236893.0)
+    ka_o, fc_o = PH.apparent_permeability(2e-19, 3e-7, 1.73e-5, 17236893.0)
+    assert ka == pytest.approx(ka_o, rel=1e-15) and fc == pytest.approx(fc_o, rel=1e-15)
+
+
+def test_mass_conserved_closed_box(orc, om):
+    node = S.closed_box((9, 10, 35))
+    f0 = _rand_pops(orc, node, 3)
+    got = _flow_run(om, node, f0, 0.9, 0.0, 200, om.OM_F64)
+    assert got.sum() == pytest.approx(f0.sum(), rel=1e-13)
