@@ -84,8 +84,9 @@ typedef struct {
 } om_flow_params;
 
 /* D3Q7 Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
- * size and relaxation time of Eq. 12, inlet/outlet concentrations, and the
- * convergence test of om_flow_params applied to the concentration. */
+ * size and relaxation time of Eq. 12, inlet/outlet concentrations.
+ * Convergence: every check_every steps both sum|dC| / sum|C| and the relative
+ * change of the total flux sum J_x drop below conv_tol. */
 typedef struct {
   double T_K, M_kg_per_mol, d_ref_nm, tau_ref, c_in, c_out, conv_tol;
   int32_t check_every;

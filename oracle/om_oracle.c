@@ -679,10 +679,13 @@ void orc_diff_fields(const uint8_t *node, int nx, int ny, int nz, const double *
   }
 }
 
-/* Solve to the steady state; convergence on C as for the flow.  Eq. 14 with
- * the volume-averaged flux: D_eff,L = (sum J_x / N) * nx / (C_in - C_out).
- * out[0] D_eff,L, out[1] sum J_x, out[2] steps, out[3] last relative change,
- * out[4] sum C. */
+/* Solve to the steady state.  Every K steps both the concentration field
+ * (sum|dC| / sum|C|) and the total flux (|d sum J_x| / |sum J_x|) must have
+ * changed by less than tol: the concentration alone can sit at its final
+ * profile while the flux is still relaxing.  Eq. 14 with the volume-averaged
+ * flux: D_eff,L = (sum J_x / N) * nx / (C_in - C_out).
+ * out[0] D_eff,L, out[1] sum J_x, out[2] steps, out[3] last relative change
+ * (the larger of the two), out[4] sum C. */
 int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin,
                    double cout, double tol, int K, int64_t max_steps, double *g, double *out) {
   int64_t N = (int64_t)nx * ny * nz;
@@ -691,7 +694,10 @@ int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *om
   double *prev = (double *)malloc(sizeof(double) * (size_t)N);
   if (!C || !J || !prev) { free(C); free(J); free(prev); return ORC_ENOMEM; }
   orc_diff_init(node, nx, ny, nz, cin, cout, g);
-  orc_diff_fields(node, nx, ny, nz, omega, g, prev, NULL);
+  orc_diff_fields(node, nx, ny, nz, omega, g, prev, J);
+  double sj_prev = 0.0;
+  for (int64_t v = 0; v < N; ++v)
+    if (node[v]) sj_prev += J[v];
   int64_t n = 0;
   double rel = 1.0, sj = 0.0, sc = 0.0;
   int rc = ORC_ENOTCONVERGED;
@@ -713,6 +719,9 @@ int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *om
       prev[v] = C[v];
     }
     rel = ac > 0.0 ? dc / ac : 0.0;
+    double relj = sj != 0.0 ? fabs(sj - sj_prev) / fabs(sj) : 0.0;
+    if (relj > rel) rel = relj;
+    sj_prev = sj;
     if (rel < tol) { rc = ORC_OK; break; }
   }
   out[0] = (sj / (double)N) * (double)nx / (cin - cout);

@@ -142,6 +142,8 @@ def _stream(stream):
     if stream is None:
         import torch
         return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, C.c_void_p):
+        return stream
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)

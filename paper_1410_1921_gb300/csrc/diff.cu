@@ -13,6 +13,7 @@
 // x = nx - 1/2 (c_out) by anti-bounce-back,
 //     g_i(x_b, t+1) = -g*_opp(i)(x_b, t) + 2 a_i C_w.
 #include <algorithm>
+#include <cmath>
 
 #include "lattice.cuh"
 
@@ -398,6 +399,7 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
   OM_CUDA(cudaEventCreate(&e1));
   double o[5];
   OM_TRY(diff_observe_any(df, o, s));
+  double sj_prev = o[0];
   const int64_t t0 = df->t;
   OM_CUDA(cudaEventRecord(e0, s));
   om_status rc = OM_ENOTCONVERGED;
@@ -406,7 +408,12 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
     int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (df->t - t0));
     OM_TRY(om_diff_step(df, k, stream));
     OM_TRY(diff_observe_any(df, o, s));
+    // converged when both the concentration field and the total flux have
+    // settled: C can sit at its final profile while the flux still relaxes
     rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+    const double relj = o[0] != 0.0 ? std::fabs(o[0] - sj_prev) / std::fabs(o[0]) : 0.0;
+    rel = std::max(rel, relj);
+    sj_prev = o[0];
     if (rel < p.conv_tol) {
       rc = OM_OK;
       break;

@@ -148,7 +148,7 @@ def test_flow_converged_permeability(orc, om, name, node, tau):
 
 
 def test_flow_converged_reconstructed(orc, om):
-    cfg = S.small_structure(4).with_(shape=(20, 20, 20))
+    cfg = S.small_structure(3).with_(shape=(20, 20, 20))
     from conftest import recon_args
     _, mask, *_ = orc.reconstruct(*recon_args(cfg))
     _, tr, _ = orc.label18(mask)
