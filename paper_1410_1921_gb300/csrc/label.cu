@@ -65,9 +65,21 @@ __global__ void uf_link(const uint8_t* mask, int nx, int ny, int nz, int* par) {
   }
 }
 
+// Root without path compression.  The flatten pass must not compress: a
+// compressing walk could overwrite a root another thread has just stored
+// with an intermediate ancestor it read earlier.
+__device__ __forceinline__ int uf_root(const volatile int* par, int x) {
+  int p = par[x];
+  while (p != x) {
+    x = p;
+    p = par[x];
+  }
+  return x;
+}
+
 __global__ void uf_flatten(int* par, int64_t N) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
-    if (par[v] >= 0) par[v] = uf_find(par, (int)v);
+    if (par[v] >= 0) par[v] = uf_root(par, (int)v);
 }
 
 __global__ void mark_faces(const int* lab, int nx, int ny, int nz, uint8_t* touch) {

@@ -134,3 +134,15 @@ def test_sweep_workload_structure_bit_exact(orc, om, eps):
     do, _ = orc.chord13(mo, cfg.dx_nm, counts=False)
     dg, _ = om.om_local_pore_diameter(mo, om.domain(cfg.shape, cfg.dx_nm), om.OM_PORE_CHORD13)
     assert np.array_equal(do, dg)
+
+
+@pytest.mark.parametrize("shape,seed", [((40, 33, 29), 3), ((64, 48, 40), 5), ((96, 64, 64), 9)])
+def test_labels_repeatable_under_contention(orc, om, shape, seed):
+    """Union-find labels must be the canonical ones on every run, not only on
+    most: thin one-voxel channels with many concurrent links are where a
+    racy root compression shows up.  Repeated runs against the oracle."""
+    m = S.blob_mask(shape, seed, n=12, rmin=2.0, rmax=7.0)
+    lo, to, co = orc.label18(m)
+    for _ in range(40):
+        lg, tg, cg = om.om_label_connectivity(m)
+        assert np.array_equal(lo, lg) and np.array_equal(to, tg) and co == cg
