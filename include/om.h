@@ -81,6 +81,7 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
+  int32_t variant; /* sweep launch variant: -1 = time them at creation, keep the fastest */
 } om_flow_params;
 
 /* D3Q7 Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
@@ -92,6 +93,7 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
+  int32_t variant; /* as om_flow_params.variant */
 } om_diff_params;
 
 typedef struct {

@@ -21,14 +21,14 @@ namespace om {
 
 template <class T>
 struct DiffArgs {
-  T* g;
-  int64_t pitch, nf;
+  T* q[7];  // population i of node n is q[i][n]
+  uint32_t nf;
   const uint2* col;
   const uint32_t* coord;
   const typename Stg<T>::C* omega;
   int nx, ny, nz, W;
-  typename Stg<T>::C s;    // slope of C_lin per lattice cell, (c_out - c_in)/nx
-  typename Stg<T>::C inv;  // storage scale
+  typename Stg<T>::C s;         // slope of C_lin per lattice cell, (c_out - c_in)/nx
+  typename Stg<T>::C up, down;  // storage scale
   double cin, cout;
 };
 
@@ -50,36 +50,37 @@ __device__ __forceinline__ void diff_neighbours(const DiffArgs<T>& a, uint32_t c
 
 // pre-collision deviations of node n at the current time
 template <class T, bool ODD>
-__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, int64_t n, const uint32_t (&nb)[7],
+__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7],
                                           int x, typename Stg<T>::C (&g)[7]) {
   using S = Stg<T>;
   using C = typename S::C;
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     if (!ODD || i == 0) {
-      g[i] = S::ld(a.g + i * a.pitch + n, a.inv);
+      g[i] = S::ld(a.q[i] + n, a.down);
     } else {
       const int o = q7_opp(i);
       const uint32_t src = nb[o];  // x - e_i
       const bool inlet = (i == 1 && x == 0), outlet = (i == 2 && x == a.nx - 1);
-      if (inlet) {
-        g[i] = -S::ld(a.g + i * a.pitch + n, a.inv) - C(0.125) * a.s;
-      } else if (outlet) {
-        g[i] = -S::ld(a.g + i * a.pitch + n, a.inv) + C(0.125) * a.s;
-      } else if (src != kNoNode) {
-        g[i] = S::ld(a.g + o * a.pitch + src, a.inv) - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
-      } else {
-        g[i] = S::ld(a.g + i * a.pitch + n, a.inv);
-      }
+      const T* p = (src != kNoNode && !inlet && !outlet) ? a.q[o] + src : a.q[i] + n;
+      const C v = S::ld(p, a.down);
+      if (inlet) g[i] = -v - C(0.125) * a.s;
+      else if (outlet) g[i] = -v + C(0.125) * a.s;
+      else if (src != kNoNode) g[i] = v - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
+      else g[i] = v;
     }
   }
 }
 
-template <class T, bool ODD>
-__global__ void __launch_bounds__(256) d3q7_sweep(DiffArgs<T> a) {
+// Launch variants for the autotuner of om_diff_create (identical arithmetic):
+// 0 = registers as the compiler wants, 1 = capped for 8 resident blocks.
+constexpr int kDiffVariants = 2;
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q7_sweep(DiffArgs<T> a) {
   using S = Stg<T>;
   using C = typename S::C;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   uint32_t nb[7];
   int x = 0;
@@ -96,20 +97,20 @@ __global__ void __launch_bounds__(256) d3q7_sweep(DiffArgs<T> a) {
   for (int i = 0; i < 7; ++i) {
     const int o = q7_opp(i);
     if (!ODD) {
-      S::st(a.g + o * a.pitch + n, g[i], a.inv);
+      S::st(a.q[o] + n, g[i], a.up);
     } else if (i == 0) {
-      S::st(a.g + n, g[0], a.inv);
+      S::st(a.q[0] + n, g[0], a.up);
     } else {
       const bool outlet = (i == 1 && x == a.nx - 1), inlet = (i == 2 && x == 0);
-      if (outlet) {
-        S::st(a.g + o * a.pitch + n, -g[i] + C(0.125) * a.s, a.inv);
-      } else if (inlet) {
-        S::st(a.g + o * a.pitch + n, -g[i] - C(0.125) * a.s, a.inv);
-      } else if (nb[i] != kNoNode) {
-        S::st(a.g + i * a.pitch + nb[i], g[i] - C(q7_w(i)) * C(q7_e(i, 0)) * a.s, a.inv);
-      } else {
-        S::st(a.g + o * a.pitch + n, g[i], a.inv);
+      T* p = a.q[o] + n;
+      C v = g[i];
+      if (outlet) v = -g[i] + C(0.125) * a.s;
+      else if (inlet) v = -g[i] - C(0.125) * a.s;
+      else if (nb[i] != kNoNode) {
+        p = a.q[i] + nb[i];
+        v = g[i] - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
       }
+      S::st(p, v, a.up);
     }
   }
 }
@@ -121,8 +122,7 @@ __global__ void __launch_bounds__(kObsThreads) d3q7_observe(DiffArgs<T> a, doubl
   using C = typename Stg<T>::C;
   double acc[5] = {0, 0, 0, 0, 0};
   const double s = (double)a.s;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < a.nf;
-       n += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.nf; n += gridDim.x * blockDim.x) {
     uint32_t nb[7];
     int x, y, z;
     unpack_xyz(a.coord[n], x, y, z);
@@ -150,7 +150,7 @@ template <class T, bool ODD>
 __global__ void d3q7_export(DiffArgs<T> a, const int64_t* vox, int64_t N, double* gdense,
                             float* cdense, float* jdense) {
   using C = typename Stg<T>::C;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   uint32_t nb[7];
   int x, y, z;
@@ -174,14 +174,14 @@ template <class T>
 __global__ void d3q7_import(DiffArgs<T> a, const int64_t* vox, int64_t N, const double* gdense,
                             int linear) {
   using S = Stg<T>;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   const int64_t v = vox[n];
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     // linear != 0: the linear profile itself, i.e. zero deviation
     double val = linear ? 0.0 : gdense[i * N + v] - q7_w(i) * (a.cin + (double)a.s * ((double)(v / ((int64_t)a.ny * a.nz)) + 0.5));
-    S::st(a.g + i * a.pitch + n, (typename S::C)val, a.inv);
+    S::st(a.q[i] + n, (typename S::C)val, a.up);
   }
 }
 
@@ -210,7 +210,8 @@ struct om_diff {
   double* obs_dev = nullptr;
   double* obs_host = nullptr;
   int64_t t = 0;
-  double inv = 1.0;
+  double up = 1.0;      // storage scale (stored = deviation * up)
+  int var[2] = {0, 0};  // launch variant of the even and odd sweeps
 };
 
 namespace {
@@ -219,9 +220,8 @@ template <class T>
 DiffArgs<T> diff_args(const om_diff* df) {
   DiffArgs<T> a;
   const om_nodeset* ns = df->ns;
-  a.g = (T*)df->g;
-  a.pitch = ns->pitch;
-  a.nf = ns->nf;
+  for (int i = 0; i < 7; ++i) a.q[i] = (T*)df->g + (size_t)i * ns->pitch;
+  a.nf = (uint32_t)ns->nf;
   a.col = ns->col;
   a.coord = ns->coord;
   a.omega = (const typename Stg<T>::C*)df->omega;
@@ -230,13 +230,25 @@ DiffArgs<T> diff_args(const om_diff* df) {
   a.nz = ns->dom.nz;
   a.W = ns->W;
   a.s = (typename Stg<T>::C)((df->p.c_out - df->p.c_in) / (double)ns->dom.nx);
-  a.inv = (typename Stg<T>::C)df->inv;
+  a.up = (typename Stg<T>::C)df->up;
+  a.down = (typename Stg<T>::C)(1.0 / df->up);
   a.cin = df->p.c_in;
   a.cout = df->p.c_out;
   return a;
 }
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <class T>
+void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const DiffArgs<T>& a) {
+  if (variant == 1) {
+    if (odd) d3q7_sweep<T, true, 8><<<nb, 256, 0, s>>>(a);
+    else d3q7_sweep<T, false, 8><<<nb, 256, 0, s>>>(a);
+  } else {
+    if (odd) d3q7_sweep<T, true, 1><<<nb, 256, 0, s>>>(a);
+    else d3q7_sweep<T, false, 1><<<nb, 256, 0, s>>>(a);
+  }
+}
 
 template <class T>
 om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
@@ -247,11 +259,47 @@ om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
   DiffArgs<T> a = diff_args<T>(df);
   const unsigned nb = blocks_for(a.nf);
   for (int64_t k = 0; k < nsteps; ++k) {
-    if (df->t & 1) d3q7_sweep<T, true><<<nb, 256, 0, s>>>(a);
-    else d3q7_sweep<T, false><<<nb, 256, 0, s>>>(a);
+    const bool odd = df->t & 1;
+    launch_sweep<T>(odd, df->var[odd], nb, s, a);
     ++df->t;
   }
   OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+// Autotuner: time each launch variant of both sweeps (6 even/odd pairs after
+// a warm-up pair), keep the fastest per parity; the caller re-initialises.
+template <class T>
+om_status diff_tune_t(om_diff* df, cudaStream_t s) {
+  if (df->ns->nf == 0) return OM_OK;
+  DiffArgs<T> a = diff_args<T>(df);
+  const unsigned nb = blocks_for(a.nf);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
+  float best[2] = {1e30f, 1e30f};
+  for (int v = 0; v < kDiffVariants; ++v) {
+    float tot[2] = {0.f, 0.f};
+    for (int r = 0; r < 7; ++r) {
+      OM_CUDA(cudaEventRecord(ev[0], s));
+      launch_sweep<T>(false, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[1], s));
+      launch_sweep<T>(true, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[2], s));
+      OM_CUDA(cudaEventSynchronize(ev[2]));
+      if (r == 0) continue;
+      float m0 = 0.f, m1 = 0.f;
+      OM_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
+      OM_CUDA(cudaEventElapsedTime(&m1, ev[1], ev[2]));
+      tot[0] += m0;
+      tot[1] += m1;
+    }
+    for (int p = 0; p < 2; ++p)
+      if (tot[p] < best[p]) {
+        best[p] = tot[p];
+        df->var[p] = v;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
   return OM_OK;
 }
 
@@ -336,7 +384,7 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   om_diff* df = new om_diff();
   df->ns = ns;
   df->p = *p;
-  df->inv = p->precision == OM_F16DEV ? 1.0 / 64.0 : 1.0;
+  df->up = p->precision == OM_F16DEV ? 64.0 : 1.0;  // FP16: keep deviations normal numbers
   const size_t cb = p->precision == OM_F64 ? 8 : 4;
   DevBuf<uint8_t> g, om;
   DevBuf<double> prev, part, obs;
@@ -362,8 +410,14 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   df->obs_host = host;
   auto setup = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_omega_t, df, d_nm_dev, s); };
   auto init = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_import_t, df, nullptr, 1, s); };
+  auto tune = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_tune_t, df, s); };
+  if (p->variant >= 0) df->var[0] = df->var[1] = std::min(p->variant, kDiffVariants - 1);
   st = setup();
   if (st == OM_OK) st = init();
+  if (st == OM_OK && p->variant < 0) {
+    st = tune();
+    if (st == OM_OK) st = init();  // back to the linear profile
+  }
   if (st == OM_OK) {
     double o[5];
     st = diff_observe_any(df, o, s);

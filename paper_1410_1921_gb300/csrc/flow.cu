@@ -29,12 +29,12 @@ namespace om {
 
 template <class T>
 struct FlowArgs {
-  T* f;
-  int64_t pitch, nf;
+  T* s[19];  // population i of node n is s[i][n] (kernel parameters: no per-slot registers)
+  uint32_t nf;
   const uint2* col;
   const uint32_t* coord;
   int nx, ny, nz, W;
-  typename Stg<T>::C wp, wm, g, inv;
+  typename Stg<T>::C wp, wm, g, up, down;
 };
 
 template <class T>
@@ -56,18 +56,16 @@ __device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c
 
 // pre-collision populations of node n at the current time
 template <class T, bool ODD>
-__device__ __forceinline__ void flow_load(const FlowArgs<T>& a, int64_t n, const uint32_t (&nb)[19],
+__device__ __forceinline__ void flow_load(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
                                           typename Stg<T>::C (&f)[19]) {
-  using S = Stg<T>;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    if (!ODD || i == 0) {
-      f[i] = S::ld(a.f + i * a.pitch + n, a.inv);
-    } else {
+    const T* p = a.s[i] + n;
+    if (ODD && i > 0) {
       const uint32_t src = nb[q19_opp(i)];
-      f[i] = src != kNoNode ? S::ld(a.f + q19_opp(i) * a.pitch + src, a.inv)
-                            : S::ld(a.f + i * a.pitch + n, a.inv);
+      if (src != kNoNode) p = a.s[q19_opp(i)] + src;
     }
+    f[i] = Stg<T>::ld(p, a.down);
   }
 }
 
@@ -104,11 +102,19 @@ __device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
   }
 }
 
-template <class T, bool ODD>
-__global__ void __launch_bounds__(256) d3q19_sweep(FlowArgs<T> a) {
+// Launch variants (chosen per parity by the autotuner of om_flow_create):
+// variant 0 lets the compiler use the registers it wants; variant 1 caps them
+// (256 threads x MINB blocks resident per SM) for more latency hiding at the
+// cost of a few spills.  Both do identical arithmetic.
+template <class T>
+constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
+constexpr int kSweepVariants = 2;
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
   using S = Stg<T>;
   using C = typename S::C;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   uint32_t nb[19];
   if (ODD) flow_neighbours(a, a.coord[n], nb);
@@ -117,15 +123,14 @@ __global__ void __launch_bounds__(256) d3q19_sweep(FlowArgs<T> a) {
   trt_collide(f, a.wp, a.wm, a.g);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    if (!ODD) {
-      S::st(a.f + q19_opp(i) * a.pitch + n, f[i], a.inv);
-    } else if (i == 0) {
-      S::st(a.f + n, f[0], a.inv);
-    } else {
+    T* p = a.s[q19_opp(i)] + n;
+    if (ODD && i > 0) {
       const uint32_t dst = nb[i];
-      if (dst != kNoNode) S::st(a.f + i * a.pitch + dst, f[i], a.inv);
-      else S::st(a.f + q19_opp(i) * a.pitch + n, f[i], a.inv);
+      if (dst != kNoNode) p = a.s[i] + dst;
+    } else if (ODD) {
+      p = a.s[0] + n;
     }
+    S::st(p, f[i], a.up);
   }
 }
 
@@ -136,8 +141,7 @@ __global__ void __launch_bounds__(kObsThreads) d3q19_observe(FlowArgs<T> a, doub
                                                              double* partials) {
   using C = typename Stg<T>::C;
   double acc[4] = {0, 0, 0, 0};
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < a.nf;
-       n += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.nf; n += gridDim.x * blockDim.x) {
     uint32_t nb[19];
     if (ODD) flow_neighbours(a, a.coord[n], nb);
     C f[19];
@@ -162,7 +166,7 @@ template <class T, bool ODD>
 __global__ void d3q19_export(FlowArgs<T> a, const int64_t* vox, int64_t N, double* fdense,
                              float* udense) {
   using C = typename Stg<T>::C;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   uint32_t nb[19];
   if (ODD) flow_neighbours(a, a.coord[n], nb);
@@ -190,20 +194,19 @@ __global__ void d3q19_export(FlowArgs<T> a, const int64_t* vox, int64_t N, doubl
 template <class T>
 __global__ void d3q19_import(FlowArgs<T> a, const int64_t* vox, int64_t N, const double* fdense) {
   using S = Stg<T>;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   const int64_t v = vox[n];
 #pragma unroll
-  for (int i = 0; i < 19; ++i)
-    S::st(a.f + i * a.pitch + n, (typename S::C)(fdense[i * N + v] - q19_w(i)), a.inv);
+  for (int i = 0; i < 19; ++i) S::st(a.s[i] + n, (typename S::C)(fdense[i * N + v] - q19_w(i)), a.up);
 }
 
 template <class T>
 __global__ void d3q19_rest(FlowArgs<T> a) {
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
 #pragma unroll
-  for (int i = 0; i < 19; ++i) Stg<T>::st(a.f + i * a.pitch + n, 0, a.inv);
+  for (int i = 0; i < 19; ++i) Stg<T>::st(a.s[i] + n, 0, a.up);
 }
 
 }  // namespace om
@@ -219,7 +222,8 @@ struct om_flow {
   double* obs_dev = nullptr;
   double* obs_host = nullptr;  // pinned
   int64_t t = 0;
-  double inv = 1.0;  // storage scale of reduced-precision formats
+  double up = 1.0;  // storage scale of reduced-precision formats (stored = deviation * up)
+  int var[2] = {0, 0};  // launch variant of the even and odd sweeps
 };
 
 namespace {
@@ -228,9 +232,8 @@ template <class T>
 FlowArgs<T> flow_args(const om_flow* fl) {
   FlowArgs<T> a;
   const om_nodeset* ns = fl->ns;
-  a.f = (T*)fl->f;
-  a.pitch = ns->pitch;
-  a.nf = ns->nf;
+  for (int i = 0; i < 19; ++i) a.s[i] = (T*)fl->f + (size_t)i * ns->pitch;
+  a.nf = (uint32_t)ns->nf;
   a.col = ns->col;
   a.coord = ns->coord;
   a.nx = ns->dom.nx;
@@ -241,11 +244,23 @@ FlowArgs<T> flow_args(const om_flow* fl) {
   a.wp = (typename Stg<T>::C)(1.0 / tau);
   a.wm = (typename Stg<T>::C)(8.0 * (2.0 * tau - 1.0) / (8.0 * tau - 1.0));
   a.g = (typename Stg<T>::C)fl->p.body_force;
-  a.inv = (typename Stg<T>::C)fl->inv;
+  a.up = (typename Stg<T>::C)fl->up;
+  a.down = (typename Stg<T>::C)(1.0 / fl->up);
   return a;
 }
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <class T>
+void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>& a) {
+  if (variant == 1) {
+    if (odd) d3q19_sweep<T, true, kMinBlocks1<T>><<<nb, 256, 0, s>>>(a);
+    else d3q19_sweep<T, false, kMinBlocks1<T>><<<nb, 256, 0, s>>>(a);
+  } else {
+    if (odd) d3q19_sweep<T, true, 1><<<nb, 256, 0, s>>>(a);
+    else d3q19_sweep<T, false, 1><<<nb, 256, 0, s>>>(a);
+  }
+}
 
 template <class T>
 om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
@@ -256,10 +271,49 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
   FlowArgs<T> a = flow_args<T>(fl);
   const unsigned nb = blocks_for(a.nf);
   for (int64_t k = 0; k < nsteps; ++k) {
-    if (fl->t & 1) d3q19_sweep<T, true><<<nb, 256, 0, s>>>(a);
-    else d3q19_sweep<T, false><<<nb, 256, 0, s>>>(a);
+    const bool odd = fl->t & 1;
+    launch_sweep<T>(odd, fl->var[odd], nb, s, a);
     ++fl->t;
   }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+// Autotuner: time every launch variant of both sweeps on this node set
+// (6 even/odd pairs each after a warm-up pair) and keep the fastest per
+// parity.  Runs from the rest state and puts the rest state back.
+template <class T>
+om_status flow_tune_t(om_flow* fl, cudaStream_t s) {
+  if (fl->ns->nf == 0) return OM_OK;
+  FlowArgs<T> a = flow_args<T>(fl);
+  const unsigned nb = blocks_for(a.nf);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
+  float best[2] = {1e30f, 1e30f};
+  for (int v = 0; v < kSweepVariants; ++v) {
+    float tot[2] = {0.f, 0.f};
+    for (int r = 0; r < 7; ++r) {
+      OM_CUDA(cudaEventRecord(ev[0], s));
+      launch_sweep<T>(false, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[1], s));
+      launch_sweep<T>(true, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[2], s));
+      OM_CUDA(cudaEventSynchronize(ev[2]));
+      if (r == 0) continue;  // warm-up pair
+      float m0 = 0.f, m1 = 0.f;
+      OM_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
+      OM_CUDA(cudaEventElapsedTime(&m1, ev[1], ev[2]));
+      tot[0] += m0;
+      tot[1] += m1;
+    }
+    for (int p = 0; p < 2; ++p)
+      if (tot[p] < best[p]) {
+        best[p] = tot[p];
+        fl->var[p] = v;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  d3q19_rest<T><<<nb, 256, 0, s>>>(a);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
@@ -337,8 +391,8 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   om_flow* fl = new om_flow();
   fl->ns = ns;
   fl->p = *p;
-  // reduced storage keeps deviations scaled by 2^-inv_exp (see lattice.cuh)
-  fl->inv = p->precision == OM_F16DEV ? 1.0 / 1024.0 : 1.0;
+  // FP16 storage keeps deviations scaled by 2^10 so they stay normal numbers
+  fl->up = p->precision == OM_F16DEV ? 1024.0 : 1.0;
   DevBuf<uint8_t> f;
   DevBuf<double> prev, part, obs;
   om_status st = f.alloc(19 * (size_t)ns->pitch * storage_bytes(p->precision));
@@ -360,7 +414,10 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   fl->obs_dev = obs.take();
   fl->obs_host = host;
   auto rest = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_rest_t, fl, s); };
+  auto tune = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_tune_t, fl, s); };
+  if (p->variant >= 0) fl->var[0] = fl->var[1] = std::min(p->variant, kSweepVariants - 1);
   st = rest();
+  if (st == OM_OK && p->variant < 0) st = tune();
   if (st == OM_OK) {
     double o[4];
     st = flow_observe_any(fl, o, s);  // prev <- u_x of the rest state

@@ -11,8 +11,8 @@ namespace om {
 
 // Population storage.  Values are stored as deviations from a reference
 // state (w_i for flow, a_i C_lin(x) for diffusion).  Reduced-precision
-// storage also multiplies by a power-of-two scale so the deviations sit in
-// the normal range of the format.
+// storage also multiplies by a power-of-two scale (`up` on store, `down` on
+// load) so the deviations sit in the normal range of the format.
 template <class T>
 struct Stg;
 
@@ -31,24 +31,26 @@ struct Stg<float> {
 template <>
 struct Stg<__half> {
   using C = float;
-  __device__ __forceinline__ static C ld(const __half* p, C inv) { return __half2float(*p) * inv; }
-  __device__ __forceinline__ static void st(__half* p, C v, C inv) { *p = __float2half_rn(v / inv); }
+  __device__ __forceinline__ static C ld(const __half* p, C down) { return __half2float(*p) * down; }
+  __device__ __forceinline__ static void st(__half* p, C v, C up) { *p = __float2half_rn(v * up); }
 };
 template <>
 struct Stg<__nv_bfloat16> {
   using C = float;
-  __device__ __forceinline__ static C ld(const __nv_bfloat16* p, C inv) {
-    return __bfloat162float(*p) * inv;
+  __device__ __forceinline__ static C ld(const __nv_bfloat16* p, C down) {
+    return __bfloat162float(*p) * down;
   }
-  __device__ __forceinline__ static void st(__nv_bfloat16* p, C v, C inv) {
-    *p = __float2bfloat16_rn(v / inv);
+  __device__ __forceinline__ static void st(__nv_bfloat16* p, C v, C up) {
+    *p = __float2bfloat16_rn(v * up);
   }
 };
 
 // Node number of voxel (x, y, z) from its column's bit map, or kNoNode.
+// Column-map indices fit 32 bits (nx*ny*W <= 1024*2048*64).
 __device__ __forceinline__ uint32_t node_at(const uint2* __restrict__ col, int ny, int W, int x,
                                             int y, int z) {
-  const uint2 b = __ldg(col + ((int64_t)x * ny + y) * W + (z >> 5));
+  const uint32_t k = ((uint32_t)x * (uint32_t)ny + (uint32_t)y) * (uint32_t)W + ((uint32_t)z >> 5);
+  const uint2 b = __ldg(col + k);
   const uint32_t bit = 1u << (z & 31);
   return (b.x & bit) ? b.y + __popc(b.x & (bit - 1u)) : kNoNode;
 }
