@@ -128,6 +128,21 @@ om_status om_label_connectivity(const uint8_t* mask, om_domain d, int32_t* label
                                 uint8_t* transport, double* connectivity_out);
 om_status om_label_connectivity_dev(const uint8_t* mask_dev, om_domain d, int32_t* labels_dev,
                                     uint8_t* transport_dev, double* connectivity_out, void* stream);
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory -- a process whose GPU memory is held by
+ * another allocator (a framework's caching pool), or a service that fixes its
+ * memory plan at start-up and cannot take cudaMalloc/cudaFree (and their
+ * device-wide synchronisation and failure modes) later on.
+ * Same results as om_label_connectivity_dev; it calls no cudaMalloc,
+ * cudaFree or allocating routine.  labels_dev (int32 N) is required;
+ * transport_dev nullable; device buffers owned by the caller.  Its scratch
+ * is a static device array of 4 MiB + 256 B that every GPU loading the
+ * library holds until exit, which limits the box to 2^24 voxels (larger ->
+ * OM_EINVAL).  The first call on a device (with it current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race. */
+om_status om_label_connectivity_noalloc(const uint8_t* mask_dev, om_domain d, int32_t* labels_dev,
+                                        uint8_t* transport_dev, double* connectivity_out, void* stream);
 
 /* Local pore diameter in nm, 0 in solid.
  * mode OM_PORE_CHORD13 (Sec. 4.1): mean over 3 axis, 6 face-diagonal and 4

@@ -73,6 +73,7 @@ _SIGS = {
     "om_reconstruct_dev": [C.c_uint64, om_domain, C.POINTER(om_recon_params), _vp, _f64p, _i64p, _vp],
     "om_label_connectivity": [_vp, om_domain, _vp, _vp, _f64p],
     "om_label_connectivity_dev": [_vp, om_domain, _vp, _vp, _f64p, _vp],
+    "om_label_connectivity_noalloc": [_vp, om_domain, _vp, _vp, _f64p, _vp],
     "om_local_pore_diameter": [_vp, om_domain, C.c_int32, _vp, _vp],
     "om_local_pore_diameter_dev": [_vp, om_domain, C.c_int32, _vp, _vp, _vp],
     "om_solve_permeability": [_vp, om_domain, C.POINTER(om_flow_params), _f64p, _f64p,
@@ -212,6 +213,21 @@ def om_label_connectivity(mask, dom=None):
 def om_label_connectivity_dev(mask_dev, dom, labels_dev=None, transport_dev=None, stream=None):
     conn = C.c_double()
     _call("om_label_connectivity_dev", _ptr(mask_dev), dom, _ptr(labels_dev), _ptr(transport_dev),
+          C.byref(conn), _stream(stream))
+    return conn.value
+
+
+def om_label_connectivity_noalloc(mask_dev, dom, labels_dev, transport_dev=None, stream=None):
+    """om_label_connectivity_dev without any device allocation.
+
+    For callers that cannot allocate device memory: their GPU memory is
+    already held by another allocator (a framework's caching pool), or their
+    memory plan is fixed at start-up and cudaMalloc/cudaFree (with their
+    device-wide synchronisation) are not allowed later.  The scratch is a
+    static 4 MiB device array, so boxes are limited to 2^24 voxels; calls
+    that overlap on the GPU race on it.  labels_dev is required."""
+    conn = C.c_double()
+    _call("om_label_connectivity_noalloc", _ptr(mask_dev), dom, _ptr(labels_dev), _ptr(transport_dev),
           C.byref(conn), _stream(stream))
     return conn.value
 

@@ -142,6 +142,15 @@ om_status label_impl(const uint8_t* mask_dev, const om_domain& d, int* labels_de
   return OM_OK;
 }
 
+// Union-find labelling alone (labels_dev: int32 N, written), for callers
+// that bring their own flag storage.
+void launch_union_find(const uint8_t* mask_dev, const om_domain& d, int* labels_dev, cudaStream_t s) {
+  const int64_t N = voxels(d);
+  uf_init<<<1216, 256, 0, s>>>(mask_dev, N, labels_dev);
+  uf_link<<<1216, 256, 0, s>>>(mask_dev, d.nx, d.ny, d.nz, labels_dev);
+  uf_flatten<<<1216, 256, 0, s>>>(labels_dev, N);
+}
+
 }  // namespace om
 
 using namespace om;
