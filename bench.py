@@ -47,11 +47,32 @@ def _args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--edge", type=int, default=256, help="structure edge (default: the 256^3 sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "converge"],
+                    help="converge: time to converged k and D_eff, plain vs batched + FP16 + warm start")
+    ap.add_argument("--n-eval", type=int, default=24, help="converge mode: structures solved")
+    ap.add_argument("--n-train", type=int, default=48, help="converge mode: training structures")
+    ap.add_argument("--epochs", type=int, default=30, help="converge mode: U-Net epochs")
     return ap.parse_args()
 
 
 def _workload(edge, rank):
+    """Weak scaling: every rank solves its own four sweep structures (seeds
+    offset by rank); no data crosses ranks."""
     return [S.sweep_structure(e, seed=1 + 1000 * rank, edge=edge) for e in S.SWEEP_POROSITIES]
+
+
+def job_totals(updates, ms, world, device):
+    """Whole-job figures: lattice updates summed over ranks, time the
+    slowest rank's.  The only collective of the benchmark."""
+    if world == 1:
+        return float(updates), float(ms)
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
 
 
 def _workload_name(edge):
@@ -255,12 +276,9 @@ def run_gpu(a):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     ck = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     updates = 2 * WINDOW * sum(nodes) * a.steps  # both models
-    total_updates = updates * world
+    total_updates, ms = job_totals(updates, ms, world, "cuda")
+    flow_updates, _ = job_totals(WINDOW * sum(nodes) * a.steps, 0.0, world, "cuda")
     value = total_updates / (ms * 1e-3) / 1e6
 
     # dominant kernel: D3Q19 sweep, algorithmic bytes per launch / event time
@@ -291,11 +309,8 @@ def run_gpu(a):
             st, D, tau, info, _ = P.om_solve_knudsen(m, d, dom, dp)
             e2e_updates += info.n_nodes * info.steps
     te = time.perf_counter() - te
-    if world > 1:
-        t = torch.tensor([te], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
-    e2e = {"value": e2e_updates * world / te / 1e6, "unit": UNIT,
+    e2e_updates, te = job_totals(e2e_updates, te, world, "cuda")
+    e2e = {"value": e2e_updates / te / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": int(sum(2 * m.nbytes + d.nbytes for _, m, d in host_inputs)),
            "d2h_bytes_per_step": int(len(host_inputs) * 2 * (2 * 8 + 48))}
 
@@ -307,7 +322,7 @@ def run_gpu(a):
                        "layout": "fluid-node SoA, AA pattern, rank-indexed neighbours",
                        "l2": f"no flush: populations {sum(nodes) * 4 * 26 / 1e9:.2f} GB per step > 129 MB L2",
                        "setup_s": t_setup},
-            "flow_mlups": WINDOW * sum(nodes) * a.steps * world / (flow_ms * 1e-3) / 1e6,
+            "flow_mlups": flow_updates / (flow_ms * 1e-3) / 1e6,
             "roofline": roofline, "clocks": ck, "e2e": e2e,
             "gpu_launches": a.steps * len(solvers) * 2 * (WINDOW + 2)}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -333,6 +348,94 @@ def run_gpu(a):
     return 0
 
 
+# ------------------------------------------------------------------ time to converged results
+def _converge_set(n, seed, edges):
+    """Structures drawn like the 150-structure set (porosity, <d>, tolerance,
+    1.5 nm voxels), with box edges restricted to `edges`."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        mean = float(rng.uniform(10.0, 60.0))
+        sd = 0.25 * mean
+        out.append(S.Recon(seed * 1000 + i, (int(rng.choice(edges)),) * 3, 1.5, mean, sd, max(3.0, mean - 3 * sd),
+                           mean + 3 * sd, float(rng.uniform(0.25, 0.50)), float(rng.uniform(0.0, 0.8))))
+    return out
+
+
+def run_converge(a):
+    """Wall time to converged k and D_eff for a set of structures: plain
+    (one FP32 cold solve per structure and model) against the batched path
+    with 16-bit diffusion storage and a U-Net warm start (network inference
+    included).  Both stop on the same test: relative change below 1e-5 over
+    1000 steps.  Training data are cold FP32 solves of other structures."""
+    import torch
+
+    from paper_1410_1921_gb300 import build as B
+    B.build()
+    import paper_1410_1921_gb300 as P
+    from paper_1410_1921_gb300 import warmstart as W
+
+    torch.cuda.set_device(0)
+    K, tol = 1000, 1e-5
+    fp = P.flow_params(precision=P.OM_F32, conv_tol=tol, check_every=K)
+    dp = P.diff_params(precision=P.OM_F32, conv_tol=tol, check_every=K)
+    t0 = time.perf_counter()
+    data = W.make_dataset(_converge_set(a.n_train, 11, (64,)), fp, dp)
+    t_data = time.perf_counter() - t0
+    net = P.UNet(2, 2, (16, 32, 64, 128), seed=5)
+    t0 = time.perf_counter()
+    hist = W.train(net, data, epochs=a.epochs, lr=2e-3, lr_end=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    structs = []
+    for cfg in _converge_set(a.n_eval, 23, (64, 96)):
+        dom, mask, tr, d = W.structure(cfg)
+        if int(tr.sum().item()) > 0:
+            structs.append((cfg, dom, mask, tr, d))
+    # plain: each structure and model solved on its own, cold, FP32
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [W.solve(dom, tr, d, fp, dp) for _, dom, mask, tr, d in structs]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    # fast: batch (FP32 flow, FP16 diffusion) warm-started from the network
+    fp16 = P.diff_params(precision=P.OM_F16DEV, conv_tol=tol, check_every=K)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = P.Batch([s[1] for s in structs], [s[3] for s in structs], [s[4] for s in structs], flow=fp, diff=fp16)
+    for k, (_, dom, mask, tr, d) in enumerate(structs):
+        y = W.predict(net, mask, d, dom)
+        b.init_fields(0, k, y, stride=2, scale=W.velocity_scale(fp))
+        b.init_fields(1, k, y[1:], stride=2, from_linear=True)
+    kl, _, info_f, st_f = b.solve(0)
+    dl, _, info_d, st_d = b.solve(1)
+    torch.cuda.synchronize()
+    t_fast = time.perf_counter() - t0
+    b.close()
+    dk = max(abs(kl[i] - plain[i]["k_lattice"]) / abs(plain[i]["k_lattice"]) for i in range(len(structs)))
+    dD = max(abs(dl[i] - plain[i]["D_lattice"]) / abs(plain[i]["D_lattice"]) for i in range(len(structs)))
+    line = {"metric": "time to converged k, D_eff: plain / (batched + FP16 diffusion + U-Net warm start)",
+            "value": t_plain / t_fast, "unit": "x", "higher_is_better": True, "n_gpus": 1,
+            "plain_s": t_plain, "fast_s": t_fast, "structures": len(structs),
+            "max_rel_diff_k": dk, "max_rel_diff_D_eff": dD,
+            "plain_steps": {"flow": int(sum(p["flow_steps"] for p in plain)),
+                            "diffusion": int(sum(p["diff_steps"] for p in plain))},
+            "fast_steps": {"flow": int(sum(i.steps for i in info_f)), "diffusion": int(sum(i.steps for i in info_d))},
+            "status_ok": bool((st_f == 0).all() and (st_d == 0).all()
+                              and all(p["flow_status"] == 0 and p["diff_status"] == 0 for p in plain)),
+            "training": {"samples": len(data), "epochs": a.epochs, "data_s": t_data, "train_s": t_train,
+                         "loss_first": hist[0], "loss_last": hist[-1]},
+            "config": {"workload": "structures drawn like the 150-structure set (1.5 nm voxels, porosity "
+                                   "U[0.25,0.5], <d> U[10,60] nm, sd <d>/4, tolerance U[0,0.8]), edges {64,96}; "
+                                   "test: relative change < 1e-5 over 1000 steps; U-Net 16-32-64-128 trained on "
+                                   "64^3 structures of the same law",
+                       "data": "synthetic"}}
+    print(json.dumps(line))
+    return 0
+
+
 if __name__ == "__main__":
     args = _args()
+    if args.mode == "converge":
+        sys.exit(run_converge(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_gpu(args))

@@ -242,6 +242,92 @@ om_status om_diff_get_fields(const om_diff* df, float* c_dev, float* jx_dev, voi
 om_status om_diff_time(const om_diff* df, int64_t* t);
 om_status om_diff_destroy(om_diff* df);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent structures (the paper's 150 reconstructions) solved
+ * together: one persistent launch per LB step advances every structure not
+ * yet converged, a check window is replayed from a captured CUDA graph, and
+ * each structure leaves the work list when it converges.  Launch shapes are
+ * timed at creation.  Both models share the parameters given; pass NULL for a
+ * model that is not needed (d_nm_dev may then be NULL too).
+ * nodes_dev[k]: uint8 N_k node mask (normally the transport set) of
+ * doms[k]; d_nm_dev[k]: float N_k pore sizes (nm).  All device pointers. */
+typedef struct om_batch om_batch;
+om_status om_batch_create(int32_t n, const om_domain* doms, const uint8_t* const* nodes_dev,
+                          const float* const* d_nm_dev, const om_flow_params* flow,
+                          const om_diff_params* diff, void* stream, om_batch** out);
+/* model 0 = flow, 1 = diffusion */
+om_status om_batch_step(om_batch* b, int32_t model, int64_t nsteps, void* stream);
+/* Run every structure of the model to its convergence test (as om_flow_solve
+ * / om_diff_solve) from the current state.  Host arrays of n entries:
+ * result = k_lattice (flow) or D_eff,L (diffusion); aux (nullable) = sum of
+ * (rho - 1) (flow) or the mean lattice diffusivity over nodes (diffusion);
+ * info (nullable; seconds and mlups are those of the whole batch); status
+ * (nullable) = OM_OK, OM_ENOTCONVERGED or OM_ENOPERC (no nodes) per
+ * structure.  Returns OM_OK unless a call fails. */
+om_status om_batch_solve(om_batch* b, int32_t model, double* result, double* aux, om_run_info* info,
+                         int32_t* status, void* stream);
+/* populations of structure `item` in the dense layout of om_flow_get_populations /
+ * om_diff_get_populations (double q*N_k, device) */
+om_status om_batch_get_populations(om_batch* b, int32_t model, int32_t item, double* dense_dev,
+                                   void* stream);
+om_status om_batch_set_populations(om_batch* b, int32_t model, int32_t item,
+                                   const double* dense_dev, void* stream);
+/* back to the initial state (rest / linear profile) at time 0 */
+om_status om_batch_reset(om_batch* b, int32_t model, void* stream);
+/* warm start of structure `item` from a device field in its voxel layout,
+ * element v at field[v * stride]: flow f = f_eq(1, (scale * field, 0, 0));
+ * diffusion g = a_i C, C = field (+ C_lin(x) when from_linear != 0).  The
+ * batch must be at an even time (after create, reset or a solve). */
+om_status om_batch_init_fields(om_batch* b, int32_t model, int32_t item, const float* field_dev,
+                               int64_t stride, double scale, int32_t from_linear, void* stream);
+om_status om_batch_destroy(om_batch* b);
+
+/* ---------------------------------------------------------------- learned warm start
+ * A 3-D U-Net predicting the steady fields from the structure, trained on
+ * fields the LB solves produce (the paper has no counterpart: its solves
+ * start cold; the LB still runs to the same convergence test afterwards).
+ * `levels` levels with channels ch[0..levels-1] (multiples of 16), two
+ * 3x3x3 convolutions + ReLU per level, 2x average pooling down, nearest 2x
+ * upsampling and skip concatenation up, a 1x1 head.  BF16 tensor-core
+ * convolutions with FP32 accumulation; FP32 master weights and Adam.
+ * Tensors are FP32 NDHWC on the device: x [B][D][H][W][in_ch] (in_ch <= 16),
+ * targets/outputs [B][D][H][W][out_ch], mask [B][D][H][W] (loss over
+ * voxels with mask != 0).  D, H, W must be multiples of 2^(levels-1).
+ * Parameters are one flat FP32 vector: per level (encoder, then decoder from
+ * the bottom) W[27][c_in][c_out] and b[c_out], then the head W[c0][out], b. */
+typedef struct om_unet om_unet;
+om_status om_unet_create(int32_t in_ch, int32_t out_ch, int32_t levels, const int32_t* ch, uint64_t seed,
+                         om_unet** out);
+om_status om_unet_param_count(const om_unet* u, int64_t* n);
+om_status om_unet_get_params(const om_unet* u, float* dst_dev, void* stream);
+om_status om_unet_set_params(om_unet* u, const float* src_dev, void* stream);
+/* gradients of the last om_unet_backward / om_unet_train_step */
+om_status om_unet_get_grads(const om_unet* u, float* dst_dev, void* stream);
+om_status om_unet_forward(om_unet* u, const float* x, int32_t B, int32_t D, int32_t H, int32_t W, float* y,
+                          void* stream);
+/* forward + masked mean-squared error + gradients (no update); loss_out host */
+om_status om_unet_backward(om_unet* u, const float* x, const float* target, const uint8_t* mask, int32_t B,
+                           int32_t D, int32_t H, int32_t W, double* loss_out, void* stream);
+/* om_unet_backward then one Adam step (beta 0.9 / 0.999, eps 1e-8) */
+om_status om_unet_train_step(om_unet* u, const float* x, const float* target, const uint8_t* mask, int32_t B,
+                             int32_t D, int32_t H, int32_t W, float lr, double* loss_out, void* stream);
+om_status om_unet_destroy(om_unet* u);
+
+/* U-Net input from a structure: x[v][0] = mask != 0, x[v][1] = d_nm[v] *
+ * d_scale (float [N][2], device). */
+om_status om_unet_pack_structure(const uint8_t* mask_dev, const float* d_nm_dev, int64_t n, double d_scale,
+                                 float* x_dev, void* stream);
+
+/* Warm starts for the solver objects from a device field in the voxel layout
+ * read with a stride (element v at field[v * stride]); values off the node
+ * set are ignored and the time is reset to 0.
+ * flow: f_i = f_eq(rho = 1, u = (scale * field, 0, 0));
+ * diffusion: g_i = a_i C with C = field, or C = C_lin(x) + field when
+ * from_linear != 0. */
+om_status om_flow_init_velocity(om_flow* fl, const float* ux_dev, int64_t stride, double scale, void* stream);
+om_status om_diff_init_concentration(om_diff* df, const float* c_dev, int64_t stride, int32_t from_linear,
+                                     void* stream);
+
 /* ---------------------------------------------------------------- misc */
 const char* om_last_error(void);
 /* library version string */

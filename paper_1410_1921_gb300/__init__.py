@@ -103,6 +103,28 @@ _SIGS = {
     "om_diff_get_fields": [_vp, _vp, _vp, _vp],
     "om_diff_time": [_vp, _i64p],
     "om_diff_destroy": [_vp],
+    "om_batch_create": [C.c_int32, C.POINTER(om_domain), C.POINTER(_vp), C.POINTER(_vp),
+                        C.POINTER(om_flow_params), C.POINTER(om_diff_params), _vp, C.POINTER(_vp)],
+    "om_batch_step": [_vp, C.c_int32, C.c_int64, _vp],
+    "om_batch_solve": [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp],
+    "om_batch_get_populations": [_vp, C.c_int32, C.c_int32, _vp, _vp],
+    "om_batch_set_populations": [_vp, C.c_int32, C.c_int32, _vp, _vp],
+    "om_batch_reset": [_vp, C.c_int32, _vp],
+    "om_batch_init_fields": [_vp, C.c_int32, C.c_int32, _vp, C.c_int64, C.c_double, C.c_int32, _vp],
+    "om_batch_destroy": [_vp],
+    "om_unet_create": [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_uint64, C.POINTER(_vp)],
+    "om_unet_param_count": [_vp, _i64p],
+    "om_unet_get_params": [_vp, _vp, _vp],
+    "om_unet_set_params": [_vp, _vp, _vp],
+    "om_unet_get_grads": [_vp, _vp, _vp],
+    "om_unet_forward": [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _vp, _vp],
+    "om_unet_backward": [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _f64p, _vp],
+    "om_unet_train_step": [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_float, _f64p,
+                           _vp],
+    "om_unet_destroy": [_vp],
+    "om_unet_pack_structure": [_vp, _vp, C.c_int64, C.c_double, _vp, _vp],
+    "om_flow_init_velocity": [_vp, _vp, C.c_int64, C.c_double, _vp],
+    "om_diff_init_concentration": [_vp, _vp, C.c_int64, C.c_int32, _vp],
 }
 
 _lib = None
@@ -337,6 +359,9 @@ class Flow:
     def get_velocity(self, out_dev, stream=None):
         _call("om_flow_get_velocity", self.h, _ptr(out_dev), _stream(stream))
 
+    def init_velocity(self, ux_dev, stride=1, scale=1.0, stream=None):
+        _call("om_flow_init_velocity", self.h, _ptr(ux_dev), stride, scale, _stream(stream))
+
     @property
     def time(self):
         t = C.c_int64()
@@ -387,6 +412,9 @@ class Diffusion:
     def get_fields(self, c_dev=None, jx_dev=None, stream=None):
         _call("om_diff_get_fields", self.h, _ptr(c_dev), _ptr(jx_dev), _stream(stream))
 
+    def init_concentration(self, c_dev, stride=1, from_linear=False, stream=None):
+        _call("om_diff_init_concentration", self.h, _ptr(c_dev), stride, int(from_linear), _stream(stream))
+
     @property
     def time(self):
         t = C.c_int64()
@@ -396,6 +424,117 @@ class Diffusion:
     def close(self):
         if self.h:
             lib().om_diff_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """om_batch: many structures solved together (om_batch_*).  nodes: list of
+    device uint8 node masks; d_nm: list of device float pore sizes (or None);
+    doms: list of om_domain."""
+
+    def __init__(self, doms, nodes, d_nm=None, flow=None, diff=None, stream=None):
+        n = len(doms)
+        self.n = n
+        self._keep = (list(nodes), list(d_nm) if d_nm is not None else None)
+        darr = (om_domain * n)(*doms)
+        narr = (C.c_void_p * n)(*[_ptr(t) for t in nodes])
+        parr = (C.c_void_p * n)(*[_ptr(t) for t in d_nm]) if d_nm is not None else None
+        self.h = C.c_void_p()
+        _call("om_batch_create", n, darr, narr, parr, C.byref(flow) if flow is not None else None,
+              C.byref(diff) if diff is not None else None, _stream(stream), C.byref(self.h))
+
+    def step(self, model, n, stream=None):
+        _call("om_batch_step", self.h, model, n, _stream(stream))
+
+    def solve(self, model, stream=None):
+        res = np.zeros(self.n)
+        aux = np.zeros(self.n)
+        info = (om_run_info * self.n)()
+        st = np.zeros(self.n, np.int32)
+        _call("om_batch_solve", self.h, model, _ptr(res), _ptr(aux), info, _ptr(st), _stream(stream))
+        return res, aux, list(info), st
+
+    def get_populations(self, model, item, out_dev, stream=None):
+        _call("om_batch_get_populations", self.h, model, item, _ptr(out_dev), _stream(stream))
+
+    def set_populations(self, model, item, f_dev, stream=None):
+        _call("om_batch_set_populations", self.h, model, item, _ptr(f_dev), _stream(stream))
+
+    def reset(self, model, stream=None):
+        _call("om_batch_reset", self.h, model, _stream(stream))
+
+    def init_fields(self, model, item, field_dev, stride=1, scale=1.0, from_linear=False, stream=None):
+        _call("om_batch_init_fields", self.h, model, item, _ptr(field_dev), stride, scale, int(from_linear),
+              _stream(stream))
+
+    def close(self):
+        if self.h:
+            lib().om_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def om_unet_pack_structure(mask_dev, d_nm_dev, d_scale, x_dev, stream=None):
+    _call("om_unet_pack_structure", _ptr(mask_dev), _ptr(d_nm_dev), mask_dev.numel(), d_scale, _ptr(x_dev),
+          _stream(stream))
+
+
+class UNet:
+    """om_unet: the warm-start network (om_unet_*).  Tensors are contiguous
+    float32 CUDA tensors in NDHWC layout."""
+
+    def __init__(self, in_ch, out_ch, channels=(16, 32, 64, 128), seed=1):
+        arr = (C.c_int32 * len(channels))(*channels)
+        self.h = C.c_void_p()
+        self.in_ch, self.out_ch = in_ch, out_ch
+        _call("om_unet_create", in_ch, out_ch, len(channels), arr, seed, C.byref(self.h))
+
+    @property
+    def n_params(self):
+        n = C.c_int64()
+        _call("om_unet_param_count", self.h, C.byref(n))
+        return n.value
+
+    def get_params(self, out_dev, stream=None):
+        _call("om_unet_get_params", self.h, _ptr(out_dev), _stream(stream))
+
+    def set_params(self, src_dev, stream=None):
+        _call("om_unet_set_params", self.h, _ptr(src_dev), _stream(stream))
+
+    def get_grads(self, out_dev, stream=None):
+        _call("om_unet_get_grads", self.h, _ptr(out_dev), _stream(stream))
+
+    def forward(self, x, y, stream=None):
+        B, D, H, W = x.shape[:4]
+        _call("om_unet_forward", self.h, _ptr(x), B, D, H, W, _ptr(y), _stream(stream))
+
+    def backward(self, x, t, m, stream=None):
+        B, D, H, W = x.shape[:4]
+        loss = C.c_double()
+        _call("om_unet_backward", self.h, _ptr(x), _ptr(t), _ptr(m), B, D, H, W, C.byref(loss), _stream(stream))
+        return loss.value
+
+    def train_step(self, x, t, m, lr, stream=None):
+        B, D, H, W = x.shape[:4]
+        loss = C.c_double()
+        _call("om_unet_train_step", self.h, _ptr(x), _ptr(t), _ptr(m), B, D, H, W, lr, C.byref(loss),
+              _stream(stream))
+        return loss.value
+
+    def close(self):
+        if self.h:
+            lib().om_unet_destroy(self.h)
             self.h = C.c_void_p()
 
     def __del__(self):

@@ -1,0 +1,929 @@
+// batch.cu -- many reconstructed structures of uneven size solved together.
+//
+// All structures of a batch share one population arena per model: structure
+// k owns the global node numbers [off_k, off_k + nf_k), and its column map is
+// rebased so neighbour lookups return global numbers directly.  A work list of
+// 256-node tiles (structure, first local node) drives persistent kernels: a
+// fixed grid of CTAs strides over the list, so one launch advances every
+// active structure by one LB step whatever their sizes, and a converged
+// structure simply leaves the list.  A check window of K steps is captured
+// once into a CUDA graph and replayed; the work list and its length live in
+// device memory, so retiring structures never invalidates the graph.
+//
+// Per-structure observables come from per-tile FP64 partial sums reduced in
+// tile order (deterministic).  Launch shapes (residency cap, CTAs per SM) are
+// picked per parity by timing them on the batch itself.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "diff_core.cuh"
+#include "flow_core.cuh"
+
+namespace om {
+
+struct BatchItem {
+  const uint2* col;       // rebased column map (global node numbers)
+  const uint32_t* coord;  // structure-local packed coordinates
+  uint32_t off, nf;
+  int nx, ny, nz, W;
+  double slope;  // diffusion: (c_out - c_in) / nx
+};
+
+constexpr int kTile = 256;
+
+__global__ void rebase_columns(uint2* col, int64_t nw, uint32_t off) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (int64_t)gridDim.x * blockDim.x)
+    col[k].y += off;
+}
+
+// ------------------------------------------------------------------ sweeps
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(kTile, MINB)
+    flow_batch_sweep(FlowArgs<T> a, const BatchItem* __restrict__ items, const uint2* __restrict__ work,
+                     const int* __restrict__ nwork) {
+  const int nw = *nwork;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const uint2 t = work[w];
+    const BatchItem& it = items[t.x];
+    const uint32_t ln = t.y + threadIdx.x;
+    if (ln >= it.nf) continue;
+    if (ODD) {
+      FlowArgs<T> b = a;
+      b.col = it.col;
+      b.coord = it.coord;
+      b.nx = it.nx;
+      b.ny = it.ny;
+      b.nz = it.nz;
+      b.W = it.W;
+      flow_node<T, true>(b, it.off + ln, ln);
+    } else {
+      flow_node<T, false>(a, it.off + ln, ln);
+    }
+  }
+}
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(kTile, MINB)
+    diff_batch_sweep(DiffArgs<T> a, const BatchItem* __restrict__ items, const uint2* __restrict__ work,
+                     const int* __restrict__ nwork) {
+  const int nw = *nwork;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const uint2 t = work[w];
+    const BatchItem& it = items[t.x];
+    const uint32_t ln = t.y + threadIdx.x;
+    if (ln >= it.nf) continue;
+    DiffArgs<T> b = a;
+    b.nx = it.nx;
+    b.s = (typename Stg<T>::C)it.slope;
+    if (ODD) {
+      b.col = it.col;
+      b.coord = it.coord;
+      b.ny = it.ny;
+      b.nz = it.nz;
+      b.W = it.W;
+    }
+    diff_node<T, ODD>(b, it.off + ln, ln);
+  }
+}
+
+// ------------------------------------------------------------------ observables
+// partials[w][NV] for every tile w of the work list
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kTile) flow_batch_observe(FlowArgs<T> a, const BatchItem* items, const uint2* work,
+                                                            const int* nwork, double* prev, double* partials) {
+  using C = typename Stg<T>::C;
+  const int nw = *nwork;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const uint2 t = work[w];
+    const BatchItem& it = items[t.x];
+    const uint32_t ln = t.y + threadIdx.x;
+    double acc[4] = {0, 0, 0, 0};
+    if (ln < it.nf) {
+      FlowArgs<T> b = a;
+      b.col = it.col;
+      b.coord = it.coord;
+      b.nx = it.nx;
+      b.ny = it.ny;
+      b.nz = it.nz;
+      b.W = it.W;
+      const uint32_t n = it.off + ln;
+      uint32_t nb[19];
+      if (ODD) flow_neighbours(b, b.coord[ln], nb);
+      C f[19];
+      flow_load<T, ODD>(b, n, nb, f);
+      double rho = 0, jx = 0;
+#pragma unroll
+      for (int i = 0; i < 19; ++i) {
+        rho += (double)f[i];
+        jx += (double)q19_e(i, 0) * (double)f[i];
+      }
+      const double ux = jx + 0.5 * (double)a.g;
+      acc[0] = ux;
+      acc[1] = fabs(ux - prev[n]);
+      acc[2] = fabs(ux);
+      acc[3] = rho;
+      prev[n] = ux;
+    }
+    block_reduce_write<4>(acc, partials + (int64_t)w * 4);
+  }
+}
+
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kTile) diff_batch_observe(DiffArgs<T> a, const BatchItem* items, const uint2* work,
+                                                            const int* nwork, double* prev, double* partials) {
+  using C = typename Stg<T>::C;
+  const int nw = *nwork;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const uint2 t = work[w];
+    const BatchItem& it = items[t.x];
+    const uint32_t ln = t.y + threadIdx.x;
+    double acc[5] = {0, 0, 0, 0, 0};
+    if (ln < it.nf) {
+      DiffArgs<T> b = a;
+      b.col = it.col;
+      b.coord = it.coord;
+      b.nx = it.nx;
+      b.ny = it.ny;
+      b.nz = it.nz;
+      b.W = it.W;
+      b.s = (typename Stg<T>::C)it.slope;
+      const uint32_t n = it.off + ln;
+      uint32_t nb[7];
+      int x, y, z;
+      unpack_xyz(b.coord[ln], x, y, z);
+      if (ODD) diff_neighbours(b, b.coord[ln], nb, x);
+      C g[7];
+      diff_load<T, ODD>(b, n, nb, x, g);
+      double dev = 0;
+#pragma unroll
+      for (int i = 0; i < 7; ++i) dev += (double)g[i];
+      const double c = dev + diff_ref(b, n, x);
+      const double om = (double)b.omega[n];
+      acc[0] = (1.0 - 0.5 * om) * ((double)g[1] - (double)g[2]);
+      acc[1] = fabs(c - prev[n]);
+      acc[2] = fabs(c);
+      acc[3] = c;
+      acc[4] = 0.25 * (1.0 / om - 0.5);
+      prev[n] = c;
+    }
+    block_reduce_write<5>(acc, partials + (int64_t)w * 5);
+  }
+}
+
+// out[k][NV] = sum of partials over the tiles [range[k].x, range[k].y), in order
+template <int NV>
+__global__ void batch_finalize(const double* partials, const int2* range, double* out) {
+  const int2 r = range[blockIdx.x];
+  __shared__ double sm[256];
+  for (int k = 0; k < NV; ++k) {
+    double acc = 0.0;
+    for (int w = r.x + threadIdx.x; w < r.y; w += blockDim.x) acc += partials[(int64_t)w * NV + k];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(int64_t)blockIdx.x * NV + k] = sm[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ set-up and exchange
+template <class C>
+__global__ void batch_omega(const int64_t* vox, const float* d_nm, uint32_t nf, double d_ref, double tau_ref, C* omega,
+                            int* bad) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nf) return;
+  const double tau = ((double)d_nm[vox[n]] / d_ref) * (tau_ref - 0.5) + 0.5;  // Eq. 12
+  if (!(tau > 0.5)) atomicExch(bad, 1);
+  omega[n] = (C)(1.0 / tau);
+}
+
+template <class T, bool ODD>
+__global__ void flow_batch_export(FlowArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, double* out) {
+  using C = typename Stg<T>::C;
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  uint32_t nb[19];
+  if (ODD) flow_neighbours(a, a.coord[ln], nb);
+  C f[19];
+  flow_load<T, ODD>(a, off + ln, nb, f);
+  const int64_t v = vox[ln];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) out[i * N + v] = (double)f[i] + q19_w(i);
+}
+
+template <class T, bool ODD>
+__global__ void diff_batch_export(DiffArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, double* out) {
+  using C = typename Stg<T>::C;
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  uint32_t nb[7];
+  int x, y, z;
+  unpack_xyz(a.coord[ln], x, y, z);
+  if (ODD) diff_neighbours(a, a.coord[ln], nb, x);
+  C g[7];
+  diff_load<T, ODD>(a, off + ln, nb, x, g);
+  const int64_t v = vox[ln];
+  const double cref = diff_ref(a, off + ln, x);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) out[i * N + v] = (double)g[i] + q7_w(i) * cref;
+}
+
+template <class T>
+__global__ void flow_batch_import(FlowArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, const double* in) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  const int64_t v = vox[ln];
+#pragma unroll
+  for (int i = 0; i < 19; ++i)
+    Stg<T>::st(a.s[i] + off + ln, (typename Stg<T>::C)(in[i * N + v] - q19_w(i)), a.up);
+}
+
+template <class T>
+__global__ void diff_batch_import(DiffArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, const double* in) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  const int64_t v = vox[ln];
+  int x, y, z;
+  unpack_xyz(a.coord[ln], x, y, z);
+  double cref = a.cin + (double)a.s * ((double)x + 0.5);
+  if constexpr (kRebased<T>) {
+    cref = 0.0;
+    for (int i = 0; i < 7; ++i) cref += in[i * N + v];
+    a.cr[off + ln] = (float)cref;
+    cref = (double)a.cr[off + ln];
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+    Stg<T>::st(a.q[i] + off + ln, (typename Stg<T>::C)(in[i * N + v] - q7_w(i) * cref), a.up);
+}
+
+// warm start of one structure: flow f = f_eq(1, (scale * field, 0, 0));
+// diffusion g = a_i C with C = field (+ C_lin(x) when from_linear)
+template <class T>
+__global__ void flow_batch_init(FlowArgs<T> a, uint32_t off, const int64_t* vox, const float* field, int64_t stride,
+                                double scale) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  const double u = scale * (double)field[vox[ln] * stride];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const double eu = (double)q19_e(i, 0) * u;
+    Stg<T>::st(a.s[i] + off + ln, (typename Stg<T>::C)(q19_w(i) * (3.0 * eu + 4.5 * eu * eu - 1.5 * u * u)), a.up);
+  }
+}
+
+template <class T>
+__global__ void diff_batch_init(DiffArgs<T> a, uint32_t off, const int64_t* vox, const float* field, int64_t stride,
+                                int from_linear) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  int x, y, z;
+  unpack_xyz(a.coord[ln], x, y, z);
+  const double clin = a.cin + (double)a.s * ((double)x + 0.5);
+  const double cv = (double)field[vox[ln] * stride] + (from_linear ? clin : 0.0);
+  double dc = cv - clin;
+  if constexpr (kRebased<T>) {
+    a.cr[off + ln] = (float)cv;
+    dc = 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Stg<T>::st(a.q[i] + off + ln, (typename Stg<T>::C)(q7_w(i) * dc), a.up);
+}
+
+// 16-bit diffusion: reference of every node of every structure set to C_lin(x)
+__global__ void batch_cr_linear(const BatchItem* items, const uint2* work, const int* nwork, double cin, float* cr) {
+  const int nw = *nwork;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const uint2 t = work[w];
+    const BatchItem& it = items[t.x];
+    const uint32_t ln = t.y + threadIdx.x;
+    if (ln >= it.nf) continue;
+    int x, y, z;
+    unpack_xyz(it.coord[ln], x, y, z);
+    cr[it.off + ln] = (float)(cin + it.slope * ((double)x + 0.5));
+  }
+}
+
+template <class T>
+__global__ void batch_rebase(DiffArgs<T> a) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < a.nf) diff_rebase_node<T>(a, n);
+}
+
+}  // namespace om
+
+using namespace om;
+
+namespace {
+
+size_t stg_bytes(int prec) { return prec == OM_F64 ? 8 : (prec == OM_F32 ? 4 : 2); }
+
+// One model's state inside a batch.
+struct Model {
+  bool on = false;
+  int prec = OM_F32;
+  int q = 0;             // populations per node
+  void* pop = nullptr;   // arena [q][pitch]
+  void* omega = nullptr; // diffusion only, compute type, [pitch]
+  float* cr = nullptr;   // diffusion with 16-bit storage: per-node reference concentration
+  double* prev = nullptr;
+  int64_t t = 0;
+  double up = 1.0;
+  int var[2] = {0, 0};   // launch variant per parity
+  int grid[2] = {152, 152};
+  cudaGraphExec_t exec = nullptr;
+  int graph_k = 0;
+};
+
+}  // namespace
+
+struct om_batch {
+  int n = 0;
+  std::vector<om_domain> dom;
+  std::vector<om_nodeset*> ns;
+  std::vector<BatchItem> items_h;
+  BatchItem* items = nullptr;
+  uint32_t total = 0;   // nodes
+  int64_t pitch = 0;
+  uint2* work = nullptr;      // device work list
+  int* nwork = nullptr;       // device count
+  uint2* work_h = nullptr;    // pinned staging
+  int2* range = nullptr;      // device per-active-item tile ranges
+  int2* range_h = nullptr;    // pinned
+  int* nwork_h = nullptr;     // pinned
+  int max_tiles = 0;
+  double* partials = nullptr; // [max_tiles][5]
+  double* obs = nullptr;      // [n][5]
+  double* obs_h = nullptr;    // pinned [n][5]
+  om_flow_params fp{};
+  om_diff_params dp{};
+  Model m[2];
+  cudaStream_t cap = nullptr;  // capture stream
+  int sms = 152;
+};
+
+namespace {
+
+// work list of all tiles of the items flagged active; ranges per active item
+int build_work(om_batch* b, const std::vector<int>& active) {
+  int w = 0;
+  for (size_t a = 0; a < active.size(); ++a) {
+    const int k = active[a];
+    const int w0 = w;
+    for (uint32_t s = 0; s < b->items_h[k].nf; s += kTile) b->work_h[w++] = make_uint2((unsigned)k, s);
+    b->range_h[a] = make_int2(w0, w);
+  }
+  *b->nwork_h = w;
+  return w;
+}
+
+om_status upload_work(om_batch* b, int nw, int nact, cudaStream_t s) {
+  if (nw > 0) OM_CUDA(cudaMemcpyAsync(b->work, b->work_h, sizeof(uint2) * nw, cudaMemcpyHostToDevice, s));
+  if (nact > 0) OM_CUDA(cudaMemcpyAsync(b->range, b->range_h, sizeof(int2) * nact, cudaMemcpyHostToDevice, s));
+  OM_CUDA(cudaMemcpyAsync(b->nwork, b->nwork_h, sizeof(int), cudaMemcpyHostToDevice, s));
+  return OM_OK;
+}
+
+template <class T>
+FlowArgs<T> bflow_args(const om_batch* b) {
+  FlowArgs<T> a{};
+  const Model& m = b->m[0];
+  for (int i = 0; i < 19; ++i) a.s[i] = (T*)m.pop + (size_t)i * b->pitch;
+  a.nf = b->total;
+  const double tau = b->fp.tau;
+  a.wp = (typename Stg<T>::C)(1.0 / tau);
+  a.wm = (typename Stg<T>::C)(8.0 * (2.0 * tau - 1.0) / (8.0 * tau - 1.0));
+  a.g = (typename Stg<T>::C)b->fp.body_force;
+  a.up = (typename Stg<T>::C)m.up;
+  a.down = (typename Stg<T>::C)(1.0 / m.up);
+  return a;
+}
+
+template <class T>
+DiffArgs<T> bdiff_args(const om_batch* b) {
+  DiffArgs<T> a{};
+  const Model& m = b->m[1];
+  for (int i = 0; i < 7; ++i) a.q[i] = (T*)m.pop + (size_t)i * b->pitch;
+  a.nf = b->total;
+  a.omega = (const typename Stg<T>::C*)m.omega;
+  a.up = (typename Stg<T>::C)m.up;
+  a.down = (typename Stg<T>::C)(1.0 / m.up);
+  a.cin = b->dp.c_in;
+  a.cout = b->dp.c_out;
+  a.cr = m.cr;
+  return a;
+}
+
+template <class T, int MINB>
+void launch_flow(const om_batch* b, bool odd, int grid, cudaStream_t s) {
+  FlowArgs<T> a = bflow_args<T>(b);
+  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
+  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
+}
+
+template <class T, int MINB>
+void launch_diff(const om_batch* b, bool odd, int grid, cudaStream_t s) {
+  DiffArgs<T> a = bdiff_args<T>(b);
+  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
+  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
+}
+
+// variant 0: no residency hint; variant 1: capped for 4 (flow; 3 in FP64) / 8
+// (diffusion) CTAs per SM
+template <class T>
+void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, cudaStream_t s) {
+  if (model == 0) {
+    if (variant == 0) launch_flow<T, 0>(b, odd, grid, s);
+    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, s);
+  } else {
+    if (variant == 0) launch_diff<T, 0>(b, odd, grid, s);
+    else launch_diff<T, 8>(b, odd, grid, s);
+  }
+}
+
+template <class T>
+om_status steps_t(om_batch* b, int model, int64_t n, cudaStream_t s) {
+  Model& m = b->m[model];
+  for (int64_t k = 0; k < n; ++k) {
+    const bool odd = m.t & 1;
+    launch_step<T>(b, model, odd, m.var[odd], m.grid[odd], s);
+    ++m.t;
+  }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status observe_t(om_batch* b, int model, int nact, cudaStream_t s) {
+  Model& m = b->m[model];
+  const int grid = b->sms * 4;
+  const int nv = model == 0 ? 4 : 5;
+  if (model == 0) {
+    FlowArgs<T> a = bflow_args<T>(b);
+    if (m.t & 1) flow_batch_observe<T, true><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials);
+    else flow_batch_observe<T, false><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials);
+    if (nact > 0) batch_finalize<4><<<nact, 256, 0, s>>>(b->partials, b->range, b->obs);
+  } else {
+    DiffArgs<T> a = bdiff_args<T>(b);
+    if (m.t & 1) diff_batch_observe<T, true><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials);
+    else diff_batch_observe<T, false><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials);
+    if (nact > 0) batch_finalize<5><<<nact, 256, 0, s>>>(b->partials, b->range, b->obs);
+  }
+  OM_CUDA(cudaGetLastError());
+  if (nact > 0)
+    OM_CUDA(cudaMemcpyAsync(b->obs_h, b->obs, sizeof(double) * nv * nact, cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  return OM_OK;
+}
+
+// Autotuner: for each parity, time (variant, CTAs per SM) shapes over 6
+// steps after a warm-up step and keep the fastest.  Steps run from the
+// initial state, which the caller restores afterwards.
+template <class T>
+om_status tune_t(om_batch* b, int model, cudaStream_t s) {
+  Model& m = b->m[model];
+  if (b->total == 0) return OM_OK;
+  const int shapes[4][2] = {{0, 2}, {0, 4}, {1, 4}, {1, 8}};  // {variant, CTAs per SM}
+  cudaEvent_t ev[3];
+  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
+  float best[2] = {1e30f, 1e30f};
+  for (const auto& sh : shapes) {
+    const int grid = sh[1] * b->sms;
+    float tot[2] = {0.f, 0.f};
+    for (int r = 0; r < 7; ++r) {
+      OM_CUDA(cudaEventRecord(ev[0], s));
+      launch_step<T>(b, model, false, sh[0], grid, s);
+      OM_CUDA(cudaEventRecord(ev[1], s));
+      launch_step<T>(b, model, true, sh[0], grid, s);
+      OM_CUDA(cudaEventRecord(ev[2], s));
+      OM_CUDA(cudaEventSynchronize(ev[2]));
+      if (r == 0) continue;
+      float a0 = 0.f, a1 = 0.f;
+      OM_CUDA(cudaEventElapsedTime(&a0, ev[0], ev[1]));
+      OM_CUDA(cudaEventElapsedTime(&a1, ev[1], ev[2]));
+      tot[0] += a0;
+      tot[1] += a1;
+    }
+    for (int p = 0; p < 2; ++p)
+      if (tot[p] < best[p]) {
+        best[p] = tot[p];
+        m.var[p] = sh[0];
+        m.grid[p] = grid;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+// capture K steps (K even, starting from an even time) into a graph
+template <class T>
+om_status capture_t(om_batch* b, int model, int K) {
+  Model& m = b->m[model];
+  if (m.exec && m.graph_k == K) return OM_OK;
+  if (m.exec) {
+    cudaGraphExecDestroy(m.exec);
+    m.exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  OM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < K; ++k) launch_step<T>(b, model, k & 1, m.var[k & 1], m.grid[k & 1], b->cap);
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  e = cudaGraphInstantiate(&m.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  m.graph_k = K;
+  return OM_OK;
+}
+
+template <class T>
+om_status init_state_t(om_batch* b, int model, cudaStream_t s) {
+  Model& m = b->m[model];
+  OM_CUDA(cudaMemsetAsync(m.pop, 0, (size_t)m.q * b->pitch * stg_bytes(m.prec), s));  // rest / linear profile
+  if (m.cr) batch_cr_linear<<<b->sms * 4, kTile, 0, s>>>(b->items, b->work, b->nwork, b->dp.c_in, m.cr);
+  OM_CUDA(cudaGetLastError());
+  m.t = 0;
+  return OM_OK;
+}
+
+template <class T>
+om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_info* info, int32_t* status,
+                  cudaStream_t s) {
+  Model& m = b->m[model];
+  const int K = model == 0 ? b->fp.check_every : b->dp.check_every;
+  const int64_t max_steps = model == 0 ? b->fp.max_steps : b->dp.max_steps;
+  const double tol = model == 0 ? b->fp.conv_tol : b->dp.conv_tol;
+  const int nv = model == 0 ? 4 : 5;
+  if (K <= 0 || (K & 1)) return fail(OM_EINVAL, "om_batch_solve: check_every must be a positive even number");
+  if (m.t & 1) return fail(OM_EINVAL, "om_batch_solve: the batch must be at an even time");
+  std::vector<int> active;
+  for (int k = 0; k < b->n; ++k) {
+    if (status) status[k] = OM_ENOPERC;
+    if (info) info[k] = om_run_info{};
+    if (result) result[k] = 0.0;
+    if (aux) aux[k] = 0.0;
+    if (b->items_h[k].nf > 0) active.push_back(k);
+  }
+  std::vector<double> sj_prev(b->n, 0.0);
+  int nw = build_work(b, active);
+  OM_TRY(upload_work(b, nw, (int)active.size(), s));
+  OM_TRY(observe_t<T>(b, model, (int)active.size(), s));  // reference state
+  for (size_t a = 0; a < active.size(); ++a) sj_prev[active[a]] = b->obs_h[a * nv + 0];
+  cudaEvent_t e0, e1;
+  OM_CUDA(cudaEventCreate(&e0));
+  OM_CUDA(cudaEventCreate(&e1));
+  OM_CUDA(cudaEventRecord(e0, s));
+  const int64_t t0 = m.t;
+  int64_t updates = 0;
+  while (!active.empty() && m.t - t0 < max_steps) {
+    const int64_t k = std::min<int64_t>(K, max_steps - (m.t - t0));
+    if (k == K) {
+      OM_TRY(capture_t<T>(b, model, K));
+      OM_CUDA(cudaGraphLaunch(m.exec, s));
+      m.t += K;
+      if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
+    } else {
+      OM_TRY(steps_t<T>(b, model, k, s));
+    }
+    for (int a : active) updates += (int64_t)b->items_h[a].nf * k;
+    OM_TRY(observe_t<T>(b, model, (int)active.size(), s));
+    std::vector<int> keep;
+    for (size_t a = 0; a < active.size(); ++a) {
+      const int it = active[a];
+      const double* o = b->obs_h + a * nv;
+      const BatchItem& bi = b->items_h[it];
+      const double N = (double)b->dom[it].nx * b->dom[it].ny * b->dom[it].nz;
+      double rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+      if (model == 1) {
+        const double relj = o[0] != 0.0 ? std::fabs(o[0] - sj_prev[it]) / std::fabs(o[0]) : 0.0;
+        rel = std::max(rel, relj);
+        sj_prev[it] = o[0];
+      }
+      if (result) {
+        if (model == 0) result[it] = ((b->fp.tau - 0.5) / 3.0) * (o[0] / N) / b->fp.body_force;
+        else result[it] = (o[0] / N) * (double)bi.nx / (b->dp.c_in - b->dp.c_out);
+      }
+      if (aux) aux[it] = model == 0 ? o[3] : o[4] / (double)bi.nf;
+      if (info) {
+        info[it].steps = m.t - t0;
+        info[it].n_nodes = bi.nf;
+        info[it].rel_change = rel;
+        info[it].mass = o[3];
+      }
+      const bool done = rel < tol;
+      if (status) status[it] = done ? OM_OK : OM_ENOTCONVERGED;
+      if (!done) keep.push_back(it);
+    }
+    if (keep.size() != active.size()) {
+      active.swap(keep);
+      nw = build_work(b, active);
+      OM_TRY(upload_work(b, nw, (int)active.size(), s));
+    }
+  }
+  OM_CUDA(cudaEventRecord(e1, s));
+  OM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  OM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info)
+    for (int k = 0; k < b->n; ++k) {
+      info[k].seconds = ms * 1e-3;
+      info[k].mlups = ms > 0 ? (double)updates / (ms * 1e-3) / 1e6 : 0.0;
+    }
+  // leave the full work list in place for later steps
+  std::vector<int> all;
+  for (int k = 0; k < b->n; ++k)
+    if (b->items_h[k].nf > 0) all.push_back(k);
+  nw = build_work(b, all);
+  OM_TRY(upload_work(b, nw, (int)all.size(), s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  return OM_OK;
+}
+
+#define OM_BATCH_DISPATCH(prec, fn, ...)                                      \
+  switch (prec) {                                                             \
+    case OM_F64: return fn<double>(__VA_ARGS__);                              \
+    case OM_F32: return fn<float>(__VA_ARGS__);                               \
+    case OM_F16DEV: return fn<__half>(__VA_ARGS__);                           \
+    case OM_BF16DEV: return fn<__nv_bfloat16>(__VA_ARGS__);                   \
+    default: return fail(OM_EINVAL, "unknown precision");                     \
+  }
+
+om_status dispatch_tune(om_batch* b, int model, cudaStream_t s) { OM_BATCH_DISPATCH(b->m[model].prec, tune_t, b, model, s); }
+om_status dispatch_init(om_batch* b, int model, cudaStream_t s) { OM_BATCH_DISPATCH(b->m[model].prec, init_state_t, b, model, s); }
+
+}  // namespace
+
+extern "C" om_status om_batch_destroy(om_batch* b) {
+  if (!b) return OM_OK;
+  for (auto* ns : b->ns) om_nodeset_destroy(ns);
+  for (auto& m : b->m) {
+    if (m.exec) cudaGraphExecDestroy(m.exec);
+    cudaFree(m.pop);
+    cudaFree(m.omega);
+    cudaFree(m.cr);
+    cudaFree(m.prev);
+  }
+  cudaFree(b->items);
+  cudaFree(b->work);
+  cudaFree(b->nwork);
+  cudaFree(b->range);
+  cudaFree(b->partials);
+  cudaFree(b->obs);
+  if (b->work_h) cudaFreeHost(b->work_h);
+  if (b->range_h) cudaFreeHost(b->range_h);
+  if (b->nwork_h) cudaFreeHost(b->nwork_h);
+  if (b->obs_h) cudaFreeHost(b->obs_h);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return OM_OK;
+}
+
+extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uint8_t* const* nodes_dev,
+                                     const float* const* d_nm_dev, const om_flow_params* fp,
+                                     const om_diff_params* dp, void* stream, om_batch** out) {
+  if (n <= 0 || !doms || !nodes_dev || !out || (!fp && !dp)) return fail(OM_EINVAL, "om_batch_create: bad arguments");
+  if (dp && !d_nm_dev) return fail(OM_EINVAL, "om_batch_create: diffusion needs pore sizes");
+  if (fp && !(fp->tau > 0.5)) return fail(OM_EINVAL, "om_batch_create: tau must exceed 1/2");
+  if (dp && (!(dp->d_ref_nm > 0.0) || !(dp->tau_ref > 0.5) || !(dp->c_in != dp->c_out)))
+    return fail(OM_EINVAL, "om_batch_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");
+  for (const auto* p : {fp ? &fp->precision : nullptr, dp ? &dp->precision : nullptr})
+    if (p && (*p < OM_F64 || *p > OM_BF16DEV)) return fail(OM_EINVAL, "om_batch_create: unknown precision");
+  cudaStream_t s = as_stream(stream);
+  om_batch* b = new om_batch();
+  auto bail = [&](om_status st) {
+    om_batch_destroy(b);
+    return st;
+  };
+  b->n = n;
+  if (fp) b->fp = *fp;
+  if (dp) b->dp = *dp;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  // node sets, offsets, rebased column maps
+  uint64_t total = 0;
+  int tiles = 0;
+  for (int k = 0; k < n; ++k) {
+    om_nodeset* ns = nullptr;
+    om_status st = om_nodeset_create(nodes_dev[k], doms[k], stream, &ns);
+    if (st != OM_OK) return bail(st);
+    b->ns.push_back(ns);
+    b->dom.push_back(doms[k]);
+    BatchItem it{};
+    it.col = ns->col;
+    it.coord = ns->coord;
+    it.off = (uint32_t)total;
+    it.nf = (uint32_t)ns->nf;
+    it.nx = doms[k].nx;
+    it.ny = doms[k].ny;
+    it.nz = doms[k].nz;
+    it.W = ns->W;
+    it.slope = dp ? (dp->c_out - dp->c_in) / (double)doms[k].nx : 0.0;
+    const int64_t nw = (int64_t)doms[k].nx * doms[k].ny * ns->W;
+    if (total > 0) rebase_columns<<<(unsigned)std::min<int64_t>((nw + 255) / 256, 4096), 256, 0, s>>>(ns->col, nw, it.off);
+    total += (uint64_t)ns->nf;
+    tiles += (int)((ns->nf + kTile - 1) / kTile);
+    b->items_h.push_back(it);
+  }
+  if (total >= 0xFFFFFFF0ull) return bail(fail(OM_EINVAL, "om_batch_create: more than 2^32 nodes"));
+  b->total = (uint32_t)total;
+  b->pitch = ((int64_t)total + 63) / 64 * 64;
+  b->max_tiles = std::max(1, tiles);
+  auto dalloc = [&](void** p, size_t bytes) -> om_status {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      *p = nullptr;
+      return fail(OM_ENOMEM, "om_batch_create: device allocation failed");
+    }
+    return OM_OK;
+  };
+  auto halloc = [&](void** p, size_t bytes) -> om_status {
+    if (cudaMallocHost(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      *p = nullptr;
+      return fail(OM_ENOMEM, "om_batch_create: pinned allocation failed");
+    }
+    return OM_OK;
+  };
+  om_status st = OM_OK;
+  if ((st = dalloc((void**)&b->items, sizeof(BatchItem) * n)) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->work, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->nwork, sizeof(int))) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->range, sizeof(int2) * n)) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->partials, sizeof(double) * 5 * b->max_tiles)) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->obs, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->work_h, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->range_h, sizeof(int2) * n)) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->nwork_h, sizeof(int))) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->obs_h, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
+  if (cudaMemcpyAsync(b->items, b->items_h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return bail(fail(OM_ECUDA, "om_batch_create: copy of the item table failed"));
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(OM_ECUDA, "om_batch_create: stream creation failed"));
+  // models
+  for (int model = 0; model < 2; ++model) {
+    const bool on = model == 0 ? fp != nullptr : dp != nullptr;
+    if (!on) continue;
+    Model& m = b->m[model];
+    m.on = true;
+    m.prec = model == 0 ? fp->precision : dp->precision;
+    m.q = model == 0 ? 19 : 7;
+    m.up = m.prec == OM_F16DEV ? (model == 0 ? 1024.0 : 64.0) : 1.0;
+    if ((st = dalloc(&m.pop, (size_t)m.q * b->pitch * stg_bytes(m.prec))) != OM_OK) return bail(st);
+    if ((st = dalloc((void**)&m.prev, sizeof(double) * b->pitch)) != OM_OK) return bail(st);
+    if (model == 1) {
+      const size_t cb = m.prec == OM_F64 ? 8 : 4;
+      if ((st = dalloc(&m.omega, cb * b->pitch)) != OM_OK) return bail(st);
+      if (stg_bytes(m.prec) <= 4 && (st = dalloc((void**)&m.cr, sizeof(float) * b->pitch)) != OM_OK) return bail(st);
+      int* bad = nullptr;
+      if ((st = dalloc((void**)&bad, sizeof(int))) != OM_OK) return bail(st);
+      cudaMemsetAsync(bad, 0, sizeof(int), s);
+      for (int k = 0; k < n; ++k) {
+        const BatchItem& it = b->items_h[k];
+        if (it.nf == 0) continue;
+        const unsigned g = (it.nf + 255) / 256;
+        if (m.prec == OM_F64)
+          batch_omega<double><<<g, 256, 0, s>>>(b->ns[k]->vox, d_nm_dev[k], it.nf, dp->d_ref_nm, dp->tau_ref,
+                                                (double*)m.omega + it.off, bad);
+        else
+          batch_omega<float><<<g, 256, 0, s>>>(b->ns[k]->vox, d_nm_dev[k], it.nf, dp->d_ref_nm, dp->tau_ref,
+                                               (float*)m.omega + it.off, bad);
+      }
+      int hb = 0;
+      cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      cudaFree(bad);
+      if (hb) return bail(fail(OM_EINVAL, "om_batch_create: a node has a pore size <= 0"));
+    }
+    // full work list, tune the launch shapes from the initial state, restore it
+    std::vector<int> all;
+    for (int k = 0; k < n; ++k)
+      if (b->items_h[k].nf > 0) all.push_back(k);
+    const int nw = build_work(b, all);
+    if ((st = upload_work(b, nw, (int)all.size(), s)) != OM_OK) return bail(st);
+    if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
+    const int variant = model == 0 ? fp->variant : dp->variant;
+    if (variant < 0) {
+      if ((st = dispatch_tune(b, model, s)) != OM_OK) return bail(st);
+      if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
+    } else {
+      m.var[0] = m.var[1] = std::min(variant, 1);
+      m.grid[0] = m.grid[1] = 4 * b->sms;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "om_batch_create", __FILE__, __LINE__));
+  *out = b;
+  return OM_OK;
+}
+
+extern "C" om_status om_batch_step(om_batch* b, int32_t model, int64_t nsteps, void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on || nsteps < 0) return fail(OM_EINVAL, "om_batch_step: bad arguments");
+  OM_BATCH_DISPATCH(b->m[model].prec, steps_t, b, model, nsteps, as_stream(stream));
+}
+
+extern "C" om_status om_batch_solve(om_batch* b, int32_t model, double* result, double* aux, om_run_info* info,
+                                    int32_t* status, void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on) return fail(OM_EINVAL, "om_batch_solve: bad arguments");
+  OM_BATCH_DISPATCH(b->m[model].prec, solve_t, b, model, result, aux, info, status, as_stream(stream));
+}
+
+namespace {
+template <class T>
+om_status exchange_t(om_batch* b, int model, int item, double* out, const double* in, cudaStream_t s) {
+  const BatchItem& it = b->items_h[item];
+  const om_nodeset* ns = b->ns[item];
+  const int64_t N = ns->N;
+  const Model& m = b->m[model];
+  if (out) OM_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * m.q * N, s));
+  if (it.nf == 0) return OM_OK;
+  const unsigned g = (it.nf + 255) / 256;
+  if (model == 0) {
+    FlowArgs<T> a = bflow_args<T>(b);
+    a.nf = it.nf;
+    a.col = it.col;
+    a.coord = it.coord;
+    a.nx = it.nx;
+    a.ny = it.ny;
+    a.nz = it.nz;
+    a.W = it.W;
+    if (in) flow_batch_import<T><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, in);
+    else if (m.t & 1) flow_batch_export<T, true><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
+    else flow_batch_export<T, false><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
+  } else {
+    DiffArgs<T> a = bdiff_args<T>(b);
+    a.nf = it.nf;
+    a.col = it.col;
+    a.coord = it.coord;
+    a.nx = it.nx;
+    a.ny = it.ny;
+    a.nz = it.nz;
+    a.W = it.W;
+    a.s = (typename Stg<T>::C)it.slope;
+    if (in) diff_batch_import<T><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, in);
+    else if (m.t & 1) diff_batch_export<T, true><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
+    else diff_batch_export<T, false><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
+  }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+}  // namespace
+
+extern "C" om_status om_batch_get_populations(om_batch* b, int32_t model, int32_t item, double* dense_dev,
+                                              void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on || item < 0 || item >= b->n || !dense_dev)
+    return fail(OM_EINVAL, "om_batch_get_populations: bad arguments");
+  OM_BATCH_DISPATCH(b->m[model].prec, exchange_t, b, model, item, dense_dev, nullptr, as_stream(stream));
+}
+
+extern "C" om_status om_batch_set_populations(om_batch* b, int32_t model, int32_t item, const double* dense_dev,
+                                              void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on || item < 0 || item >= b->n || !dense_dev)
+    return fail(OM_EINVAL, "om_batch_set_populations: bad arguments");
+  if (b->m[model].t & 1) return fail(OM_EINVAL, "om_batch_set_populations: the batch must be at an even time");
+  OM_BATCH_DISPATCH(b->m[model].prec, exchange_t, b, model, item, nullptr, dense_dev, as_stream(stream));
+}
+
+namespace {
+template <class T>
+om_status init_item_t(om_batch* b, int model, int item, const float* field, int64_t stride, double scale,
+                      int from_linear, cudaStream_t s) {
+  const BatchItem& it = b->items_h[item];
+  if (it.nf == 0) return OM_OK;
+  const unsigned g = (it.nf + 255) / 256;
+  if (model == 0) {
+    FlowArgs<T> a = bflow_args<T>(b);
+    a.nf = it.nf;
+    flow_batch_init<T><<<g, 256, 0, s>>>(a, it.off, b->ns[item]->vox, field, stride, scale);
+  } else {
+    DiffArgs<T> a = bdiff_args<T>(b);
+    a.nf = it.nf;
+    a.coord = it.coord;
+    a.s = (typename Stg<T>::C)it.slope;
+    diff_batch_init<T><<<g, 256, 0, s>>>(a, it.off, b->ns[item]->vox, field, stride, from_linear);
+  }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+}  // namespace
+
+extern "C" om_status om_batch_init_fields(om_batch* b, int32_t model, int32_t item, const float* field_dev,
+                                          int64_t stride, double scale, int32_t from_linear, void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on || item < 0 || item >= b->n || !field_dev || stride < 1)
+    return fail(OM_EINVAL, "om_batch_init_fields: bad arguments");
+  if (b->m[model].t & 1) return fail(OM_EINVAL, "om_batch_init_fields: the batch must be at an even time");
+  OM_BATCH_DISPATCH(b->m[model].prec, init_item_t, b, model, item, field_dev, stride, scale, from_linear,
+                    as_stream(stream));
+}
+
+extern "C" om_status om_batch_reset(om_batch* b, int32_t model, void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on) return fail(OM_EINVAL, "om_batch_reset: bad arguments");
+  return dispatch_init(b, model, as_stream(stream));
+}

@@ -3,10 +3,12 @@
 //
 // g*_i = g_i - omega(x) (g_i - a_i C), C = sum g_i, a = {1/4, 1/8 x 6}, with
 // omega = 1/tau_g from the local pore size by Eq. 12.  Populations are
-// stored as deviations from a_i C_lin(x), C_lin the linear profile between
-// the two fixed concentrations, which keeps the stored values small; the
-// reference differs by a_i s e_ix (s = dC_lin/dx) between neighbours, which
-// the odd step adds when it moves a population across x.
+// stored as deviations from a reference equilibrium a_i C_ref: in FP64 the
+// linear profile C_lin(x) between the two fixed concentrations (the odd step
+// adds the jump a_i s e_ix, s = dC_lin/dx, when a population changes cell);
+// in FP32 and 16-bit storage a per-node concentration moved to the node's
+// current C once per check window (see diff_core.cuh), the odd step adding
+// a_i (C_ref(source) - C_ref(target)).
 //
 // Boundaries: bounce-back at walls and missing neighbours (no flux), periodic
 // y and z, and fixed concentration on the half links x = -1/2 (c_in) and
@@ -15,62 +17,9 @@
 #include <algorithm>
 #include <cmath>
 
-#include "lattice.cuh"
+#include "diff_core.cuh"
 
 namespace om {
-
-template <class T>
-struct DiffArgs {
-  T* q[7];  // population i of node n is q[i][n]
-  uint32_t nf;
-  const uint2* col;
-  const uint32_t* coord;
-  const typename Stg<T>::C* omega;
-  int nx, ny, nz, W;
-  typename Stg<T>::C s;         // slope of C_lin per lattice cell, (c_out - c_in)/nx
-  typename Stg<T>::C up, down;  // storage scale
-  double cin, cout;
-};
-
-// nb[i] = node of x + e_i, kNoNode for walls; x faces flagged separately
-template <class T>
-__device__ __forceinline__ void diff_neighbours(const DiffArgs<T>& a, uint32_t c, uint32_t (&nb)[7],
-                                                int& x) {
-  int y, z;
-  unpack_xyz(c, x, y, z);
-  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
-  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
-  nb[1] = x + 1 < a.nx ? node_at(a.col, a.ny, a.W, x + 1, y, z) : kNoNode;
-  nb[2] = x > 0 ? node_at(a.col, a.ny, a.W, x - 1, y, z) : kNoNode;
-  nb[3] = node_at(a.col, a.ny, a.W, x, yp, z);
-  nb[4] = node_at(a.col, a.ny, a.W, x, ym, z);
-  nb[5] = node_at(a.col, a.ny, a.W, x, y, zp);
-  nb[6] = node_at(a.col, a.ny, a.W, x, y, zm);
-}
-
-// pre-collision deviations of node n at the current time
-template <class T, bool ODD>
-__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7],
-                                          int x, typename Stg<T>::C (&g)[7]) {
-  using S = Stg<T>;
-  using C = typename S::C;
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    if (!ODD || i == 0) {
-      g[i] = S::ld(a.q[i] + n, a.down);
-    } else {
-      const int o = q7_opp(i);
-      const uint32_t src = nb[o];  // x - e_i
-      const bool inlet = (i == 1 && x == 0), outlet = (i == 2 && x == a.nx - 1);
-      const T* p = (src != kNoNode && !inlet && !outlet) ? a.q[o] + src : a.q[i] + n;
-      const C v = S::ld(p, a.down);
-      if (inlet) g[i] = -v - C(0.125) * a.s;
-      else if (outlet) g[i] = -v + C(0.125) * a.s;
-      else if (src != kNoNode) g[i] = v - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
-      else g[i] = v;
-    }
-  }
-}
 
 // Launch variants for the autotuner of om_diff_create (identical arithmetic):
 // 0 = registers as the compiler wants, 1 = capped for 8 resident blocks.
@@ -78,41 +27,9 @@ constexpr int kDiffVariants = 2;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q7_sweep(DiffArgs<T> a) {
-  using S = Stg<T>;
-  using C = typename S::C;
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
-  uint32_t nb[7];
-  int x = 0;
-  if (ODD) diff_neighbours(a, a.coord[n], nb, x);
-  C g[7];
-  diff_load<T, ODD>(a, n, nb, x, g);
-  const C om = a.omega[n];
-  C c = g[0];
-#pragma unroll
-  for (int i = 1; i < 7; ++i) c += g[i];
-#pragma unroll
-  for (int i = 0; i < 7; ++i) g[i] = g[i] - om * (g[i] - C(q7_w(i)) * c);
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    const int o = q7_opp(i);
-    if (!ODD) {
-      S::st(a.q[o] + n, g[i], a.up);
-    } else if (i == 0) {
-      S::st(a.q[0] + n, g[0], a.up);
-    } else {
-      const bool outlet = (i == 1 && x == a.nx - 1), inlet = (i == 2 && x == 0);
-      T* p = a.q[o] + n;
-      C v = g[i];
-      if (outlet) v = -g[i] + C(0.125) * a.s;
-      else if (inlet) v = -g[i] - C(0.125) * a.s;
-      else if (nb[i] != kNoNode) {
-        p = a.q[i] + nb[i];
-        v = g[i] - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
-      }
-      S::st(p, v, a.up);
-    }
-  }
+  diff_node<T, ODD>(a, n, n);
 }
 
 // Observables: sum J_x, sum |C - prev|, sum |C|, sum C, sum D_L; prev <- C.
@@ -121,7 +38,6 @@ __global__ void __launch_bounds__(kObsThreads) d3q7_observe(DiffArgs<T> a, doubl
                                                             double* partials) {
   using C = typename Stg<T>::C;
   double acc[5] = {0, 0, 0, 0, 0};
-  const double s = (double)a.s;
   for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.nf; n += gridDim.x * blockDim.x) {
     uint32_t nb[7];
     int x, y, z;
@@ -132,8 +48,7 @@ __global__ void __launch_bounds__(kObsThreads) d3q7_observe(DiffArgs<T> a, doubl
     double dev = 0;
 #pragma unroll
     for (int i = 0; i < 7; ++i) dev += (double)g[i];
-    const double cref = a.cin + s * ((double)x + 0.5);
-    const double c = dev + cref;
+    const double c = dev + diff_ref(a, n, x);
     const double om = (double)a.omega[n];
     const double jx = (1.0 - 0.5 * om) * ((double)g[1] - (double)g[2]);
     acc[0] += jx;
@@ -159,7 +74,7 @@ __global__ void d3q7_export(DiffArgs<T> a, const int64_t* vox, int64_t N, double
   C g[7];
   diff_load<T, ODD>(a, n, nb, x, g);
   const int64_t v = vox[n];
-  const double cref = a.cin + (double)a.s * ((double)x + 0.5);
+  const double cref = diff_ref(a, n, x);
   double dev = 0;
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
@@ -170,6 +85,8 @@ __global__ void d3q7_export(DiffArgs<T> a, const int64_t* vox, int64_t N, double
   if (jdense) jdense[v] = (float)((1.0 - 0.5 * (double)a.omega[n]) * ((double)g[1] - (double)g[2]));
 }
 
+// populations from the dense layout (linear != 0: the linear profile a_i C_lin);
+// 16-bit storage takes the node's C as its reference
 template <class T>
 __global__ void d3q7_import(DiffArgs<T> a, const int64_t* vox, int64_t N, const double* gdense,
                             int linear) {
@@ -177,12 +94,50 @@ __global__ void d3q7_import(DiffArgs<T> a, const int64_t* vox, int64_t N, const 
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   const int64_t v = vox[n];
+  int x, y, z;
+  unpack_xyz(a.coord[n], x, y, z);
+  const double clin = a.cin + (double)a.s * ((double)x + 0.5);
+  double ref = clin;
+  if constexpr (kRebased<T>) {
+    if (!linear) {
+      ref = 0.0;
+      for (int i = 0; i < 7; ++i) ref += gdense[i * N + v];
+    }
+    a.cr[n] = (float)ref;
+    ref = (double)a.cr[n];
+  }
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
-    // linear != 0: the linear profile itself, i.e. zero deviation
-    double val = linear ? 0.0 : gdense[i * N + v] - q7_w(i) * (a.cin + (double)a.s * ((double)(v / ((int64_t)a.ny * a.nz)) + 0.5));
-    S::st(a.q[i] + n, (typename S::C)val, a.up);
+    const double g = linear ? q7_w(i) * clin : gdense[i * N + v];
+    S::st(a.q[i] + n, (typename S::C)(g - q7_w(i) * ref), a.up);
   }
+}
+
+// warm start: g_i = a_i C (deviation a_i (C - C_lin(x))) in the even layout
+template <class T>
+__global__ void d3q7_init_c(DiffArgs<T> a, const int64_t* vox, const float* c, int64_t stride, int from_linear) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  int x, y, z;
+  unpack_xyz(a.coord[n], x, y, z);
+  const double clin = a.cin + (double)a.s * ((double)x + 0.5);
+  const double cv = (double)c[vox[n] * stride] + (from_linear ? clin : 0.0);
+  double dc;
+  if constexpr (kRebased<T>) {
+    a.cr[n] = (float)cv;
+    dc = 0.0;
+  } else {
+    dc = cv - clin;
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Stg<T>::st(a.q[i] + n, (typename Stg<T>::C)(q7_w(i) * dc), a.up);
+}
+
+template <class T>
+__global__ void d3q7_rebase(DiffArgs<T> a) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  diff_rebase_node<T>(a, n);
 }
 
 template <class T>
@@ -205,6 +160,7 @@ struct om_diff {
   om_diff_params p{};
   void* g = nullptr;
   void* omega = nullptr;
+  float* cr = nullptr;  // per-node reference concentration (16-bit storage)
   double* prev = nullptr;
   double* partials = nullptr;
   double* obs_dev = nullptr;
@@ -212,6 +168,10 @@ struct om_diff {
   int64_t t = 0;
   double up = 1.0;      // storage scale (stored = deviation * up)
   int var[2] = {0, 0};  // launch variant of the even and odd sweeps
+  // a captured window of graph_k steps starting at an even time (replayed by *_step)
+  cudaGraphExec_t exec = nullptr;
+  int graph_k = 0;
+  cudaStream_t cap = nullptr;
 };
 
 namespace {
@@ -234,6 +194,7 @@ DiffArgs<T> diff_args(const om_diff* df) {
   a.down = (typename Stg<T>::C)(1.0 / df->up);
   a.cin = df->p.c_in;
   a.cout = df->p.c_out;
+  a.cr = df->cr;
   return a;
 }
 
@@ -245,11 +206,36 @@ void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const Diff
     if (odd) d3q7_sweep<T, true, 8><<<nb, 256, 0, s>>>(a);
     else d3q7_sweep<T, false, 8><<<nb, 256, 0, s>>>(a);
   } else {
-    if (odd) d3q7_sweep<T, true, 1><<<nb, 256, 0, s>>>(a);
-    else d3q7_sweep<T, false, 1><<<nb, 256, 0, s>>>(a);
+    if (odd) d3q7_sweep<T, true, 0><<<nb, 256, 0, s>>>(a);
+    else d3q7_sweep<T, false, 0><<<nb, 256, 0, s>>>(a);
   }
 }
 
+// Capture K sweeps (K even, from an even time) into a CUDA graph once.
+template <class T>
+om_status diff_capture_t(om_diff* df, int K) {
+  if (df->exec && df->graph_k == K) return OM_OK;
+  if (df->exec) {
+    cudaGraphExecDestroy(df->exec);
+    df->exec = nullptr;
+  }
+  if (!df->cap) OM_CUDA(cudaStreamCreateWithFlags(&df->cap, cudaStreamNonBlocking));
+  DiffArgs<T> a = diff_args<T>(df);
+  const unsigned nb = blocks_for(a.nf);
+  cudaGraph_t g = nullptr;
+  OM_CUDA(cudaStreamBeginCapture(df->cap, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < K; ++k) launch_sweep<T>(k & 1, df->var[k & 1], nb, df->cap, a);
+  cudaError_t e = cudaStreamEndCapture(df->cap, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  e = cudaGraphInstantiate(&df->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  df->graph_k = K;
+  return OM_OK;
+}
+
+// Advance nsteps: whole check windows from even times replay the captured
+// graph; anything else is launched one sweep at a time.
 template <class T>
 om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
   if (df->ns->nf == 0) {
@@ -258,10 +244,20 @@ om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
   }
   DiffArgs<T> a = diff_args<T>(df);
   const unsigned nb = blocks_for(a.nf);
-  for (int64_t k = 0; k < nsteps; ++k) {
+  const int K = df->p.check_every;
+  while (nsteps > 0) {
+    if (K >= 2 && !(K & 1) && !(df->t & 1) && nsteps >= K) {
+      OM_TRY(diff_capture_t<T>(df, K));
+      OM_CUDA(cudaGraphLaunch(df->exec, s));
+      df->t += K;
+      nsteps -= K;
+      if (kRebased<T>) d3q7_rebase<T><<<nb, 256, 0, s>>>(a);  // once per window
+      continue;
+    }
     const bool odd = df->t & 1;
     launch_sweep<T>(odd, df->var[odd], nb, s, a);
     ++df->t;
+    --nsteps;
   }
   OM_CUDA(cudaGetLastError());
   return OM_OK;
@@ -340,6 +336,16 @@ om_status diff_import_t(om_diff* df, const double* gd, int linear, cudaStream_t 
 }
 
 template <class T>
+om_status diff_init_c_t(om_diff* df, const float* c, int64_t stride, int from_linear, cudaStream_t s) {
+  df->t = 0;
+  if (df->ns->nf == 0) return OM_OK;
+  DiffArgs<T> a = diff_args<T>(df);
+  d3q7_init_c<T><<<blocks_for(a.nf), 256, 0, s>>>(a, df->ns->vox, c, stride, from_linear);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
 om_status diff_omega_t(om_diff* df, const float* d_nm, cudaStream_t s) {
   if (df->ns->nf == 0) return OM_OK;
   DevBuf<int> bad;
@@ -388,7 +394,9 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   const size_t cb = p->precision == OM_F64 ? 8 : 4;
   DevBuf<uint8_t> g, om;
   DevBuf<double> prev, part, obs;
+  DevBuf<float> cr;
   om_status st = g.alloc(7 * (size_t)ns->pitch * storage_bytes(p->precision));
+  if (st == OM_OK && storage_bytes(p->precision) <= 4) st = cr.alloc(ns->pitch);
   if (st == OM_OK) st = om.alloc((size_t)ns->pitch * cb);
   if (st == OM_OK) st = prev.alloc(ns->nf);
   if (st == OM_OK) st = part.alloc((size_t)kObsBlocks * 8);
@@ -404,6 +412,7 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   }
   df->g = g.take();
   df->omega = om.take();
+  df->cr = cr.take();
   df->prev = prev.take();
   df->partials = part.take();
   df->obs_dev = obs.take();
@@ -516,6 +525,16 @@ extern "C" om_status om_diff_set_populations(om_diff* df, const double* g_dev, v
   return diff_observe_any(df, o, s);
 }
 
+extern "C" om_status om_diff_init_concentration(om_diff* df, const float* c_dev, int64_t stride, int32_t from_linear,
+                                                void* stream) {
+  if (!df || !c_dev || stride < 1) return fail(OM_EINVAL, "om_diff_init_concentration: bad argument");
+  cudaStream_t s = as_stream(stream);
+  auto init = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_init_c_t, df, c_dev, stride, from_linear, s); };
+  OM_TRY(init());
+  double o[5];
+  return diff_observe_any(df, o, s);
+}
+
 extern "C" om_status om_diff_time(const om_diff* df, int64_t* t) {
   if (!df || !t) return fail(OM_EINVAL, "om_diff_time: null pointer");
   *t = df->t;
@@ -524,8 +543,11 @@ extern "C" om_status om_diff_time(const om_diff* df, int64_t* t) {
 
 extern "C" om_status om_diff_destroy(om_diff* df) {
   if (!df) return OM_OK;
+  if (df->exec) cudaGraphExecDestroy(df->exec);
+  if (df->cap) cudaStreamDestroy(df->cap);
   cudaFree(df->g);
   cudaFree(df->omega);
+  cudaFree(df->cr);
   cudaFree(df->prev);
   cudaFree(df->partials);
   cudaFree(df->obs_dev);

@@ -1,0 +1,162 @@
+// diff_core.cuh -- device side of the D3Q7 Knudsen-diffusion sweep (Sec. 3.2,
+// Eqs. 10-12), shared by the single-structure kernels (diff.cu) and the
+// batched kernels (batch.cu).  See diff.cu for the scheme.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace om {
+
+template <class T>
+struct DiffArgs {
+  T* q[7];  // population i of node n is q[i][n]
+  uint32_t nf;
+  const uint2* col;
+  const uint32_t* coord;
+  const typename Stg<T>::C* omega;
+  int nx, ny, nz, W;
+  typename Stg<T>::C s;         // slope of C_lin per lattice cell, (c_out - c_in)/nx
+  typename Stg<T>::C up, down;  // storage scale
+  double cin, cout;
+  float* cr;  // 16-bit storage: per-node reference concentration (see kRebased)
+};
+
+// Reference state of the stored deviations.  FP64 storage: a_i C_lin(x),
+// the linear inlet-outlet profile, a function of position.  FP32 and 16-bit
+// storage: a_i Cr(node), a per-node concentration that the solver moves to
+// the node's current C every check window ("rebasing"), so what is stored is
+// the small non-equilibrium part plus the drift since the last rebase.
+// Deviations from C_lin are ~10 % of C in a tortuous structure; rounding
+// them each step biases the flux (Eq. 14) by ~1e-4 relative in FP32 and by
+// tens of percent in FP16, while the rebased deviations keep both within the
+// convergence tolerance of the FP64 result.
+template <class T>
+constexpr bool kRebased = sizeof(T) <= 4;
+
+// nb[i] = node of x + e_i, kNoNode for walls; x faces flagged separately
+template <class T>
+__device__ __forceinline__ void diff_neighbours(const DiffArgs<T>& a, uint32_t c, uint32_t (&nb)[7],
+                                                int& x) {
+  int y, z;
+  unpack_xyz(c, x, y, z);
+  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
+  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
+  nb[1] = x + 1 < a.nx ? node_at(a.col, a.ny, a.W, x + 1, y, z) : kNoNode;
+  nb[2] = x > 0 ? node_at(a.col, a.ny, a.W, x - 1, y, z) : kNoNode;
+  nb[3] = node_at(a.col, a.ny, a.W, x, yp, z);
+  nb[4] = node_at(a.col, a.ny, a.W, x, ym, z);
+  nb[5] = node_at(a.col, a.ny, a.W, x, y, zp);
+  nb[6] = node_at(a.col, a.ny, a.W, x, y, zm);
+}
+
+// pre-collision deviations of node n at the current time
+template <class T, bool ODD>
+__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7],
+                                          int x, typename Stg<T>::C (&g)[7]) {
+  using S = Stg<T>;
+  using C = typename S::C;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    if (!ODD || i == 0) {
+      g[i] = S::ld(a.q[i] + n, a.down);
+    } else {
+      const int o = q7_opp(i);
+      const uint32_t src = nb[o];  // x - e_i
+      const bool inlet = (i == 1 && x == 0), outlet = (i == 2 && x == a.nx - 1);
+      const T* p = (src != kNoNode && !inlet && !outlet) ? a.q[o] + src : a.q[i] + n;
+      const C v = S::ld(p, a.down);
+      if constexpr (kRebased<T>) {
+        const C rn = a.cr[n];
+        if (inlet) g[i] = -v + C(0.25) * ((C)a.cin - rn);
+        else if (outlet) g[i] = -v + C(0.25) * ((C)a.cout - rn);
+        else if (src != kNoNode) g[i] = v + C(q7_w(i)) * (a.cr[src] - rn);
+        else g[i] = v;
+      } else {
+        if (inlet) g[i] = -v - C(0.125) * a.s;
+        else if (outlet) g[i] = -v + C(0.125) * a.s;
+        else if (src != kNoNode) g[i] = v - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
+        else g[i] = v;
+      }
+    }
+  }
+}
+
+
+// One fused collide-stream update of node n (global slot index, coordinates
+// coord[ln]); the AA read/write pattern of flow_node with the anti-bounce-back
+// inlet/outlet and the C_lin reference shift.
+template <class T, bool ODD>
+__device__ __forceinline__ void diff_node(const DiffArgs<T>& a, uint32_t n, uint32_t ln) {
+  using S = Stg<T>;
+  using C = typename S::C;
+  uint32_t nb[7];
+  int x = 0;
+  if (ODD) diff_neighbours(a, a.coord[ln], nb, x);
+  C g[7];
+  diff_load<T, ODD>(a, n, nb, x, g);
+  const C om = a.omega[n];
+  C c = g[0];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) c += g[i];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) g[i] = g[i] - om * (g[i] - C(q7_w(i)) * c);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const int o = q7_opp(i);
+    if (!ODD) {
+      S::st(a.q[o] + n, g[i], a.up);
+    } else if (i == 0) {
+      S::st(a.q[0] + n, g[0], a.up);
+    } else {
+      const bool outlet = (i == 1 && x == a.nx - 1), inlet = (i == 2 && x == 0);
+      T* p = a.q[o] + n;
+      C v = g[i];
+      if constexpr (kRebased<T>) {
+        const C rn = a.cr[n];
+        if (outlet) v = -g[i] + C(0.25) * ((C)a.cout - rn);
+        else if (inlet) v = -g[i] + C(0.25) * ((C)a.cin - rn);
+        else if (nb[i] != kNoNode) {
+          p = a.q[i] + nb[i];
+          v = g[i] + C(q7_w(i)) * (rn - a.cr[nb[i]]);
+        }
+      } else {
+        if (outlet) v = -g[i] + C(0.125) * a.s;
+        else if (inlet) v = -g[i] - C(0.125) * a.s;
+        else if (nb[i] != kNoNode) {
+          p = a.q[i] + nb[i];
+          v = g[i] - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
+        }
+      }
+      S::st(p, v, a.up);
+    }
+  }
+}
+
+// Reference concentration of node n (with coordinates x): C_lin(x) or Cr[n]
+template <class T>
+__device__ __forceinline__ double diff_ref(const DiffArgs<T>& a, uint32_t n, int x) {
+  if constexpr (kRebased<T>) return (double)a.cr[n];
+  else return a.cin + (double)a.s * ((double)x + 0.5);
+}
+
+// Move node n's reference to its current concentration (even time only):
+// Cr += sum_i dev_i, dev_i -= a_i (Cr_new - Cr_old).
+template <class T>
+__device__ __forceinline__ void diff_rebase_node(const DiffArgs<T>& a, uint32_t n) {
+  if constexpr (kRebased<T>) {
+    using S = Stg<T>;
+    float d[7], sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      d[i] = S::ld(a.q[i] + n, a.down);
+      sum += d[i];
+    }
+    const float old = a.cr[n];
+    const float now = old + sum;
+    a.cr[n] = now;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) S::st(a.q[i] + n, d[i] + (float)q7_w(i) * (old - now), a.up);
+  }
+}
+
+}  // namespace om

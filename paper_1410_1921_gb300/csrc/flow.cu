@@ -23,87 +23,12 @@
 // are periodic (body-force driving).
 #include <algorithm>
 
-#include "lattice.cuh"
+#include "flow_core.cuh"
 
 namespace om {
 
-template <class T>
-struct FlowArgs {
-  T* s[19];  // population i of node n is s[i][n] (kernel parameters: no per-slot registers)
-  uint32_t nf;
-  const uint2* col;
-  const uint32_t* coord;
-  int nx, ny, nz, W;
-  typename Stg<T>::C wp, wm, g, up, down;
-};
-
-template <class T>
-__device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c, uint32_t (&nb)[19]) {
-  int x, y, z;
-  unpack_xyz(c, x, y, z);
-  const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
-  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
-  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
-#pragma unroll
-  for (int i = 1; i < 19; ++i) {
-    const int ex = q19_e(i, 0), ey = q19_e(i, 1), ez = q19_e(i, 2);
-    const int xx = ex > 0 ? xp : (ex < 0 ? xm : x);
-    const int yy = ey > 0 ? yp : (ey < 0 ? ym : y);
-    const int zz = ez > 0 ? zp : (ez < 0 ? zm : z);
-    nb[i] = node_at(a.col, a.ny, a.W, xx, yy, zz);
-  }
-}
-
-// pre-collision populations of node n at the current time
-template <class T, bool ODD>
-__device__ __forceinline__ void flow_load(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
-                                          typename Stg<T>::C (&f)[19]) {
-#pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    const T* p = a.s[i] + n;
-    if (ODD && i > 0) {
-      const uint32_t src = nb[q19_opp(i)];
-      if (src != kNoNode) p = a.s[q19_opp(i)] + src;
-    }
-    f[i] = Stg<T>::ld(p, a.down);
-  }
-}
-
-template <class C>
-__device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
-  C rho = f[0];
-#pragma unroll
-  for (int i = 1; i < 19; ++i) rho += f[i];
-  C jx = 0, jy = 0, jz = 0;
-#pragma unroll
-  for (int i = 1; i < 19; ++i) {
-    if (q19_e(i, 0)) jx += q19_e(i, 0) > 0 ? f[i] : -f[i];
-    if (q19_e(i, 1)) jy += q19_e(i, 1) > 0 ? f[i] : -f[i];
-    if (q19_e(i, 2)) jz += q19_e(i, 2) > 0 ? f[i] : -f[i];
-  }
-  const C ux = jx + C(0.5) * g, uy = jy, uz = jz;
-  const C usq15 = C(1.5) * (ux * ux + uy * uy + uz * uz);
-  const C frc = (C(1) - C(0.5) * wm) * C(3) * g;
-  f[0] = f[0] - wp * (f[0] - C(1.0 / 3.0) * (rho - usq15));
-#pragma unroll
-  for (int i = 1; i < 19; ++i) {
-    const int o = q19_opp(i);
-    if (o < i) continue;  // each pair once, from its first member
-    const C w = C(q19_w(i));
-    const C eu = C(q19_e(i, 0)) * ux + C(q19_e(i, 1)) * uy + C(q19_e(i, 2)) * uz;
-    const C sym = w * (rho + C(4.5) * eu * eu - usq15);
-    const C asym = C(3) * w * eu;
-    const C fp = C(0.5) * (f[i] + f[o]);
-    const C fm = C(0.5) * (f[i] - f[o]);
-    const C A = wp * (fp - sym);
-    const C B = wm * (fm - asym) - w * C(q19_e(i, 0)) * frc;
-    f[i] = f[i] - A - B;
-    f[o] = f[o] - A + B;
-  }
-}
-
 // Launch variants (chosen per parity by the autotuner of om_flow_create):
-// variant 0 lets the compiler use the registers it wants; variant 1 caps them
+// variant 0 leaves registers to the compiler (no residency hint); variant 1 caps them
 // (256 threads x MINB blocks resident per SM) for more latency hiding at the
 // cost of a few spills.  Both do identical arithmetic.
 template <class T>
@@ -112,26 +37,9 @@ constexpr int kSweepVariants = 2;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
-  using S = Stg<T>;
-  using C = typename S::C;
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
-  uint32_t nb[19];
-  if (ODD) flow_neighbours(a, a.coord[n], nb);
-  C f[19];
-  flow_load<T, ODD>(a, n, nb, f);
-  trt_collide(f, a.wp, a.wm, a.g);
-#pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    T* p = a.s[q19_opp(i)] + n;
-    if (ODD && i > 0) {
-      const uint32_t dst = nb[i];
-      if (dst != kNoNode) p = a.s[i] + dst;
-    } else if (ODD) {
-      p = a.s[0] + n;
-    }
-    S::st(p, f[i], a.up);
-  }
+  flow_node<T, ODD>(a, n, n);
 }
 
 // Observables (FP64, fixed grid): sum u_x, sum |u_x - prev|, sum |u_x|,
@@ -201,6 +109,19 @@ __global__ void d3q19_import(FlowArgs<T> a, const int64_t* vox, int64_t N, const
   for (int i = 0; i < 19; ++i) S::st(a.s[i] + n, (typename S::C)(fdense[i * N + v] - q19_w(i)), a.up);
 }
 
+// warm start: f_i = f_eq(rho = 1, u = (ux, 0, 0)) in the even layout
+template <class T>
+__global__ void d3q19_init_u(FlowArgs<T> a, const int64_t* vox, const float* ux, int64_t stride, double scale) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  const double u = scale * (double)ux[vox[n] * stride];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const double eu = (double)q19_e(i, 0) * u;
+    Stg<T>::st(a.s[i] + n, (typename Stg<T>::C)(q19_w(i) * (3.0 * eu + 4.5 * eu * eu - 1.5 * u * u)), a.up);
+  }
+}
+
 template <class T>
 __global__ void d3q19_rest(FlowArgs<T> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -224,6 +145,10 @@ struct om_flow {
   int64_t t = 0;
   double up = 1.0;  // storage scale of reduced-precision formats (stored = deviation * up)
   int var[2] = {0, 0};  // launch variant of the even and odd sweeps
+  // a captured window of graph_k steps starting at an even time (replayed by *_step)
+  cudaGraphExec_t exec = nullptr;
+  int graph_k = 0;
+  cudaStream_t cap = nullptr;
 };
 
 namespace {
@@ -257,11 +182,36 @@ void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const Flow
     if (odd) d3q19_sweep<T, true, kMinBlocks1<T>><<<nb, 256, 0, s>>>(a);
     else d3q19_sweep<T, false, kMinBlocks1<T>><<<nb, 256, 0, s>>>(a);
   } else {
-    if (odd) d3q19_sweep<T, true, 1><<<nb, 256, 0, s>>>(a);
-    else d3q19_sweep<T, false, 1><<<nb, 256, 0, s>>>(a);
+    if (odd) d3q19_sweep<T, true, 0><<<nb, 256, 0, s>>>(a);
+    else d3q19_sweep<T, false, 0><<<nb, 256, 0, s>>>(a);
   }
 }
 
+// Capture K sweeps (K even, from an even time) into a CUDA graph once.
+template <class T>
+om_status flow_capture_t(om_flow* fl, int K) {
+  if (fl->exec && fl->graph_k == K) return OM_OK;
+  if (fl->exec) {
+    cudaGraphExecDestroy(fl->exec);
+    fl->exec = nullptr;
+  }
+  if (!fl->cap) OM_CUDA(cudaStreamCreateWithFlags(&fl->cap, cudaStreamNonBlocking));
+  FlowArgs<T> a = flow_args<T>(fl);
+  const unsigned nb = blocks_for(a.nf);
+  cudaGraph_t g = nullptr;
+  OM_CUDA(cudaStreamBeginCapture(fl->cap, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < K; ++k) launch_sweep<T>(k & 1, fl->var[k & 1], nb, fl->cap, a);
+  cudaError_t e = cudaStreamEndCapture(fl->cap, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  e = cudaGraphInstantiate(&fl->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  fl->graph_k = K;
+  return OM_OK;
+}
+
+// Advance nsteps: whole check windows from even times replay the captured
+// graph; anything else is launched one sweep at a time.
 template <class T>
 om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
   if (fl->ns->nf == 0) {
@@ -270,10 +220,19 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
   }
   FlowArgs<T> a = flow_args<T>(fl);
   const unsigned nb = blocks_for(a.nf);
-  for (int64_t k = 0; k < nsteps; ++k) {
+  const int K = fl->p.check_every;
+  while (nsteps > 0) {
+    if (K >= 2 && !(K & 1) && !(fl->t & 1) && nsteps >= K) {
+      OM_TRY(flow_capture_t<T>(fl, K));
+      OM_CUDA(cudaGraphLaunch(fl->exec, s));
+      fl->t += K;
+      nsteps -= K;
+      continue;
+    }
     const bool odd = fl->t & 1;
     launch_sweep<T>(odd, fl->var[odd], nb, s, a);
     ++fl->t;
+    --nsteps;
   }
   OM_CUDA(cudaGetLastError());
   return OM_OK;
@@ -349,6 +308,16 @@ om_status flow_import_t(om_flow* fl, const double* fd, cudaStream_t s) {
   if (fl->ns->nf == 0) return OM_OK;
   FlowArgs<T> a = flow_args<T>(fl);
   d3q19_import<T><<<blocks_for(a.nf), 256, 0, s>>>(a, fl->ns->vox, fl->ns->N, fd);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <class T>
+om_status flow_init_u_t(om_flow* fl, const float* ux, int64_t stride, double scale, cudaStream_t s) {
+  fl->t = 0;
+  if (fl->ns->nf == 0) return OM_OK;
+  FlowArgs<T> a = flow_args<T>(fl);
+  d3q19_init_u<T><<<blocks_for(a.nf), 256, 0, s>>>(a, fl->ns->vox, ux, stride, scale);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
@@ -509,6 +478,16 @@ extern "C" om_status om_flow_set_populations(om_flow* fl, const double* f_dev, v
   return flow_observe_any(fl, o, s);
 }
 
+extern "C" om_status om_flow_init_velocity(om_flow* fl, const float* ux_dev, int64_t stride, double scale,
+                                           void* stream) {
+  if (!fl || !ux_dev || stride < 1) return fail(OM_EINVAL, "om_flow_init_velocity: bad argument");
+  cudaStream_t s = as_stream(stream);
+  auto init = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_init_u_t, fl, ux_dev, stride, scale, s); };
+  OM_TRY(init());
+  double o[4];
+  return flow_observe_any(fl, o, s);
+}
+
 extern "C" om_status om_flow_time(const om_flow* fl, int64_t* t) {
   if (!fl || !t) return fail(OM_EINVAL, "om_flow_time: null pointer");
   *t = fl->t;
@@ -517,6 +496,8 @@ extern "C" om_status om_flow_time(const om_flow* fl, int64_t* t) {
 
 extern "C" om_status om_flow_destroy(om_flow* fl) {
   if (!fl) return OM_OK;
+  if (fl->exec) cudaGraphExecDestroy(fl->exec);
+  if (fl->cap) cudaStreamDestroy(fl->cap);
   cudaFree(fl->f);
   cudaFree(fl->prev);
   cudaFree(fl->partials);

@@ -1,0 +1,155 @@
+// flow_core.cuh -- device side of the D3Q19 flow sweep (Sec. 3.1, Eqs. 1-9,
+// App. A), shared by the single-structure kernels (flow.cu) and the batched
+// kernels (batch.cu).  See flow.cu for the scheme.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace om {
+
+// Node indices returned by the column map are global slot indices (a batch
+// rebases each structure's map by its offset); coordinates are indexed by
+// the structure-local node number.
+template <class T>
+struct FlowArgs {
+  T* s[19];  // population i of node n is s[i][n] (kernel parameters: no per-slot registers)
+  uint32_t nf;
+  const uint2* col;
+  const uint32_t* coord;
+  int nx, ny, nz, W;
+  typename Stg<T>::C wp, wm, g, up, down;
+};
+
+// Node numbers of the voxels z-1, z, z+1 of one (x, y) column.  The three
+// usually share one 32-voxel word of the column map, so one load and a
+// popcount serve all of them; a neighbour across a word edge or the periodic
+// wrap takes its own word.
+__device__ __forceinline__ void column3(const uint2* __restrict__ col, uint32_t base, int z, int zp, int zm,
+                                        uint32_t& rm, uint32_t& r0, uint32_t& rp) {
+  const int zb = z & 31;
+  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
+  const uint32_t b0 = (w.x >> zb) & 1u;
+  const uint32_t rank0 = w.y + __popc(w.x & ((1u << zb) - 1u));
+  r0 = b0 ? rank0 : kNoNode;
+  if (zb != 31 && zp == z + 1) {
+    rp = ((w.x >> (zb + 1)) & 1u) ? rank0 + b0 : kNoNode;
+  } else {
+    const uint2 v = __ldg(col + base + ((uint32_t)zp >> 5));
+    const uint32_t bit = 1u << (zp & 31);
+    rp = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
+  }
+  if (zb != 0 && zm == z - 1) {
+    rm = ((w.x >> (zb - 1)) & 1u) ? rank0 - 1u : kNoNode;
+  } else {
+    const uint2 v = __ldg(col + base + ((uint32_t)zm >> 5));
+    const uint32_t bit = 1u << (zm & 31);
+    rm = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
+  }
+}
+
+__device__ __forceinline__ uint32_t column1(const uint2* __restrict__ col, uint32_t base, int z) {
+  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
+  const uint32_t bit = 1u << (z & 31);
+  return (w.x & bit) ? w.y + __popc(w.x & (bit - 1u)) : kNoNode;
+}
+
+// nb[i] = node number of x + e_i (kNoNode off the node set); periodic x, y, z
+template <class T>
+__device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c, uint32_t (&nb)[19]) {
+  int x, y, z;
+  unpack_xyz(c, x, y, z);
+  const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
+  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
+  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
+  const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
+  auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
+  uint32_t self;
+  column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
+  column3(a.col, base(xp, y), z, zp, zm, nb[13], nb[1], nb[11]);
+  column3(a.col, base(xm, y), z, zp, zm, nb[14], nb[2], nb[12]);
+  column3(a.col, base(x, yp), z, zp, zm, nb[17], nb[3], nb[15]);
+  column3(a.col, base(x, ym), z, zp, zm, nb[18], nb[4], nb[16]);
+  nb[7] = column1(a.col, base(xp, yp), z);
+  nb[8] = column1(a.col, base(xm, yp), z);
+  nb[9] = column1(a.col, base(xp, ym), z);
+  nb[10] = column1(a.col, base(xm, ym), z);
+  (void)self;
+}
+
+// pre-collision populations of node n at the current time
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_load(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
+                                          typename Stg<T>::C (&f)[19]) {
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const T* p = a.s[i] + n;
+    if (ODD && i > 0) {
+      const uint32_t src = nb[q19_opp(i)];
+      if (src != kNoNode) p = a.s[q19_opp(i)] + src;
+    }
+    f[i] = Stg<T>::ld(p, a.down);
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
+  C rho = f[0];
+#pragma unroll
+  for (int i = 1; i < 19; ++i) rho += f[i];
+  C jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    if (q19_e(i, 0)) jx += q19_e(i, 0) > 0 ? f[i] : -f[i];
+    if (q19_e(i, 1)) jy += q19_e(i, 1) > 0 ? f[i] : -f[i];
+    if (q19_e(i, 2)) jz += q19_e(i, 2) > 0 ? f[i] : -f[i];
+  }
+  const C ux = jx + C(0.5) * g, uy = jy, uz = jz;
+  const C usq15 = C(1.5) * (ux * ux + uy * uy + uz * uz);
+  const C frc = (C(1) - C(0.5) * wm) * C(3) * g;
+  f[0] = f[0] - wp * (f[0] - C(1.0 / 3.0) * (rho - usq15));
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    const int o = q19_opp(i);
+    if (o < i) continue;  // each pair once, from its first member
+    const C w = C(q19_w(i));
+    const C eu = C(q19_e(i, 0)) * ux + C(q19_e(i, 1)) * uy + C(q19_e(i, 2)) * uz;
+    const C sym = w * (rho + C(4.5) * eu * eu - usq15);
+    const C asym = C(3) * w * eu;
+    const C fp = C(0.5) * (f[i] + f[o]);
+    const C fm = C(0.5) * (f[i] - f[o]);
+    const C A = wp * (fp - sym);
+    const C B = wm * (fm - asym) - w * C(q19_e(i, 0)) * frc;
+    f[i] = f[i] - A - B;
+    f[o] = f[o] - A + B;
+  }
+}
+
+
+// One fused collide-stream update of node n (global slot index) whose
+// coordinates are coord[ln].  Even steps: read and write the node's own slots
+// (post-collision f*_i to slot opposite(i)).  Odd steps: read slot
+// opposite(i) of x - e_i, write slot i of x + e_i; a missing neighbour is
+// halfway bounce-back (own slot i read, own slot opposite(i) written).
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_node(const FlowArgs<T>& a, uint32_t n, uint32_t ln) {
+  using S = Stg<T>;
+  using C = typename S::C;
+  uint32_t nb[19];
+  if (ODD) flow_neighbours(a, a.coord[ln], nb);
+  C f[19];
+  flow_load<T, ODD>(a, n, nb, f);
+  trt_collide(f, a.wp, a.wm, a.g);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    T* p = a.s[q19_opp(i)] + n;
+    if (ODD && i > 0) {
+      const uint32_t dst = nb[i];
+      if (dst != kNoNode) p = a.s[i] + dst;
+    } else if (ODD) {
+      p = a.s[0] + n;
+    }
+    S::st(p, f[i], a.up);
+  }
+}
+
+}  // namespace om

@@ -76,3 +76,28 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* part
 }
 
 }  // namespace om
+
+namespace om {
+// Block reduction of NV doubles written to out[0..NV) (any block size that
+// is a multiple of 32, at most 1024).  Ends with a barrier, so a block may
+// call it again in a loop.
+template <int NV>
+__device__ __forceinline__ void block_reduce_write(double (&v)[NV], double* out) {
+  __shared__ double sm[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[k][wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double acc = 0.0;
+    for (int w = 0; w < nw; ++w) acc += sm[threadIdx.x][w];
+    out[threadIdx.x] = acc;
+  }
+  __syncthreads();
+}
+}  // namespace om

@@ -1,0 +1,692 @@
+// unet.cu -- the learned warm start: a 3-D U-Net that maps the structure
+// (pore mask, local pore size) to the steady fields the LB solves produce
+// (velocity u_x, concentration C), trained on the GPU by this file's own
+// forward and backward passes; the LB then iterates from the prediction to
+// the same convergence test, so the plain solve stays the judge of the
+// result.
+//
+// Network (levels L, channels c_0..c_{L-1}): per encoder level two 3x3x3
+// convolutions with ReLU, 2x average pooling between levels; per decoder
+// level nearest 2x upsampling, the skip tensor concatenated (read as a second
+// conv input, never materialised) and two 3x3x3 convolutions with ReLU; a
+// 1x1 head without activation.  Masked mean-squared error; Adam.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "unet_kernels.cuh"
+
+namespace om {
+namespace nn {
+namespace {
+
+constexpr int kT = 256;
+inline unsigned blocks(int64_t n, int t = kT) { return (unsigned)std::min<int64_t>((n + t - 1) / t, 1 << 20); }
+
+__global__ void pack_input(const float* x, int cin, int64_t V, bf16* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * 16; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / 16;
+    const int c = (int)(i % 16);
+    out[i] = __float2bfloat16_rn(c < cin ? x[v * cin + c] : 0.f);
+  }
+}
+
+// fine grid gf -> coarse grid (gf / 2)
+__global__ void avgpool2(const bf16* in, Grid gf, int C, bf16* out) {
+  const Grid gc{gf.B, gf.D / 2, gf.H / 2, gf.W / 2};
+  const int64_t n = gc.voxels() * C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t r = i / C;
+    const int x = (int)(r % gc.W); r /= gc.W;
+    const int y = (int)(r % gc.H); r /= gc.H;
+    const int z = (int)(r % gc.D);
+    const int b = (int)(r / gc.D);
+    float s = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int64_t vf = (((int64_t)b * gf.D + 2 * z + (q >> 2)) * gf.H + 2 * y + ((q >> 1) & 1)) * gf.W + 2 * x + (q & 1);
+      s += __bfloat162float(in[vf * C + c]);
+    }
+    out[i] = __float2bfloat16_rn(0.125f * s);
+  }
+}
+
+// d(fine) = d(coarse parent) / 8
+__global__ void avgpool2_bwd(const bf16* dout, Grid gf, int C, bf16* din) {
+  const int64_t n = gf.voxels() * C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t r = i / C;
+    const int x = (int)(r % gf.W); r /= gf.W;
+    const int y = (int)(r % gf.H); r /= gf.H;
+    const int z = (int)(r % gf.D);
+    const int b = (int)(r / gf.D);
+    const int64_t vc = (((int64_t)b * (gf.D / 2) + z / 2) * (gf.H / 2) + y / 2) * (gf.W / 2) + x / 2;
+    din[i] = __float2bfloat16_rn(0.125f * __bfloat162float(dout[vc * C + c]));
+  }
+}
+
+// nearest 2x: coarse [V_c x C] -> fine rows of ldo, channels [oo, oo + C)
+__global__ void upsample2(const bf16* in, Grid gf, int C, bf16* out, int ldo, int oo) {
+  const int64_t n = gf.voxels() * C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t v = i / C;
+    int64_t r = v;
+    const int x = (int)(r % gf.W); r /= gf.W;
+    const int y = (int)(r % gf.H); r /= gf.H;
+    const int z = (int)(r % gf.D);
+    const int b = (int)(r / gf.D);
+    const int64_t vc = (((int64_t)b * (gf.D / 2) + z / 2) * (gf.H / 2) + y / 2) * (gf.W / 2) + x / 2;
+    out[v * ldo + oo + c] = in[vc * C + c];
+  }
+}
+
+// d(coarse) = sum of the 8 fine children, read from rows of ldi at offset oi
+__global__ void upsample2_bwd(const bf16* dfine, int ldi, int oi, Grid gf, int C, bf16* dcoarse) {
+  const Grid gc{gf.B, gf.D / 2, gf.H / 2, gf.W / 2};
+  const int64_t n = gc.voxels() * C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    int64_t r = i / C;
+    const int x = (int)(r % gc.W); r /= gc.W;
+    const int y = (int)(r % gc.H); r /= gc.H;
+    const int z = (int)(r % gc.D);
+    const int b = (int)(r / gc.D);
+    float s = 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int64_t vf = (((int64_t)b * gf.D + 2 * z + (q >> 2)) * gf.H + 2 * y + ((q >> 1) & 1)) * gf.W + 2 * x + (q & 1);
+      s += __bfloat162float(dfine[vf * ldi + oi + c]);
+    }
+    dcoarse[i] = __float2bfloat16_rn(s);
+  }
+}
+
+// gradient at the pre-activation: g * [y > 0]; g read from rows of ldg at og
+__global__ void relu_bwd(const bf16* g, int ldg, int og, const bf16* y, int N, int64_t V, bf16* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / N;
+    const int c = (int)(i % N);
+    out[i] = __bfloat162float(y[i]) > 0.f ? g[v * ldg + og + c] : __float2bfloat16_rn(0.f);
+  }
+}
+
+// a[i] += b (rows of ldb at ob), BF16
+__global__ void add_into(bf16* a, int N, int64_t V, const bf16* b, int ldb, int ob) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / N;
+    const int c = (int)(i % N);
+    a[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[v * ldb + ob + c]));
+  }
+}
+
+// db[c] += sum_v g[v][c] (per-block partial sums, then atomics)
+__global__ void bias_grad(const bf16* g, int N, int64_t V, float* db) {
+  extern __shared__ float sh[];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) sh[c] = 0.f;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&sh[i % N], __bfloat162float(g[i]));
+  __syncthreads();
+  for (int c = threadIdx.x; c < N; c += blockDim.x) atomicAdd(&db[c], sh[c]);
+}
+
+// 1x1 head: y[v][o] = b[o] + sum_c x[v][c] w[c][o]  (FP32 out)
+__global__ void head_fwd(const bf16* x, int C, const float* w, const float* b, int O, int64_t V, float* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * O; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / O;
+    const int o = (int)(i % O);
+    float s = b[o];
+    for (int c = 0; c < C; ++c) s += __bfloat162float(x[v * C + c]) * w[c * O + o];
+    y[i] = s;
+  }
+}
+
+// masked MSE: loss = sum m (y - t)^2 * scale, dy = 2 m (y - t) * scale
+__global__ void mse_grad(const float* y, const float* t, const uint8_t* m, int O, int64_t V, float scale, float* dy,
+                         double* loss) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * O; i += (int64_t)gridDim.x * blockDim.x) {
+    const float keep = m[i / O] ? 1.f : 0.f;
+    const float d = (y[i] - t[i]) * keep;
+    dy[i] = 2.f * d * scale;
+    acc += (double)d * d * scale;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// head backward: dw[c][o] += sum_v x[v][c] dy[v][o]; db[o] += sum_v dy; dx[v][c] = sum_o dy w[c][o]
+__global__ void head_bwd_dx(const float* dy, const float* w, int C, int O, int64_t V, bf16* dx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * C; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / C;
+    const int c = (int)(i % C);
+    float s = 0.f;
+    for (int o = 0; o < O; ++o) s += dy[v * O + o] * w[c * O + o];
+    dx[i] = __float2bfloat16_rn(s);
+  }
+}
+__global__ void head_bwd_dw(const bf16* x, const float* dy, int C, int O, int64_t V, float* dw, float* db) {
+  // one block per (c, o) pair plus the bias row c == C
+  const int c = blockIdx.x / O, o = blockIdx.x % O;
+  float s = 0.f;
+  for (int64_t v = threadIdx.x; v < V; v += blockDim.x)
+    s += (c < C ? __bfloat162float(x[v * C + c]) : 1.f) * dy[v * O + o];
+  __shared__ float sh[kT];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (c < C) dw[c * O + o] += sh[0];
+    else db[o] += sh[0];
+  }
+}
+
+// FP32 master W[27][K][N] -> forward operand WT[27][N][K] (BF16)
+__global__ void weights_fwd(const float* W, int K, int N, bf16* WT) {
+  const int64_t n = 27LL * K * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / ((int64_t)K * N));
+    const int r = (int)(i % ((int64_t)K * N));
+    const int ci = r / N, co = r % N;
+    WT[((int64_t)k * N + co) * K + ci] = __float2bfloat16_rn(W[i]);
+  }
+}
+// data-gradient operand WD[27][K][N] = W[26 - k][K][N] (BF16): the forward
+// kernel with inputs dY (N channels) and output channels K
+__global__ void weights_dgrad(const float* W, int K, int N, bf16* WD) {
+  const int64_t n = 27LL * K * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / ((int64_t)K * N));
+    const int64_t r = i % ((int64_t)K * N);
+    WD[i] = __float2bfloat16_rn(W[(int64_t)(26 - k) * K * N + r]);
+  }
+}
+
+__global__ void adam_step(float* w, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                          float eps, float bc1, float bc2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct Conv {
+  int cin1, cin2, cout;
+  int64_t w_off, b_off;  // into the flat parameter vector
+  bf16* wt = nullptr;    // forward operand
+  bf16* wd = nullptr;    // data-gradient operand
+};
+
+template <class T>
+struct Buf {
+  T* p = nullptr;
+  size_t n = 0;
+  om_status ensure(size_t count) {
+    if (count <= n) return OM_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (cudaMalloc((void**)&p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(OM_ENOMEM, "U-Net: device allocation failed");
+    }
+    n = count;
+    return OM_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace
+}  // namespace nn
+}  // namespace om
+
+using namespace om;
+using namespace om::nn;
+
+struct om_unet {
+  int in_ch = 0, out_ch = 0, L = 0;
+  std::vector<int> ch;
+  std::vector<Conv> enc1, enc2, dec1, dec2;  // per level (dec: levels 0..L-2)
+  int64_t head_w = 0, head_b = 0, nparam = 0;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grad, Adam moments
+  int64_t step = 0;
+  Grid grid{0, 0, 0, 0};
+  // activations per level
+  Buf<bf16> x0;
+  std::vector<Buf<bf16>> in, a, s, u, b, h;
+  Buf<float> out, dout;
+  // gradients (scratch)
+  std::vector<Buf<bf16>> d1, d2, dcat, ds;
+  Buf<double> loss;
+};
+
+namespace {
+
+om_status conv_forward(const om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
+                       bf16* y, const Grid& g, cudaStream_t s) {
+  ConvArgs a{};
+  a.x1 = x1, a.c1 = c.cin1, a.ld1 = ld1, a.o1 = o1;
+  a.x2 = x2, a.c2 = c.cin2, a.ld2 = ld2, a.o2 = o2;
+  a.wt = c.wt;
+  a.bias = U->w + c.b_off;
+  a.N = c.cout;
+  a.y = y, a.ldy = c.cout, a.oy = 0;
+  a.yf = nullptr;
+  a.relu = 1;
+  a.g = g;
+  const unsigned gx = (unsigned)((g.voxels() + kConvBM - 1) / kConvBM);
+  if (c.cout % 64 == 0) conv3d_igemm<64><<<dim3(gx, c.cout / 64), 128, 0, s>>>(a);
+  else if (c.cout % 32 == 0) conv3d_igemm<32><<<dim3(gx, c.cout / 32), 128, 0, s>>>(a);
+  else conv3d_igemm<16><<<dim3(gx, c.cout / 16), 128, 0, s>>>(a);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+// dX (rows of cin1 + cin2) = data gradient of conv c for the pre-activation gradient dyp
+om_status conv_dgrad(const Conv& c, const bf16* dyp, bf16* dx, const Grid& g, cudaStream_t s) {
+  ConvArgs a{};
+  a.x1 = dyp, a.c1 = c.cout, a.ld1 = c.cout, a.o1 = 0;
+  a.x2 = nullptr, a.c2 = 0;
+  a.wt = c.wd;
+  a.bias = nullptr;
+  a.N = c.cin1 + c.cin2;
+  a.y = dx, a.ldy = a.N, a.oy = 0;
+  a.relu = 0;
+  a.g = g;
+  const unsigned gx = (unsigned)((g.voxels() + kConvBM - 1) / kConvBM);
+  if (a.N % 64 == 0) conv3d_igemm<64><<<dim3(gx, a.N / 64), 128, 0, s>>>(a);
+  else if (a.N % 32 == 0) conv3d_igemm<32><<<dim3(gx, a.N / 32), 128, 0, s>>>(a);
+  else conv3d_igemm<16><<<dim3(gx, a.N / 16), 128, 0, s>>>(a);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+template <int MT, int NT>
+void launch_wgrad(const WgradArgs& a, int K, cudaStream_t s) {
+  const unsigned gx = (unsigned)((a.g.voxels() + a.chunk - 1) / a.chunk);
+  conv3d_wgrad<MT, NT><<<dim3(gx, 27, (K / MT) * (a.N / NT)), MT * 2, 0, s>>>(a);
+}
+
+om_status conv_wgrad(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
+                     const bf16* dyp, const Grid& g, cudaStream_t s) {
+  WgradArgs a{};
+  a.x1 = x1, a.c1 = c.cin1, a.ld1 = ld1, a.o1 = o1;
+  a.x2 = x2, a.c2 = c.cin2, a.ld2 = ld2, a.o2 = o2;
+  a.dy = dyp;
+  a.N = c.cout;
+  a.dw = U->g + c.w_off;
+  a.g = g;
+  a.chunk = 1024;
+  const int K = c.cin1 + c.cin2;
+  const int MT = K % 64 == 0 ? 64 : (K % 32 == 0 ? 32 : 16);
+  const int NT = c.cout % 64 == 0 ? 64 : (c.cout % 32 == 0 ? 32 : 16);
+  if (MT == 64 && NT == 64) launch_wgrad<64, 64>(a, K, s);
+  else if (MT == 64 && NT == 32) launch_wgrad<64, 32>(a, K, s);
+  else if (MT == 64 && NT == 16) launch_wgrad<64, 16>(a, K, s);
+  else if (MT == 32 && NT == 64) launch_wgrad<32, 64>(a, K, s);
+  else if (MT == 32 && NT == 32) launch_wgrad<32, 32>(a, K, s);
+  else if (MT == 32 && NT == 16) launch_wgrad<32, 16>(a, K, s);
+  else if (MT == 16 && NT == 64) launch_wgrad<16, 64>(a, K, s);
+  else if (MT == 16 && NT == 32) launch_wgrad<16, 32>(a, K, s);
+  else launch_wgrad<16, 16>(a, K, s);
+  bias_grad<<<std::min<int64_t>(blocks(g.voxels() * c.cout), 1216), kT, c.cout * sizeof(float), s>>>(
+      dyp, c.cout, g.voxels(), U->g + c.b_off);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+Grid level_grid(const Grid& g, int l) { return Grid{g.B, g.D >> l, g.H >> l, g.W >> l}; }
+
+om_status prepare(om_unet* U, const Grid& g) {
+  if (g.B == U->grid.B && g.D == U->grid.D && g.H == U->grid.H && g.W == U->grid.W) return OM_OK;
+  const int L = U->L;
+  for (int l = 0; l < L; ++l) {
+    const int64_t V = level_grid(g, l).voxels();
+    const int cprev = l == 0 ? 16 : U->ch[l - 1];
+    const int cnext = l + 1 < L ? U->ch[l + 1] : 0;
+    const int c = U->ch[l];
+    if (l > 0) OM_TRY(U->in[l].ensure(V * cprev));
+    OM_TRY(U->a[l].ensure(V * c));
+    OM_TRY(U->s[l].ensure(V * c));
+    if (l + 1 < L) {
+      OM_TRY(U->u[l].ensure(V * cnext));
+      OM_TRY(U->b[l].ensure(V * c));
+      OM_TRY(U->h[l].ensure(V * c));
+      OM_TRY(U->dcat[l].ensure(V * (cnext + c)));
+    }
+    const int64_t wmax = std::max((int64_t)c, std::max((int64_t)cprev, (int64_t)(cnext + c)));
+    OM_TRY(U->d1[l].ensure(V * wmax));
+    OM_TRY(U->d2[l].ensure(V * wmax));
+    OM_TRY(U->ds[l].ensure(V * c));
+  }
+  OM_TRY(U->x0.ensure(g.voxels() * 16));
+  OM_TRY(U->out.ensure(g.voxels() * U->out_ch));
+  OM_TRY(U->dout.ensure(g.voxels() * U->out_ch));
+  U->grid = g;
+  return OM_OK;
+}
+
+om_status refresh_operands(om_unet* U, cudaStream_t s) {
+  auto conv = [&](Conv& c) {
+    const int K = c.cin1 + c.cin2;
+    weights_fwd<<<blocks(27LL * K * c.cout), kT, 0, s>>>(U->w + c.w_off, K, c.cout, c.wt);
+    weights_dgrad<<<blocks(27LL * K * c.cout), kT, 0, s>>>(U->w + c.w_off, K, c.cout, c.wd);
+  };
+  for (int l = 0; l < U->L; ++l) {
+    conv(U->enc1[l]);
+    conv(U->enc2[l]);
+    if (l + 1 < U->L) {
+      conv(U->dec1[l]);
+      conv(U->dec2[l]);
+    }
+  }
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+om_status forward(om_unet* U, const float* x, const Grid& g, cudaStream_t s) {
+  OM_TRY(prepare(U, g));
+  OM_TRY(refresh_operands(U, s));
+  const int L = U->L;
+  pack_input<<<blocks(g.voxels() * 16), kT, 0, s>>>(x, U->in_ch, g.voxels(), U->x0.p);
+  for (int l = 0; l < L; ++l) {
+    const Grid gl = level_grid(g, l);
+    const bf16* in = l == 0 ? U->x0.p : U->in[l].p;
+    const int cin = l == 0 ? 16 : U->ch[l - 1];
+    if (l > 0) avgpool2<<<blocks(gl.voxels() * cin), kT, 0, s>>>(U->s[l - 1].p, level_grid(g, l - 1), cin, U->in[l].p);
+    OM_TRY(conv_forward(U, U->enc1[l], in, cin, 0, nullptr, 0, 0, U->a[l].p, gl, s));
+    OM_TRY(conv_forward(U, U->enc2[l], U->a[l].p, U->ch[l], 0, nullptr, 0, 0, U->s[l].p, gl, s));
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const Grid gl = level_grid(g, l);
+    const bf16* below = l + 1 == L - 1 ? U->s[L - 1].p : U->h[l + 1].p;
+    const int cb = U->ch[l + 1];
+    upsample2<<<blocks(gl.voxels() * cb), kT, 0, s>>>(below, gl, cb, U->u[l].p, cb, 0);
+    OM_TRY(conv_forward(U, U->dec1[l], U->u[l].p, cb, 0, U->s[l].p, U->ch[l], 0, U->b[l].p, gl, s));
+    OM_TRY(conv_forward(U, U->dec2[l], U->b[l].p, U->ch[l], 0, nullptr, 0, 0, U->h[l].p, gl, s));
+  }
+  const bf16* top = L > 1 ? U->h[0].p : U->s[0].p;
+  head_fwd<<<blocks(g.voxels() * U->out_ch), kT, 0, s>>>(top, U->ch[0], U->w + U->head_w, U->w + U->head_b, U->out_ch,
+                                                         g.voxels(), U->out.p);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+// gradients of the masked MSE w.r.t. every parameter, into U->g
+om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g, double* loss_out, cudaStream_t s) {
+  const int L = U->L;
+  const int64_t V = g.voxels();
+  OM_CUDA(cudaMemsetAsync(U->g, 0, sizeof(float) * U->nparam, s));
+  OM_TRY(U->loss.ensure(1));
+  OM_CUDA(cudaMemsetAsync(U->loss.p, 0, sizeof(double), s));
+  // masked mean over pore voxels and output channels: the count is taken on the host
+  std::vector<uint8_t> hm((size_t)V);
+  OM_CUDA(cudaMemcpyAsync(hm.data(), mk, (size_t)V, cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  int64_t cnt = 0;
+  for (uint8_t q : hm) cnt += q != 0;
+  const float scale = cnt > 0 ? 1.f / (float)(cnt * U->out_ch) : 0.f;
+  mse_grad<<<std::min<unsigned>(blocks(V * U->out_ch), 1216), kT, 0, s>>>(U->out.p, t, mk, U->out_ch, V, scale, U->dout.p,
+                                                                           U->loss.p);
+  // head
+  const int c0 = U->ch[0];
+  const bf16* top = L > 1 ? U->h[0].p : U->s[0].p;
+  head_bwd_dw<<<(c0 + 1) * U->out_ch, kT, 0, s>>>(top, U->dout.p, c0, U->out_ch, V, U->g + U->head_w, U->g + U->head_b);
+  head_bwd_dx<<<blocks(V * c0), kT, 0, s>>>(U->dout.p, U->w + U->head_w, c0, U->out_ch, V, U->d1[0].p);
+  // decoder, top level down: d1[l] holds the gradient of the level's output h_l
+  for (int l = 0; l + 1 < L; ++l) {
+    const Grid gl = level_grid(g, l);
+    const int64_t Vl = gl.voxels();
+    const int c = U->ch[l], cb = U->ch[l + 1];
+    // h_l = relu(conv(b_l))
+    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d1[l].p, c, 0, U->h[l].p, c, Vl, U->d2[l].p);
+    OM_TRY(conv_wgrad(U, U->dec2[l], U->b[l].p, c, 0, nullptr, 0, 0, U->d2[l].p, gl, s));
+    OM_TRY(conv_dgrad(U->dec2[l], U->d2[l].p, U->d1[l].p, gl, s));
+    // b_l = relu(conv(concat(u_l, s_l)))
+    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d1[l].p, c, 0, U->b[l].p, c, Vl, U->d2[l].p);
+    OM_TRY(conv_wgrad(U, U->dec1[l], U->u[l].p, cb, 0, U->s[l].p, c, 0, U->d2[l].p, gl, s));
+    OM_TRY(conv_dgrad(U->dec1[l], U->d2[l].p, U->dcat[l].p, gl, s));
+    // u_l = up(h_{l+1}) (or s_{L-1} at the bottom): gradient of the level below
+    upsample2_bwd<<<blocks(level_grid(g, l + 1).voxels() * cb), kT, 0, s>>>(U->dcat[l].p, cb + c, 0, gl, cb,
+                                                                            U->d1[l + 1].p);
+  }
+  // encoder, bottom level up: ds[l] = gradient of s_l
+  for (int l = L - 1; l >= 0; --l) {
+    const Grid gl = level_grid(g, l);
+    const int64_t Vl = gl.voxels();
+    const int c = U->ch[l];
+    const int cin = l == 0 ? 16 : U->ch[l - 1];
+    // s_l receives: from the level below (pooling) and from the decoder's skip
+    if (l == L - 1) {
+      OM_CUDA(cudaMemcpyAsync(U->ds[l].p, U->d1[l].p, sizeof(bf16) * Vl * c, cudaMemcpyDeviceToDevice, s));
+    } else {
+      avgpool2_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d2[l + 1].p, gl, c, U->ds[l].p);
+      add_into<<<blocks(Vl * c), kT, 0, s>>>(U->ds[l].p, c, Vl, U->dcat[l].p, U->ch[l + 1] + c, U->ch[l + 1]);
+    }
+    // s_l = relu(conv(a_l))
+    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->ds[l].p, c, 0, U->s[l].p, c, Vl, U->d1[l].p);
+    OM_TRY(conv_wgrad(U, U->enc2[l], U->a[l].p, c, 0, nullptr, 0, 0, U->d1[l].p, gl, s));
+    OM_TRY(conv_dgrad(U->enc2[l], U->d1[l].p, U->d2[l].p, gl, s));
+    // a_l = relu(conv(in_l))
+    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d2[l].p, c, 0, U->a[l].p, c, Vl, U->d1[l].p);
+    const bf16* in = l == 0 ? U->x0.p : U->in[l].p;
+    OM_TRY(conv_wgrad(U, U->enc1[l], in, cin, 0, nullptr, 0, 0, U->d1[l].p, gl, s));
+    // d2[l] = gradient of in_l (pooled s_{l-1}); not needed at the input
+    if (l > 0) OM_TRY(conv_dgrad(U->enc1[l], U->d1[l].p, U->d2[l].p, gl, s));
+  }
+  double h = 0.0;
+  OM_CUDA(cudaMemcpyAsync(&h, U->loss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  if (loss_out) *loss_out = h;
+  return OM_OK;
+}
+
+uint64_t splitmix(uint64_t& st) {
+  st += 0x9E3779B97F4A7C15ULL;
+  uint64_t z = st;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+om_status check_grid(const om_unet* U, const Grid& g) {
+  const int q = 1 << (U->L - 1);
+  if (g.B <= 0 || g.D <= 0 || g.H <= 0 || g.W <= 0 || g.D % q || g.H % q || g.W % q)
+    return fail(OM_EINVAL, "U-Net: box edges must be positive multiples of 2^(levels-1)");
+  return OM_OK;
+}
+
+}  // namespace
+
+extern "C" om_status om_unet_destroy(om_unet* U) {
+  if (!U) return OM_OK;
+  auto drop = [](std::vector<Buf<bf16>>& v) {
+    for (auto& b : v) b.release();
+  };
+  drop(U->in), drop(U->a), drop(U->s), drop(U->u), drop(U->b), drop(U->h);
+  drop(U->d1), drop(U->d2), drop(U->dcat), drop(U->ds);
+  U->x0.release(), U->out.release(), U->dout.release(), U->loss.release();
+  for (auto* v : {&U->enc1, &U->enc2, &U->dec1, &U->dec2})
+    for (auto& c : *v) {
+      cudaFree(c.wt);
+      cudaFree(c.wd);
+    }
+  cudaFree(U->w), cudaFree(U->g), cudaFree(U->m), cudaFree(U->v);
+  delete U;
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_create(int32_t in_ch, int32_t out_ch, int32_t levels, const int32_t* ch, uint64_t seed,
+                                    om_unet** out) {
+  if (!out || !ch || in_ch < 1 || in_ch > 16 || out_ch < 1 || levels < 1 || levels > 6)
+    return fail(OM_EINVAL, "om_unet_create: 1..16 inputs, >= 1 output, 1..6 levels");
+  for (int l = 0; l < levels; ++l)
+    if (ch[l] < 16 || ch[l] % 16 || ch[l] > 256) return fail(OM_EINVAL, "om_unet_create: channels must be multiples of 16 up to 256");
+  om_unet* U = new om_unet();
+  U->in_ch = in_ch, U->out_ch = out_ch, U->L = levels;
+  U->ch.assign(ch, ch + levels);
+  int64_t off = 0;
+  auto add = [&](int c1, int c2, int co) {
+    Conv c;
+    c.cin1 = c1, c.cin2 = c2, c.cout = co;
+    c.w_off = off;
+    off += 27LL * (c1 + c2) * co;
+    c.b_off = off;
+    off += co;
+    return c;
+  };
+  for (int l = 0; l < levels; ++l) {
+    U->enc1.push_back(add(l == 0 ? 16 : ch[l - 1], 0, ch[l]));
+    U->enc2.push_back(add(ch[l], 0, ch[l]));
+  }
+  U->dec1.resize(std::max(0, levels - 1));
+  U->dec2.resize(std::max(0, levels - 1));
+  for (int l = levels - 2; l >= 0; --l) {
+    U->dec1[l] = add(ch[l + 1], ch[l], ch[l]);
+    U->dec2[l] = add(ch[l], 0, ch[l]);
+  }
+  U->head_w = off;
+  off += (int64_t)ch[0] * out_ch;
+  U->head_b = off;
+  off += out_ch;
+  U->nparam = off;
+  const int L = levels;
+  U->in.resize(L), U->a.resize(L), U->s.resize(L), U->u.resize(L), U->b.resize(L), U->h.resize(L);
+  U->d1.resize(L), U->d2.resize(L), U->dcat.resize(L), U->ds.resize(L);
+  // He-uniform initial weights from a SplitMix64 stream, zero biases
+  std::vector<float> w((size_t)off, 0.f);
+  uint64_t st = seed;
+  auto init = [&](const Conv& c, int fan_in) {
+    const double bound = std::sqrt(6.0 / fan_in);
+    for (int64_t i = 0; i < 27LL * (c.cin1 + c.cin2) * c.cout; ++i)
+      w[(size_t)(c.w_off + i)] = (float)(bound * (2.0 * ((double)(splitmix(st) >> 11) * 0x1.0p-53) - 1.0));
+  };
+  for (int l = 0; l < L; ++l) {
+    init(U->enc1[l], 27 * (l == 0 ? in_ch : ch[l - 1]));
+    init(U->enc2[l], 27 * ch[l]);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    init(U->dec1[l], 27 * (ch[l + 1] + ch[l]));
+    init(U->dec2[l], 27 * ch[l]);
+  }
+  const double hb = std::sqrt(6.0 / ch[0]);
+  for (int64_t i = 0; i < (int64_t)ch[0] * out_ch; ++i)
+    w[(size_t)(U->head_w + i)] = (float)(hb * (2.0 * ((double)(splitmix(st) >> 11) * 0x1.0p-53) - 1.0));
+  auto dal = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  bool ok = dal((void**)&U->w, sizeof(float) * off) && dal((void**)&U->g, sizeof(float) * off) &&
+            dal((void**)&U->m, sizeof(float) * off) && dal((void**)&U->v, sizeof(float) * off);
+  for (auto* v : {&U->enc1, &U->enc2, &U->dec1, &U->dec2})
+    for (auto& c : *v) {
+      const size_t n = 27ull * (c.cin1 + c.cin2) * c.cout;
+      ok = ok && dal((void**)&c.wt, n * sizeof(bf16)) && dal((void**)&c.wd, n * sizeof(bf16));
+    }
+  if (!ok) {
+    om_unet_destroy(U);
+    return fail(OM_ENOMEM, "om_unet_create: device allocation failed");
+  }
+  if (cudaMemcpy(U->w, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(U->m, 0, sizeof(float) * off) != cudaSuccess || cudaMemset(U->v, 0, sizeof(float) * off) != cudaSuccess) {
+    om_unet_destroy(U);
+    return fail(OM_ECUDA, "om_unet_create: initialisation failed");
+  }
+  *out = U;
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_param_count(const om_unet* U, int64_t* n) {
+  if (!U || !n) return fail(OM_EINVAL, "om_unet_param_count: null pointer");
+  *n = U->nparam;
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_get_params(const om_unet* U, float* dst_dev, void* stream) {
+  if (!U || !dst_dev) return fail(OM_EINVAL, "om_unet_get_params: null pointer");
+  OM_CUDA(cudaMemcpyAsync(dst_dev, U->w, sizeof(float) * U->nparam, cudaMemcpyDeviceToDevice, as_stream(stream)));
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_set_params(om_unet* U, const float* src_dev, void* stream) {
+  if (!U || !src_dev) return fail(OM_EINVAL, "om_unet_set_params: null pointer");
+  OM_CUDA(cudaMemcpyAsync(U->w, src_dev, sizeof(float) * U->nparam, cudaMemcpyDeviceToDevice, as_stream(stream)));
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_get_grads(const om_unet* U, float* dst_dev, void* stream) {
+  if (!U || !dst_dev) return fail(OM_EINVAL, "om_unet_get_grads: null pointer");
+  OM_CUDA(cudaMemcpyAsync(dst_dev, U->g, sizeof(float) * U->nparam, cudaMemcpyDeviceToDevice, as_stream(stream)));
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_forward(om_unet* U, const float* x, int32_t B, int32_t D, int32_t H, int32_t W, float* y,
+                                     void* stream) {
+  if (!U || !x || !y) return fail(OM_EINVAL, "om_unet_forward: null pointer");
+  const Grid g{B, D, H, W};
+  OM_TRY(check_grid(U, g));
+  cudaStream_t s = as_stream(stream);
+  OM_TRY(forward(U, x, g, s));
+  OM_CUDA(cudaMemcpyAsync(y, U->out.p, sizeof(float) * g.voxels() * U->out_ch, cudaMemcpyDeviceToDevice, s));
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_backward(om_unet* U, const float* x, const float* t, const uint8_t* m, int32_t B,
+                                      int32_t D, int32_t H, int32_t W, double* loss_out, void* stream) {
+  if (!U || !x || !t || !m) return fail(OM_EINVAL, "om_unet_backward: null pointer");
+  const Grid g{B, D, H, W};
+  OM_TRY(check_grid(U, g));
+  cudaStream_t s = as_stream(stream);
+  OM_TRY(forward(U, x, g, s));
+  return backward(U, t, m, g, loss_out, s);
+}
+
+namespace om {
+namespace nn {
+__global__ void pack_structure(const uint8_t* mask, const float* d, int64_t n, float ds, float* x) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    x[2 * v] = mask[v] ? 1.f : 0.f;
+    x[2 * v + 1] = d[v] * ds;
+  }
+}
+}  // namespace nn
+}  // namespace om
+
+extern "C" om_status om_unet_pack_structure(const uint8_t* mask_dev, const float* d_nm_dev, int64_t n, double d_scale,
+                                           float* x_dev, void* stream) {
+  if (!mask_dev || !d_nm_dev || !x_dev || n < 0) return fail(OM_EINVAL, "om_unet_pack_structure: bad argument");
+  if (n == 0) return OM_OK;
+  om::nn::pack_structure<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1 << 20), 256, 0, as_stream(stream)>>>(
+      mask_dev, d_nm_dev, n, (float)d_scale, x_dev);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_train_step(om_unet* U, const float* x, const float* t, const uint8_t* m, int32_t B,
+                                        int32_t D, int32_t H, int32_t W, float lr, double* loss_out, void* stream) {
+  OM_TRY(om_unet_backward(U, x, t, m, B, D, H, W, loss_out, stream));
+  cudaStream_t s = as_stream(stream);
+  ++U->step;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.f - std::pow(b1, (float)U->step), bc2 = 1.f - std::pow(b2, (float)U->step);
+  adam_step<<<blocks(U->nparam), kT, 0, s>>>(U->w, U->g, U->m, U->v, U->nparam, lr, b1, b2, 1e-8f, bc1, bc2);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}

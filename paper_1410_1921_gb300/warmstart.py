@@ -1,0 +1,136 @@
+"""Learned warm start: LB-solved training fields, U-Net training, warm solves.
+
+Orchestration only: every step runs in the library's kernels (reconstruction,
+labelling, pore size, LB solves, U-Net forward/backward/Adam, warm-start
+initialisation).  Training targets are assembled on the host from the solved
+fields (data preparation, outside the solve path).
+
+Targets per voxel: u_x / U0 with U0 = g L0^2 / nu (L0 = 10 lattice units),
+and C - C_lin(x), the concentration's departure from the linear inlet-outlet
+profile; the loss is taken over the node set.  Inputs: pore mask and d / 60 nm.
+"""
+import time
+
+import numpy as np
+import torch
+
+from . import (OM_F32, OM_PORE_CHORD13, Diffusion, Flow, NodeSet, UNet, diff_params, domain, flow_params,
+               om_label_connectivity_dev, om_local_pore_diameter_dev, om_reconstruct_dev, om_unet_pack_structure,
+               recon_params)
+
+D_SCALE = 1.0 / 60.0
+L0 = 10.0
+
+
+def velocity_scale(fp):
+    nu = (fp.tau - 0.5) / 3.0
+    return fp.body_force * L0 * L0 / nu
+
+
+def structure(cfg, stream=None):
+    """Reconstruct, label and size one structure on the device.  Returns
+    (dom, mask, transport, d_nm) as flat CUDA tensors."""
+    dom = domain(cfg.shape, cfg.dx_nm)
+    N = dom.nx * dom.ny * dom.nz
+    mask = torch.empty(N, dtype=torch.uint8, device="cuda")
+    rp = recon_params(cfg.mean_nm, cfg.sd_nm, cfg.dmin_nm, cfg.dmax_nm, cfg.porosity, cfg.xi, cfg.p0, cfg.dist,
+                      cfg.max_trials)
+    om_reconstruct_dev(cfg.seed, dom, rp, mask, stream=stream)
+    tr = torch.empty(N, dtype=torch.uint8, device="cuda")
+    om_label_connectivity_dev(mask, dom, None, tr, stream=stream)
+    d = torch.empty(N, dtype=torch.float32, device="cuda")
+    om_local_pore_diameter_dev(mask, dom, OM_PORE_CHORD13, d, stream=stream)
+    return dom, mask, tr, d
+
+
+def net_input(mask, d, dom):
+    x = torch.empty(mask.numel() * 2, dtype=torch.float32, device="cuda")
+    om_unet_pack_structure(mask, d, D_SCALE, x)
+    return x.view(1, dom.nx, dom.ny, dom.nz, 2)
+
+
+def solve(dom, tr, d, fp, dp, prediction=None):
+    """Flow and diffusion solves on the transport set, cold or warm-started
+    from a network output (float [N][2]).  Returns a dict of results, step
+    counts, wall times and the solved fields (ux, C)."""
+    ns = NodeSet(tr, dom)
+    out = {"nodes": ns.n_nodes}
+    N = tr.numel()
+    t0 = time.perf_counter()
+    fl = Flow(ns, fp)
+    if prediction is not None:
+        fl.init_velocity(prediction, stride=2, scale=velocity_scale(fp))
+    st, kl, info = fl.solve()
+    torch.cuda.synchronize()
+    out.update(flow_status=st, k_lattice=kl, flow_steps=info.steps, flow_s=time.perf_counter() - t0)
+    u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+    fl.get_velocity(u)
+    out["ux"] = u[:N].clone()
+    fl.close()
+    t0 = time.perf_counter()
+    df = Diffusion(ns, d, dp)
+    if prediction is not None:
+        df.init_concentration(prediction[1:], stride=2, from_linear=True)
+    st, Dl, info = df.solve()
+    torch.cuda.synchronize()
+    out.update(diff_status=st, D_lattice=Dl, diff_steps=info.steps, diff_s=time.perf_counter() - t0)
+    c = torch.empty(N, dtype=torch.float32, device="cuda")
+    df.get_fields(c, None)
+    out["C"] = c
+    df.close()
+    ns.close()
+    return out
+
+
+def targets(res, dom, fp, dp):
+    """Training target [1, nx, ny, nz, 2] from solved fields (host assembly)."""
+    ux = res["ux"].cpu().numpy().reshape(dom.nx, dom.ny, dom.nz) / velocity_scale(fp)
+    x = (np.arange(dom.nx) + 0.5)[:, None, None]
+    clin = dp.c_in + (dp.c_out - dp.c_in) * x / dom.nx
+    c = res["C"].cpu().numpy().reshape(dom.nx, dom.ny, dom.nz) - clin
+    t = np.stack([ux, c], -1)[None].astype(np.float32)
+    return torch.from_numpy(t).cuda()
+
+
+def make_dataset(cfgs, fp=None, dp=None, log=None):
+    """Solve every structure (cold, FP32) and keep (input, target, mask)."""
+    fp = fp or flow_params(precision=OM_F32)
+    dp = dp or diff_params(precision=OM_F32)
+    data = []
+    for cfg in cfgs:
+        dom, mask, tr, d = structure(cfg)
+        if int(tr.sum().item()) == 0:
+            continue
+        res = solve(dom, tr, d, fp, dp)
+        data.append((net_input(mask, d, dom), targets(res, dom, fp, dp), tr.view(1, dom.nx, dom.ny, dom.nz)))
+        if log:
+            log(f"sample {len(data)}: {cfg.shape} eps={cfg.porosity:.2f} nodes={res['nodes']} "
+                f"flow {res['flow_steps']} diff {res['diff_steps']} steps")
+    return data
+
+
+def train(net, data, epochs, lr=1e-3, lr_end=1e-4, seed=0, log=None):
+    """Adam over the samples in shuffled order; learning rate decays
+    geometrically from lr to lr_end.  Returns the loss history (per epoch)."""
+    rng = np.random.default_rng(seed)
+    hist = []
+    total = max(1, epochs * len(data))
+    k = 0
+    for ep in range(epochs):
+        acc = 0.0
+        for i in rng.permutation(len(data)):
+            x, t, m = data[i]
+            rate = lr * (lr_end / lr) ** (k / total)
+            acc += net.train_step(x, t, m, rate)
+            k += 1
+        hist.append(acc / len(data))
+        if log:
+            log(f"epoch {ep}: loss {hist[-1]:.4e}")
+    return hist
+
+
+def predict(net, mask, d, dom):
+    x = net_input(mask, d, dom)
+    y = torch.empty(mask.numel() * 2, dtype=torch.float32, device="cuda")
+    net.forward(x, y)
+    return y

@@ -1,0 +1,137 @@
+"""Batched solves (om_batch_*): many structures advanced together by one
+persistent launch per step, a graph-replayed check window and per-structure
+early retirement.  Parity with the oracle per step (random populations, FP64
+and FP32) and at convergence, plus structures without nodes."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from conftest import recon_args
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda") if dtype is None else t.to("cuda", dtype)
+
+
+MASKS = [lambda: S.blob_mask((14, 19, 37), 11, n=7), lambda: S.random_mask((9, 33, 35), 0.7, 3),
+         lambda: S.square_duct(5, 6), lambda: np.ones((4, 5, 3), np.uint8)]
+
+
+def _rand_flow(orc, m, seed):
+    w = orc.weights19()
+    return w[:, None, None, None] * (1 + 0.1 * S.random_field((19,) + m.shape, seed, -1, 1)) * m
+
+
+def _rand_diff(m, seed):
+    a = np.array([0.25] + [0.125] * 6)
+    c = S.random_field(m.shape, seed, 0.0, 1.0)
+    return a[:, None, None, None] * c[None] * (1 + 0.2 * S.random_field((7,) + m.shape, seed + 1, -1, 1)) * m
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("steps", [1, 2, 10])
+def test_batch_flow_steps_match_oracle(orc, om, prec, steps):
+    masks = [f() for f in MASKS]
+    P = om.OM_F64 if prec == "f64" else om.OM_F32
+    tau, g = 0.83, 3e-4
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks],
+                 flow=om.flow_params(tau=tau, body_force=g, precision=P))
+    f0 = [_rand_flow(orc, m, 7 * k + steps) for k, m in enumerate(masks)]
+    for k, f in enumerate(f0):
+        b.set_populations(0, k, _dev(f))
+    b.step(0, steps)
+    for k, m in enumerate(masks):
+        out = torch.empty(19 * m.size, dtype=torch.float64, device="cuda")
+        b.get_populations(0, k, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape((19,) + m.shape)
+        ref = orc.flow_step(m, f0[k], tau, g, steps)
+        dev = np.abs(f0[k] - orc.weights19()[:, None, None, None] * m).max()
+        tol = 1e-13 * steps if prec == "f64" else 64 * U32 * dev * steps + 1e-12
+        assert np.abs(got - ref).max() <= tol, k
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("steps", [1, 2, 10])
+def test_batch_diffusion_steps_match_oracle(orc, om, prec, steps):
+    masks = [f() for f in MASKS]
+    P = om.OM_F64 if prec == "f64" else om.OM_F32
+    ds = [(S.random_field(m.shape, 40 + k, 3.0, 90.0) * m).astype(np.float32) for k, m in enumerate(masks)]
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks], [_dev(d) for d in ds],
+                 diff=om.diff_params(c_in=0.9, c_out=0.2, precision=P))
+    g0 = [_rand_diff(m, 3 * k + steps) for k, m in enumerate(masks)]
+    for k, g in enumerate(g0):
+        b.set_populations(1, k, _dev(g))
+    b.step(1, steps)
+    for k, m in enumerate(masks):
+        out = torch.empty(7 * m.size, dtype=torch.float64, device="cuda")
+        b.get_populations(1, k, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape((7,) + m.shape)
+        ref = orc.diff_step(m, g0[k], orc.omega_field(m, ds[k]), 0.9, 0.2, steps)
+        tol = 1e-13 * steps if prec == "f64" else 64 * U32 * np.abs(g0[k]).max() * steps + 1e-12
+        assert np.abs(got - ref).max() <= tol, k
+
+
+def _structures(orc):
+    # reconstructed transport sets whose oracle solves converge in seconds
+    cfgs = [S.small_structure(s).with_(shape=shape) for s, shape in [(3, (16, 24, 20)), (10, (24, 16, 16)),
+                                                                    (11, (24, 16, 16))]]
+    out = []
+    for cfg in cfgs:
+        _, mask, *_ = orc.reconstruct(*recon_args(cfg))
+        _, tr, _ = orc.label18(mask)
+        d, _ = orc.chord13(mask, cfg.dx_nm, counts=False)
+        out.append((tr, d))
+    out.append((np.zeros((6, 7, 8), np.uint8), np.zeros((6, 7, 8), np.float32)))  # nothing percolates
+    return out
+
+
+@pytest.mark.timeout(900)
+def test_batch_solves_match_oracle(orc, om):
+    st = _structures(orc)
+    doms = [om.domain(t.shape, 2.0) for t, _ in st]
+    ref = []
+    for tr, d in st[:-1]:
+        rc1, kL, *_ = orc.flow_solve(tr, tau=1.0, g=1e-6, tol=1e-8, K=100, max_steps=200000)
+        rc2, D, *_ = orc.diff_solve(tr, orc.omega_field(tr, d), 1.0, 0.0, tol=1e-8, K=100, max_steps=400000)
+        assert rc1 == 0 and rc2 == 0
+        ref.append((kL, D))
+    # FP32 rounding puts a floor of ~1e-7 under the relative-change measures
+    # (sums of |du|, |dC| over all nodes); checking every 2000 steps against
+    # 1e-6 asks for a rate of change of 5e-10 per step, close to the
+    # oracle's 1e-10
+    for P, K, tol, rel in ((om.OM_F64, 100, 1e-8, 1e-9), (om.OM_F32, 2000, 1e-6, 1e-5)):
+        b = om.Batch(doms, [_dev(t) for t, _ in st], [_dev(d) for _, d in st],
+                     flow=om.flow_params(conv_tol=tol, check_every=K, max_steps=400000, precision=P),
+                     diff=om.diff_params(conv_tol=tol, check_every=K, max_steps=400000, precision=P))
+        kl, _, info_f, st_f = b.solve(0)
+        dl, mean_dl, info_d, st_d = b.solve(1)
+        assert st_f[-1] == om.OM_ENOPERC and st_d[-1] == om.OM_ENOPERC
+        steps = set()
+        for k, (kL, D) in enumerate(ref):
+            assert st_f[k] == om.OM_OK and st_d[k] == om.OM_OK
+            assert kl[k] == pytest.approx(kL, rel=rel)
+            assert dl[k] == pytest.approx(D, rel=rel)
+            steps.add(info_d[k].steps)
+        assert len(steps) > 1  # structures retire at their own check
+        b.close()
+
+
+@pytest.mark.timeout(300)
+def test_batch_matches_single_structure_solver(orc, om):
+    st = _structures(orc)[1:3]
+    doms = [om.domain(t.shape, 2.0) for t, _ in st]
+    b = om.Batch(doms, [_dev(t) for t, _ in st], flow=om.flow_params(conv_tol=1e-6))
+    kl, _, info, status = b.solve(0)
+    for k, (tr, _) in enumerate(st):
+        ns = om.NodeSet(_dev(tr), doms[k])
+        s1, k1, i1 = om.Flow(ns, om.flow_params(conv_tol=1e-6)).solve()
+        assert status[k] == om.OM_OK and s1 == om.OM_OK
+        assert kl[k] == pytest.approx(k1, rel=1e-6)
+        assert abs(info[k].steps - i1.steps) <= 100

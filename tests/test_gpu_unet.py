@@ -1,0 +1,85 @@
+"""The warm-start U-Net's CUDA kernels against the FP64 reference.
+
+The reference rounds inputs, weights and stored activations to BF16 where the
+CUDA path stores BF16, so both evaluate the same network; the remaining
+difference is FP32 accumulation (and BF16 rounding of the backward pass's
+operands), which bounds the tolerances: a stored activation that rounds to
+the neighbouring BF16 value on one side moves by 2^-8 relative, and such
+flips compound over the network's ~16 layers, so outputs are compared within
+3 % of their scale element-wise and 1 % on average; gradients within 5 % in
+L2 per parameter tensor with cosine similarity above 0.995 (BF16 gradient
+operands carry 2^-9 relative rounding each)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(shape, in_ch, out_ch, seed):
+    g = torch.Generator().manual_seed(seed)
+    B, D, H, W = shape
+    zz, yy, xx = torch.meshgrid(torch.linspace(0, 1, D), torch.linspace(0, 1, H), torch.linspace(0, 1, W),
+                                indexing="ij")
+    x = torch.rand(B, D, H, W, in_ch, generator=g)
+    x[..., 0] = (x[..., 0] > 0.4).float()
+    t = torch.stack([torch.sin(3 * zz + 2 * xx) * yy, xx * (1 - xx)], -1)[None].expand(B, D, H, W, 2)[..., :out_ch]
+    m = (x[..., 0] > 0).to(torch.uint8)
+    return x.contiguous(), t.contiguous(), m.contiguous()
+
+
+@pytest.mark.parametrize("ch,shape", [((16, 32), (1, 16, 16, 16)), ((16, 32, 64, 128), (1, 16, 24, 32)),
+                                      ((32, 48), (2, 8, 12, 16))])
+def test_unet_forward_and_gradients_match_reference(om, ch, shape):
+    from oracle import unet as R
+    in_ch, out_ch = 2, 2
+    net = om.UNet(in_ch, out_ch, ch, seed=7)
+    n = net.n_params
+    flat = torch.empty(n, dtype=torch.float32, device="cuda")
+    net.get_params(flat)
+    x, t, m = _case(shape, in_ch, out_ch, 3)
+    y = torch.empty(*shape, out_ch, dtype=torch.float32, device="cuda")
+    net.forward(x.cuda(), y)
+    loss = net.backward(x.cuda(), t.cuda(), m.cuda())
+    grads = torch.empty(n, dtype=torch.float32, device="cuda")
+    net.get_grads(grads)
+    torch.cuda.synchronize()
+    ref_loss, ref_grad, ref_y = R.loss_and_grads(flat.cpu().double(), x.double(), t.double(), m, in_ch, out_ch, ch,
+                                                 round_bf16=True)
+    yg = y.cpu().double()
+    scale = ref_y.abs().max().item()
+    assert (yg - ref_y).abs().max().item() <= 3e-2 * scale
+    assert (yg - ref_y).abs().mean().item() <= 1e-2 * ref_y.abs().mean().item()
+    assert loss == pytest.approx(ref_loss, rel=2e-2)
+    gg = grads.cpu().double()
+    off = 0
+    for name, shp in R.layout(in_ch, out_ch, ch):
+        k = int(np.prod(shp))
+        a, b = gg[off:off + k], ref_grad[off:off + k]
+        off += k
+        if b.norm() < 1e-12 * ref_grad.norm():
+            continue  # e.g. weights of the zero-padded input channels
+        if name == "enc0.1.w":  # only the first in_ch input channels carry signal
+            a = a.reshape(27, 16, -1)[:, :in_ch].reshape(-1)
+            b = b.reshape(27, 16, -1)[:, :in_ch].reshape(-1)
+        rel = ((a - b).norm() / b.norm()).item()
+        cos = (torch.dot(a, b) / (a.norm() * b.norm())).item()
+        assert rel <= 5e-2 and cos >= 0.995, (name, rel, cos)
+
+
+def test_unet_training_reduces_loss(om):
+    net = om.UNet(2, 2, (16, 32, 64), seed=11)
+    x, t, m = _case((2, 16, 16, 16), 2, 2, 5)
+    x, t, m = x.cuda(), t.cuda(), m.cuda()
+    first = net.train_step(x, t, m, 2e-3)
+    for _ in range(80):
+        last = net.train_step(x, t, m, 2e-3)
+    assert last < 0.3 * first
+
+
+def test_unet_rejects_bad_shapes(om):
+    net = om.UNet(2, 2, (16, 32, 64), seed=1)
+    x = torch.zeros(1, 10, 16, 16, 2, device="cuda")
+    y = torch.zeros(1, 10, 16, 16, 2, device="cuda")
+    with pytest.raises(om.OmError):
+        net.forward(x, y)  # 10 is not a multiple of 4
