@@ -45,7 +45,8 @@ typedef enum {
   OM_ENOMEM = 2,         /* device or host allocation failed */
   OM_ECUDA = 3,          /* a CUDA call failed; see om_last_error() */
   OM_EINFEASIBLE = 4,    /* reconstruction: trial cap hit before the porosity */
-  OM_ENOPERC = 5,        /* no transport pore spans x = 0 .. nx-1 */
+  OM_ENOPERC = 5,        /* no transport pore spans x = 0 .. nx-1; flow: or no
+                          * lattice link crosses the periodic x boundary */
   OM_ENOTCONVERGED = 6,  /* step cap hit; outputs hold the last check */
   OM_ETIMEOUT = 7        /* a bounded device wait gave up */
 } om_status;
@@ -81,7 +82,12 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
-  int32_t variant; /* sweep launch variant: -1 = time them at creation, keep the fastest */
+  /* sweep launch variant, the same arithmetic in every one: -1 = time them
+   * all at creation and keep the fastest per parity; 0..4 = force one (0/1
+   * one thread per node without/with a register cap, 2/3 the same on a
+   * resident grid striding over nodes, 4 a tighter cap); larger values
+   * clamp to 4 */
+  int32_t variant;
 } om_flow_params;
 
 /* D3Q7 Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
@@ -93,7 +99,7 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
-  int32_t variant; /* as om_flow_params.variant */
+  int32_t variant; /* as om_flow_params.variant, 0..3 (larger values clamp to 3) */
 } om_diff_params;
 
 typedef struct {
@@ -167,7 +173,10 @@ om_status om_local_pore_diameter_dev(const uint8_t* mask_dev, om_domain d, int32
  * x, y, z, halfway bounce-back at walls, to convergence.
  * k_m2 = k_lattice * dx^2 (Eq. 15), k_lattice = nu <u_x> / g with <.> over
  * all N voxels.  ux_out (nullable, host float N): u_x, 0 off the node set.
- * info (nullable).  OM_ENOPERC when no pore spans the box. */
+ * info (nullable).  OM_ENOPERC when no pore spans the box, or when no
+ * D3Q19 link joins a node at x = nx-1 to one at x = 0: the periodic x
+ * boundary is then a wall, the steady net flux is zero, and k_m2 and
+ * k_lattice are set to 0 without stepping. */
 om_status om_solve_permeability(const uint8_t* mask, om_domain d, const om_flow_params* params,
                                 double* k_m2, double* k_lattice, om_run_info* info, float* ux_out);
 
@@ -213,7 +222,9 @@ om_status om_flow_step(om_flow* fl, int64_t nsteps, void* stream);
  * out[1] sum |u_x - u_x at the previous observe|, out[2] sum |u_x|,
  * out[3] sum (rho - 1).  Host out, synchronises. */
 om_status om_flow_observe(om_flow* fl, double* out, void* stream);
-/* run to convergence (om_flow_params) from the current state */
+/* Run to convergence (om_flow_params) from the current state.  OM_ENOPERC
+ * (k_lattice = 0, no steps) when no lattice link crosses the periodic x
+ * boundary: the net flux then vanishes at steady state. */
 om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* info, void* stream);
 /* populations at the current time in the dense layout f[i*N + voxel],
  * i in the order of the App. A transformation matrix, 0 off the node set.
@@ -262,8 +273,9 @@ om_status om_batch_step(om_batch* b, int32_t model, int64_t nsteps, void* stream
  * result = k_lattice (flow) or D_eff,L (diffusion); aux (nullable) = sum of
  * (rho - 1) (flow) or the mean lattice diffusivity over nodes (diffusion);
  * info (nullable; seconds and mlups are those of the whole batch); status
- * (nullable) = OM_OK, OM_ENOTCONVERGED or OM_ENOPERC (no nodes) per
- * structure.  Returns OM_OK unless a call fails. */
+ * (nullable) = OM_OK, OM_ENOTCONVERGED or OM_ENOPERC (no nodes; flow: or
+ * no link across the periodic x boundary, result 0) per structure.  Returns
+ * OM_OK unless a call fails. */
 om_status om_batch_solve(om_batch* b, int32_t model, double* result, double* aux, om_run_info* info,
                          int32_t* status, void* stream);
 /* populations of structure `item` in the dense layout of om_flow_get_populations /

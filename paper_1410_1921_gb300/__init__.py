@@ -347,7 +347,7 @@ class Flow:
         kl = C.c_double()
         info = om_run_info()
         st = _call("om_flow_solve", self.h, C.byref(kl), C.byref(info), _stream(stream),
-                   ok=(OM_OK, OM_ENOTCONVERGED))
+                   ok=(OM_OK, OM_ENOTCONVERGED, OM_ENOPERC))
         return st, kl.value, info
 
     def get_populations(self, out_dev, stream=None):

@@ -268,7 +268,7 @@ __global__ void flow_batch_init(FlowArgs<T> a, uint32_t off, const int64_t* vox,
                                 double scale) {
   const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
   if (ln >= a.nf) return;
-  const double u = scale * (double)field[vox[ln] * stride];
+  const double u = warm_velocity(scale * (double)field[vox[ln] * stride]);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const double eu = (double)q19_e(i, 0) * u;
@@ -284,7 +284,8 @@ __global__ void diff_batch_init(DiffArgs<T> a, uint32_t off, const int64_t* vox,
   int x, y, z;
   unpack_xyz(a.coord[ln], x, y, z);
   const double clin = a.cin + (double)a.s * ((double)x + 0.5);
-  const double cv = (double)field[vox[ln] * stride] + (from_linear ? clin : 0.0);
+  const double cv =
+      warm_concentration((double)field[vox[ln] * stride] + (from_linear ? clin : 0.0), clin, a.cin, a.cout);
   double dc = cv - clin;
   if constexpr (kRebased<T>) {
     a.cr[off + ln] = (float)cv;
@@ -567,7 +568,8 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
     if (info) info[k] = om_run_info{};
     if (result) result[k] = 0.0;
     if (aux) aux[k] = 0.0;
-    if (b->items_h[k].nf > 0) active.push_back(k);
+    // flow: no lattice link across the periodic x boundary means zero flux
+    if (b->items_h[k].nf > 0 && (model == 1 || b->ns[k]->wrap_links > 0)) active.push_back(k);
   }
   std::vector<double> sj_prev(b->n, 0.0);
   int nw = build_work(b, active);
@@ -616,8 +618,10 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
         info[it].mass = o[3];
       }
       const bool done = rel < tol;
-      if (status) status[it] = done ? OM_OK : OM_ENOTCONVERGED;
-      if (!done) keep.push_back(it);
+      // non-finite sums: the item diverged; it leaves the batch unconverged
+      const bool diverged = !std::isfinite(o[0]) || !std::isfinite(o[2]);
+      if (status) status[it] = done && !diverged ? OM_OK : OM_ENOTCONVERGED;
+      if (!done && !diverged) keep.push_back(it);
     }
     if (keep.size() != active.size()) {
       active.swap(keep);

@@ -113,6 +113,23 @@ __host__ __device__ inline void unpack_xyz(uint32_t c, int& x, int& y, int& z) {
 constexpr int kObsBlocks = 1216;  // 8 x 152 SMs: fixed grid of reductions
 constexpr int kObsThreads = 256;
 
+// Blocks of `threads` threads of `kernel` that fit on the device at once
+// (SMs x resident blocks per SM), capped at nb: the grid of a kernel whose
+// threads stride over their work.  Cached per kernel and device.
+template <class K>
+inline unsigned resident_grid(K kernel, unsigned nb, int threads = 256) {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cache[dev] <= 0) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+    cache[dev] = sms * per > 0 ? sms * per : 1;
+  }
+  return nb < (unsigned)cache[dev] ? nb : (unsigned)cache[dev];
+}
+
 om_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total_dev,
                              cudaStream_t s);
 // sum the per-block partials [nblk][nval] in fixed order into out[nval]
@@ -130,4 +147,5 @@ struct om_nodeset {
   uint2* col = nullptr;       // [nx*ny*W]: {node bits, nodes before this word}
   uint32_t* coord = nullptr;  // [nf] packed x, y, z
   int64_t* vox = nullptr;     // [nf] voxel index
+  int64_t wrap_links = 0;     // D3Q19 links from node voxels at x = nx-1 to node voxels at x = 0
 };

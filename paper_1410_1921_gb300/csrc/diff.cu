@@ -21,15 +21,36 @@
 
 namespace om {
 
-// Launch variants for the autotuner of om_diff_create (identical arithmetic):
-// 0 = registers as the compiler wants, 1 = capped for 8 resident blocks.
-constexpr int kDiffVariants = 2;
+// Launch variants for the autotuner of om_diff_create (identical
+// arithmetic): 0 = one thread per node, registers as the compiler wants;
+// 1 = capped for 8 resident blocks; 2, 3 = the same on a resident grid whose
+// threads stride over nodes, loading the next node's coordinates before
+// updating the current one (the flow sweep's variants 2 and 3).
+constexpr int kDiffVariants = 4;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q7_sweep(DiffArgs<T> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   diff_node<T, ODD>(a, n, n);
+}
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q7_sweep_strided(DiffArgs<T> a) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  uint32_t c = ODD ? __ldg(a.coord + n) : 0u;
+  for (;;) {
+    const uint64_t nn = (uint64_t)n + stride;
+    const bool more = nn < a.nf;
+    uint32_t cn = 0u;
+    if (ODD && more) cn = __ldg(a.coord + nn);
+    diff_node_at<T, ODD>(a, n, c);
+    if (!more) break;
+    n = (uint32_t)nn;
+    c = cn;
+  }
 }
 
 // Observables: sum J_x, sum |C - prev|, sum |C|, sum C, sum D_L; prev <- C.
@@ -121,7 +142,7 @@ __global__ void d3q7_init_c(DiffArgs<T> a, const int64_t* vox, const float* c, i
   int x, y, z;
   unpack_xyz(a.coord[n], x, y, z);
   const double clin = a.cin + (double)a.s * ((double)x + 0.5);
-  const double cv = (double)c[vox[n] * stride] + (from_linear ? clin : 0.0);
+  const double cv = warm_concentration((double)c[vox[n] * stride] + (from_linear ? clin : 0.0), clin, a.cin, a.cout);
   double dc;
   if constexpr (kRebased<T>) {
     a.cr[n] = (float)cv;
@@ -200,15 +221,28 @@ DiffArgs<T> diff_args(const om_diff* df) {
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+template <class T, bool ODD>
+void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const DiffArgs<T>& a) {
+  switch (variant) {
+    case 1: d3q7_sweep<T, ODD, 8><<<nb, 256, 0, s>>>(a); break;
+    case 2: {
+      auto k = d3q7_sweep_strided<T, ODD, 0>;
+      k<<<resident_grid(k, nb), 256, 0, s>>>(a);
+      break;
+    }
+    case 3: {
+      auto k = d3q7_sweep_strided<T, ODD, 8>;
+      k<<<resident_grid(k, nb), 256, 0, s>>>(a);
+      break;
+    }
+    default: d3q7_sweep<T, ODD, 0><<<nb, 256, 0, s>>>(a); break;
+  }
+}
+
 template <class T>
 void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const DiffArgs<T>& a) {
-  if (variant == 1) {
-    if (odd) d3q7_sweep<T, true, 8><<<nb, 256, 0, s>>>(a);
-    else d3q7_sweep<T, false, 8><<<nb, 256, 0, s>>>(a);
-  } else {
-    if (odd) d3q7_sweep<T, true, 0><<<nb, 256, 0, s>>>(a);
-    else d3q7_sweep<T, false, 0><<<nb, 256, 0, s>>>(a);
-  }
+  if (odd) launch_sweep_p<T, true>(variant, nb, s, a);
+  else launch_sweep_p<T, false>(variant, nb, s, a);
 }
 
 // Capture K sweeps (K even, from an even time) into a CUDA graph once.
@@ -467,12 +501,17 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
   OM_CUDA(cudaEventRecord(e0, s));
   om_status rc = OM_ENOTCONVERGED;
   double rel = 1.0;
+  bool diverged = false;
   while (df->t - t0 < p.max_steps) {
     int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (df->t - t0));
     OM_TRY(om_diff_step(df, k, stream));
     OM_TRY(diff_observe_any(df, o, s));
     // converged when both the concentration field and the total flux have
     // settled: C can sit at its final profile while the flux still relaxes
+    if (!std::isfinite(o[0]) || !std::isfinite(o[2])) {
+      diverged = true;
+      break;
+    }
     rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
     const double relj = o[0] != 0.0 ? std::fabs(o[0] - sj_prev) / std::fabs(o[0]) : 0.0;
     rel = std::max(rel, relj);
@@ -499,7 +538,8 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
     info->seconds = ms * 1e-3;
     info->mlups = ms > 0 ? (double)ns->nf * (double)info->steps / (ms * 1e-3) / 1e6 : 0.0;
   }
-  if (rc != OM_OK) set_error("om_diff_solve: step cap reached before convergence");
+  if (diverged) set_error("om_diff_solve: the populations diverged (non-finite concentration sums)");
+  else if (rc != OM_OK) set_error("om_diff_solve: step cap reached before convergence");
   return rc;
 }
 

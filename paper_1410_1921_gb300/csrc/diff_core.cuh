@@ -41,18 +41,41 @@ __device__ __forceinline__ void diff_neighbours(const DiffArgs<T>& a, uint32_t c
   unpack_xyz(c, x, y, z);
   const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
   const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
-  nb[1] = x + 1 < a.nx ? node_at(a.col, a.ny, a.W, x + 1, y, z) : kNoNode;
-  nb[2] = x > 0 ? node_at(a.col, a.ny, a.W, x - 1, y, z) : kNoNode;
-  nb[3] = node_at(a.col, a.ny, a.W, x, yp, z);
-  nb[4] = node_at(a.col, a.ny, a.W, x, ym, z);
-  nb[5] = node_at(a.col, a.ny, a.W, x, y, zp);
-  nb[6] = node_at(a.col, a.ny, a.W, x, y, zm);
+  const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
+  auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
+  uint32_t self;
+  column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
+  nb[1] = x + 1 < a.nx ? column1(a.col, base(x + 1, y), z) : kNoNode;
+  nb[2] = x > 0 ? column1(a.col, base(x - 1, y), z) : kNoNode;
+  nb[3] = column1(a.col, base(x, yp), z);
+  nb[4] = column1(a.col, base(x, ym), z);
+  (void)self;
 }
 
-// pre-collision deviations of node n at the current time
+// Reference concentrations an odd step needs (rebased storage): the node's
+// own, and each neighbour's (0 where there is none).  Read once into
+// registers: the stores of the step could alias them for the compiler.
+template <class T>
+struct DiffRefs {
+  typename Stg<T>::C n, nb[7];
+};
+
+template <class T>
+__device__ __forceinline__ void diff_refs(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7],
+                                          DiffRefs<T>& r) {
+  using C = typename Stg<T>::C;
+  if constexpr (kRebased<T>) {
+    r.n = a.cr[n];
+#pragma unroll
+    for (int i = 1; i < 7; ++i) r.nb[i] = nb[i] != kNoNode ? (C)a.cr[nb[i]] : C(0);
+  }
+}
+
+// pre-collision deviations of node n at the current time (odd steps: with
+// the reference concentrations r of diff_refs)
 template <class T, bool ODD>
-__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7],
-                                          int x, typename Stg<T>::C (&g)[7]) {
+__device__ __forceinline__ void diff_load_r(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7], int x,
+                                            const DiffRefs<T>& r, typename Stg<T>::C (&g)[7]) {
   using S = Stg<T>;
   using C = typename S::C;
 #pragma unroll
@@ -66,10 +89,9 @@ __device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, cons
       const T* p = (src != kNoNode && !inlet && !outlet) ? a.q[o] + src : a.q[i] + n;
       const C v = S::ld(p, a.down);
       if constexpr (kRebased<T>) {
-        const C rn = a.cr[n];
-        if (inlet) g[i] = -v + C(0.25) * ((C)a.cin - rn);
-        else if (outlet) g[i] = -v + C(0.25) * ((C)a.cout - rn);
-        else if (src != kNoNode) g[i] = v + C(q7_w(i)) * (a.cr[src] - rn);
+        if (inlet) g[i] = -v + C(0.25) * ((C)a.cin - r.n);
+        else if (outlet) g[i] = -v + C(0.25) * ((C)a.cout - r.n);
+        else if (src != kNoNode) g[i] = v + C(q7_w(i)) * (r.nb[o] - r.n);
         else g[i] = v;
       } else {
         if (inlet) g[i] = -v - C(0.125) * a.s;
@@ -81,25 +103,36 @@ __device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, cons
   }
 }
 
-
-// One fused collide-stream update of node n (global slot index, coordinates
-// coord[ln]); the AA read/write pattern of flow_node with the anti-bounce-back
-// inlet/outlet and the C_lin reference shift.
 template <class T, bool ODD>
-__device__ __forceinline__ void diff_node(const DiffArgs<T>& a, uint32_t n, uint32_t ln) {
+__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7], int x,
+                                          typename Stg<T>::C (&g)[7]) {
+  DiffRefs<T> r{};
+  if (ODD) diff_refs(a, n, nb, r);
+  diff_load_r<T, ODD>(a, n, nb, x, r, g);
+}
+
+// One fused collide-stream update of node n (global slot index) with packed
+// coordinates c (read on odd steps only); the AA read/write pattern of
+// flow_node_at with the anti-bounce-back inlet/outlet and the reference shift.
+template <class T, bool ODD>
+__device__ __forceinline__ void diff_node_at(const DiffArgs<T>& a, uint32_t n, uint32_t c) {
   using S = Stg<T>;
   using C = typename S::C;
   uint32_t nb[7];
   int x = 0;
-  if (ODD) diff_neighbours(a, a.coord[ln], nb, x);
+  DiffRefs<T> r{};
+  if (ODD) {
+    diff_neighbours(a, c, nb, x);
+    diff_refs(a, n, nb, r);
+  }
   C g[7];
-  diff_load<T, ODD>(a, n, nb, x, g);
+  diff_load_r<T, ODD>(a, n, nb, x, r, g);
   const C om = a.omega[n];
-  C c = g[0];
+  C cc = g[0];
 #pragma unroll
-  for (int i = 1; i < 7; ++i) c += g[i];
+  for (int i = 1; i < 7; ++i) cc += g[i];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) g[i] = g[i] - om * (g[i] - C(q7_w(i)) * c);
+  for (int i = 0; i < 7; ++i) g[i] = g[i] - om * (g[i] - C(q7_w(i)) * cc);
 #pragma unroll
   for (int i = 0; i < 7; ++i) {
     const int o = q7_opp(i);
@@ -112,12 +145,11 @@ __device__ __forceinline__ void diff_node(const DiffArgs<T>& a, uint32_t n, uint
       T* p = a.q[o] + n;
       C v = g[i];
       if constexpr (kRebased<T>) {
-        const C rn = a.cr[n];
-        if (outlet) v = -g[i] + C(0.25) * ((C)a.cout - rn);
-        else if (inlet) v = -g[i] + C(0.25) * ((C)a.cin - rn);
+        if (outlet) v = -g[i] + C(0.25) * ((C)a.cout - r.n);
+        else if (inlet) v = -g[i] + C(0.25) * ((C)a.cin - r.n);
         else if (nb[i] != kNoNode) {
           p = a.q[i] + nb[i];
-          v = g[i] + C(q7_w(i)) * (rn - a.cr[nb[i]]);
+          v = g[i] + C(q7_w(i)) * (r.n - r.nb[i]);
         }
       } else {
         if (outlet) v = -g[i] + C(0.125) * a.s;
@@ -130,6 +162,12 @@ __device__ __forceinline__ void diff_node(const DiffArgs<T>& a, uint32_t n, uint
       S::st(p, v, a.up);
     }
   }
+}
+
+// diff_node_at for node n whose coordinates are coord[ln]
+template <class T, bool ODD>
+__device__ __forceinline__ void diff_node(const DiffArgs<T>& a, uint32_t n, uint32_t ln) {
+  diff_node_at<T, ODD>(a, n, ODD ? a.coord[ln] : 0u);
 }
 
 // Reference concentration of node n (with coordinates x): C_lin(x) or Cr[n]

@@ -22,24 +22,49 @@
 // the node's own slot i and writes its own slot opposite(i).  x, y and z
 // are periodic (body-force driving).
 #include <algorithm>
+#include <cmath>
 
 #include "flow_core.cuh"
 
 namespace om {
 
-// Launch variants (chosen per parity by the autotuner of om_flow_create):
-// variant 0 leaves registers to the compiler (no residency hint); variant 1 caps them
-// (256 threads x MINB blocks resident per SM) for more latency hiding at the
-// cost of a few spills.  Both do identical arithmetic.
+// Launch variants (chosen per parity by the autotuner of om_flow_create),
+// all doing identical arithmetic:
+//   0  one thread per node, registers left to the compiler;
+//   1  one thread per node, registers capped so MINB blocks of 256 threads
+//      stay resident per SM (more latency hiding, a few spills);
+//   2  a grid of resident blocks only, each thread striding over nodes and
+//      loading the next node's coordinates before updating the current one,
+//      so that load's latency overlaps the update (odd steps);
+//   3  variant 2 with the register cap of variant 1;
+//   4  one thread per node with a tighter cap (MINB + 1 blocks).
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
-constexpr int kSweepVariants = 2;
+constexpr int kSweepVariants = 5;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   flow_node<T, ODD>(a, n, n);
+}
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q19_sweep_strided(FlowArgs<T> a) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  uint32_t c = ODD ? __ldg(a.coord + n) : 0u;
+  for (;;) {
+    const uint64_t nn = (uint64_t)n + stride;
+    const bool more = nn < a.nf;
+    uint32_t cn = 0u;
+    if (ODD && more) cn = __ldg(a.coord + nn);
+    flow_node_at<T, ODD>(a, n, c);
+    if (!more) break;
+    n = (uint32_t)nn;
+    c = cn;
+  }
 }
 
 // Observables (FP64, fixed grid): sum u_x, sum |u_x - prev|, sum |u_x|,
@@ -114,7 +139,7 @@ template <class T>
 __global__ void d3q19_init_u(FlowArgs<T> a, const int64_t* vox, const float* ux, int64_t stride, double scale) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
-  const double u = scale * (double)ux[vox[n] * stride];
+  const double u = warm_velocity(scale * (double)ux[vox[n] * stride]);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const double eu = (double)q19_e(i, 0) * u;
@@ -176,15 +201,30 @@ FlowArgs<T> flow_args(const om_flow* fl) {
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+template <class T, bool ODD>
+void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>& a) {
+  constexpr int M = kMinBlocks1<T>;
+  switch (variant) {
+    case 1: d3q19_sweep<T, ODD, M><<<nb, 256, 0, s>>>(a); break;
+    case 2: {
+      auto k = d3q19_sweep_strided<T, ODD, 0>;
+      k<<<resident_grid(k, nb), 256, 0, s>>>(a);
+      break;
+    }
+    case 3: {
+      auto k = d3q19_sweep_strided<T, ODD, M>;
+      k<<<resident_grid(k, nb), 256, 0, s>>>(a);
+      break;
+    }
+    case 4: d3q19_sweep<T, ODD, M + 1><<<nb, 256, 0, s>>>(a); break;
+    default: d3q19_sweep<T, ODD, 0><<<nb, 256, 0, s>>>(a); break;
+  }
+}
+
 template <class T>
 void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>& a) {
-  if (variant == 1) {
-    if (odd) d3q19_sweep<T, true, kMinBlocks1<T>><<<nb, 256, 0, s>>>(a);
-    else d3q19_sweep<T, false, kMinBlocks1<T>><<<nb, 256, 0, s>>>(a);
-  } else {
-    if (odd) d3q19_sweep<T, true, 0><<<nb, 256, 0, s>>>(a);
-    else d3q19_sweep<T, false, 0><<<nb, 256, 0, s>>>(a);
-  }
+  if (odd) launch_sweep_p<T, true>(variant, nb, s, a);
+  else launch_sweep_p<T, false>(variant, nb, s, a);
 }
 
 // Capture K sweeps (K even, from an even time) into a CUDA graph once.
@@ -416,6 +456,16 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
   if (p.check_every <= 0 || (p.check_every & 1))
     return fail(OM_EINVAL, "om_flow_solve: check_every must be a positive even number");
   if (!(p.body_force != 0.0)) return fail(OM_EINVAL, "om_flow_solve: body_force must be nonzero");
+  if (fl->ns->wrap_links == 0) {
+    // x is periodic for the flow: with no lattice link across the x boundary
+    // it is a wall, and the steady net flux (hence k) is exactly zero
+    if (k_lattice) *k_lattice = 0.0;
+    if (info) {
+      *info = om_run_info{};
+      info->n_nodes = fl->ns->nf;
+    }
+    return fail(OM_ENOPERC, "om_flow_solve: no pore link crosses the periodic x boundary (k = 0)");
+  }
   cudaStream_t s = as_stream(stream);
   cudaEvent_t e0, e1;
   OM_CUDA(cudaEventCreate(&e0));
@@ -426,10 +476,15 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
   OM_CUDA(cudaEventRecord(e0, s));
   om_status rc = OM_ENOTCONVERGED;
   double rel = 1.0;
+  bool diverged = false;
   while (fl->t - t0 < p.max_steps) {
     int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (fl->t - t0));
     OM_TRY(om_flow_step(fl, k, stream));
     OM_TRY(flow_observe_any(fl, o, s));
+    if (!std::isfinite(o[0]) || !std::isfinite(o[2])) {
+      diverged = true;
+      break;
+    }
     rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
     if (rel < p.conv_tol) {
       rc = OM_OK;
@@ -452,7 +507,8 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
     info->seconds = ms * 1e-3;
     info->mlups = ms > 0 ? (double)fl->ns->nf * (double)info->steps / (ms * 1e-3) / 1e6 : 0.0;
   }
-  if (rc != OM_OK) set_error("om_flow_solve: step cap reached before convergence");
+  if (diverged) set_error("om_flow_solve: the populations diverged (non-finite velocity sums)");
+  else if (rc != OM_OK) set_error("om_flow_solve: step cap reached before convergence");
   return rc;
 }
 

@@ -20,39 +20,6 @@ struct FlowArgs {
   typename Stg<T>::C wp, wm, g, up, down;
 };
 
-// Node numbers of the voxels z-1, z, z+1 of one (x, y) column.  The three
-// usually share one 32-voxel word of the column map, so one load and a
-// popcount serve all of them; a neighbour across a word edge or the periodic
-// wrap takes its own word.
-__device__ __forceinline__ void column3(const uint2* __restrict__ col, uint32_t base, int z, int zp, int zm,
-                                        uint32_t& rm, uint32_t& r0, uint32_t& rp) {
-  const int zb = z & 31;
-  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
-  const uint32_t b0 = (w.x >> zb) & 1u;
-  const uint32_t rank0 = w.y + __popc(w.x & ((1u << zb) - 1u));
-  r0 = b0 ? rank0 : kNoNode;
-  if (zb != 31 && zp == z + 1) {
-    rp = ((w.x >> (zb + 1)) & 1u) ? rank0 + b0 : kNoNode;
-  } else {
-    const uint2 v = __ldg(col + base + ((uint32_t)zp >> 5));
-    const uint32_t bit = 1u << (zp & 31);
-    rp = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
-  }
-  if (zb != 0 && zm == z - 1) {
-    rm = ((w.x >> (zb - 1)) & 1u) ? rank0 - 1u : kNoNode;
-  } else {
-    const uint2 v = __ldg(col + base + ((uint32_t)zm >> 5));
-    const uint32_t bit = 1u << (zm & 31);
-    rm = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
-  }
-}
-
-__device__ __forceinline__ uint32_t column1(const uint2* __restrict__ col, uint32_t base, int z) {
-  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
-  const uint32_t bit = 1u << (z & 31);
-  return (w.x & bit) ? w.y + __popc(w.x & (bit - 1u)) : kNoNode;
-}
-
 // nb[i] = node number of x + e_i (kNoNode off the node set); periodic x, y, z
 template <class T>
 __device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c, uint32_t (&nb)[19]) {
@@ -125,17 +92,18 @@ __device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
 }
 
 
-// One fused collide-stream update of node n (global slot index) whose
-// coordinates are coord[ln].  Even steps: read and write the node's own slots
-// (post-collision f*_i to slot opposite(i)).  Odd steps: read slot
-// opposite(i) of x - e_i, write slot i of x + e_i; a missing neighbour is
-// halfway bounce-back (own slot i read, own slot opposite(i) written).
+// One fused collide-stream update of node n (global slot index) with packed
+// coordinates c (read on odd steps only).  Even steps: read and write the
+// node's own slots (post-collision f*_i to slot opposite(i)).  Odd steps:
+// read slot opposite(i) of x - e_i, write slot i of x + e_i; a missing
+// neighbour is halfway bounce-back (own slot i read, own slot opposite(i)
+// written).
 template <class T, bool ODD>
-__device__ __forceinline__ void flow_node(const FlowArgs<T>& a, uint32_t n, uint32_t ln) {
+__device__ __forceinline__ void flow_node_at(const FlowArgs<T>& a, uint32_t n, uint32_t c) {
   using S = Stg<T>;
   using C = typename S::C;
   uint32_t nb[19];
-  if (ODD) flow_neighbours(a, a.coord[ln], nb);
+  if (ODD) flow_neighbours(a, c, nb);
   C f[19];
   flow_load<T, ODD>(a, n, nb, f);
   trt_collide(f, a.wp, a.wm, a.g);
@@ -150,6 +118,12 @@ __device__ __forceinline__ void flow_node(const FlowArgs<T>& a, uint32_t n, uint
     }
     S::st(p, f[i], a.up);
   }
+}
+
+// flow_node_at for node n whose coordinates are coord[ln]
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_node(const FlowArgs<T>& a, uint32_t n, uint32_t ln) {
+  flow_node_at<T, ODD>(a, n, ODD ? a.coord[ln] : 0u);
 }
 
 }  // namespace om

@@ -55,6 +55,51 @@ __device__ __forceinline__ uint32_t node_at(const uint2* __restrict__ col, int n
   return (b.x & bit) ? b.y + __popc(b.x & (bit - 1u)) : kNoNode;
 }
 
+// Node numbers of the voxels z-1, z, z+1 of one (x, y) column.  The three
+// usually share one 32-voxel word of the column map, so one load and a
+// popcount serve all of them; a neighbour across a word edge or the periodic
+// wrap takes its own word.
+__device__ __forceinline__ void column3(const uint2* __restrict__ col, uint32_t base, int z, int zp, int zm,
+                                        uint32_t& rm, uint32_t& r0, uint32_t& rp) {
+  const int zb = z & 31;
+  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
+  const uint32_t b0 = (w.x >> zb) & 1u;
+  const uint32_t rank0 = w.y + __popc(w.x & ((1u << zb) - 1u));
+  r0 = b0 ? rank0 : kNoNode;
+  if (zb != 31 && zp == z + 1) {
+    rp = ((w.x >> (zb + 1)) & 1u) ? rank0 + b0 : kNoNode;
+  } else {
+    const uint2 v = __ldg(col + base + ((uint32_t)zp >> 5));
+    const uint32_t bit = 1u << (zp & 31);
+    rp = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
+  }
+  if (zb != 0 && zm == z - 1) {
+    rm = ((w.x >> (zb - 1)) & 1u) ? rank0 - 1u : kNoNode;
+  } else {
+    const uint2 v = __ldg(col + base + ((uint32_t)zm >> 5));
+    const uint32_t bit = 1u << (zm & 31);
+    rm = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
+  }
+}
+
+__device__ __forceinline__ uint32_t column1(const uint2* __restrict__ col, uint32_t base, int z) {
+  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
+  const uint32_t bit = 1u << (z & 31);
+  return (w.x & bit) ? w.y + __popc(w.x & (bit - 1u)) : kNoNode;
+}
+
+// Warm-start fields come from outside the solver (a network's output).  A
+// non-finite value falls back to the cold start; a velocity is kept inside
+// the low-Mach range the lattice is stable in; a concentration inside
+// [min(c_in, c_out), max(c_in, c_out)], where the steady state lies (maximum
+// principle: no sources, Dirichlet ends, no-flux walls).
+__device__ __forceinline__ double warm_velocity(double u) {
+  return isfinite(u) ? fmin(fmax(u, -0.1), 0.1) : 0.0;
+}
+__device__ __forceinline__ double warm_concentration(double c, double clin, double cin, double cout) {
+  return isfinite(c) ? fmin(fmax(c, fmin(cin, cout)), fmax(cin, cout)) : clin;
+}
+
 // Fixed-grid block reduction of NV doubles into partials[blockIdx.x][NV].
 template <int NV>
 __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* partials) {

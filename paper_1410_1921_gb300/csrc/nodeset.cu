@@ -47,6 +47,29 @@ __global__ void ns_fill(const uint32_t* bits, const uint32_t* rank, int ny, int 
   }
 }
 
+// Links of the flow lattice across the periodic x boundary: node voxels
+// (nx-1, y, z) whose neighbour (0, y + dy, z + dz), |dy| + |dz| <= 1, along
+// one of the five velocities with e_x = +1, is a node voxel (y, z periodic).
+// Without any, the x wrap is a wall for the flow and its steady net flux is
+// zero.
+__global__ void ns_wrap_links(const uint8_t* nodes, int nx, int ny, int nz, unsigned long long* count) {
+  const int64_t plane = (int64_t)ny * nz;
+  const uint8_t* last = nodes + (int64_t)(nx - 1) * plane;
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!last[i]) continue;
+    const int y = (int)(i / nz), z = (int)(i - (int64_t)y * nz);
+    const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+    const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+    c += nodes[(int64_t)y * nz + z] != 0;
+    c += nodes[(int64_t)yp * nz + z] != 0;
+    c += nodes[(int64_t)ym * nz + z] != 0;
+    c += nodes[(int64_t)y * nz + zp] != 0;
+    c += nodes[(int64_t)y * nz + zm] != 0;
+  }
+  if (c) atomicAdd(count, c);
+}
+
 }  // namespace om
 
 using namespace om;
@@ -61,15 +84,21 @@ extern "C" om_status om_nodeset_create(const uint8_t* nodes_dev, om_domain d, vo
   const int64_t nw = ncol * W;
   DevBuf<uint32_t> bits, cnt, rank;
   DevBuf<uint64_t> total;
+  DevBuf<unsigned long long> wrap;
   OM_TRY(bits.alloc(nw));
   OM_TRY(cnt.alloc(nw));
   OM_TRY(rank.alloc(nw));
   OM_TRY(total.alloc(1));
+  OM_TRY(wrap.alloc(1));
+  OM_CUDA(cudaMemsetAsync(wrap.p, 0, sizeof(unsigned long long), s));
   ns_bits<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(nodes_dev, d.ny, d.nz, W, ncol, bits.p, cnt.p);
+  ns_wrap_links<<<152, 256, 0, s>>>(nodes_dev, d.nx, d.ny, d.nz, wrap.p);
   OM_CUDA(cudaGetLastError());
   OM_TRY(exclusive_scan_u32(cnt.p, rank.p, nw, total.p, s));
   uint64_t nf = 0;
+  unsigned long long nwrap = 0;
   OM_CUDA(cudaMemcpyAsync(&nf, total.p, sizeof nf, cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaMemcpyAsync(&nwrap, wrap.p, sizeof nwrap, cudaMemcpyDeviceToHost, s));
   OM_CUDA(cudaStreamSynchronize(s));
 
   om_nodeset* ns = new om_nodeset();
@@ -78,6 +107,7 @@ extern "C" om_status om_nodeset_create(const uint8_t* nodes_dev, om_domain d, vo
   ns->N = voxels(d);
   ns->nf = (int64_t)nf;
   ns->pitch = ((int64_t)nf + 63) / 64 * 64;
+  ns->wrap_links = (int64_t)nwrap;
   DevBuf<uint2> col;
   DevBuf<uint32_t> coord;
   DevBuf<int64_t> vox;

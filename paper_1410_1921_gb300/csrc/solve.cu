@@ -66,6 +66,10 @@ extern "C" om_status om_solve_permeability(const uint8_t* mask, om_domain d, con
   OM_TRY(om_flow_create(sc.ns, params, sc.s, &sc.fl));
   double kl = 0.0;
   om_status st = om_flow_solve(sc.fl, &kl, info, sc.s);
+  if (st == OM_ENOPERC) {
+    if (k_lattice) *k_lattice = 0.0;
+    if (k_m2) *k_m2 = 0.0;
+  }
   if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
   const double dx = d.dx_nm * 1e-9;
   if (k_lattice) *k_lattice = kl;

@@ -14,9 +14,9 @@ import time
 import numpy as np
 import torch
 
-from . import (OM_F32, OM_PORE_CHORD13, Diffusion, Flow, NodeSet, UNet, diff_params, domain, flow_params,
-               om_label_connectivity_dev, om_local_pore_diameter_dev, om_reconstruct_dev, om_unet_pack_structure,
-               recon_params)
+from . import (OM_ENOPERC, OM_F32, OM_OK, OM_PORE_CHORD13, Diffusion, Flow, NodeSet, UNet, diff_params, domain,
+               flow_params, om_label_connectivity_dev, om_local_pore_diameter_dev, om_reconstruct_dev,
+               om_unet_pack_structure, recon_params)
 
 D_SCALE = 1.0 / 60.0
 L0 = 10.0
@@ -93,7 +93,9 @@ def targets(res, dom, fp, dp):
 
 
 def make_dataset(cfgs, fp=None, dp=None, log=None):
-    """Solve every structure (cold, FP32) and keep (input, target, mask)."""
+    """Solve every structure (cold, FP32) and keep (input, target, mask) of
+    those whose solves reached the convergence test (a flow with no link
+    across the periodic x boundary counts: its field is exactly u = 0)."""
     fp = fp or flow_params(precision=OM_F32)
     dp = dp or diff_params(precision=OM_F32)
     data = []
@@ -102,6 +104,8 @@ def make_dataset(cfgs, fp=None, dp=None, log=None):
         if int(tr.sum().item()) == 0:
             continue
         res = solve(dom, tr, d, fp, dp)
+        if res["flow_status"] not in (OM_OK, OM_ENOPERC) or res["diff_status"] != OM_OK:
+            continue
         data.append((net_input(mask, d, dom), targets(res, dom, fp, dp), tr.view(1, dom.nx, dom.ny, dom.nz)))
         if log:
             log(f"sample {len(data)}: {cfg.shape} eps={cfg.porosity:.2f} nodes={res['nodes']} "

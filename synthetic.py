@@ -117,6 +117,20 @@ def sphere_in_cube(L):
     return (~solid).astype(np.uint8)
 
 
+def offset_channel(nx=12, ny=10, nz=3, shift=4):
+    """Two half-length slits along x, rows y = 1, 2 for x < nx/2 and rows
+    y = 1+shift, 2+shift for x >= nx/2, joined by a riser at x = nx/2 - 1,
+    nx/2.  The structure spans x, but with shift >= 3 no D3Q19 link joins
+    the x = nx-1 face to the x = 0 face across the periodic boundary; with
+    shift = 2 one diagonal link per z layer does."""
+    m = np.zeros((nx, ny, nz), np.uint8)
+    h = nx // 2
+    m[:h, 1:3, :] = 1
+    m[h:, 1 + shift:3 + shift, :] = 1
+    m[h - 1:h + 1, 1:3 + shift, :] = 1
+    return m
+
+
 def closed_box(shape):
     """Pore interior with a one-voxel solid shell on every face."""
     m = np.zeros(shape, np.uint8)

@@ -31,10 +31,10 @@ def _dev(a, dtype=None):
     return t.to("cuda") if dtype is None else t.to("cuda", dtype)
 
 
-def _flow_run(om, node, f0, tau, g, steps, prec):
+def _flow_run(om, node, f0, tau, g, steps, prec, variant=-1):
     dom = om.domain(node.shape)
     ns = om.NodeSet(_dev(node), dom)
-    fl = om.Flow(ns, om.flow_params(tau=tau, body_force=g, precision=prec))
+    fl = om.Flow(ns, om.flow_params(tau=tau, body_force=g, precision=prec, variant=variant))
     fl.set_populations(_dev(f0))
     fl.step(steps)
     out = torch.empty(19 * node.size, dtype=torch.float64, device="cuda")
@@ -43,10 +43,11 @@ def _flow_run(om, node, f0, tau, g, steps, prec):
     return out.cpu().numpy().reshape((19,) + node.shape)
 
 
-def _diff_run(om, node, d_nm, g0, steps, prec, cin=1.0, cout=0.0):
+def _diff_run(om, node, d_nm, g0, steps, prec, cin=1.0, cout=0.0, variant=-1):
     dom = om.domain(node.shape)
     ns = om.NodeSet(_dev(node), dom)
-    df = om.Diffusion(ns, _dev(d_nm, torch.float32), om.diff_params(c_in=cin, c_out=cout, precision=prec))
+    df = om.Diffusion(ns, _dev(d_nm, torch.float32),
+                      om.diff_params(c_in=cin, c_out=cout, precision=prec, variant=variant))
     df.set_populations(_dev(g0))
     df.step(steps)
     out = torch.empty(7 * node.size, dtype=torch.float64, device="cuda")
@@ -126,6 +127,43 @@ def test_diffusion_steps_fp32(orc, om, geom, steps):
     ref = orc.diff_step(node, g0, orc.omega_field(node, d), 1.0, 0.0, steps)
     got = _diff_run(om, node, d, g0, steps, om.OM_F32)
     assert np.abs(got - ref).max() <= 64 * U32 * np.abs(g0).max() * steps + 1e-12
+
+
+# Every launch variant of the sweeps does the same arithmetic per node: each
+# matches the oracle, and on a structure with more nodes than one resident
+# grid has threads (so the striding variants loop) all give identical bits.
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_flow_variants_match_oracle(orc, om, variant):
+    node = GEOMS["blobs"]()
+    f0 = _rand_pops(orc, node, 7)
+    ref = orc.flow_step(node, f0, 0.8, 1e-5, 7)
+    got = _flow_run(om, node, f0, 0.8, 1e-5, 7, om.OM_F64, variant)
+    assert np.abs(got - ref).max() <= 1e-13 * 7
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_diffusion_variants_match_oracle(orc, om, variant):
+    node = GEOMS["ragged"]()
+    g0 = _rand_diff(node, 8)
+    d = _rand_d(node, 9)
+    ref = orc.diff_step(node, g0, orc.omega_field(node, d), 0.9, 0.2, 7)
+    got = _diff_run(om, node, d, g0, 7, om.OM_F64, 0.9, 0.2, variant)
+    assert np.abs(got - ref).max() <= 1e-13 * 7
+
+
+@pytest.mark.parametrize("prec", ["OM_F32", "OM_F16DEV"])
+def test_sweep_variants_identical_bits(orc, om, prec):
+    node = S.random_mask((64, 96, 112), 0.7, 21)  # ~4.8e5 nodes: > SMs x resident threads
+    P = getattr(om, prec)
+    f0 = _rand_pops(orc, node, 22, amp=0.05)
+    first = _flow_run(om, node, f0, 1.0, 1e-5, 5, P, 0)
+    for v in range(1, 5):
+        assert np.array_equal(_flow_run(om, node, f0, 1.0, 1e-5, 5, P, v), first), v
+    g0 = _rand_diff(node, 23)
+    d = _rand_d(node, 24)
+    first = _diff_run(om, node, d, g0, 5, P, 1.0, 0.0, 0)
+    for v in range(1, 4):
+        assert np.array_equal(_diff_run(om, node, d, g0, 5, P, 1.0, 0.0, v), first), v
 
 
 # ------------------------------------------------------------------ to convergence
@@ -222,6 +260,27 @@ def test_no_percolation_reports(om):
     with pytest.raises(om.OmError) as e:
         om.om_solve_permeability(m, om.domain(m.shape), om.flow_params())
     assert e.value.status == om.OM_ENOPERC
+
+
+def test_flow_without_link_across_x_boundary(orc, om):
+    # no D3Q19 link joins x = nx-1 to x = 0: the periodic boundary is a wall,
+    # k = 0 exactly, reported without stepping; with one link per layer the
+    # solve runs and matches the oracle
+    for shift, closed in ((4, True), (2, False)):
+        m = S.offset_channel(shift=shift)
+        dom = om.domain(m.shape)
+        ns = om.NodeSet(_dev(m), dom)
+        fl = om.Flow(ns, om.flow_params(precision=om.OM_F64, conv_tol=1e-10, body_force=1e-5))
+        st, kl, info = fl.solve()
+        if closed:
+            assert st == om.OM_ENOPERC and kl == 0.0 and info.steps == 0
+            with pytest.raises(om.OmError) as e:
+                om.om_solve_permeability(m, dom, om.flow_params())
+            assert e.value.status == om.OM_ENOPERC
+        else:
+            rc, k_ref, *_ = orc.flow_solve(m, 1.0, 1e-5, 1e-10, 100, 200_000)
+            assert st == om.OM_OK and rc == 0
+            assert kl == pytest.approx(k_ref, rel=1e-8)
 
 
 def test_step_cap_reports_not_converged(om):

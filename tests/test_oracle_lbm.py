@@ -192,6 +192,25 @@ def test_flow_momentum_gain_periodic(orc):
     assert np.allclose(rho, 1.0, rtol=1e-14)
 
 
+def test_flow_without_link_across_x_boundary_has_zero_flux(orc):
+    # x is periodic for the flow.  With no lattice link from the x = nx-1 face
+    # to the x = 0 face the boundary acts as a wall: at steady state the net
+    # flux through every cross-section is the same and through the wall it is
+    # zero, so sum u_x decays to rounding level.  One diagonal link per z
+    # layer (shift 2) carries a finite flux.
+    g = 1e-5
+    for shift, closed in ((4, True), (3, True), (2, False)):
+        m = S.offset_channel(shift=shift)
+        _, tr, _ = orc.label18(m)
+        assert tr.sum() == m.sum()  # the structure spans x: it is a transport set
+        f = orc.flow_step(m, orc.flow_init(m), tau=1.0, g=g, steps=4000)
+        ux = orc.flow_velocity(m, f, g)[0] * m
+        if closed:
+            assert abs(ux.sum()) < 1e-8 * m.sum() * g  # rounding level (shift 2: ~0.4 m.sum() g)
+        else:
+            assert ux.sum() > 1e-3 * m.sum() * g
+
+
 # ------------------------------------------------------------------ diffusion
 def test_straight_channel_diffusion_exact(orc):
     """Layered plane channel with a different pore size per layer: from a
