@@ -49,16 +49,20 @@ def net_input(mask, d, dom):
     return x.view(1, dom.nx, dom.ny, dom.nz, 2)
 
 
-def solve(dom, tr, d, fp, dp, prediction=None):
+def solve(dom, tr, d, fp, dp, prediction=None, warm_flow=False):
     """Flow and diffusion solves on the transport set, cold or warm-started
-    from a network output (float [N][2]).  Returns a dict of results, step
-    counts, wall times and the solved fields (ux, C)."""
+    from a network output (float [N][2]): the diffusion from its
+    concentration channel, the flow from its velocity channel only with
+    warm_flow (velocity warm starts were measured to slow the flow's
+    convergence: the predicted field is not divergence-free and excites slow
+    pressure modes).  Returns a dict of results, step counts, wall times and
+    the solved fields (ux, C)."""
     ns = NodeSet(tr, dom)
     out = {"nodes": ns.n_nodes}
     N = tr.numel()
     t0 = time.perf_counter()
     fl = Flow(ns, fp)
-    if prediction is not None:
+    if prediction is not None and warm_flow:
         fl.init_velocity(prediction, stride=2, scale=velocity_scale(fp))
     st, kl, info = fl.solve()
     torch.cuda.synchronize()
