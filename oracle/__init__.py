@@ -68,6 +68,14 @@ def lib():
         L.orc_flow_solve.restype = C.c_int
         L.orc_flow_solve.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                      C.c_double, C.c_int, C.c_int64, _f64p, _f64p]
+        L.orc_pressure_bc.restype = C.c_int
+        L.orc_pressure_bc.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _f64p]
+        L.orc_flow_step_p.restype = C.c_int
+        L.orc_flow_step_p.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                      _f64p]
+        L.orc_flow_solve_p.restype = C.c_int
+        L.orc_flow_solve_p.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, C.c_int, C.c_int64, _f64p, _f64p]
         L.orc_tau_knudsen.restype = C.c_double
         L.orc_tau_knudsen.argtypes = [C.c_double] * 3
         L.orc_diff_init.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _f64p]
@@ -230,6 +238,36 @@ def flow_solve(node, tau=1.0, g=1e-6, tol=1e-6, K=100, max_steps=1_000_000):
     out = np.zeros(4)
     rc = lib().orc_flow_solve(_p(n, _u8p), *n.shape, tau, g, tol, K, max_steps, _p(f, _f64p),
                               _p(out, _f64p))
+    return rc, out[0], out[1], int(out[2]), out[3], f.reshape((19,) + n.shape)
+
+
+def pressure_bc(node, f, rho_in, rho_out):
+    """The boundary replacement of the pressure-driven flow (Sec. 3.3) on a
+    copy of f [19, nx, ny, nz]."""
+    n = _u8(node)
+    f = np.ascontiguousarray(f, np.float64).copy()
+    rc = lib().orc_pressure_bc(_p(n, _u8p), *n.shape, rho_in, rho_out, _p(f, _f64p))
+    assert rc == ORC_OK
+    return f
+
+
+def flow_step_p(node, f, tau, rho_in, rho_out, steps=1):
+    """Advance the pressure-driven flow (a copy of f is returned)."""
+    n = _u8(node)
+    f = np.ascontiguousarray(f, np.float64).copy()
+    for _ in range(steps):
+        rc = lib().orc_flow_step_p(_p(n, _u8p), *n.shape, tau, rho_in, rho_out, _p(f, _f64p))
+        assert rc == ORC_OK
+    return f
+
+
+def flow_solve_p(node, tau=1.0, rho_in=1.00005, rho_out=0.99995, tol=1e-6, K=100, max_steps=1_000_000):
+    """Pressure-driven solve.  Returns (status, k_L, <u_x>, steps, rel_change, f)."""
+    n = _u8(node)
+    f = np.zeros(19 * n.size)
+    out = np.zeros(4)
+    rc = lib().orc_flow_solve_p(_p(n, _u8p), *n.shape, tau, rho_in, rho_out, tol, K, max_steps, _p(f, _f64p),
+                                _p(out, _f64p))
     return rc, out[0], out[1], int(out[2]), out[3], f.reshape((19,) + n.shape)
 
 

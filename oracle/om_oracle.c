@@ -600,6 +600,163 @@ int orc_flow_solve(const uint8_t *node, int nx, int ny, int nz, double tau, doub
   return rc;
 }
 
+/* ----------------------------------------------------------------------
+ * Pressure-driven flow (Sec. 3.3): x is not periodic; the nodes of the
+ * layers x = 0 and x = nx-1 carry the inlet and outlet densities by the
+ * non-equilibrium extrapolation of Guo et al.: before each collision every
+ * population of such a boundary node b is replaced by
+ *     f_i(b) = f_i^eq(rho_b, u_b) + [f_i(b1) - f_i^eq(rho(b1), u(b1))],
+ * b1 = b + n and b2 = b + 2n along the inward normal n = (+-1, 0, 0).  The
+ * boundary velocity is extrapolated to second order, u_b = 2 u(b1) - u(b2),
+ * when b1 and b2 are nodes, taken as u(b1) when only b1 is, and with no node
+ * at b1 the population is the equilibrium at rest, f_i^eq(rho_b, 0).  f^eq
+ * is the equilibrium whose moments are A1-A9 (j in place of rho0 u, rho0 = 1):
+ *     f_i^eq = w_i (rho + 3 e_i.j + 4.5 (e_i.j)^2 - 1.5 j.j).
+ * No body force acts.  Needs nx >= 4 (the inlet's b2 is not an outlet node).
+ * ---------------------------------------------------------------------- */
+static double orc_feq19(int i, double rho, double jx, double jy, double jz) {
+  orc_tables();
+  double eu = (double)T_e[3 * i] * jx + (double)T_e[3 * i + 1] * jy + (double)T_e[3 * i + 2] * jz;
+  double jj = jx * jx + jy * jy + jz * jz;
+  return T_w[i] * (rho + 3.0 * eu + 4.5 * eu * eu - 1.5 * jj);
+}
+
+static void orc_moments19(const double *f, int64_t N, int64_t v, double *rho, double *j) {
+  orc_tables();
+  double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  for (int i = 0; i < 19; ++i) {
+    double fi = f[(int64_t)i * N + v];
+    r += fi;
+    jx += (double)T_e[3 * i] * fi;
+    jy += (double)T_e[3 * i + 1] * fi;
+    jz += (double)T_e[3 * i + 2] * fi;
+  }
+  *rho = r;
+  j[0] = jx;
+  j[1] = jy;
+  j[2] = jz;
+}
+
+/* Replace the populations of the boundary nodes (both faces) in place.  The
+ * values of b1 and b2 are read before any boundary node is written (they are
+ * interior nodes for nx >= 4). */
+int orc_pressure_bc(const uint8_t *node, int nx, int ny, int nz, double rho_in, double rho_out, double *f) {
+  if (nx < 4) return ORC_EINVAL;
+  int64_t N = (int64_t)nx * ny * nz;
+  for (int side = 0; side < 2; ++side) {
+    int xb = side == 0 ? 0 : nx - 1, dir = side == 0 ? 1 : -1;
+    double rho_b = side == 0 ? rho_in : rho_out;
+    for (int y = 0; y < ny; ++y)
+      for (int z = 0; z < nz; ++z) {
+        int64_t b = vidx(xb, y, z, ny, nz);
+        if (!node[b]) continue;
+        int64_t b1 = vidx(xb + dir, y, z, ny, nz), b2 = vidx(xb + 2 * dir, y, z, ny, nz);
+        double out[19];
+        if (!node[b1]) {
+          for (int i = 0; i < 19; ++i) out[i] = orc_feq19(i, rho_b, 0.0, 0.0, 0.0);
+        } else {
+          double r1, j1[3], ub[3];
+          orc_moments19(f, N, b1, &r1, j1);
+          if (node[b2]) {
+            double r2, j2[3];
+            orc_moments19(f, N, b2, &r2, j2);
+            for (int k = 0; k < 3; ++k) ub[k] = 2.0 * j1[k] - j2[k];
+          } else {
+            for (int k = 0; k < 3; ++k) ub[k] = j1[k];
+          }
+          for (int i = 0; i < 19; ++i)
+            out[i] = orc_feq19(i, rho_b, ub[0], ub[1], ub[2]) +
+                     (f[(int64_t)i * N + b1] - orc_feq19(i, r1, j1[0], j1[1], j1[2]));
+        }
+        for (int i = 0; i < 19; ++i) f[(int64_t)i * N + b] = out[i];
+      }
+  }
+  return ORC_OK;
+}
+
+/* One step of the pressure-driven flow: boundary replacement, collision of
+ * every node (no force), streaming with halfway bounce-back off non-nodes
+ * and off the x ends (those populations are replaced before the next
+ * collision), periodic in y and z. */
+int orc_flow_step_p(const uint8_t *node, int nx, int ny, int nz, double tau, double rho_in, double rho_out,
+                    double *f) {
+  int rc = orc_pressure_bc(node, nx, ny, nz, rho_in, rho_out, f);
+  if (rc) return rc;
+  int64_t N = (int64_t)nx * ny * nz;
+  double *fs = (double *)malloc(sizeof(double) * 19 * (size_t)N);
+  if (!fs) return ORC_ENOMEM;
+  int e[57], opp[19];
+  orc_velocities19(e);
+  for (int i = 0; i < 19; ++i) opp[i] = orc_opp19(i);
+  double fin[19], fo[19];
+  for (int64_t v = 0; v < N; ++v) {
+    if (!node[v]) continue;
+    for (int i = 0; i < 19; ++i) fin[i] = f[(int64_t)i * N + v];
+    orc_mrt_collide_node(fin, tau, 0.0, fo);
+    for (int i = 0; i < 19; ++i) fs[(int64_t)i * N + v] = fo[i];
+  }
+  for (int64_t v = 0; v < N; ++v) {
+    if (!node[v]) continue;
+    int x = (int)(v / ((int64_t)ny * nz)), y = (int)((v / nz) % ny), z = (int)(v % nz);
+    for (int i = 0; i < 19; ++i) {
+      int xs = x - e[3 * i];
+      int inside = xs >= 0 && xs < nx;
+      int64_t src = inside ? vidx(xs, wrap(y - e[3 * i + 1], ny), wrap(z - e[3 * i + 2], nz), ny, nz) : -1;
+      f[(int64_t)i * N + v] = (inside && node[src]) ? fs[(int64_t)i * N + src] : fs[(int64_t)opp[i] * N + v];
+    }
+  }
+  free(fs);
+  return ORC_OK;
+}
+
+/* Solve the pressure-driven flow to the steady state (the test of
+ * orc_flow_solve on the interior layers x = 1 .. nx-2).  Darcy (Eq. 13):
+ * k_L = nu <u_x> L / (dp / rho0) with dp = c_s^2 (rho_in - rho_out), L =
+ * nx - 1 (the distance between the boundary layers) and <u_x> the
+ * superficial velocity, the sum of u_x = j_x over the interior layers divided
+ * by their voxel count (every layer carries the same flux at steady state).
+ * out[0] k_L, out[1] <u_x>, out[2] steps, out[3] last relative change. */
+int orc_flow_solve_p(const uint8_t *node, int nx, int ny, int nz, double tau, double rho_in, double rho_out,
+                     double tol, int K, int64_t max_steps, double *f, double *out) {
+  if (nx < 4) return ORC_EINVAL;
+  int64_t N = (int64_t)nx * ny * nz, plane = (int64_t)ny * nz;
+  double *ux = (double *)malloc(sizeof(double) * (size_t)N);
+  double *prev = (double *)malloc(sizeof(double) * (size_t)N);
+  if (!ux || !prev) { free(ux); free(prev); return ORC_ENOMEM; }
+  orc_flow_init(node, nx, ny, nz, f);
+  orc_flow_velocity(node, nx, ny, nz, 0.0, f, prev, NULL, NULL, NULL);
+  int64_t n = 0;
+  double rel = 1.0, sum = 0.0;
+  int rc = ORC_ENOTCONVERGED;
+  while (n < max_steps) {
+    for (int k = 0; k < K && n < max_steps; ++k, ++n) {
+      int r = orc_flow_step_p(node, nx, ny, nz, tau, rho_in, rho_out, f);
+      if (r) { free(ux); free(prev); return r; }
+    }
+    orc_flow_velocity(node, nx, ny, nz, 0.0, f, ux, NULL, NULL, NULL);
+    double du = 0.0, au = 0.0;
+    sum = 0.0;
+    for (int64_t v = plane; v < N - plane; ++v) {
+      if (!node[v]) continue;
+      du += fabs(ux[v] - prev[v]);
+      au += fabs(ux[v]);
+      sum += ux[v];
+      prev[v] = ux[v];
+    }
+    rel = au > 0.0 ? du / au : 0.0;
+    if (rel < tol) { rc = ORC_OK; break; }
+  }
+  double nu = (tau - 0.5) / 3.0;
+  double mean_u = sum / (double)(N - 2 * plane);
+  out[0] = nu * mean_u * (double)(nx - 1) / ((rho_in - rho_out) / 3.0);
+  out[1] = mean_u;
+  out[2] = (double)n;
+  out[3] = rel;
+  free(ux);
+  free(prev);
+  return rc;
+}
+
 /* ======================================================================
  * 7. BGK diffusion (Sec. 3.2, Eq. 10) on D3Q7: g_i^eq = a_i C with
  *    a_0 = 1/4, a_1..6 = 1/8 (c_s^2 = 1/4), C = sum g_i, one relaxation time

@@ -211,6 +211,70 @@ def test_flow_without_link_across_x_boundary_has_zero_flux(orc):
             assert ux.sum() > 1e-3 * m.sum() * g
 
 
+# ------------------------------------------------------------------ pressure-driven flow (Sec. 3.3)
+@pytest.mark.parametrize("geom,tau", [("slit", 1.0), ("duct", 0.8)])
+def test_pressure_driven_matches_body_force_in_straight_channels(orc, geom, tau):
+    # fully developed flow in a straight channel: the pressure drop over the
+    # nx - 1 lattice units between the boundary layers drives the same
+    # Poiseuille profile as the equivalent body force, so both readings of
+    # Eq. 13 give the same k (the body-force slit is exact at the nodes)
+    m = S.slit(12, 7, 2) if geom == "slit" else S.square_duct(10, 5)
+    rc, k, *_ = orc.flow_solve_p(m, tau, 1.00005, 0.99995, 1e-10, 100, 200_000)
+    rcb, kb, *_ = orc.flow_solve(m, tau, 1e-6, 1e-10, 100, 200_000)
+    assert rc == 0 and rcb == 0
+    assert k == pytest.approx(kb, rel=1e-8)
+
+
+def test_pressure_driven_flux_is_conserved_and_odd_in_the_drop(orc):
+    m = S.offset_channel(shift=4)
+    rc, k, u, n, rel, f = orc.flow_solve_p(m, 1.0, 1.00005, 0.99995, 1e-10, 100, 200_000)
+    assert rc == 0
+    ux = orc.flow_velocity(m, f, 0.0)[0] * m
+    layer = ux.sum(axis=(1, 2))[1:-1]  # every interior layer carries the same flux
+    assert np.allclose(layer, layer.mean(), rtol=1e-8)
+    assert u == pytest.approx(layer.mean() / (m.shape[1] * m.shape[2]), rel=1e-12)
+    rc2, k2, u2, *_ = orc.flow_solve_p(m, 1.0, 0.99995, 1.00005, 1e-10, 100, 200_000)
+    assert u2 == pytest.approx(-u, rel=1e-6) and k2 == pytest.approx(k, rel=1e-6)
+
+
+def test_pressure_drive_needs_no_link_across_x(orc):
+    # the offset channel carries no flux under the periodic body force (no
+    # link joins the x faces) but does between pressure reservoirs; with one
+    # diagonal link per layer the junction still throttles the periodic flow
+    for shift in (4, 2):
+        m = S.offset_channel(shift=shift)
+        rc, k, *_ = orc.flow_solve_p(m, 1.0, 1.00005, 0.99995, 1e-10, 100, 200_000)
+        assert rc == 0 and k > 0.05
+        if shift == 2:
+            rcb, kb, *_ = orc.flow_solve(m, 1.0, 1e-6, 1e-10, 100, 200_000)
+            assert kb < 0.5 * k
+
+
+def test_pressure_bc_reproduces_a_linear_equilibrium_state(orc):
+    # f = f_eq(rho(x), j) with rho linear in x and uniform j is a fixed point
+    # of the extrapolation when the boundary densities continue the line
+    m = np.ones((6, 3, 4), np.uint8)
+    x = np.arange(6)
+    rho = 1.0 + 1e-3 * (2.5 - x)
+    j = np.array([2e-4, -1e-4, 5e-5])
+    e = orc.velocities19()
+    w = orc.weights19()
+    ej = e @ j
+    feq = w[:, None] * (rho[None, :] + 3 * ej[:, None] + 4.5 * ej[:, None] ** 2 - 1.5 * j @ j)
+    f = np.broadcast_to(feq[:, :, None, None], (19, 6, 3, 4)).copy()
+    g = orc.pressure_bc(m, f, rho[0], rho[-1])
+    assert np.allclose(g, f, rtol=0, atol=1e-15)
+    # a non-equilibrium part without mass or momentum, different on every
+    # layer: the boundary layers take the one of their inward neighbour
+    a = np.array([3.0, 1.0, -2.0, 0.5, 4.0, -1.0]) * 1e-4
+    neq = (w * (e[:, 0] ** 2 - 1.0 / 3.0))[:, None] * a[None, :]
+    h = orc.pressure_bc(m, f + neq[:, :, None, None], rho[0], rho[-1])
+    want = f + neq[:, :, None, None]
+    want[:, 0] = f[:, 0] + neq[:, 1, None, None]
+    want[:, -1] = f[:, -1] + neq[:, -2, None, None]
+    assert np.allclose(h, want, rtol=0, atol=1e-15)
+
+
 # ------------------------------------------------------------------ diffusion
 def test_straight_channel_diffusion_exact(orc):
     """Layered plane channel with a different pore size per layer: from a
