@@ -88,7 +88,20 @@ typedef struct {
    * resident grid striding over nodes, 4 a tighter cap); larger values
    * clamp to 4 */
   int32_t variant;
+  /* OM_DRIVE_FORCE: body_force along x, x periodic.  OM_DRIVE_PRESSURE
+   * (Sec. 3.3): no force, x not periodic, densities 1 + delta_rho/2 and
+   * 1 - delta_rho/2 on the node layers x = 0 and x = nx-1 by Guo's
+   * non-equilibrium extrapolation (u_b = 2 u(b1) - u(b2) from the two inward
+   * neighbours; u(b1) without b2; the rest equilibrium without b1); needs
+   * nx >= 4 and 0 < |delta_rho| < 0.1.  k_lattice = nu <u_x> (nx - 1) /
+   * (delta_rho / 3), <u_x> averaged over the voxels of the layers 1..nx-2,
+   * on which the convergence test is also taken.  Batches accept only
+   * OM_DRIVE_FORCE. */
+  int32_t drive;
+  double delta_rho;
 } om_flow_params;
+
+enum { OM_DRIVE_FORCE = 0, OM_DRIVE_PRESSURE = 1 };
 
 /* D3Q7 Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
  * size and relaxation time of Eq. 12, inlet/outlet concentrations.
@@ -169,14 +182,15 @@ om_status om_local_pore_diameter_dev(const uint8_t* mask_dev, om_domain d, int32
 /* ---------------------------------------------------------------- solves */
 
 /* Intrinsic permeability (Eq. 13) of the transport pores of `mask` (host,
- * N bytes): D3Q19 flow driven by params->body_force along x, periodic in
- * x, y, z, halfway bounce-back at walls, to convergence.
- * k_m2 = k_lattice * dx^2 (Eq. 15), k_lattice = nu <u_x> / g with <.> over
- * all N voxels.  ux_out (nullable, host float N): u_x, 0 off the node set.
- * info (nullable).  OM_ENOPERC when no pore spans the box, or when no
- * D3Q19 link joins a node at x = nx-1 to one at x = 0: the periodic x
- * boundary is then a wall, the steady net flux is zero, and k_m2 and
- * k_lattice are set to 0 without stepping. */
+ * N bytes): D3Q19 flow, halfway bounce-back at walls, periodic in y and z,
+ * to convergence, driven as params->drive says: by params->body_force along
+ * x with x periodic (k_lattice = nu <u_x> / g, <.> over all N voxels), or by
+ * the pressure ends of om_flow_params.drive.  k_m2 = k_lattice * dx^2
+ * (Eq. 15).  ux_out (nullable, host float N): u_x, 0 off the node set.
+ * info (nullable).  OM_ENOPERC when no pore spans the box, or, with the
+ * body-force drive, when no D3Q19 link joins a node at x = nx-1 to one at
+ * x = 0: the periodic x boundary is then a wall, the steady net flux is
+ * zero, and k_m2 and k_lattice are set to 0 without stepping. */
 om_status om_solve_permeability(const uint8_t* mask, om_domain d, const om_flow_params* params,
                                 double* k_m2, double* k_lattice, om_run_info* info, float* ux_out);
 
@@ -219,12 +233,13 @@ om_status om_flow_create(const om_nodeset* ns, const om_flow_params* params, voi
 /* advance nsteps LB steps (Sec. 3.1, steps 1-5 per step) */
 om_status om_flow_step(om_flow* fl, int64_t nsteps, void* stream);
 /* Observables of the current state (FP64, node order): out[0] sum u_x,
- * out[1] sum |u_x - u_x at the previous observe|, out[2] sum |u_x|,
- * out[3] sum (rho - 1).  Host out, synchronises. */
+ * out[1] sum |u_x - u_x at the previous observe|, out[2] sum |u_x| (the
+ * pressure drive sums these three over the layers x = 1..nx-2), out[3]
+ * sum (rho - 1) over all nodes.  Host out, synchronises. */
 om_status om_flow_observe(om_flow* fl, double* out, void* stream);
-/* Run to convergence (om_flow_params) from the current state.  OM_ENOPERC
- * (k_lattice = 0, no steps) when no lattice link crosses the periodic x
- * boundary: the net flux then vanishes at steady state. */
+/* Run to convergence (om_flow_params) from the current state.  Body-force
+ * drive: OM_ENOPERC (k_lattice = 0, no steps) when no lattice link crosses
+ * the periodic x boundary: the net flux then vanishes at steady state. */
 om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* info, void* stream);
 /* populations at the current time in the dense layout f[i*N + voxel],
  * i in the order of the App. A transformation matrix, 0 off the node set.

@@ -695,6 +695,7 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if (n <= 0 || !doms || !nodes_dev || !out || (!fp && !dp)) return fail(OM_EINVAL, "om_batch_create: bad arguments");
   if (dp && !d_nm_dev) return fail(OM_EINVAL, "om_batch_create: diffusion needs pore sizes");
   if (fp && !(fp->tau > 0.5)) return fail(OM_EINVAL, "om_batch_create: tau must exceed 1/2");
+  if (fp && fp->drive != OM_DRIVE_FORCE) return fail(OM_EINVAL, "om_batch_create: batches take the body-force drive");
   if (dp && (!(dp->d_ref_nm > 0.0) || !(dp->tau_ref > 0.5) || !(dp->c_in != dp->c_out)))
     return fail(OM_EINVAL, "om_batch_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");
   for (const auto* p : {fp ? &fp->precision : nullptr, dp ? &dp->precision : nullptr})

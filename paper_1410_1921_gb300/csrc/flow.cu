@@ -21,6 +21,18 @@
 // (solid or non-transport voxel) is halfway bounce-back: the odd step reads
 // the node's own slot i and writes its own slot opposite(i).  x, y and z
 // are periodic (body-force driving).
+//
+// Pressure drive (Sec. 3.3, om_flow_params.drive = OM_DRIVE_PRESSURE).  x
+// is not periodic and no force acts; the nodes of the layers x = 0 and
+// x = nx - 1 carry densities 1 +- delta_rho/2 by the non-equilibrium
+// extrapolation of Guo et al.: before every sweep a boundary kernel forms,
+// for each such node b with inward neighbours b1, b2,
+//     f_i(b) = f_i^eq(rho_b, u_b) + f_i(b1) - f_i^eq(rho(b1), u(b1)),
+// u_b = 2 u(b1) - u(b2) (u(b1) without b2; f^eq(rho_b, 0) without b1), from
+// the pre-collision populations of b1 and b2 (their own slots at even times,
+// gathered from their neighbours at odd times), into a side buffer that the
+// sweep reads in place of b's own populations.  The sweep writes nothing the
+// boundary kernel reads, so the two never race.
 #include <algorithm>
 #include <cmath>
 
@@ -86,10 +98,11 @@ __global__ void __launch_bounds__(kObsThreads) d3q19_observe(FlowArgs<T> a, doub
       jx += (double)q19_e(i, 0) * (double)f[i];
     }
     const double ux = jx + 0.5 * (double)a.g;
+    acc[3] += rho;
+    if (flow_boundary_index(a, n) >= 0) continue;  // pressure drive: velocity sums over interior layers
     acc[0] += ux;
     acc[1] += fabs(ux - prev[n]);
     acc[2] += fabs(ux);
-    acc[3] += rho;
     prev[n] = ux;
   }
   block_reduce_store<4>(acc, partials);
@@ -147,6 +160,68 @@ __global__ void d3q19_init_u(FlowArgs<T> a, const int64_t* vox, const float* ux,
   }
 }
 
+// Pressure drive: the extrapolated pre-collision deviations of every
+// boundary node into bc (Sec. 3.3; see the file comment).  Deviations from
+// w_i: f_i^eq - w_i = w_i (rho - 1 + 3 e_i.j + 4.5 (e_i.j)^2 - 1.5 j.j).
+template <class C>
+__device__ __forceinline__ C feq19_dev(int i, C drho, C jx, C jy, C jz) {
+  const C eu = C(q19_e(i, 0)) * jx + C(q19_e(i, 1)) * jy + C(q19_e(i, 2)) * jz;
+  return C(q19_w(i)) * (drho + C(3) * eu + C(4.5) * eu * eu - C(1.5) * (jx * jx + jy * jy + jz * jz));
+}
+
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_moments_at(const FlowArgs<T>& a, uint32_t n, typename Stg<T>::C (&f)[19],
+                                                typename Stg<T>::C& r, typename Stg<T>::C (&j)[3]) {
+  using C = typename Stg<T>::C;
+  uint32_t nb[19];
+  if (ODD) flow_neighbours(a, a.coord[n], nb);
+  flow_load<T, ODD>(a, n, nb, f);
+  r = 0;
+  j[0] = j[1] = j[2] = 0;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    r += f[i];
+    j[0] += C(q19_e(i, 0)) * f[i];
+    j[1] += C(q19_e(i, 1)) * f[i];
+    j[2] += C(q19_e(i, 2)) * f[i];
+  }
+}
+
+template <class T, bool ODD>
+__global__ void d3q19_pressure_bc(FlowArgs<T> a, typename Stg<T>::C* bc, double drho_in, double drho_out) {
+  using C = typename Stg<T>::C;
+  const uint32_t nbt = a.n_in + a.n_out;
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nbt) return;
+  const uint32_t b = k < a.n_in ? k : a.nf - a.n_out + (k - a.n_in);
+  int x, y, z;
+  unpack_xyz(a.coord[b], x, y, z);
+  const int dir = x == 0 ? 1 : -1;
+  const C drb = (C)(x == 0 ? drho_in : drho_out);
+  const uint32_t b1 = node_at(a.col, a.ny, a.W, x + dir, y, z);
+  C out[19];
+  if (b1 == kNoNode) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) out[i] = feq19_dev<C>(i, drb, C(0), C(0), C(0));
+  } else {
+    C f1[19], r1, j1[3], ub[3];
+    flow_moments_at<T, ODD>(a, b1, f1, r1, j1);
+    const uint32_t b2 = node_at(a.col, a.ny, a.W, x + 2 * dir, y, z);
+    if (b2 != kNoNode) {
+      C f2[19], r2, j2[3];
+      flow_moments_at<T, ODD>(a, b2, f2, r2, j2);
+      for (int d = 0; d < 3; ++d) ub[d] = C(2) * j1[d] - j2[d];
+    } else {
+      for (int d = 0; d < 3; ++d) ub[d] = j1[d];
+    }
+#pragma unroll
+    for (int i = 0; i < 19; ++i)
+      out[i] = feq19_dev<C>(i, drb, ub[0], ub[1], ub[2]) + (f1[i] - feq19_dev<C>(i, r1, j1[0], j1[1], j1[2]));
+  }
+#pragma unroll
+  for (int i = 0; i < 19; ++i) bc[(size_t)i * nbt + k] = out[i];
+}
+
 template <class T>
 __global__ void d3q19_rest(FlowArgs<T> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,6 +245,10 @@ struct om_flow {
   int64_t t = 0;
   double up = 1.0;  // storage scale of reduced-precision formats (stored = deviation * up)
   int var[2] = {0, 0};  // launch variant of the even and odd sweeps
+  // pressure drive: boundary nodes [0, n_in) and [nf - n_out, nf), their
+  // extrapolated populations (storage arithmetic type, [19][n_in + n_out])
+  uint32_t n_in = 0, n_out = 0;
+  void* bc = nullptr;
   // a captured window of graph_k steps starting at an even time (replayed by *_step)
   cudaGraphExec_t exec = nullptr;
   int graph_k = 0;
@@ -196,8 +275,16 @@ FlowArgs<T> flow_args(const om_flow* fl) {
   a.g = (typename Stg<T>::C)fl->p.body_force;
   a.up = (typename Stg<T>::C)fl->up;
   a.down = (typename Stg<T>::C)(1.0 / fl->up);
+  if (fl->p.drive == OM_DRIVE_PRESSURE) {
+    a.g = 0;
+    a.px = 0;
+    a.n_in = fl->n_in;
+    a.n_out = fl->n_out;
+    a.bc = (const typename Stg<T>::C*)fl->bc;
+  }
   return a;
 }
+
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -227,6 +314,19 @@ void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const Flow
   else launch_sweep_p<T, false>(variant, nb, s, a);
 }
 
+// One LB step: the pressure boundary kernel (pressure drive) and the sweep.
+template <class T>
+void launch_step(const om_flow* fl, bool odd, int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>& a) {
+  const uint32_t nbt = a.n_in + a.n_out;
+  if (nbt) {
+    using C = typename Stg<T>::C;
+    const double h = 0.5 * fl->p.delta_rho;
+    if (odd) d3q19_pressure_bc<T, true><<<(nbt + 127) / 128, 128, 0, s>>>(a, (C*)fl->bc, h, -h);
+    else d3q19_pressure_bc<T, false><<<(nbt + 127) / 128, 128, 0, s>>>(a, (C*)fl->bc, h, -h);
+  }
+  launch_sweep<T>(odd, variant, nb, s, a);
+}
+
 // Capture K sweeps (K even, from an even time) into a CUDA graph once.
 template <class T>
 om_status flow_capture_t(om_flow* fl, int K) {
@@ -240,7 +340,7 @@ om_status flow_capture_t(om_flow* fl, int K) {
   const unsigned nb = blocks_for(a.nf);
   cudaGraph_t g = nullptr;
   OM_CUDA(cudaStreamBeginCapture(fl->cap, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) launch_sweep<T>(k & 1, fl->var[k & 1], nb, fl->cap, a);
+  for (int k = 0; k < K; ++k) launch_step<T>(fl, k & 1, fl->var[k & 1], nb, fl->cap, a);
   cudaError_t e = cudaStreamEndCapture(fl->cap, &g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
   e = cudaGraphInstantiate(&fl->exec, g, 0);
@@ -270,7 +370,7 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
       continue;
     }
     const bool odd = fl->t & 1;
-    launch_sweep<T>(odd, fl->var[odd], nb, s, a);
+    launch_step<T>(fl, odd, fl->var[odd], nb, s, a);
     ++fl->t;
     --nsteps;
   }
@@ -396,10 +496,34 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   if (!(p->tau > 0.5)) return fail(OM_EINVAL, "om_flow_create: tau must exceed 1/2");
   if (p->precision < OM_F64 || p->precision > OM_BF16DEV)
     return fail(OM_EINVAL, "om_flow_create: unknown precision");
+  if (p->drive != OM_DRIVE_FORCE && p->drive != OM_DRIVE_PRESSURE)
+    return fail(OM_EINVAL, "om_flow_create: unknown drive");
+  if (p->drive == OM_DRIVE_PRESSURE) {
+    if (ns->dom.nx < 4) return fail(OM_EINVAL, "om_flow_create: the pressure drive needs nx >= 4");
+    if (!(std::fabs(p->delta_rho) > 0.0 && std::fabs(p->delta_rho) < 0.1))
+      return fail(OM_EINVAL, "om_flow_create: the pressure drive needs 0 < |delta_rho| < 0.1");
+  }
   cudaStream_t s = as_stream(stream);
   om_flow* fl = new om_flow();
   fl->ns = ns;
   fl->p = *p;
+  if (p->drive == OM_DRIVE_PRESSURE && ns->nf > 0) {
+    // nodes before column (1, 0) lie at x = 0; from column (nx - 1, 0) on, at x = nx - 1
+    uint2 w[2];
+    const om_domain& d = ns->dom;
+    cudaError_t e = cudaMemcpyAsync(&w[0], ns->col + (size_t)1 * d.ny * ns->W, sizeof(uint2),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&w[1], ns->col + (size_t)(d.nx - 1) * d.ny * ns->W, sizeof(uint2),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      delete fl;
+      return cuda_fail(e, "om_flow_create: boundary ranks", __FILE__, __LINE__);
+    }
+    fl->n_in = w[0].y;
+    fl->n_out = (uint32_t)ns->nf - w[1].y;
+  }
   // FP16 storage keeps deviations scaled by 2^10 so they stay normal numbers
   fl->up = p->precision == OM_F16DEV ? 1024.0 : 1.0;
   DevBuf<uint8_t> f;
@@ -408,6 +532,12 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   if (st == OM_OK) st = prev.alloc(ns->nf);
   if (st == OM_OK) st = part.alloc((size_t)kObsBlocks * 8);
   if (st == OM_OK) st = obs.alloc(8);
+  DevBuf<uint8_t> bc;
+  const size_t nbt = (size_t)fl->n_in + fl->n_out;
+  const size_t cbytes = p->precision == OM_F64 ? 8 : 4;  // the storage type's arithmetic type
+  if (st == OM_OK && nbt) st = bc.alloc(19 * nbt * cbytes);
+  if (st == OM_OK && nbt && cudaMemsetAsync(bc.p, 0, 19 * nbt * cbytes, s) != cudaSuccess)
+    st = fail(OM_ECUDA, "om_flow_create: memset failed");
   double* host = nullptr;
   if (st == OM_OK && cudaMallocHost((void**)&host, 8 * sizeof(double)) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -422,6 +552,7 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   fl->partials = part.take();
   fl->obs_dev = obs.take();
   fl->obs_host = host;
+  fl->bc = bc.take();
   auto rest = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_rest_t, fl, s); };
   auto tune = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_tune_t, fl, s); };
   if (p->variant >= 0) fl->var[0] = fl->var[1] = std::min(p->variant, kSweepVariants - 1);
@@ -455,8 +586,9 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
   const om_flow_params& p = fl->p;
   if (p.check_every <= 0 || (p.check_every & 1))
     return fail(OM_EINVAL, "om_flow_solve: check_every must be a positive even number");
-  if (!(p.body_force != 0.0)) return fail(OM_EINVAL, "om_flow_solve: body_force must be nonzero");
-  if (fl->ns->wrap_links == 0) {
+  const bool pressure = p.drive == OM_DRIVE_PRESSURE;
+  if (!pressure && !(p.body_force != 0.0)) return fail(OM_EINVAL, "om_flow_solve: body_force must be nonzero");
+  if (!pressure && fl->ns->wrap_links == 0) {
     // x is periodic for the flow: with no lattice link across the x boundary
     // it is a wall, and the steady net flux (hence k) is exactly zero
     if (k_lattice) *k_lattice = 0.0;
@@ -498,7 +630,13 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const double nu = (p.tau - 0.5) / 3.0;
-  if (k_lattice) *k_lattice = nu * (o[0] / (double)fl->ns->N) / p.body_force;
+  if (k_lattice) {
+    const om_domain& d = fl->ns->dom;
+    if (pressure)  // Eq. 13: <u_x> over the interior layers, dp = (rho_in - rho_out)/3 over nx - 1
+      *k_lattice = nu * (o[0] / ((double)(d.nx - 2) * d.ny * d.nz)) * (double)(d.nx - 1) / (p.delta_rho / 3.0);
+    else
+      *k_lattice = nu * (o[0] / (double)fl->ns->N) / p.body_force;
+  }
   if (info) {
     info->steps = fl->t - t0;
     info->n_nodes = fl->ns->nf;
@@ -558,6 +696,7 @@ extern "C" om_status om_flow_destroy(om_flow* fl) {
   cudaFree(fl->prev);
   cudaFree(fl->partials);
   cudaFree(fl->obs_dev);
+  cudaFree(fl->bc);
   if (fl->obs_host) cudaFreeHost(fl->obs_host);
   delete fl;
   return OM_OK;

@@ -18,29 +18,54 @@ struct FlowArgs {
   const uint32_t* coord;
   int nx, ny, nz, W;
   typename Stg<T>::C wp, wm, g, up, down;
+  // Pressure drive (Sec. 3.3): x is not periodic (px = 0); nodes [0, n_in)
+  // lie at x = 0 and [nf - n_out, nf) at x = nx - 1, and their pre-collision
+  // deviations are bc[i * (n_in + n_out) + k], written before every sweep by
+  // the boundary kernel.  Body-force drive: px = 1, n_in = n_out = 0.
+  int px = 1;
+  uint32_t n_in = 0, n_out = 0;
+  const typename Stg<T>::C* bc = nullptr;
 };
 
-// nb[i] = node number of x + e_i (kNoNode off the node set); periodic x, y, z
+// nb[i] = node number of x + e_i (kNoNode off the node set); periodic y, z,
+// and x unless a.px = 0 (no neighbour beyond the x faces)
 template <class T>
 __device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c, uint32_t (&nb)[19]) {
   int x, y, z;
   unpack_xyz(c, x, y, z);
   const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
+  const bool hp = a.px || x + 1 < a.nx, hm = a.px || x > 0;
   const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
   const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
   const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
   auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
   uint32_t self;
   column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
-  column3(a.col, base(xp, y), z, zp, zm, nb[13], nb[1], nb[11]);
-  column3(a.col, base(xm, y), z, zp, zm, nb[14], nb[2], nb[12]);
+  if (hp) {
+    column3(a.col, base(xp, y), z, zp, zm, nb[13], nb[1], nb[11]);
+    nb[7] = column1(a.col, base(xp, yp), z);
+    nb[9] = column1(a.col, base(xp, ym), z);
+  } else {
+    nb[13] = nb[1] = nb[11] = nb[7] = nb[9] = kNoNode;
+  }
+  if (hm) {
+    column3(a.col, base(xm, y), z, zp, zm, nb[14], nb[2], nb[12]);
+    nb[8] = column1(a.col, base(xm, yp), z);
+    nb[10] = column1(a.col, base(xm, ym), z);
+  } else {
+    nb[14] = nb[2] = nb[12] = nb[8] = nb[10] = kNoNode;
+  }
   column3(a.col, base(x, yp), z, zp, zm, nb[17], nb[3], nb[15]);
   column3(a.col, base(x, ym), z, zp, zm, nb[18], nb[4], nb[16]);
-  nb[7] = column1(a.col, base(xp, yp), z);
-  nb[8] = column1(a.col, base(xm, yp), z);
-  nb[9] = column1(a.col, base(xp, ym), z);
-  nb[10] = column1(a.col, base(xm, ym), z);
   (void)self;
+}
+
+// Index of node n among the boundary nodes of the pressure drive, or -1
+template <class T>
+__device__ __forceinline__ int64_t flow_boundary_index(const FlowArgs<T>& a, uint32_t n) {
+  if (n < a.n_in) return n;
+  if (a.n_out && n >= a.nf - a.n_out) return (int64_t)a.n_in + (n - (a.nf - a.n_out));
+  return -1;
 }
 
 // pre-collision populations of node n at the current time
@@ -106,6 +131,14 @@ __device__ __forceinline__ void flow_node_at(const FlowArgs<T>& a, uint32_t n, u
   if (ODD) flow_neighbours(a, c, nb);
   C f[19];
   flow_load<T, ODD>(a, n, nb, f);
+  if (a.n_in + a.n_out) {  // pressure drive: boundary nodes take the extrapolated populations
+    const int64_t k = flow_boundary_index(a, n);
+    if (k >= 0) {
+      const uint32_t nbt = a.n_in + a.n_out;
+#pragma unroll
+      for (int i = 0; i < 19; ++i) f[i] = a.bc[(size_t)i * nbt + k];
+    }
+  }
   trt_collide(f, a.wp, a.wm, a.g);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {

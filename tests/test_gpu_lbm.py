@@ -31,10 +31,12 @@ def _dev(a, dtype=None):
     return t.to("cuda") if dtype is None else t.to("cuda", dtype)
 
 
-def _flow_run(om, node, f0, tau, g, steps, prec, variant=-1):
+def _flow_run(om, node, f0, tau, g, steps, prec, variant=-1, drho=None):
     dom = om.domain(node.shape)
     ns = om.NodeSet(_dev(node), dom)
-    fl = om.Flow(ns, om.flow_params(tau=tau, body_force=g, precision=prec, variant=variant))
+    drive = om.OM_DRIVE_FORCE if drho is None else om.OM_DRIVE_PRESSURE
+    fl = om.Flow(ns, om.flow_params(tau=tau, body_force=g, precision=prec, variant=variant, drive=drive,
+                                    delta_rho=drho or 1e-4))
     fl.set_populations(_dev(f0))
     fl.step(steps)
     out = torch.empty(19 * node.size, dtype=torch.float64, device="cuda")
@@ -164,6 +166,73 @@ def test_sweep_variants_identical_bits(orc, om, prec):
     first = _diff_run(om, node, d, g0, 5, P, 1.0, 0.0, 0)
     for v in range(1, 4):
         assert np.array_equal(_diff_run(om, node, d, g0, 5, P, 1.0, 0.0, v), first), v
+
+
+# ------------------------------------------------------------------ pressure drive (Sec. 3.3)
+PGEOMS = {
+    "offset": lambda: S.offset_channel(shift=4),
+    "blobs": lambda: S.blob_mask((14, 19, 37), 11, n=7),
+    "ragged": lambda: S.random_mask((9, 33, 35), 0.7, 3),
+    "duct": lambda: S.square_duct(6, 5),
+    "open4": lambda: np.ones((4, 5, 3), np.uint8),
+}
+
+
+@pytest.mark.parametrize("geom", list(PGEOMS))
+@pytest.mark.parametrize("steps", [1, 2, 3, 10])
+def test_pressure_drive_steps_fp64(orc, om, geom, steps):
+    node = PGEOMS[geom]()
+    f0 = _rand_pops(orc, node, 300 + steps, amp=0.05)
+    ref = orc.flow_step_p(node, f0, 0.8, 1.001, 0.999, steps)
+    got = _flow_run(om, node, f0, 0.8, 0.0, steps, om.OM_F64, drho=0.002)
+    assert np.abs(got - ref).max() <= 1e-13 * steps
+
+
+@pytest.mark.parametrize("geom", ["offset", "blobs", "ragged"])
+@pytest.mark.parametrize("variant", [0, 2])
+def test_pressure_drive_steps_fp32(orc, om, geom, variant):
+    node = PGEOMS[geom]()
+    f0 = _rand_pops(orc, node, 400, amp=0.05)
+    ref = orc.flow_step_p(node, f0, 1.0, 1.001, 0.999, 9)
+    got = _flow_run(om, node, f0, 1.0, 0.0, 9, om.OM_F32, variant, drho=0.002)
+    dev = np.abs(f0 - orc.weights19()[:, None, None, None] * node).max()
+    assert np.abs(got - ref).max() <= 64 * U32 * dev * 9 + 1e-12
+
+
+@pytest.mark.parametrize("prec,rel", [("OM_F64", 1e-8), ("OM_F32", 1e-5)])
+def test_pressure_drive_converged_permeability(orc, om, prec, rel):
+    node = S.blob_mask((12, 16, 16), 3, n=6, rmin=3.5, rmax=6.0)
+    _, tr, _ = orc.label18(node)
+    rc, k_ref, *_ = orc.flow_solve_p(tr, 1.0, 1.00005, 0.99995, 1e-9, 100, 100_000)
+    assert rc == 0
+    ns = om.NodeSet(_dev(tr), om.domain(tr.shape))
+    fl = om.Flow(ns, om.flow_params(conv_tol=1e-9 if prec == "OM_F64" else 1e-7, max_steps=100_000,
+                                    precision=getattr(om, prec), drive=om.OM_DRIVE_PRESSURE, delta_rho=1e-4))
+    st, kl, info = fl.solve()
+    assert st == om.OM_OK
+    assert kl == pytest.approx(k_ref, rel=rel)
+
+
+def test_pressure_drive_through_offset_channel_and_entry_point(orc, om):
+    # no link across x: zero flux with the periodic body force, a finite k
+    # between pressure reservoirs, through the host entry point as well
+    m = S.offset_channel(shift=4)
+    rc, k_ref, *_ = orc.flow_solve_p(m, 1.0, 1.00005, 0.99995, 1e-10, 100, 200_000)
+    fp = om.flow_params(precision=om.OM_F64, conv_tol=1e-10, drive=om.OM_DRIVE_PRESSURE, delta_rho=1e-4)
+    st, k, kl, info, _ = om.om_solve_permeability(m, om.domain(m.shape), fp)
+    assert st == om.OM_OK and kl == pytest.approx(k_ref, rel=1e-9) and kl > 0.05
+    assert k == pytest.approx(kl * 1e-18, rel=1e-12)  # Eq. 15 at 1 nm
+
+
+def test_pressure_drive_rejected_where_unsupported(om):
+    m = np.ones((3, 4, 4), np.uint8)
+    dom = om.domain(m.shape)
+    ns = om.NodeSet(_dev(m), dom)
+    with pytest.raises(om.OmError):
+        om.Flow(ns, om.flow_params(drive=om.OM_DRIVE_PRESSURE))  # nx < 4
+    m4 = np.ones((6, 4, 4), np.uint8)
+    with pytest.raises(om.OmError):
+        om.Batch([om.domain(m4.shape)], [_dev(m4)], flow=om.flow_params(drive=om.OM_DRIVE_PRESSURE))
 
 
 # ------------------------------------------------------------------ to convergence
