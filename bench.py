@@ -390,10 +390,11 @@ def run_converge(a):
     K, tol, cap = 1000, 1e-5, a.max_steps
     fp = P.flow_params(precision=P.OM_F32, conv_tol=tol, check_every=K, max_steps=cap)
     dp = P.diff_params(precision=P.OM_F32, conv_tol=tol, check_every=K, max_steps=cap)
+    fields = ("ux", "c") if a.warm == "both" else ("c",)
     t0 = time.perf_counter()
-    data = W.make_dataset(_converge_set(a.n_train, 11, (64,)), fp, dp)
+    data = W.make_dataset(_converge_set(a.n_train, 11, (64,)), fp, dp, fields=fields)
     t_data = time.perf_counter() - t0
-    net = P.UNet(2, 2, (16, 32, 64, 128), seed=5)
+    net = P.UNet(2, len(fields), (16, 32, 64, 128), seed=5)
     t0 = time.perf_counter()
     hist = W.train(net, data, epochs=a.epochs, lr=2e-3, lr_end=1e-4)
     torch.cuda.synchronize()
@@ -415,11 +416,12 @@ def run_converge(a):
     t0 = time.perf_counter()
     b = P.Batch([s[1] for s in structs], [s[3] for s in structs], [s[4] for s in structs], flow=fp, diff=fp16)
     if a.warm != "none":
+        nch, ci = len(fields), fields.index("c")
         for k, (_, dom, mask, tr, d) in enumerate(structs):
             y = W.predict(net, mask, d, dom)
             if a.warm == "both":
-                b.init_fields(0, k, y, stride=2, scale=W.velocity_scale(fp))
-            b.init_fields(1, k, y[1:], stride=2, from_linear=True)
+                b.init_fields(0, k, y[fields.index("ux"):], stride=nch, scale=W.velocity_scale(fp))
+            b.init_fields(1, k, y[ci:], stride=nch, from_linear=True)
     kl, _, info_f, st_f = b.solve(0)
     dl, _, info_d, st_d = b.solve(1)
     torch.cuda.synchronize()

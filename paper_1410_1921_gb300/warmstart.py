@@ -5,9 +5,10 @@ labelling, pore size, LB solves, U-Net forward/backward/Adam, warm-start
 initialisation).  Training targets are assembled on the host from the solved
 fields (data preparation, outside the solve path).
 
-Targets per voxel: u_x / U0 with U0 = g L0^2 / nu (L0 = 10 lattice units),
-and C - C_lin(x), the concentration's departure from the linear inlet-outlet
-profile; the loss is taken over the node set.  Inputs: pore mask and d / 60 nm.
+Targets per voxel, the network's output channels in the order of `fields`:
+"ux" = u_x / U0 with U0 = g L0^2 / nu (L0 = 10 lattice units), "c" = C -
+C_lin(x), the concentration's departure from the linear inlet-outlet profile;
+the loss is taken over the node set.  Inputs: pore mask and d / 60 nm.
 """
 import time
 
@@ -20,6 +21,7 @@ from . import (OM_ENOPERC, OM_F32, OM_OK, OM_PORE_CHORD13, Diffusion, Flow, Node
 
 D_SCALE = 1.0 / 60.0
 L0 = 10.0
+FIELDS = ("ux", "c")
 
 
 def velocity_scale(fp):
@@ -49,32 +51,34 @@ def net_input(mask, d, dom):
     return x.view(1, dom.nx, dom.ny, dom.nz, 2)
 
 
-def solve(dom, tr, d, fp, dp, prediction=None, warm_flow=False):
+def solve(dom, tr, d, fp, dp, prediction=None, warm_flow=False, fields=FIELDS, flow=True):
     """Flow and diffusion solves on the transport set, cold or warm-started
-    from a network output (float [N][2]): the diffusion from its
-    concentration channel, the flow from its velocity channel only with
-    warm_flow (velocity warm starts were measured to slow the flow's
-    convergence: the predicted field is not divergence-free and excites slow
-    pressure modes).  Returns a dict of results, step counts, wall times and
-    the solved fields (ux, C)."""
+    from a network output (float [N][len(fields)]): the diffusion from its
+    "c" channel, the flow from its "ux" channel only with warm_flow (velocity
+    warm starts were measured to slow the flow's convergence: the predicted
+    field is not divergence-free and excites slow pressure modes).  flow=False
+    skips the flow solve.  Returns a dict of results, step counts, wall times
+    and the solved fields (ux, C)."""
     ns = NodeSet(tr, dom)
     out = {"nodes": ns.n_nodes}
     N = tr.numel()
-    t0 = time.perf_counter()
-    fl = Flow(ns, fp)
-    if prediction is not None and warm_flow:
-        fl.init_velocity(prediction, stride=2, scale=velocity_scale(fp))
-    st, kl, info = fl.solve()
-    torch.cuda.synchronize()
-    out.update(flow_status=st, k_lattice=kl, flow_steps=info.steps, flow_s=time.perf_counter() - t0)
-    u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
-    fl.get_velocity(u)
-    out["ux"] = u[:N].clone()
-    fl.close()
+    nch = len(fields)
+    if flow:
+        t0 = time.perf_counter()
+        fl = Flow(ns, fp)
+        if prediction is not None and warm_flow and "ux" in fields:
+            fl.init_velocity(prediction[fields.index("ux"):], stride=nch, scale=velocity_scale(fp))
+        st, kl, info = fl.solve()
+        torch.cuda.synchronize()
+        out.update(flow_status=st, k_lattice=kl, flow_steps=info.steps, flow_s=time.perf_counter() - t0)
+        u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+        fl.get_velocity(u)
+        out["ux"] = u[:N].clone()
+        fl.close()
     t0 = time.perf_counter()
     df = Diffusion(ns, d, dp)
-    if prediction is not None:
-        df.init_concentration(prediction[1:], stride=2, from_linear=True)
+    if prediction is not None and "c" in fields:
+        df.init_concentration(prediction[fields.index("c"):], stride=nch, from_linear=True)
     st, Dl, info = df.solve()
     torch.cuda.synchronize()
     out.update(diff_status=st, D_lattice=Dl, diff_steps=info.steps, diff_s=time.perf_counter() - t0)
@@ -86,34 +90,43 @@ def solve(dom, tr, d, fp, dp, prediction=None, warm_flow=False):
     return out
 
 
-def targets(res, dom, fp, dp):
-    """Training target [1, nx, ny, nz, 2] from solved fields (host assembly)."""
-    ux = res["ux"].cpu().numpy().reshape(dom.nx, dom.ny, dom.nz) / velocity_scale(fp)
-    x = (np.arange(dom.nx) + 0.5)[:, None, None]
-    clin = dp.c_in + (dp.c_out - dp.c_in) * x / dom.nx
-    c = res["C"].cpu().numpy().reshape(dom.nx, dom.ny, dom.nz) - clin
-    t = np.stack([ux, c], -1)[None].astype(np.float32)
+def targets(res, dom, fp, dp, fields=FIELDS):
+    """Training target [1, nx, ny, nz, len(fields)] from solved fields (host
+    assembly)."""
+    ch = []
+    for f in fields:
+        if f == "ux":
+            ch.append(res["ux"].cpu().numpy().reshape(dom.nx, dom.ny, dom.nz) / velocity_scale(fp))
+        elif f == "c":
+            x = (np.arange(dom.nx) + 0.5)[:, None, None]
+            clin = dp.c_in + (dp.c_out - dp.c_in) * x / dom.nx
+            ch.append(res["C"].cpu().numpy().reshape(dom.nx, dom.ny, dom.nz) - clin)
+        else:
+            raise ValueError(f"unknown field {f!r}")
+    t = np.stack(ch, -1)[None].astype(np.float32)
     return torch.from_numpy(t).cuda()
 
 
-def make_dataset(cfgs, fp=None, dp=None, log=None):
+def make_dataset(cfgs, fp=None, dp=None, log=None, fields=FIELDS):
     """Solve every structure (cold, FP32) and keep (input, target, mask) of
     those whose solves reached the convergence test (a flow with no link
-    across the periodic x boundary counts: its field is exactly u = 0)."""
+    across the periodic x boundary counts: its field is exactly u = 0).  The
+    flow is solved only when "ux" is among the fields."""
     fp = fp or flow_params(precision=OM_F32)
     dp = dp or diff_params(precision=OM_F32)
+    flow = "ux" in fields
     data = []
     for cfg in cfgs:
         dom, mask, tr, d = structure(cfg)
         if int(tr.sum().item()) == 0:
             continue
-        res = solve(dom, tr, d, fp, dp)
-        if res["flow_status"] not in (OM_OK, OM_ENOPERC) or res["diff_status"] != OM_OK:
+        res = solve(dom, tr, d, fp, dp, flow=flow)
+        if (flow and res["flow_status"] not in (OM_OK, OM_ENOPERC)) or res["diff_status"] != OM_OK:
             continue
-        data.append((net_input(mask, d, dom), targets(res, dom, fp, dp), tr.view(1, dom.nx, dom.ny, dom.nz)))
+        data.append((net_input(mask, d, dom), targets(res, dom, fp, dp, fields), tr.view(1, dom.nx, dom.ny, dom.nz)))
         if log:
             log(f"sample {len(data)}: {cfg.shape} eps={cfg.porosity:.2f} nodes={res['nodes']} "
-                f"flow {res['flow_steps']} diff {res['diff_steps']} steps")
+                f"flow {res.get('flow_steps', 0)} diff {res['diff_steps']} steps")
     return data
 
 
@@ -138,7 +151,8 @@ def train(net, data, epochs, lr=1e-3, lr_end=1e-4, seed=0, log=None):
 
 
 def predict(net, mask, d, dom):
+    """Network output, flat float [N][net.out_ch] on the device."""
     x = net_input(mask, d, dom)
-    y = torch.empty(mask.numel() * 2, dtype=torch.float32, device="cuda")
+    y = torch.empty(mask.numel() * net.out_ch, dtype=torch.float32, device="cuda")
     net.forward(x, y)
     return y
