@@ -103,16 +103,19 @@ typedef struct {
 
 enum { OM_DRIVE_FORCE = 0, OM_DRIVE_PRESSURE = 1 };
 
-/* D3Q7 Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
+/* Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
  * size and relaxation time of Eq. 12, inlet/outlet concentrations.
  * Convergence: every check_every steps both sum|dC| / sum|C| and the relative
- * change of the total flux sum J_x drop below conv_tol. */
+ * change of the total flux sum J_x drop below conv_tol.  lattice: 7 (D3Q7,
+ * c_s^2 = 1/4) or 19 (the paper's D3Q19 with the flow's velocities and
+ * weights, c_s^2 = 1/3); D_L = c_s^2 (tau_g - 1/2).  Batches take 7 only. */
 typedef struct {
   double T_K, M_kg_per_mol, d_ref_nm, tau_ref, c_in, c_out, conv_tol;
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
   int32_t variant; /* as om_flow_params.variant, 0..3 (larger values clamp to 3) */
+  int32_t lattice;
 } om_diff_params;
 
 typedef struct {

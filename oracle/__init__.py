@@ -79,6 +79,16 @@ def lib():
         L.orc_tau_knudsen.restype = C.c_double
         L.orc_tau_knudsen.argtypes = [C.c_double] * 3
         L.orc_diff_init.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _f64p]
+        L.orc_diffq_init.restype = C.c_int
+        L.orc_diffq_init.argtypes = [C.c_int, _u8p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _f64p]
+        L.orc_diffq_step.restype = C.c_int
+        L.orc_diffq_step.argtypes = [C.c_int, _u8p, C.c_int, C.c_int, C.c_int, _f64p, C.c_double, C.c_double,
+                                     _f64p]
+        L.orc_diffq_fields.restype = C.c_int
+        L.orc_diffq_fields.argtypes = [C.c_int, _u8p, C.c_int, C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p]
+        L.orc_diffq_solve.restype = C.c_int
+        L.orc_diffq_solve.argtypes = [C.c_int, _u8p, C.c_int, C.c_int, C.c_int, _f64p, C.c_double, C.c_double,
+                                      C.c_double, C.c_int, C.c_int64, _f64p, _f64p]
         L.orc_diff_step.restype = C.c_int
         L.orc_diff_step.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, _f64p, C.c_double, C.c_double,
                                     _f64p]
@@ -287,19 +297,22 @@ def omega_field(node, d_nm, d_ref_nm=60.0, tau_ref=1.0):
     return om
 
 
-def diff_init(node, cin=1.0, cout=0.0):
+def diff_init(node, cin=1.0, cout=0.0, q=7):
+    """a_i C_lin(x) on the node set, q = 7 (D3Q7) or 19 (the paper's D3Q19)."""
     n = _u8(node)
-    g = np.zeros(7 * n.size)
-    lib().orc_diff_init(_p(n, _u8p), *n.shape, cin, cout, _p(g, _f64p))
-    return g.reshape((7,) + n.shape)
+    g = np.zeros(q * n.size)
+    assert lib().orc_diffq_init(q, _p(n, _u8p), *n.shape, cin, cout, _p(g, _f64p)) == ORC_OK
+    return g.reshape((q,) + n.shape)
 
 
 def diff_step(node, g, omega, cin=1.0, cout=0.0, steps=1):
+    """Advance g [q, nx, ny, nz] (q = 7 or 19, from its shape); a copy."""
     n = _u8(node)
     g = np.ascontiguousarray(g, np.float64).copy()
+    q = g.shape[0]
     om = np.ascontiguousarray(omega, np.float64)
     for _ in range(steps):
-        rc = lib().orc_diff_step(_p(n, _u8p), *n.shape, _p(om, _f64p), cin, cout, _p(g, _f64p))
+        rc = lib().orc_diffq_step(q, _p(n, _u8p), *n.shape, _p(om, _f64p), cin, cout, _p(g, _f64p))
         assert rc == ORC_OK
     return g
 
@@ -309,17 +322,17 @@ def diff_fields(node, g, omega):
     g = np.ascontiguousarray(g, np.float64)
     om = np.ascontiguousarray(omega, np.float64)
     Cf, J = np.zeros(n.size), np.zeros(n.size)
-    lib().orc_diff_fields(_p(n, _u8p), *n.shape, _p(om, _f64p), _p(g, _f64p), _p(Cf, _f64p),
-                          _p(J, _f64p))
+    assert lib().orc_diffq_fields(g.shape[0], _p(n, _u8p), *n.shape, _p(om, _f64p), _p(g, _f64p), _p(Cf, _f64p),
+                                  _p(J, _f64p)) == ORC_OK
     return Cf.reshape(n.shape), J.reshape(n.shape)
 
 
-def diff_solve(node, omega, cin=1.0, cout=0.0, tol=1e-6, K=100, max_steps=1_000_000):
+def diff_solve(node, omega, cin=1.0, cout=0.0, tol=1e-6, K=100, max_steps=1_000_000, q=7):
     """Returns (status, D_eff_L, sum_Jx, steps, rel_change, sum_C, g)."""
     n = _u8(node)
     om = np.ascontiguousarray(omega, np.float64)
-    g = np.zeros(7 * n.size)
+    g = np.zeros(q * n.size)
     out = np.zeros(5)
-    rc = lib().orc_diff_solve(_p(n, _u8p), *n.shape, _p(om, _f64p), cin, cout, tol, K, max_steps,
-                              _p(g, _f64p), _p(out, _f64p))
-    return rc, out[0], out[1], int(out[2]), out[3], out[4], g.reshape((7,) + n.shape)
+    rc = lib().orc_diffq_solve(q, _p(n, _u8p), *n.shape, _p(om, _f64p), cin, cout, tol, K, max_steps,
+                               _p(g, _f64p), _p(out, _f64p))
+    return rc, out[0], out[1], int(out[2]), out[3], out[4], g.reshape((q,) + n.shape)

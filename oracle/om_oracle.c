@@ -758,58 +758,97 @@ int orc_flow_solve_p(const uint8_t *node, int nx, int ny, int nz, double tau, do
 }
 
 /* ======================================================================
- * 7. BGK diffusion (Sec. 3.2, Eq. 10) on D3Q7: g_i^eq = a_i C with
- *    a_0 = 1/4, a_1..6 = 1/8 (c_s^2 = 1/4), C = sum g_i, one relaxation time
- *    per node from the local pore size (Eq. 12, supplied as omega = 1/tau_g).
- *    Bounce-back at walls; periodic y, z; fixed concentration at the half
- *    links x = -1/2 (C_in) and x = nx - 1/2 (C_out) by anti-bounce-back.
- *    Velocity order: rest, +x, -x, +y, -y, +z, -z.
+ * 7. BGK diffusion (Sec. 3.2, Eq. 10): g_i^eq = a_i C, C = sum g_i, one
+ *    relaxation time per node from the local pore size (Eq. 12, supplied as
+ *    omega = 1/tau_g), on D3Q7 (a_0 = 1/4, a_1..6 = 1/8, c_s^2 = 1/4; order
+ *    rest, +x, -x, +y, -y, +z, -z) or the paper's D3Q19 (Eq. 2 velocities,
+ *    Eq. 3 weights, c_s^2 = 1/3).  Bounce-back at walls; periodic y, z; fixed
+ *    concentration at the half links x = -1/2 (C_in) and x = nx - 1/2 (C_out)
+ *    by anti-bounce-back of every population whose link crosses the face.
  * ====================================================================== */
-static const int E7[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
-static const int OPP7[7] = {0, 2, 1, 4, 3, 6, 5};
-static double orc_a7(int i) { return i == 0 ? 0.25 : 0.125; }
+/* The diffusion lattice: D3Q7 (rest, +x, -x, +y, -y, +z, -z; a_0 = 1/4,
+ * a_1..6 = 1/8; c_s^2 = 1/4) or the paper's D3Q19 (the velocities and
+ * weights of Eqs. 2-3 in the order of orc_velocities19: 1/3, 1/18, 1/36;
+ * c_s^2 = 1/3).  The BGK relaxation, bounce-back and anti-bounce-back rules
+ * below are the same for both. */
+typedef struct {
+  int q;
+  int e[19][3];
+  int opp[19];
+  double w[19];
+} orc_dlat;
+
+static int orc_dlat_make(int q, orc_dlat *L) {
+  static const int E7[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  static const int OPP7[7] = {0, 2, 1, 4, 3, 6, 5};
+  L->q = q;
+  if (q == 7) {
+    for (int i = 0; i < 7; ++i) {
+      for (int d = 0; d < 3; ++d) L->e[i][d] = E7[i][d];
+      L->opp[i] = OPP7[i];
+      L->w[i] = i == 0 ? 0.25 : 0.125;
+    }
+    return ORC_OK;
+  }
+  if (q == 19) {
+    int e[57];
+    orc_velocities19(e);
+    for (int i = 0; i < 19; ++i) {
+      for (int d = 0; d < 3; ++d) L->e[i][d] = e[3 * i + d];
+      L->opp[i] = orc_opp19(i);
+      L->w[i] = orc_w19(i);
+    }
+    return ORC_OK;
+  }
+  return ORC_EINVAL;
+}
 
 /* Eq. 12: tau_g = (d / d_ref)(tau_ref - 1/2) + 1/2 */
 double orc_tau_knudsen(double d_nm, double d_ref_nm, double tau_ref) {
   return (d_nm / d_ref_nm) * (tau_ref - 0.5) + 0.5;
 }
 
-void orc_diff_init(const uint8_t *node, int nx, int ny, int nz, double cin, double cout, double *g) {
+int orc_diffq_init(int q, const uint8_t *node, int nx, int ny, int nz, double cin, double cout, double *g) {
+  orc_dlat L;
+  if (orc_dlat_make(q, &L)) return ORC_EINVAL;
   int64_t N = (int64_t)nx * ny * nz;
   for (int64_t v = 0; v < N; ++v) {
     int x = (int)(v / ((int64_t)ny * nz));
     double c = cin + (cout - cin) * (((double)x + 0.5) / (double)nx);
-    for (int i = 0; i < 7; ++i) g[(int64_t)i * N + v] = node[v] ? orc_a7(i) * c : 0.0;
+    for (int i = 0; i < q; ++i) g[(int64_t)i * N + v] = node[v] ? L.w[i] * c : 0.0;
   }
+  return ORC_OK;
 }
 
-int orc_diff_step(const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin,
-                  double cout, double *g) {
+int orc_diffq_step(int q, const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin,
+                   double cout, double *g) {
+  orc_dlat L;
+  if (orc_dlat_make(q, &L)) return ORC_EINVAL;
   int64_t N = (int64_t)nx * ny * nz;
-  double *gs = (double *)malloc(sizeof(double) * 7 * (size_t)N);
+  double *gs = (double *)malloc(sizeof(double) * (size_t)q * (size_t)N);
   if (!gs) return ORC_ENOMEM;
   for (int64_t v = 0; v < N; ++v) {
     if (!node[v]) continue;
     double C = 0.0;
-    for (int i = 0; i < 7; ++i) C += g[(int64_t)i * N + v];
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < q; ++i) C += g[(int64_t)i * N + v];
+    for (int i = 0; i < q; ++i) {
       double gi = g[(int64_t)i * N + v];
-      gs[(int64_t)i * N + v] = gi - omega[v] * (gi - orc_a7(i) * C);
+      gs[(int64_t)i * N + v] = gi - omega[v] * (gi - L.w[i] * C);
     }
   }
   for (int64_t v = 0; v < N; ++v) {
     if (!node[v]) continue;
     int x = (int)(v / ((int64_t)ny * nz)), y = (int)((v / nz) % ny), z = (int)(v % nz);
-    for (int i = 0; i < 7; ++i) {
-      int sx = x - E7[i][0];
+    for (int i = 0; i < q; ++i) {
+      int sx = x - L.e[i][0];
       double val;
       if (sx < 0)
-        val = -gs[(int64_t)OPP7[i] * N + v] + 2.0 * orc_a7(i) * cin;
+        val = -gs[(int64_t)L.opp[i] * N + v] + 2.0 * L.w[i] * cin;
       else if (sx >= nx)
-        val = -gs[(int64_t)OPP7[i] * N + v] + 2.0 * orc_a7(i) * cout;
+        val = -gs[(int64_t)L.opp[i] * N + v] + 2.0 * L.w[i] * cout;
       else {
-        int64_t src = vidx(sx, wrap(y - E7[i][1], ny), wrap(z - E7[i][2], nz), ny, nz);
-        val = node[src] ? gs[(int64_t)i * N + src] : gs[(int64_t)OPP7[i] * N + v];
+        int64_t src = vidx(sx, wrap(y - L.e[i][1], ny), wrap(z - L.e[i][2], nz), ny, nz);
+        val = node[src] ? gs[(int64_t)i * N + src] : gs[(int64_t)L.opp[i] * N + v];
       }
       g[(int64_t)i * N + v] = val;
     }
@@ -819,21 +858,24 @@ int orc_diff_step(const uint8_t *node, int nx, int ny, int nz, const double *ome
 }
 
 /* C = sum g_i; diffusive flux J_x = (1 - omega/2) sum_i e_ix g_i */
-void orc_diff_fields(const uint8_t *node, int nx, int ny, int nz, const double *omega,
-                     const double *g, double *C, double *Jx) {
+int orc_diffq_fields(int q, const uint8_t *node, int nx, int ny, int nz, const double *omega, const double *g,
+                     double *C, double *Jx) {
+  orc_dlat L;
+  if (orc_dlat_make(q, &L)) return ORC_EINVAL;
   int64_t N = (int64_t)nx * ny * nz;
   for (int64_t v = 0; v < N; ++v) {
     double c = 0.0, j = 0.0;
     if (node[v]) {
-      for (int i = 0; i < 7; ++i) {
+      for (int i = 0; i < q; ++i) {
         c += g[(int64_t)i * N + v];
-        j += E7[i][0] * g[(int64_t)i * N + v];
+        j += L.e[i][0] * g[(int64_t)i * N + v];
       }
       j *= (1.0 - 0.5 * omega[v]);
     }
     if (C) C[v] = c;
     if (Jx) Jx[v] = j;
   }
+  return ORC_OK;
 }
 
 /* Solve to the steady state.  Every K steps both the concentration field
@@ -843,15 +885,16 @@ void orc_diff_fields(const uint8_t *node, int nx, int ny, int nz, const double *
  * flux: D_eff,L = (sum J_x / N) * nx / (C_in - C_out).
  * out[0] D_eff,L, out[1] sum J_x, out[2] steps, out[3] last relative change
  * (the larger of the two), out[4] sum C. */
-int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin,
-                   double cout, double tol, int K, int64_t max_steps, double *g, double *out) {
+int orc_diffq_solve(int q, const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin,
+                    double cout, double tol, int K, int64_t max_steps, double *g, double *out) {
+  if (q != 7 && q != 19) return ORC_EINVAL;
   int64_t N = (int64_t)nx * ny * nz;
   double *C = (double *)malloc(sizeof(double) * (size_t)N);
   double *J = (double *)malloc(sizeof(double) * (size_t)N);
   double *prev = (double *)malloc(sizeof(double) * (size_t)N);
   if (!C || !J || !prev) { free(C); free(J); free(prev); return ORC_ENOMEM; }
-  orc_diff_init(node, nx, ny, nz, cin, cout, g);
-  orc_diff_fields(node, nx, ny, nz, omega, g, prev, J);
+  orc_diffq_init(q, node, nx, ny, nz, cin, cout, g);
+  orc_diffq_fields(q, node, nx, ny, nz, omega, g, prev, J);
   double sj_prev = 0.0;
   for (int64_t v = 0; v < N; ++v)
     if (node[v]) sj_prev += J[v];
@@ -860,10 +903,10 @@ int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *om
   int rc = ORC_ENOTCONVERGED;
   while (n < max_steps) {
     for (int k = 0; k < K && n < max_steps; ++k, ++n) {
-      int r = orc_diff_step(node, nx, ny, nz, omega, cin, cout, g);
+      int r = orc_diffq_step(q, node, nx, ny, nz, omega, cin, cout, g);
       if (r) { free(C); free(J); free(prev); return r; }
     }
-    orc_diff_fields(node, nx, ny, nz, omega, g, C, J);
+    orc_diffq_fields(q, node, nx, ny, nz, omega, g, C, J);
     double dc = 0.0, ac = 0.0;
     sj = 0.0;
     sc = 0.0;
@@ -890,4 +933,21 @@ int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *om
   free(J);
   free(prev);
   return rc;
+}
+
+/* The D3Q7 entry points (the lattice of the benchmark workloads). */
+void orc_diff_init(const uint8_t *node, int nx, int ny, int nz, double cin, double cout, double *g) {
+  orc_diffq_init(7, node, nx, ny, nz, cin, cout, g);
+}
+int orc_diff_step(const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin, double cout,
+                  double *g) {
+  return orc_diffq_step(7, node, nx, ny, nz, omega, cin, cout, g);
+}
+void orc_diff_fields(const uint8_t *node, int nx, int ny, int nz, const double *omega, const double *g,
+                     double *C, double *Jx) {
+  orc_diffq_fields(7, node, nx, ny, nz, omega, g, C, Jx);
+}
+int orc_diff_solve(const uint8_t *node, int nx, int ny, int nz, const double *omega, double cin, double cout,
+                   double tol, int K, int64_t max_steps, double *g, double *out) {
+  return orc_diffq_solve(7, node, nx, ny, nz, omega, cin, cout, tol, K, max_steps, g, out);
 }

@@ -53,7 +53,7 @@ class om_diff_params(C.Structure):
     _fields_ = [("T_K", C.c_double), ("M_kg_per_mol", C.c_double), ("d_ref_nm", C.c_double),
                 ("tau_ref", C.c_double), ("c_in", C.c_double), ("c_out", C.c_double),
                 ("conv_tol", C.c_double), ("check_every", C.c_int32), ("max_steps", C.c_int64),
-                ("precision", C.c_int32), ("variant", C.c_int32)]
+                ("precision", C.c_int32), ("variant", C.c_int32), ("lattice", C.c_int32)]
 
 
 class om_run_info(C.Structure):
@@ -202,9 +202,9 @@ def flow_params(tau=1.0, body_force=1e-6, conv_tol=1e-6, check_every=100, max_st
 
 
 def diff_params(T_K=300.0, M_kg_per_mol=0.016, d_ref_nm=60.0, tau_ref=1.0, c_in=1.0, c_out=0.0,
-                conv_tol=1e-6, check_every=100, max_steps=10_000_000, precision=OM_F32, variant=-1):
+                conv_tol=1e-6, check_every=100, max_steps=10_000_000, precision=OM_F32, variant=-1, lattice=7):
     return om_diff_params(T_K, M_kg_per_mol, d_ref_nm, tau_ref, c_in, c_out, conv_tol, check_every,
-                          max_steps, precision, variant)
+                          max_steps, precision, variant, lattice)
 
 
 # ------------------------------------------------------------------ host-buffer entry points

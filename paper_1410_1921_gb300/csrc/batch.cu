@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kTile) diff_batch_observe(DiffArgs<T> a, const
       unpack_xyz(b.coord[ln], x, y, z);
       if (ODD) diff_neighbours(b, b.coord[ln], nb, x);
       C g[7];
-      diff_load<T, ODD>(b, n, nb, x, g);
+      diff_load<T, D3Q7, ODD>(b, n, nb, x, g);
       double dev = 0;
 #pragma unroll
       for (int i = 0; i < 7; ++i) dev += (double)g[i];
@@ -225,7 +225,7 @@ __global__ void diff_batch_export(DiffArgs<T> a, uint32_t off, const int64_t* vo
   unpack_xyz(a.coord[ln], x, y, z);
   if (ODD) diff_neighbours(a, a.coord[ln], nb, x);
   C g[7];
-  diff_load<T, ODD>(a, off + ln, nb, x, g);
+  diff_load<T, D3Q7, ODD>(a, off + ln, nb, x, g);
   const int64_t v = vox[ln];
   const double cref = diff_ref(a, off + ln, x);
 #pragma unroll
@@ -694,6 +694,7 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
                                      const om_diff_params* dp, void* stream, om_batch** out) {
   if (n <= 0 || !doms || !nodes_dev || !out || (!fp && !dp)) return fail(OM_EINVAL, "om_batch_create: bad arguments");
   if (dp && !d_nm_dev) return fail(OM_EINVAL, "om_batch_create: diffusion needs pore sizes");
+  if (dp && dp->lattice != 7) return fail(OM_EINVAL, "om_batch_create: batches take the D3Q7 diffusion lattice");
   if (fp && !(fp->tau > 0.5)) return fail(OM_EINVAL, "om_batch_create: tau must exceed 1/2");
   if (fp && fp->drive != OM_DRIVE_FORCE) return fail(OM_EINVAL, "om_batch_create: batches take the body-force drive");
   if (dp && (!(dp->d_ref_nm > 0.0) || !(dp->tau_ref > 0.5) || !(dp->c_in != dp->c_out)))

@@ -1,8 +1,10 @@
-// diff.cu -- D3Q7 BGK Knudsen-diffusion sweep (Sec. 3.2, Eqs. 10-12) in the
-// AA pattern on the fluid-node layout of nodeset.cu.
+// diff.cu -- BGK Knudsen-diffusion sweep (Sec. 3.2, Eqs. 10-12) in the AA
+// pattern on the fluid-node layout of nodeset.cu, on D3Q7 (a = {1/4, 1/8 x
+// 6}, c_s^2 = 1/4) or the paper's D3Q19 (Eq. 2-3 velocities and weights,
+// c_s^2 = 1/3), chosen by om_diff_params.lattice.
 //
-// g*_i = g_i - omega(x) (g_i - a_i C), C = sum g_i, a = {1/4, 1/8 x 6}, with
-// omega = 1/tau_g from the local pore size by Eq. 12.  Populations are
+// g*_i = g_i - omega(x) (g_i - a_i C), C = sum g_i, with omega = 1/tau_g
+// from the local pore size by Eq. 12.  Populations are
 // stored as deviations from a reference equilibrium a_i C_ref: in FP64 the
 // linear profile C_lin(x) between the two fixed concentrations (the odd step
 // adds the jump a_i s e_ix, s = dC_lin/dx, when a population changes cell);
@@ -28,15 +30,15 @@ namespace om {
 // updating the current one (the flow sweep's variants 2 and 3).
 constexpr int kDiffVariants = 4;
 
-template <class T, bool ODD, int MINB>
-__global__ void __launch_bounds__(256, MINB) d3q7_sweep(DiffArgs<T> a) {
+template <class T, class L, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) diff_sweep(DiffArgs<T, L> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   diff_node<T, ODD>(a, n, n);
 }
 
-template <class T, bool ODD, int MINB>
-__global__ void __launch_bounds__(256, MINB) d3q7_sweep_strided(DiffArgs<T> a) {
+template <class T, class L, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) diff_sweep_strided(DiffArgs<T, L> a) {
   const uint32_t stride = gridDim.x * blockDim.x;
   uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(256, MINB) d3q7_sweep_strided(DiffArgs<T> a) {
     const bool more = nn < a.nf;
     uint32_t cn = 0u;
     if (ODD && more) cn = __ldg(a.coord + nn);
-    diff_node_at<T, ODD>(a, n, c);
+    diff_node_at<T, L, ODD>(a, n, c);
     if (!more) break;
     n = (uint32_t)nn;
     c = cn;
@@ -54,62 +56,66 @@ __global__ void __launch_bounds__(256, MINB) d3q7_sweep_strided(DiffArgs<T> a) {
 }
 
 // Observables: sum J_x, sum |C - prev|, sum |C|, sum C, sum D_L; prev <- C.
-template <class T, bool ODD>
-__global__ void __launch_bounds__(kObsThreads) d3q7_observe(DiffArgs<T> a, double* prev,
+template <class T, class L, bool ODD>
+__global__ void __launch_bounds__(kObsThreads) diff_observe(DiffArgs<T, L> a, double* prev,
                                                             double* partials) {
   using C = typename Stg<T>::C;
   double acc[5] = {0, 0, 0, 0, 0};
   for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.nf; n += gridDim.x * blockDim.x) {
-    uint32_t nb[7];
+    uint32_t nb[L::Q];
     int x, y, z;
     unpack_xyz(a.coord[n], x, y, z);
     if (ODD) diff_neighbours(a, a.coord[n], nb, x);
-    C g[7];
-    diff_load<T, ODD>(a, n, nb, x, g);
-    double dev = 0;
+    C g[L::Q];
+    diff_load<T, L, ODD>(a, n, nb, x, g);
+    double dev = 0, ex = 0;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) dev += (double)g[i];
+    for (int i = 0; i < L::Q; ++i) {
+      dev += (double)g[i];
+      if (L::e(i, 0)) ex += L::e(i, 0) > 0 ? (double)g[i] : -(double)g[i];
+    }
     const double c = dev + diff_ref(a, n, x);
     const double om = (double)a.omega[n];
-    const double jx = (1.0 - 0.5 * om) * ((double)g[1] - (double)g[2]);
+    const double jx = (1.0 - 0.5 * om) * ex;
     acc[0] += jx;
     acc[1] += fabs(c - prev[n]);
     acc[2] += fabs(c);
     acc[3] += c;
-    acc[4] += 0.25 * (1.0 / om - 0.5);
+    acc[4] += L::cs2 * (1.0 / om - 0.5);
     prev[n] = c;
   }
   block_reduce_store<5>(acc, partials);
 }
 
-template <class T, bool ODD>
-__global__ void d3q7_export(DiffArgs<T> a, const int64_t* vox, int64_t N, double* gdense,
+template <class T, class L, bool ODD>
+__global__ void diff_export(DiffArgs<T, L> a, const int64_t* vox, int64_t N, double* gdense,
                             float* cdense, float* jdense) {
   using C = typename Stg<T>::C;
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
-  uint32_t nb[7];
+  uint32_t nb[L::Q];
   int x, y, z;
   unpack_xyz(a.coord[n], x, y, z);
   if (ODD) diff_neighbours(a, a.coord[n], nb, x);
-  C g[7];
-  diff_load<T, ODD>(a, n, nb, x, g);
+  C g[L::Q];
+  diff_load<T, L, ODD>(a, n, nb, x, g);
   const int64_t v = vox[n];
   const double cref = diff_ref(a, n, x);
-  double dev = 0;
+  double dev = 0, ex = 0;
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < L::Q; ++i) {
     dev += (double)g[i];
-    if (gdense) gdense[i * N + v] = (double)g[i] + q7_w(i) * cref;
+    if (L::e(i, 0)) ex += L::e(i, 0) > 0 ? (double)g[i] : -(double)g[i];
+    if (gdense) gdense[i * N + v] = (double)g[i] + L::w(i) * cref;
   }
   if (cdense) cdense[v] = (float)(dev + cref);
-  if (jdense) jdense[v] = (float)((1.0 - 0.5 * (double)a.omega[n]) * ((double)g[1] - (double)g[2]));
+  if (jdense) jdense[v] = (float)((1.0 - 0.5 * (double)a.omega[n]) * ex);
 }
 
 // populations from the dense layout (linear != 0: the linear profile a_i C_lin);
 // 16-bit storage takes the node's C as its reference
-template <class T>
-__global__ void d3q7_import(DiffArgs<T> a, const int64_t* vox, int64_t N, const double* gdense,
+template <class T, class L>
+__global__ void diff_import(DiffArgs<T, L> a, const int64_t* vox, int64_t N, const double* gdense,
                             int linear) {
   using S = Stg<T>;
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,21 +128,21 @@ __global__ void d3q7_import(DiffArgs<T> a, const int64_t* vox, int64_t N, const 
   if constexpr (kRebased<T>) {
     if (!linear) {
       ref = 0.0;
-      for (int i = 0; i < 7; ++i) ref += gdense[i * N + v];
+      for (int i = 0; i < L::Q; ++i) ref += gdense[i * N + v];
     }
     a.cr[n] = (float)ref;
     ref = (double)a.cr[n];
   }
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    const double g = linear ? q7_w(i) * clin : gdense[i * N + v];
-    S::st(a.q[i] + n, (typename S::C)(g - q7_w(i) * ref), a.up);
+  for (int i = 0; i < L::Q; ++i) {
+    const double g = linear ? L::w(i) * clin : gdense[i * N + v];
+    S::st(a.q[i] + n, (typename S::C)(g - L::w(i) * ref), a.up);
   }
 }
 
 // warm start: g_i = a_i C (deviation a_i (C - C_lin(x))) in the even layout
-template <class T>
-__global__ void d3q7_init_c(DiffArgs<T> a, const int64_t* vox, const float* c, int64_t stride, int from_linear) {
+template <class T, class L>
+__global__ void diff_init_c(DiffArgs<T, L> a, const int64_t* vox, const float* c, int64_t stride, int from_linear) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   int x, y, z;
@@ -151,18 +157,18 @@ __global__ void d3q7_init_c(DiffArgs<T> a, const int64_t* vox, const float* c, i
     dc = cv - clin;
   }
 #pragma unroll
-  for (int i = 0; i < 7; ++i) Stg<T>::st(a.q[i] + n, (typename Stg<T>::C)(q7_w(i) * dc), a.up);
+  for (int i = 0; i < L::Q; ++i) Stg<T>::st(a.q[i] + n, (typename Stg<T>::C)(L::w(i) * dc), a.up);
 }
 
-template <class T>
-__global__ void d3q7_rebase(DiffArgs<T> a) {
+template <class T, class L>
+__global__ void diff_rebase(DiffArgs<T, L> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   diff_rebase_node<T>(a, n);
 }
 
 template <class T>
-__global__ void d3q7_omega(const int64_t* vox, const float* d_nm, int64_t nf, double d_ref,
+__global__ void diff_omega(const int64_t* vox, const float* d_nm, int64_t nf, double d_ref,
                            double tau_ref, typename Stg<T>::C* omega, int* bad) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nf) return;
@@ -182,6 +188,7 @@ struct om_diff {
   void* g = nullptr;
   void* omega = nullptr;
   float* cr = nullptr;  // per-node reference concentration (16-bit storage)
+  int q = 7;            // lattice: 7 (D3Q7) or 19 (D3Q19)
   double* prev = nullptr;
   double* partials = nullptr;
   double* obs_dev = nullptr;
@@ -197,11 +204,11 @@ struct om_diff {
 
 namespace {
 
-template <class T>
-DiffArgs<T> diff_args(const om_diff* df) {
-  DiffArgs<T> a;
+template <class T, class L>
+DiffArgs<T, L> diff_args(const om_diff* df) {
+  DiffArgs<T, L> a;
   const om_nodeset* ns = df->ns;
-  for (int i = 0; i < 7; ++i) a.q[i] = (T*)df->g + (size_t)i * ns->pitch;
+  for (int i = 0; i < L::Q; ++i) a.q[i] = (T*)df->g + (size_t)i * ns->pitch;
   a.nf = (uint32_t)ns->nf;
   a.col = ns->col;
   a.coord = ns->coord;
@@ -221,32 +228,37 @@ DiffArgs<T> diff_args(const om_diff* df) {
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-template <class T, bool ODD>
-void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const DiffArgs<T>& a) {
+// residency cap of variants 1 and 3: 8 blocks of 256 on D3Q7, 4 on D3Q19
+template <class L>
+constexpr int kDiffMinBlocks = L::Q == 7 ? 8 : 4;
+
+template <class T, class L, bool ODD>
+void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const DiffArgs<T, L>& a) {
+  constexpr int M = kDiffMinBlocks<L>;
   switch (variant) {
-    case 1: d3q7_sweep<T, ODD, 8><<<nb, 256, 0, s>>>(a); break;
+    case 1: diff_sweep<T, L, ODD, M><<<nb, 256, 0, s>>>(a); break;
     case 2: {
-      auto k = d3q7_sweep_strided<T, ODD, 0>;
+      auto k = diff_sweep_strided<T, L, ODD, 0>;
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
     case 3: {
-      auto k = d3q7_sweep_strided<T, ODD, 8>;
+      auto k = diff_sweep_strided<T, L, ODD, M>;
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
-    default: d3q7_sweep<T, ODD, 0><<<nb, 256, 0, s>>>(a); break;
+    default: diff_sweep<T, L, ODD, 0><<<nb, 256, 0, s>>>(a); break;
   }
 }
 
-template <class T>
-void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const DiffArgs<T>& a) {
-  if (odd) launch_sweep_p<T, true>(variant, nb, s, a);
-  else launch_sweep_p<T, false>(variant, nb, s, a);
+template <class T, class L>
+void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const DiffArgs<T, L>& a) {
+  if (odd) launch_sweep_p<T, L, true>(variant, nb, s, a);
+  else launch_sweep_p<T, L, false>(variant, nb, s, a);
 }
 
 // Capture K sweeps (K even, from an even time) into a CUDA graph once.
-template <class T>
+template <class T, class L>
 om_status diff_capture_t(om_diff* df, int K) {
   if (df->exec && df->graph_k == K) return OM_OK;
   if (df->exec) {
@@ -254,11 +266,11 @@ om_status diff_capture_t(om_diff* df, int K) {
     df->exec = nullptr;
   }
   if (!df->cap) OM_CUDA(cudaStreamCreateWithFlags(&df->cap, cudaStreamNonBlocking));
-  DiffArgs<T> a = diff_args<T>(df);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
   const unsigned nb = blocks_for(a.nf);
   cudaGraph_t g = nullptr;
   OM_CUDA(cudaStreamBeginCapture(df->cap, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) launch_sweep<T>(k & 1, df->var[k & 1], nb, df->cap, a);
+  for (int k = 0; k < K; ++k) launch_sweep<T, L>(k & 1, df->var[k & 1], nb, df->cap, a);
   cudaError_t e = cudaStreamEndCapture(df->cap, &g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
   e = cudaGraphInstantiate(&df->exec, g, 0);
@@ -270,26 +282,26 @@ om_status diff_capture_t(om_diff* df, int K) {
 
 // Advance nsteps: whole check windows from even times replay the captured
 // graph; anything else is launched one sweep at a time.
-template <class T>
+template <class T, class L>
 om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
   if (df->ns->nf == 0) {
     df->t += nsteps;
     return OM_OK;
   }
-  DiffArgs<T> a = diff_args<T>(df);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
   const unsigned nb = blocks_for(a.nf);
   const int K = df->p.check_every;
   while (nsteps > 0) {
     if (K >= 2 && !(K & 1) && !(df->t & 1) && nsteps >= K) {
-      OM_TRY(diff_capture_t<T>(df, K));
+      OM_TRY((diff_capture_t<T, L>(df, K)));
       OM_CUDA(cudaGraphLaunch(df->exec, s));
       df->t += K;
       nsteps -= K;
-      if (kRebased<T>) d3q7_rebase<T><<<nb, 256, 0, s>>>(a);  // once per window
+      if (kRebased<T>) diff_rebase<T, L><<<nb, 256, 0, s>>>(a);  // once per window
       continue;
     }
     const bool odd = df->t & 1;
-    launch_sweep<T>(odd, df->var[odd], nb, s, a);
+    launch_sweep<T, L>(odd, df->var[odd], nb, s, a);
     ++df->t;
     --nsteps;
   }
@@ -299,10 +311,10 @@ om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
 
 // Autotuner: time each launch variant of both sweeps (6 even/odd pairs after
 // a warm-up pair), keep the fastest per parity; the caller re-initialises.
-template <class T>
+template <class T, class L>
 om_status diff_tune_t(om_diff* df, cudaStream_t s) {
   if (df->ns->nf == 0) return OM_OK;
-  DiffArgs<T> a = diff_args<T>(df);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
   const unsigned nb = blocks_for(a.nf);
   cudaEvent_t ev[3];
   for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
@@ -311,9 +323,9 @@ om_status diff_tune_t(om_diff* df, cudaStream_t s) {
     float tot[2] = {0.f, 0.f};
     for (int r = 0; r < 7; ++r) {
       OM_CUDA(cudaEventRecord(ev[0], s));
-      launch_sweep<T>(false, v, nb, s, a);
+      launch_sweep<T, L>(false, v, nb, s, a);
       OM_CUDA(cudaEventRecord(ev[1], s));
-      launch_sweep<T>(true, v, nb, s, a);
+      launch_sweep<T, L>(true, v, nb, s, a);
       OM_CUDA(cudaEventRecord(ev[2], s));
       OM_CUDA(cudaEventSynchronize(ev[2]));
       if (r == 0) continue;
@@ -333,11 +345,11 @@ om_status diff_tune_t(om_diff* df, cudaStream_t s) {
   return OM_OK;
 }
 
-template <class T>
+template <class T, class L>
 om_status diff_observe_t(om_diff* df, double* out, cudaStream_t s) {
-  DiffArgs<T> a = diff_args<T>(df);
-  if (df->t & 1) d3q7_observe<T, true><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
-  else d3q7_observe<T, false><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
+  if (df->t & 1) diff_observe<T, L, true><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
+  else diff_observe<T, L, false><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
   launch_finalize(df->partials, kObsBlocks, 5, df->obs_dev, s);
   OM_CUDA(cudaGetLastError());
   OM_CUDA(cudaMemcpyAsync(df->obs_host, df->obs_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -346,46 +358,46 @@ om_status diff_observe_t(om_diff* df, double* out, cudaStream_t s) {
   return OM_OK;
 }
 
-template <class T>
+template <class T, class L>
 om_status diff_export_t(const om_diff* df, double* gd, float* cd, float* jd, cudaStream_t s) {
   const om_nodeset* ns = df->ns;
-  if (gd) OM_CUDA(cudaMemsetAsync(gd, 0, sizeof(double) * 7 * ns->N, s));
+  if (gd) OM_CUDA(cudaMemsetAsync(gd, 0, sizeof(double) * L::Q * ns->N, s));
   if (cd) OM_CUDA(cudaMemsetAsync(cd, 0, sizeof(float) * ns->N, s));
   if (jd) OM_CUDA(cudaMemsetAsync(jd, 0, sizeof(float) * ns->N, s));
   if (ns->nf == 0) return OM_OK;
-  DiffArgs<T> a = diff_args<T>(df);
-  if (df->t & 1) d3q7_export<T, true><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, gd, cd, jd);
-  else d3q7_export<T, false><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, gd, cd, jd);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
+  if (df->t & 1) diff_export<T, L, true><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, gd, cd, jd);
+  else diff_export<T, L, false><<<blocks_for(a.nf), 256, 0, s>>>(a, ns->vox, ns->N, gd, cd, jd);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
 
-template <class T>
+template <class T, class L>
 om_status diff_import_t(om_diff* df, const double* gd, int linear, cudaStream_t s) {
   if (df->ns->nf == 0) return OM_OK;
-  DiffArgs<T> a = diff_args<T>(df);
-  d3q7_import<T><<<blocks_for(a.nf), 256, 0, s>>>(a, df->ns->vox, df->ns->N, gd, linear);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
+  diff_import<T, L><<<blocks_for(a.nf), 256, 0, s>>>(a, df->ns->vox, df->ns->N, gd, linear);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
 
-template <class T>
+template <class T, class L>
 om_status diff_init_c_t(om_diff* df, const float* c, int64_t stride, int from_linear, cudaStream_t s) {
   df->t = 0;
   if (df->ns->nf == 0) return OM_OK;
-  DiffArgs<T> a = diff_args<T>(df);
-  d3q7_init_c<T><<<blocks_for(a.nf), 256, 0, s>>>(a, df->ns->vox, c, stride, from_linear);
+  DiffArgs<T, L> a = diff_args<T, L>(df);
+  diff_init_c<T, L><<<blocks_for(a.nf), 256, 0, s>>>(a, df->ns->vox, c, stride, from_linear);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
 
-template <class T>
+template <class T, class L>
 om_status diff_omega_t(om_diff* df, const float* d_nm, cudaStream_t s) {
   if (df->ns->nf == 0) return OM_OK;
   DevBuf<int> bad;
   OM_TRY(bad.alloc(1));
   OM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-  d3q7_omega<T><<<blocks_for(df->ns->nf), 256, 0, s>>>(df->ns->vox, d_nm, df->ns->nf, df->p.d_ref_nm,
+  diff_omega<T><<<blocks_for(df->ns->nf), 256, 0, s>>>(df->ns->vox, d_nm, df->ns->nf, df->p.d_ref_nm,
                                                        df->p.tau_ref, (typename Stg<T>::C*)df->omega,
                                                        bad.p);
   OM_CUDA(cudaGetLastError());
@@ -396,13 +408,19 @@ om_status diff_omega_t(om_diff* df, const float* d_nm, cudaStream_t s) {
   return OM_OK;
 }
 
-#define OM_DIFF_DISPATCH(df, fn, ...)                                        \
+#define OM_DIFF_DISPATCH_L(df, L, fn, ...)                                   \
   switch ((df)->p.precision) {                                               \
-    case OM_F64: return fn<double>(__VA_ARGS__);                             \
-    case OM_F32: return fn<float>(__VA_ARGS__);                              \
-    case OM_F16DEV: return fn<__half>(__VA_ARGS__);                          \
-    case OM_BF16DEV: return fn<__nv_bfloat16>(__VA_ARGS__);                  \
+    case OM_F64: return fn<double, L>(__VA_ARGS__);                          \
+    case OM_F32: return fn<float, L>(__VA_ARGS__);                           \
+    case OM_F16DEV: return fn<__half, L>(__VA_ARGS__);                       \
+    case OM_BF16DEV: return fn<__nv_bfloat16, L>(__VA_ARGS__);               \
     default: return fail(OM_EINVAL, "unknown precision");                    \
+  }
+#define OM_DIFF_DISPATCH(df, fn, ...)                                        \
+  if ((df)->q == 19) {                                                       \
+    OM_DIFF_DISPATCH_L(df, D3Q19, fn, __VA_ARGS__)                           \
+  } else {                                                                   \
+    OM_DIFF_DISPATCH_L(df, D3Q7, fn, __VA_ARGS__)                            \
   }
 
 size_t storage_bytes(int prec) { return prec == OM_F64 ? 8 : (prec == OM_F32 ? 4 : 2); }
@@ -420,16 +438,18 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
     return fail(OM_EINVAL, "om_diff_create: unknown precision");
   if (!(p->d_ref_nm > 0.0) || !(p->tau_ref > 0.5) || !(p->c_in != p->c_out))
     return fail(OM_EINVAL, "om_diff_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");
+  if (p->lattice != 7 && p->lattice != 19) return fail(OM_EINVAL, "om_diff_create: lattice must be 7 or 19");
   cudaStream_t s = as_stream(stream);
   om_diff* df = new om_diff();
   df->ns = ns;
   df->p = *p;
+  df->q = p->lattice;
   df->up = p->precision == OM_F16DEV ? 64.0 : 1.0;  // FP16: keep deviations normal numbers
   const size_t cb = p->precision == OM_F64 ? 8 : 4;
   DevBuf<uint8_t> g, om;
   DevBuf<double> prev, part, obs;
   DevBuf<float> cr;
-  om_status st = g.alloc(7 * (size_t)ns->pitch * storage_bytes(p->precision));
+  om_status st = g.alloc((size_t)df->q * ns->pitch * storage_bytes(p->precision));
   if (st == OM_OK && storage_bytes(p->precision) <= 4) st = cr.alloc(ns->pitch);
   if (st == OM_OK) st = om.alloc((size_t)ns->pitch * cb);
   if (st == OM_OK) st = prev.alloc(ns->nf);

@@ -1,15 +1,16 @@
-// diff_core.cuh -- device side of the D3Q7 Knudsen-diffusion sweep (Sec. 3.2,
-// Eqs. 10-12), shared by the single-structure kernels (diff.cu) and the
-// batched kernels (batch.cu).  See diff.cu for the scheme.
+// diff_core.cuh -- device side of the Knudsen-diffusion sweep (Sec. 3.2,
+// Eqs. 10-12) on D3Q7 or the paper's D3Q19 (the lattice L), shared by the
+// single-structure kernels (diff.cu) and the batched kernels (batch.cu, D3Q7).
+// See diff.cu for the scheme.
 #pragma once
 
 #include "lattice.cuh"
 
 namespace om {
 
-template <class T>
+template <class T, class L = D3Q7>
 struct DiffArgs {
-  T* q[7];  // population i of node n is q[i][n]
+  T* q[L::Q];  // population i of node n is q[i][n]
   uint32_t nf;
   const uint2* col;
   const uint32_t* coord;
@@ -33,130 +34,146 @@ struct DiffArgs {
 template <class T>
 constexpr bool kRebased = sizeof(T) <= 4;
 
-// nb[i] = node of x + e_i, kNoNode for walls; x faces flagged separately
-template <class T>
-__device__ __forceinline__ void diff_neighbours(const DiffArgs<T>& a, uint32_t c, uint32_t (&nb)[7],
+// nb[i] = node of x + e_i, kNoNode for walls and beyond the x faces (those
+// links are the Dirichlet half links); periodic y, z
+template <class T, class L>
+__device__ __forceinline__ void diff_neighbours(const DiffArgs<T, L>& a, uint32_t c, uint32_t (&nb)[L::Q],
                                                 int& x) {
   int y, z;
   unpack_xyz(c, x, y, z);
-  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
-  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
-  const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
-  auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
-  uint32_t self;
-  column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
-  nb[1] = x + 1 < a.nx ? column1(a.col, base(x + 1, y), z) : kNoNode;
-  nb[2] = x > 0 ? column1(a.col, base(x - 1, y), z) : kNoNode;
-  nb[3] = column1(a.col, base(x, yp), z);
-  nb[4] = column1(a.col, base(x, ym), z);
-  (void)self;
+  if constexpr (L::Q == 19) {
+    q19_neighbours(a.col, a.nx, a.ny, a.nz, a.W, 0, c, nb);
+  } else {
+    const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
+    const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
+    const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
+    auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
+    uint32_t self;
+    column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
+    nb[1] = x + 1 < a.nx ? column1(a.col, base(x + 1, y), z) : kNoNode;
+    nb[2] = x > 0 ? column1(a.col, base(x - 1, y), z) : kNoNode;
+    nb[3] = column1(a.col, base(x, yp), z);
+    nb[4] = column1(a.col, base(x, ym), z);
+    (void)self;
+  }
 }
 
 // Reference concentrations an odd step needs (rebased storage): the node's
 // own, and each neighbour's (0 where there is none).  Read once into
 // registers: the stores of the step could alias them for the compiler.
-template <class T>
+template <class T, class L>
 struct DiffRefs {
-  typename Stg<T>::C n, nb[7];
+  typename Stg<T>::C n, nb[L::Q];
 };
 
-template <class T>
-__device__ __forceinline__ void diff_refs(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7],
-                                          DiffRefs<T>& r) {
+template <class T, class L>
+__device__ __forceinline__ void diff_refs(const DiffArgs<T, L>& a, uint32_t n, const uint32_t (&nb)[L::Q],
+                                          DiffRefs<T, L>& r) {
   using C = typename Stg<T>::C;
   if constexpr (kRebased<T>) {
     r.n = a.cr[n];
 #pragma unroll
-    for (int i = 1; i < 7; ++i) r.nb[i] = nb[i] != kNoNode ? (C)a.cr[nb[i]] : C(0);
+    for (int i = 1; i < L::Q; ++i) r.nb[i] = nb[i] != kNoNode ? (C)a.cr[nb[i]] : C(0);
   }
 }
 
+// Population i of a node at x arrives through the inlet half link x = -1/2
+// (e_ix = +1 at x = 0) or the outlet one x = nx - 1/2 (e_ix = -1 at x = nx-1).
+template <class L>
+__device__ __forceinline__ bool from_inlet(int i, int x) { return L::e(i, 0) == 1 && x == 0; }
+template <class L>
+__device__ __forceinline__ bool from_outlet(int i, int x, int nx) { return L::e(i, 0) == -1 && x == nx - 1; }
+
 // pre-collision deviations of node n at the current time (odd steps: with
 // the reference concentrations r of diff_refs)
-template <class T, bool ODD>
-__device__ __forceinline__ void diff_load_r(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7], int x,
-                                            const DiffRefs<T>& r, typename Stg<T>::C (&g)[7]) {
+template <class T, class L, bool ODD>
+__device__ __forceinline__ void diff_load_r(const DiffArgs<T, L>& a, uint32_t n, const uint32_t (&nb)[L::Q], int x,
+                                            const DiffRefs<T, L>& r, typename Stg<T>::C (&g)[L::Q]) {
   using S = Stg<T>;
   using C = typename S::C;
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < L::Q; ++i) {
     if (!ODD || i == 0) {
       g[i] = S::ld(a.q[i] + n, a.down);
     } else {
-      const int o = q7_opp(i);
+      const int o = L::opp(i);
       const uint32_t src = nb[o];  // x - e_i
-      const bool inlet = (i == 1 && x == 0), outlet = (i == 2 && x == a.nx - 1);
+      const bool inlet = from_inlet<L>(i, x), outlet = from_outlet<L>(i, x, a.nx);
       const T* p = (src != kNoNode && !inlet && !outlet) ? a.q[o] + src : a.q[i] + n;
       const C v = S::ld(p, a.down);
+      const C w = C(L::w(i));
       if constexpr (kRebased<T>) {
-        if (inlet) g[i] = -v + C(0.25) * ((C)a.cin - r.n);
-        else if (outlet) g[i] = -v + C(0.25) * ((C)a.cout - r.n);
-        else if (src != kNoNode) g[i] = v + C(q7_w(i)) * (r.nb[o] - r.n);
+        if (inlet) g[i] = -v + C(2) * w * ((C)a.cin - r.n);
+        else if (outlet) g[i] = -v + C(2) * w * ((C)a.cout - r.n);
+        else if (src != kNoNode) g[i] = v + w * (r.nb[o] - r.n);
         else g[i] = v;
       } else {
-        if (inlet) g[i] = -v - C(0.125) * a.s;
-        else if (outlet) g[i] = -v + C(0.125) * a.s;
-        else if (src != kNoNode) g[i] = v - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
+        // C_lin(0) = c_in + s/2, C_lin(nx - 1) = c_out - s/2
+        if (inlet) g[i] = -v - w * a.s;
+        else if (outlet) g[i] = -v + w * a.s;
+        else if (src != kNoNode) g[i] = v - w * C(L::e(i, 0)) * a.s;
         else g[i] = v;
       }
     }
   }
 }
 
-template <class T, bool ODD>
-__device__ __forceinline__ void diff_load(const DiffArgs<T>& a, uint32_t n, const uint32_t (&nb)[7], int x,
-                                          typename Stg<T>::C (&g)[7]) {
-  DiffRefs<T> r{};
+template <class T, class L, bool ODD>
+__device__ __forceinline__ void diff_load(const DiffArgs<T, L>& a, uint32_t n, const uint32_t (&nb)[L::Q], int x,
+                                          typename Stg<T>::C (&g)[L::Q]) {
+  DiffRefs<T, L> r{};
   if (ODD) diff_refs(a, n, nb, r);
-  diff_load_r<T, ODD>(a, n, nb, x, r, g);
+  diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
 }
 
 // One fused collide-stream update of node n (global slot index) with packed
 // coordinates c (read on odd steps only); the AA read/write pattern of
 // flow_node_at with the anti-bounce-back inlet/outlet and the reference shift.
-template <class T, bool ODD>
-__device__ __forceinline__ void diff_node_at(const DiffArgs<T>& a, uint32_t n, uint32_t c) {
+template <class T, class L, bool ODD>
+__device__ __forceinline__ void diff_node_at(const DiffArgs<T, L>& a, uint32_t n, uint32_t c) {
   using S = Stg<T>;
   using C = typename S::C;
-  uint32_t nb[7];
+  uint32_t nb[L::Q];
   int x = 0;
-  DiffRefs<T> r{};
+  DiffRefs<T, L> r{};
   if (ODD) {
     diff_neighbours(a, c, nb, x);
     diff_refs(a, n, nb, r);
   }
-  C g[7];
-  diff_load_r<T, ODD>(a, n, nb, x, r, g);
+  C g[L::Q];
+  diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
   const C om = a.omega[n];
   C cc = g[0];
 #pragma unroll
-  for (int i = 1; i < 7; ++i) cc += g[i];
+  for (int i = 1; i < L::Q; ++i) cc += g[i];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) g[i] = g[i] - om * (g[i] - C(q7_w(i)) * cc);
+  for (int i = 0; i < L::Q; ++i) g[i] = g[i] - om * (g[i] - C(L::w(i)) * cc);
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    const int o = q7_opp(i);
+  for (int i = 0; i < L::Q; ++i) {
+    const int o = L::opp(i);
     if (!ODD) {
       S::st(a.q[o] + n, g[i], a.up);
     } else if (i == 0) {
       S::st(a.q[0] + n, g[0], a.up);
     } else {
-      const bool outlet = (i == 1 && x == a.nx - 1), inlet = (i == 2 && x == 0);
+      // leaves through the outlet (e_ix = +1 at nx-1) or the inlet half link
+      const bool outlet = L::e(i, 0) == 1 && x == a.nx - 1, inlet = L::e(i, 0) == -1 && x == 0;
       T* p = a.q[o] + n;
       C v = g[i];
+      const C w = C(L::w(i));
       if constexpr (kRebased<T>) {
-        if (outlet) v = -g[i] + C(0.25) * ((C)a.cout - r.n);
-        else if (inlet) v = -g[i] + C(0.25) * ((C)a.cin - r.n);
+        if (outlet) v = -g[i] + C(2) * w * ((C)a.cout - r.n);
+        else if (inlet) v = -g[i] + C(2) * w * ((C)a.cin - r.n);
         else if (nb[i] != kNoNode) {
           p = a.q[i] + nb[i];
-          v = g[i] + C(q7_w(i)) * (r.n - r.nb[i]);
+          v = g[i] + w * (r.n - r.nb[i]);
         }
       } else {
-        if (outlet) v = -g[i] + C(0.125) * a.s;
-        else if (inlet) v = -g[i] - C(0.125) * a.s;
+        if (outlet) v = -g[i] + w * a.s;
+        else if (inlet) v = -g[i] - w * a.s;
         else if (nb[i] != kNoNode) {
           p = a.q[i] + nb[i];
-          v = g[i] - C(q7_w(i)) * C(q7_e(i, 0)) * a.s;
+          v = g[i] - w * C(L::e(i, 0)) * a.s;
         }
       }
       S::st(p, v, a.up);
@@ -165,27 +182,27 @@ __device__ __forceinline__ void diff_node_at(const DiffArgs<T>& a, uint32_t n, u
 }
 
 // diff_node_at for node n whose coordinates are coord[ln]
-template <class T, bool ODD>
-__device__ __forceinline__ void diff_node(const DiffArgs<T>& a, uint32_t n, uint32_t ln) {
-  diff_node_at<T, ODD>(a, n, ODD ? a.coord[ln] : 0u);
+template <class T, bool ODD, class L = D3Q7>
+__device__ __forceinline__ void diff_node(const DiffArgs<T, L>& a, uint32_t n, uint32_t ln) {
+  diff_node_at<T, L, ODD>(a, n, ODD ? a.coord[ln] : 0u);
 }
 
 // Reference concentration of node n (with coordinates x): C_lin(x) or Cr[n]
-template <class T>
-__device__ __forceinline__ double diff_ref(const DiffArgs<T>& a, uint32_t n, int x) {
+template <class T, class L>
+__device__ __forceinline__ double diff_ref(const DiffArgs<T, L>& a, uint32_t n, int x) {
   if constexpr (kRebased<T>) return (double)a.cr[n];
   else return a.cin + (double)a.s * ((double)x + 0.5);
 }
 
 // Move node n's reference to its current concentration (even time only):
 // Cr += sum_i dev_i, dev_i -= a_i (Cr_new - Cr_old).
-template <class T>
-__device__ __forceinline__ void diff_rebase_node(const DiffArgs<T>& a, uint32_t n) {
+template <class T, class L>
+__device__ __forceinline__ void diff_rebase_node(const DiffArgs<T, L>& a, uint32_t n) {
   if constexpr (kRebased<T>) {
     using S = Stg<T>;
-    float d[7], sum = 0.f;
+    float d[L::Q], sum = 0.f;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < L::Q; ++i) {
       d[i] = S::ld(a.q[i] + n, a.down);
       sum += d[i];
     }
@@ -193,7 +210,7 @@ __device__ __forceinline__ void diff_rebase_node(const DiffArgs<T>& a, uint32_t 
     const float now = old + sum;
     a.cr[n] = now;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) S::st(a.q[i] + n, d[i] + (float)q7_w(i) * (old - now), a.up);
+    for (int i = 0; i < L::Q; ++i) S::st(a.q[i] + n, d[i] + (float)L::w(i) * (old - now), a.up);
   }
 }
 

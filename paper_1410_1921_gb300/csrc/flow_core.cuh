@@ -31,33 +31,7 @@ struct FlowArgs {
 // and x unless a.px = 0 (no neighbour beyond the x faces)
 template <class T>
 __device__ __forceinline__ void flow_neighbours(const FlowArgs<T>& a, uint32_t c, uint32_t (&nb)[19]) {
-  int x, y, z;
-  unpack_xyz(c, x, y, z);
-  const int xp = x + 1 == a.nx ? 0 : x + 1, xm = x == 0 ? a.nx - 1 : x - 1;
-  const bool hp = a.px || x + 1 < a.nx, hm = a.px || x > 0;
-  const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
-  const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
-  const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
-  auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
-  uint32_t self;
-  column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
-  if (hp) {
-    column3(a.col, base(xp, y), z, zp, zm, nb[13], nb[1], nb[11]);
-    nb[7] = column1(a.col, base(xp, yp), z);
-    nb[9] = column1(a.col, base(xp, ym), z);
-  } else {
-    nb[13] = nb[1] = nb[11] = nb[7] = nb[9] = kNoNode;
-  }
-  if (hm) {
-    column3(a.col, base(xm, y), z, zp, zm, nb[14], nb[2], nb[12]);
-    nb[8] = column1(a.col, base(xm, yp), z);
-    nb[10] = column1(a.col, base(xm, ym), z);
-  } else {
-    nb[14] = nb[2] = nb[12] = nb[8] = nb[10] = kNoNode;
-  }
-  column3(a.col, base(x, yp), z, zp, zm, nb[17], nb[3], nb[15]);
-  column3(a.col, base(x, ym), z, zp, zm, nb[18], nb[4], nb[16]);
-  (void)self;
+  q19_neighbours(a.col, a.nx, a.ny, a.nz, a.W, a.px, c, nb);
 }
 
 // Index of node n among the boundary nodes of the pressure drive, or -1

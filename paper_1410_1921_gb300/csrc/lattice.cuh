@@ -88,6 +88,57 @@ __device__ __forceinline__ uint32_t column1(const uint2* __restrict__ col, uint3
   return (w.x & bit) ? w.y + __popc(w.x & (bit - 1u)) : kNoNode;
 }
 
+// nb[i] = node number of x + e_i for the D3Q19 velocities (kNoNode off the
+// node set) of the node with packed coordinates c; periodic y, z, and x when
+// px (else no neighbour beyond the x faces).
+__device__ __forceinline__ void q19_neighbours(const uint2* __restrict__ col, int nx, int ny, int nz, int W,
+                                               int px, uint32_t c, uint32_t (&nb)[19]) {
+  int x, y, z;
+  unpack_xyz(c, x, y, z);
+  const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+  const bool hp = px || x + 1 < nx, hm = px || x > 0;
+  const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+  const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+  const uint32_t uy = (uint32_t)ny, uW = (uint32_t)W;
+  auto base = [&](int xx, int yy) { return ((uint32_t)xx * uy + (uint32_t)yy) * uW; };
+  uint32_t self;
+  column3(col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
+  if (hp) {
+    column3(col, base(xp, y), z, zp, zm, nb[13], nb[1], nb[11]);
+    nb[7] = column1(col, base(xp, yp), z);
+    nb[9] = column1(col, base(xp, ym), z);
+  } else {
+    nb[13] = nb[1] = nb[11] = nb[7] = nb[9] = kNoNode;
+  }
+  if (hm) {
+    column3(col, base(xm, y), z, zp, zm, nb[14], nb[2], nb[12]);
+    nb[8] = column1(col, base(xm, yp), z);
+    nb[10] = column1(col, base(xm, ym), z);
+  } else {
+    nb[14] = nb[2] = nb[12] = nb[8] = nb[10] = kNoNode;
+  }
+  column3(col, base(x, yp), z, zp, zm, nb[17], nb[3], nb[15]);
+  column3(col, base(x, ym), z, zp, zm, nb[18], nb[4], nb[16]);
+  (void)self;
+}
+
+// Diffusion lattices: D3Q7 (rest, +-x, +-y, +-z; a = 1/4, 1/8; c_s^2 = 1/4)
+// and the paper's D3Q19 (the flow's velocity set and weights, c_s^2 = 1/3).
+struct D3Q7 {
+  static constexpr int Q = 7;
+  static constexpr double cs2 = 0.25;
+  __host__ __device__ static constexpr int e(int i, int d) { return q7_e(i, d); }
+  __host__ __device__ static constexpr int opp(int i) { return q7_opp(i); }
+  __host__ __device__ static constexpr double w(int i) { return q7_w(i); }
+};
+struct D3Q19 {
+  static constexpr int Q = 19;
+  static constexpr double cs2 = 1.0 / 3.0;
+  __host__ __device__ static constexpr int e(int i, int d) { return q19_e(i, d); }
+  __host__ __device__ static constexpr int opp(int i) { return q19_opp(i); }
+  __host__ __device__ static constexpr double w(int i) { return q19_w(i); }
+};
+
 // Warm-start fields come from outside the solver (a network's output).  A
 // non-finite value falls back to the cold start; a velocity is kept inside
 // the low-Mach range the lattice is stable in; a concentration inside

@@ -111,7 +111,8 @@ extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om
   double o[5];
   OM_TRY(om_diff_observe(sc.df, o, sc.s));
   // Eq. 15 with the time step set by the reference pore (Eqs. 11-12)
-  const double DL_ref = 0.25 * (params->tau_ref - 0.5);
+  const double cs2 = params->lattice == 19 ? 1.0 / 3.0 : 0.25;  // D3Q19 or D3Q7
+  const double DL_ref = cs2 * (params->tau_ref - 0.5);
   const double DK_ref = knudsen(params->d_ref_nm * 1e-9, params->T_K, params->M_kg_per_mol);
   if (D_eff_m2s) *D_eff_m2s = Dl * DK_ref / DL_ref;
   if (tortuosity) {
