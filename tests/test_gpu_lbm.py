@@ -46,16 +46,17 @@ def _flow_run(om, node, f0, tau, g, steps, prec, variant=-1, drho=None):
 
 
 def _diff_run(om, node, d_nm, g0, steps, prec, cin=1.0, cout=0.0, variant=-1):
+    q = g0.shape[0]
     dom = om.domain(node.shape)
     ns = om.NodeSet(_dev(node), dom)
     df = om.Diffusion(ns, _dev(d_nm, torch.float32),
-                      om.diff_params(c_in=cin, c_out=cout, precision=prec, variant=variant))
+                      om.diff_params(c_in=cin, c_out=cout, precision=prec, variant=variant, lattice=q))
     df.set_populations(_dev(g0))
     df.step(steps)
-    out = torch.empty(7 * node.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(q * node.size, dtype=torch.float64, device="cuda")
     df.get_populations(out)
     torch.cuda.synchronize()
-    return out.cpu().numpy().reshape((7,) + node.shape)
+    return out.cpu().numpy().reshape((q,) + node.shape)
 
 
 GEOMS = {
@@ -97,10 +98,10 @@ def test_flow_steps_fp32(orc, om, geom, steps):
     assert np.abs(got - ref).max() <= 64 * U32 * dev * steps + 1e-12
 
 
-def _rand_diff(node, seed):
-    a = np.array([0.25] + [0.125] * 6)
+def _rand_diff(node, seed, q=7):
+    a = np.array([0.25] + [0.125] * 6) if q == 7 else np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
     c = S.random_field(node.shape, seed, 0.0, 1.0)
-    r = S.random_field((7,) + node.shape, seed + 1, -1, 1)
+    r = S.random_field((q,) + node.shape, seed + 1, -1, 1)
     return a[:, None, None, None] * c[None] * (1 + 0.2 * r) * node
 
 
@@ -161,11 +162,81 @@ def test_sweep_variants_identical_bits(orc, om, prec):
     first = _flow_run(om, node, f0, 1.0, 1e-5, 5, P, 0)
     for v in range(1, 5):
         assert np.array_equal(_flow_run(om, node, f0, 1.0, 1e-5, 5, P, v), first), v
-    g0 = _rand_diff(node, 23)
     d = _rand_d(node, 24)
-    first = _diff_run(om, node, d, g0, 5, P, 1.0, 0.0, 0)
-    for v in range(1, 4):
-        assert np.array_equal(_diff_run(om, node, d, g0, 5, P, 1.0, 0.0, v), first), v
+    for q in (7, 19):
+        g0 = _rand_diff(node, 23, q=q)
+        first = _diff_run(om, node, d, g0, 5, P, 1.0, 0.0, 0)
+        for v in range(1, 4):
+            assert np.array_equal(_diff_run(om, node, d, g0, 5, P, 1.0, 0.0, v), first), (q, v)
+
+
+# ------------------------------------------------------------------ D3Q19 diffusion (Sec. 3.2)
+@pytest.mark.parametrize("geom", ["blobs", "ragged", "duct", "tiny", "line"])
+@pytest.mark.parametrize("steps", [1, 2, 3, 10])
+def test_d3q19_diffusion_steps_fp64(orc, om, geom, steps):
+    node = GEOMS[geom]()
+    g0 = _rand_diff(node, 500 + steps, q=19)
+    d = _rand_d(node, 510 + steps)
+    ref = orc.diff_step(node, g0, orc.omega_field(node, d), 0.9, 0.2, steps)
+    got = _diff_run(om, node, d, g0, steps, om.OM_F64, 0.9, 0.2)
+    assert np.abs(got - ref).max() <= 1e-13 * steps
+
+
+@pytest.mark.parametrize("geom", ["blobs", "ragged"])
+@pytest.mark.parametrize("variant", [0, 2])
+def test_d3q19_diffusion_steps_fp32(orc, om, geom, variant):
+    node = GEOMS[geom]()
+    g0 = _rand_diff(node, 600, q=19)
+    d = _rand_d(node, 601)
+    ref = orc.diff_step(node, g0, orc.omega_field(node, d), 1.0, 0.0, 9)
+    got = _diff_run(om, node, d, g0, 9, om.OM_F32, variant=variant)
+    assert np.abs(got - ref).max() <= 64 * U32 * np.abs(g0).max() * 9 + 1e-12
+
+
+@pytest.mark.parametrize("prec,rel", [("OM_F64", 1e-9), ("OM_F32", 1e-5)])
+def test_d3q19_diffusion_converged(orc, om, prec, rel):
+    node = S.blob_mask((12, 16, 16), 3, n=6, rmin=3.5, rmax=6.0)
+    _, tr, _ = orc.label18(node)
+    d = (S.random_field(tr.shape, 7, 10.0, 60.0) * tr).astype(np.float32)
+    rc, D_ref, *_ = orc.diff_solve(tr, orc.omega_field(tr, d), 1.0, 0.0, tol=1e-10, K=100, max_steps=400_000, q=19)
+    assert rc == 0
+    ns = om.NodeSet(_dev(tr), om.domain(tr.shape))
+    df = om.Diffusion(ns, _dev(d, torch.float32),
+                      om.diff_params(conv_tol=1e-10 if prec == "OM_F64" else 1e-7, max_steps=400_000,
+                                     precision=getattr(om, prec), lattice=19))
+    st, Dl, info = df.solve()
+    assert st == om.OM_OK
+    assert Dl == pytest.approx(D_ref, rel=rel)
+
+
+def test_d3q19_knudsen_entry_point_units(orc, om):
+    # D_L,ref = (tau_ref - 1/2)/3 on D3Q19 (Sec. 3.2): the same structure
+    # gives D_eff = D_eff,L * D_K(d_ref) / D_L,ref
+    m = np.ones((8, 5, 4), np.uint8)
+    d = np.full(m.shape, 30.0, np.float32)
+    dom = om.domain(m.shape)
+    dp = om.diff_params(precision=om.OM_F64, conv_tol=1e-12, lattice=19)
+    st, D, tort, info, _ = om.om_solve_knudsen(m, d, dom, dp)
+    tau = orc.tau_knudsen(30.0)
+    DK_ref = 60e-9 / 3 * np.sqrt(8 * 8.314462618 * 300.0 / (np.pi * 0.016))
+    assert D == pytest.approx((tau - 0.5) / 3 * DK_ref / (0.5 / 3), rel=1e-9)  # open box: D_eff = D_K(30 nm)
+    assert tort == pytest.approx(1.0, rel=1e-9)
+
+
+def test_d3q19_edge_contacts_conduct(orc, om):
+    n = 8
+    m = np.zeros((n, n, 2), np.uint8)
+    for x in range(n):
+        m[x, x, :] = 1
+    d = np.full(m.shape, 60.0, np.float32)
+    out = {}
+    for q in (7, 19):
+        ns = om.NodeSet(_dev(m), om.domain(m.shape))
+        df = om.Diffusion(ns, _dev(d, torch.float32), om.diff_params(precision=om.OM_F64, conv_tol=1e-12,
+                                                                     max_steps=400_000, lattice=q))
+        out[q] = df.solve()[1]
+    rc, D19, *_ = orc.diff_solve(m, orc.omega_field(m, d), 1.0, 0.0, tol=1e-12, K=100, max_steps=400_000, q=19)
+    assert abs(out[7]) < 1e-14 and out[19] == pytest.approx(D19, rel=1e-9) and out[19] > 1e-3
 
 
 # ------------------------------------------------------------------ pressure drive (Sec. 3.3)
