@@ -50,8 +50,8 @@ def _args():
     ap.add_argument("--mode", default="throughput", choices=["throughput", "converge"],
                     help="converge: time to converged k and D_eff, plain vs batched + FP16 + warm start")
     ap.add_argument("--n-eval", type=int, default=24, help="converge mode: structures solved")
-    ap.add_argument("--n-train", type=int, default=48, help="converge mode: training structures")
-    ap.add_argument("--epochs", type=int, default=30, help="converge mode: U-Net epochs")
+    ap.add_argument("--n-train", type=int, default=96, help="converge mode: training structures")
+    ap.add_argument("--epochs", type=int, default=60, help="converge mode: U-Net epochs")
     ap.add_argument("--max-steps", type=int, default=500_000, help="converge mode: step cap per solve")
     ap.add_argument("--warm", default="diffusion", choices=["both", "diffusion", "none"],
                     help="converge mode: which models the network warm-starts (velocity warm starts "
@@ -396,7 +396,7 @@ def run_converge(a):
     t_data = time.perf_counter() - t0
     net = P.UNet(2, len(fields), (16, 32, 64, 128), seed=5)
     t0 = time.perf_counter()
-    hist = W.train(net, data, epochs=a.epochs, lr=2e-3, lr_end=1e-4)
+    hist = W.train(net, data, epochs=a.epochs, lr=1e-3, lr_end=5e-5)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     structs = []

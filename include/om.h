@@ -324,7 +324,10 @@ om_status om_batch_destroy(om_batch* b);
  * targets/outputs [B][D][H][W][out_ch], mask [B][D][H][W] (loss over
  * voxels with mask != 0).  D, H, W must be multiples of 2^(levels-1).
  * Parameters are one flat FP32 vector: per level (encoder, then decoder from
- * the bottom) W[27][c_in][c_out] and b[c_out], then the head W[c0][out], b. */
+ * the bottom) W[27][c_in][c_out] and b[c_out], then the head W[c0][out], b.
+ * om_unet_create draws the convolution weights He-uniform from a SplitMix64
+ * stream of `seed` and sets biases and the head to zero (the first output is
+ * 0: the cold start). */
 typedef struct om_unet om_unet;
 om_status om_unet_create(int32_t in_ch, int32_t out_ch, int32_t levels, const int32_t* ch, uint64_t seed,
                          om_unet** out);

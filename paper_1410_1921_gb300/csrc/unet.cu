@@ -582,9 +582,10 @@ extern "C" om_status om_unet_create(int32_t in_ch, int32_t out_ch, int32_t level
     init(U->dec1[l], 27 * (ch[l + 1] + ch[l]));
     init(U->dec2[l], 27 * ch[l]);
   }
-  const double hb = std::sqrt(6.0 / ch[0]);
-  for (int64_t i = 0; i < (int64_t)ch[0] * out_ch; ++i)
-    w[(size_t)(U->head_w + i)] = (float)(hb * (2.0 * ((double)(splitmix(st) >> 11) * 0x1.0p-53) - 1.0));
+  // the 1x1 head starts at zero: the network's first output is 0 (the cold
+  // start) and the first Adam steps cannot blow the decoder's ReLUs up (with
+  // a He-initialised head the first outputs are O(10) and training stalls
+  // in a state that predicts a constant)
   auto dal = [&](void** p, size_t bytes) -> bool {
     if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
       (void)cudaGetLastError();

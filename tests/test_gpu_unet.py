@@ -37,6 +37,11 @@ def test_unet_forward_and_gradients_match_reference(om, ch, shape):
     n = net.n_params
     flat = torch.empty(n, dtype=torch.float32, device="cuda")
     net.get_params(flat)
+    # the head starts at zero, which would leave every other gradient zero:
+    # give it values so the whole backward pass is compared
+    nh = ch[0] * out_ch + out_ch
+    flat[n - nh:] = (0.3 * torch.randn(nh, generator=torch.Generator().manual_seed(11))).cuda()
+    net.set_params(flat)
     x, t, m = _case(shape, in_ch, out_ch, 3)
     y = torch.empty(*shape, out_ch, dtype=torch.float32, device="cuda")
     net.forward(x.cuda(), y)
