@@ -83,10 +83,13 @@ typedef struct {
   int64_t max_steps;
   int32_t precision;
   /* sweep launch variant, the same arithmetic in every one: -1 = time them
-   * all at creation and keep the fastest per parity; 0..4 = force one (0/1
-   * one thread per node without/with a register cap, 2/3 the same on a
-   * resident grid striding over nodes, 4 a tighter cap); larger values
-   * clamp to 4 */
+   * all at creation and keep the fastest per parity (solvers whose node
+   * count lies in the same power-of-two octave as one timed before in this
+   * process, with the same precision and device, reuse its choice); 0..5 =
+   * force one (0/1 one thread per node without/with a register cap, 2/3 the
+   * same on a resident grid striding over nodes, 4 a tighter cap, 5 the
+   * resident grid two nodes deep with the next node's column-map words
+   * prefetched); larger values clamp to 5 */
   int32_t variant;
   /* OM_DRIVE_FORCE: body_force along x, x periodic.  OM_DRIVE_PRESSURE
    * (Sec. 3.3): no force, x not periodic, densities 1 + delta_rho/2 and
@@ -114,7 +117,7 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
-  int32_t variant; /* as om_flow_params.variant, 0..3 (larger values clamp to 3) */
+  int32_t variant; /* as om_flow_params.variant: 0..3 as there, 4 = its 5 (larger values clamp to 4) */
   int32_t lattice;
 } om_diff_params;
 

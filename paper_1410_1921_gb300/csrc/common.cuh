@@ -130,6 +130,13 @@ inline unsigned resident_grid(K kernel, unsigned nb, int threads = 256) {
   return nb < (unsigned)cache[dev] ? nb : (unsigned)cache[dev];
 }
 
+// Launch variants the autotuner chose, remembered for the life of the
+// process per (solver kind, precision, device, octave of the node count):
+// the first solver of a class times the variants, later ones reuse the choice.
+enum { kTuneFlow = 0, kTuneDiff7 = 1, kTuneDiff19 = 2 };
+bool tuned_lookup(int kind, int prec, int64_t nf, int var[2]);
+void tuned_store(int kind, int prec, int64_t nf, const int var[2]);
+
 om_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total_dev,
                              cudaStream_t s);
 // sum the per-block partials [nblk][nval] in fixed order into out[nval]

@@ -27,8 +27,10 @@ namespace om {
 // arithmetic): 0 = one thread per node, registers as the compiler wants;
 // 1 = capped for 8 resident blocks; 2, 3 = the same on a resident grid whose
 // threads stride over nodes, loading the next node's coordinates before
-// updating the current one (the flow sweep's variants 2 and 3).
-constexpr int kDiffVariants = 4;
+// updating the current one (the flow sweep's variants 2 and 3); 4 = variant
+// 2 two nodes deep with the next node's column-map words prefetched into L1
+// (the flow sweep's variant 5).
+constexpr int kDiffVariants = 5;
 
 template <class T, class L, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) diff_sweep(DiffArgs<T, L> a) {
@@ -52,6 +54,29 @@ __global__ void __launch_bounds__(256, MINB) diff_sweep_strided(DiffArgs<T, L> a
     if (!more) break;
     n = (uint32_t)nn;
     c = cn;
+  }
+}
+
+template <class T, class L, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) diff_sweep_pipelined(DiffArgs<T, L> a) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  if (!ODD) {
+    for (; n < a.nf; n += stride) diff_node_at<T, L, false>(a, n, 0u);
+    return;
+  }
+  uint32_t c0 = __ldg(a.coord + n);
+  uint32_t c1 = (uint64_t)n + stride < a.nf ? __ldg(a.coord + n + stride) : 0u;
+  for (;;) {
+    const uint64_t nn = (uint64_t)n + stride, nn2 = nn + stride;
+    const uint32_t c2 = nn2 < a.nf ? __ldg(a.coord + nn2) : 0u;
+    if (nn < a.nf) prefetch_columns<L::Q>(a.col, a.nx, a.ny, a.W, 0, c1);
+    diff_node_at<T, L, true>(a, n, c0);
+    if (nn >= a.nf) break;
+    n = (uint32_t)nn;
+    c0 = c1;
+    c1 = c2;
   }
 }
 
@@ -247,6 +272,11 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const DiffArgs<T, 
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
+    case 4: {
+      auto k = diff_sweep_pipelined<T, L, ODD, 0>;
+      k<<<resident_grid(k, nb), 256, 0, s>>>(a);
+      break;
+    }
     default: diff_sweep<T, L, ODD, 0><<<nb, 256, 0, s>>>(a); break;
   }
 }
@@ -310,10 +340,13 @@ om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
 }
 
 // Autotuner: time each launch variant of both sweeps (6 even/odd pairs after
-// a warm-up pair), keep the fastest per parity; the caller re-initialises.
+// a warm-up pair), keep the fastest per parity (reused for later node sets of
+// the same size class in this process); the caller re-initialises.
 template <class T, class L>
 om_status diff_tune_t(om_diff* df, cudaStream_t s) {
   if (df->ns->nf == 0) return OM_OK;
+  const int kind = L::Q == 19 ? kTuneDiff19 : kTuneDiff7;
+  if (tuned_lookup(kind, df->p.precision, df->ns->nf, df->var)) return OM_OK;
   DiffArgs<T, L> a = diff_args<T, L>(df);
   const unsigned nb = blocks_for(a.nf);
   cudaEvent_t ev[3];
@@ -342,6 +375,7 @@ om_status diff_tune_t(om_diff* df, cudaStream_t s) {
       }
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  tuned_store(kind, df->p.precision, df->ns->nf, df->var);
   return OM_OK;
 }
 

@@ -49,10 +49,13 @@ namespace om {
 //      loading the next node's coordinates before updating the current one,
 //      so that load's latency overlaps the update (odd steps);
 //   3  variant 2 with the register cap of variant 1;
-//   4  one thread per node with a tighter cap (MINB + 1 blocks).
+//   4  one thread per node with a tighter cap (MINB + 1 blocks);
+//   5  variant 2 two nodes deep: the coordinates of the node after next are
+//      loaded, and the column-map words of the next node prefetched into
+//      L1, while the current node is updated (odd steps).
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
-constexpr int kSweepVariants = 5;
+constexpr int kSweepVariants = 6;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
@@ -76,6 +79,29 @@ __global__ void __launch_bounds__(256, MINB) d3q19_sweep_strided(FlowArgs<T> a) 
     if (!more) break;
     n = (uint32_t)nn;
     c = cn;
+  }
+}
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q19_sweep_pipelined(FlowArgs<T> a) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  if (!ODD) {
+    for (; n < a.nf; n += stride) flow_node_at<T, false>(a, n, 0u);
+    return;
+  }
+  uint32_t c0 = __ldg(a.coord + n);
+  uint32_t c1 = (uint64_t)n + stride < a.nf ? __ldg(a.coord + n + stride) : 0u;
+  for (;;) {
+    const uint64_t nn = (uint64_t)n + stride, nn2 = nn + stride;
+    const uint32_t c2 = nn2 < a.nf ? __ldg(a.coord + nn2) : 0u;
+    if (nn < a.nf) prefetch_columns<19>(a.col, a.nx, a.ny, a.W, a.px, c1);
+    flow_node_at<T, true>(a, n, c0);
+    if (nn >= a.nf) break;
+    n = (uint32_t)nn;
+    c0 = c1;
+    c1 = c2;
   }
 }
 
@@ -304,6 +330,11 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>&
       break;
     }
     case 4: d3q19_sweep<T, ODD, M + 1><<<nb, 256, 0, s>>>(a); break;
+    case 5: {
+      auto k = d3q19_sweep_pipelined<T, ODD, 0>;
+      k<<<resident_grid(k, nb), 256, 0, s>>>(a);
+      break;
+    }
     default: d3q19_sweep<T, ODD, 0><<<nb, 256, 0, s>>>(a); break;
   }
 }
@@ -380,10 +411,12 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
 
 // Autotuner: time every launch variant of both sweeps on this node set
 // (6 even/odd pairs each after a warm-up pair) and keep the fastest per
-// parity.  Runs from the rest state and puts the rest state back.
+// parity; a node set of a size class tuned before in this process reuses
+// that choice.  Runs from the rest state and puts the rest state back.
 template <class T>
 om_status flow_tune_t(om_flow* fl, cudaStream_t s) {
   if (fl->ns->nf == 0) return OM_OK;
+  if (tuned_lookup(kTuneFlow, fl->p.precision, fl->ns->nf, fl->var)) return OM_OK;
   FlowArgs<T> a = flow_args<T>(fl);
   const unsigned nb = blocks_for(a.nf);
   cudaEvent_t ev[3];
@@ -412,6 +445,7 @@ om_status flow_tune_t(om_flow* fl, cudaStream_t s) {
       }
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  tuned_store(kTuneFlow, fl->p.precision, fl->ns->nf, fl->var);
   d3q19_rest<T><<<nb, 256, 0, s>>>(a);
   OM_CUDA(cudaGetLastError());
   return OM_OK;

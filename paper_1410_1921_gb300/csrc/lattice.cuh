@@ -122,6 +122,33 @@ __device__ __forceinline__ void q19_neighbours(const uint2* __restrict__ col, in
   (void)self;
 }
 
+// Ask L1 for the column-map words the neighbour lookup of the node with
+// packed coordinates c will read (z's 32-voxel word of the columns (x + dx,
+// y + dy): all nine for D3Q19, the five with |dx| + |dy| <= 1 for D3Q7), so
+// that a node's lookup finds them on chip when its turn comes.  No register
+// holds the result; x wraps only when px.
+template <int Q>
+__device__ __forceinline__ void prefetch_columns(const uint2* col, int nx, int ny, int W, int px, uint32_t c) {
+  int x, y, z;
+  unpack_xyz(c, x, y, z);
+  const uint32_t w = (uint32_t)z >> 5;
+#pragma unroll
+  for (int dx = -1; dx <= 1; ++dx) {
+    int xx = x + dx;
+    if (xx < 0 || xx >= nx) {
+      if (!px) continue;
+      xx = xx < 0 ? xx + nx : xx - nx;
+    }
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (Q == 7 && dx != 0 && dy != 0) continue;
+      const int yy = y + dy < 0 ? y + dy + ny : (y + dy >= ny ? y + dy - ny : y + dy);
+      const uint2* p = col + ((uint32_t)xx * (uint32_t)ny + (uint32_t)yy) * (uint32_t)W + w;
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));  // in bounds: xx, yy, w valid
+    }
+  }
+}
+
 // Diffusion lattices: D3Q7 (rest, +-x, +-y, +-z; a = 1/4, 1/8; c_s^2 = 1/4)
 // and the paper's D3Q19 (the flow's velocity set and weights, c_s^2 = 1/3).
 struct D3Q7 {

@@ -4,6 +4,9 @@
 
 #include "common.cuh"
 
+#include <map>
+#include <mutex>
+
 namespace om {
 
 static thread_local std::string g_err;
@@ -141,6 +144,43 @@ __global__ void finalize_partials(const double* partials, int nblk, int nval, do
     if (threadIdx.x == 0) out[k] = sm[0];
     __syncthreads();
   }
+}
+
+// ------------------------------------------------------------------ tuning cache
+namespace {
+struct TuneKey {
+  int kind, prec, dev, octave;
+  bool operator<(const TuneKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (prec != o.prec) return prec < o.prec;
+    if (dev != o.dev) return dev < o.dev;
+    return octave < o.octave;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+TuneKey tune_key(int kind, int prec, int64_t nf) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  int oct = 0;
+  while (oct < 62 && (int64_t(1) << (oct + 1)) <= nf) ++oct;
+  return TuneKey{kind, prec, dev, oct};
+}
+}  // namespace
+
+bool tuned_lookup(int kind, int prec, int64_t nf, int var[2]) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(tune_key(kind, prec, nf));
+  if (it == g_tune.end()) return false;
+  var[0] = it->second.first;
+  var[1] = it->second.second;
+  return true;
+}
+
+void tuned_store(int kind, int prec, int64_t nf, const int var[2]) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(kind, prec, nf)] = {var[0], var[1]};
 }
 
 void launch_finalize(const double* partials, int nblk, int nval, double* out, cudaStream_t s) {

@@ -135,7 +135,7 @@ def test_diffusion_steps_fp32(orc, om, geom, steps):
 # Every launch variant of the sweeps does the same arithmetic per node: each
 # matches the oracle, and on a structure with more nodes than one resident
 # grid has threads (so the striding variants loop) all give identical bits.
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_flow_variants_match_oracle(orc, om, variant):
     node = GEOMS["blobs"]()
     f0 = _rand_pops(orc, node, 7)
@@ -144,7 +144,7 @@ def test_flow_variants_match_oracle(orc, om, variant):
     assert np.abs(got - ref).max() <= 1e-13 * 7
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_diffusion_variants_match_oracle(orc, om, variant):
     node = GEOMS["ragged"]()
     g0 = _rand_diff(node, 8)
@@ -160,13 +160,13 @@ def test_sweep_variants_identical_bits(orc, om, prec):
     P = getattr(om, prec)
     f0 = _rand_pops(orc, node, 22, amp=0.05)
     first = _flow_run(om, node, f0, 1.0, 1e-5, 5, P, 0)
-    for v in range(1, 5):
+    for v in range(1, 6):
         assert np.array_equal(_flow_run(om, node, f0, 1.0, 1e-5, 5, P, v), first), v
     d = _rand_d(node, 24)
     for q in (7, 19):
         g0 = _rand_diff(node, 23, q=q)
         first = _diff_run(om, node, d, g0, 5, P, 1.0, 0.0, 0)
-        for v in range(1, 4):
+        for v in range(1, 5):
             assert np.array_equal(_diff_run(om, node, d, g0, 5, P, 1.0, 0.0, v), first), (q, v)
 
 
