@@ -247,7 +247,12 @@ def run_gpu(a):
             fl = P.Flow(ns, P.flow_params(precision=P.OM_F32, check_every=WINDOW), stream=sp)
             df = P.Diffusion(ns, d, P.diff_params(precision=P.OM_F32, check_every=WINDOW), stream=sp)
             solvers.append((cfg, ns, fl, df))
-            host_inputs.append((dom, mask.cpu().numpy(), d.cpu().numpy()))
+            # the e2e inputs live in pinned host memory (numpy views of pinned tensors)
+            hm = torch.empty(mask.shape, dtype=mask.dtype, pin_memory=True)
+            hd = torch.empty(d.shape, dtype=d.dtype, pin_memory=True)
+            hm.copy_(mask)
+            hd.copy_(d)
+            host_inputs.append((dom, hm.numpy(), hd.numpy()))
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     nodes = [ns.n_nodes for _, ns, _, _ in solvers]

@@ -3,8 +3,12 @@
 // Pore voxels are joined with their 18 neighbours (the D3Q19 links; y and z
 // periodic, x not) by a lock-free union-find: a root is only ever linked
 // below a smaller index, so every component ends as a tree rooted at its
-// smallest voxel index, the canonical label.  Transport voxels belong to a
+// smallest voxel index, the canonical label.  Runs of pore voxels along z
+// start as single trees, and two runs that touch along several voxels are
+// joined once, at the lowest voxel of their overlap.  Transport voxels belong to a
 // component with voxels on both x faces.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace om {
@@ -37,30 +41,56 @@ __device__ __forceinline__ void uf_union(int* par, int a, int b) {
   }
 }
 
-__global__ void uf_init(const uint8_t* mask, int64_t N, int* par) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
-    par[v] = mask[v] ? (int)v : -1;
+// Runs of pore voxels along z (not wrapping at z = 0) start as one tree
+// each: every voxel points at the first voxel of its run, which is its own
+// root and the run's smallest index.  One thread per (x, y) column.
+__global__ void uf_init_runs(const uint8_t* mask, int64_t ncol, int nz, int* par) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = c * nz;
+    int head = -1;
+    for (int z = 0; z < nz; ++z) {
+      const int64_t v = base + z;
+      if (!mask[v]) {
+        par[v] = -1;
+        head = -1;
+        continue;
+      }
+      if (head < 0) head = (int)v;
+      par[v] = head;
+    }
+  }
 }
 
-// the forward half of the 18 neighbour offsets; the other half is the same
-// pairs seen from the other voxel
-__global__ void uf_link(const uint8_t* mask, int nx, int ny, int nz, int* par) {
+// The forward half of the 18 neighbour offsets (the other half is the same
+// pairs seen from the other voxel).  Voxel v is joined to its neighbour u =
+// v + o unless the pair one step lower in z, (v - 1, u - 1), is a pore pair
+// inside the same two runs: that pair already joins the two runs.  So each
+// overlap of two runs issues one union, at its lowest voxel.  One block row
+// of threads per (x, y) column, threads along z: no 64-bit index division.
+__global__ void uf_link_runs(const uint8_t* mask, int nx, int ny, int nz, int* par) {
   constexpr int8_t H[9][3] = {{1, 0, 0}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
                               {0, 1, 0}, {0, 1, 1}, {0, 1, -1}, {0, 0, 1}};
-  const int64_t N = (int64_t)nx * ny * nz;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
-    if (!mask[v]) continue;
-    const int x = (int)(v / ((int64_t)ny * nz));
-    const int y = (int)((v / nz) % ny), z = (int)(v % nz);
+  const int64_t ncol = (int64_t)nx * ny;
+  for (int64_t c = blockIdx.x; c < ncol; c += gridDim.x) {
+    const int x = (int)(c / ny), y = (int)(c - (int64_t)x * ny);
+    const int64_t base = c * nz;
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+      const int64_t v = base + z;
+      if (!mask[v]) continue;
+      const bool below = z > 0 && mask[v - 1];  // v - 1 in the same run
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const int xx = x + H[k][0];
-      if (xx >= nx) continue;
-      int yy = y + H[k][1], zz = z + H[k][2];
-      yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-      zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-      const int64_t u = ((int64_t)xx * ny + yy) * nz + zz;
-      if (mask[u]) uf_union(par, (int)v, (int)u);
+      for (int k = 0; k < 9; ++k) {
+        const int xx = x + H[k][0];
+        if (xx >= nx) continue;
+        int yy = y + H[k][1], zz = z + H[k][2];
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        const int64_t u = ((int64_t)xx * ny + yy) * nz + zz;
+        if (!mask[u]) continue;
+        if (k == 8 && zz > 0) continue;              // z + 1 without wrap: the same run
+        if (below && zz > 0 && mask[u - 1]) continue;  // (v-1, u-1) joins these runs
+        uf_union(par, (int)v, (int)u);
+      }
     }
   }
 }
@@ -115,6 +145,8 @@ __global__ void transport_from_labels(const int* lab, const uint8_t* touch, int6
 
 }  // namespace
 
+void launch_union_find(const uint8_t* mask_dev, const om_domain& d, int* labels_dev, cudaStream_t s);
+
 // labels (int32 N) and transport flags on the device; counts of pore and
 // transport voxels returned through the host pointers when non-null.
 om_status label_impl(const uint8_t* mask_dev, const om_domain& d, int* labels_dev, uint8_t* transport_dev,
@@ -128,9 +160,7 @@ om_status label_impl(const uint8_t* mask_dev, const om_domain& d, int* labels_de
   OM_TRY(cnt.alloc(2));
   OM_CUDA(cudaMemsetAsync(touch.p, 0, (N + 3) / 4 * 4, s));
   OM_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), s));
-  uf_init<<<1216, 256, 0, s>>>(mask_dev, N, labels_dev);
-  uf_link<<<1216, 256, 0, s>>>(mask_dev, d.nx, d.ny, d.nz, labels_dev);
-  uf_flatten<<<1216, 256, 0, s>>>(labels_dev, N);
+  launch_union_find(mask_dev, d, labels_dev, s);
   mark_faces<<<152, 256, 0, s>>>(labels_dev, d.nx, d.ny, d.nz, touch.p);
   transport_from_labels<<<1216, 256, 0, s>>>(labels_dev, touch.p, N, transport_dev, cnt.p);
   OM_CUDA(cudaGetLastError());
@@ -145,9 +175,11 @@ om_status label_impl(const uint8_t* mask_dev, const om_domain& d, int* labels_de
 // Union-find labelling alone (labels_dev: int32 N, written), for callers
 // that bring their own flag storage.
 void launch_union_find(const uint8_t* mask_dev, const om_domain& d, int* labels_dev, cudaStream_t s) {
-  const int64_t N = voxels(d);
-  uf_init<<<1216, 256, 0, s>>>(mask_dev, N, labels_dev);
-  uf_link<<<1216, 256, 0, s>>>(mask_dev, d.nx, d.ny, d.nz, labels_dev);
+  const int64_t N = voxels(d), ncol = (int64_t)d.nx * d.ny;
+  const int zt = d.nz >= 128 ? 128 : (d.nz >= 64 ? 64 : 32);  // threads along z per column
+  uf_init_runs<<<(unsigned)std::min<int64_t>((ncol + 255) / 256, 4864), 256, 0, s>>>(mask_dev, ncol, d.nz,
+                                                                                     labels_dev);
+  uf_link_runs<<<(unsigned)std::min<int64_t>(ncol, 152 * 64), zt, 0, s>>>(mask_dev, d.nx, d.ny, d.nz, labels_dev);
   uf_flatten<<<1216, 256, 0, s>>>(labels_dev, N);
 }
 
