@@ -338,6 +338,7 @@ struct Model {
   int grid[2] = {152, 152};
   cudaGraphExec_t exec = nullptr;
   int graph_k = 0;
+  int graph_layout = -1;  // work-list layout the graph was captured for
 };
 
 }  // namespace
@@ -356,6 +357,14 @@ struct om_batch {
   int2* range = nullptr;      // device per-active-item tile ranges
   int2* range_h = nullptr;    // pinned
   int* nwork_h = nullptr;     // pinned
+  // the work list in groups of items whose populations fit in L2 together:
+  // group g's tiles are work[gstart[g] .. gstart[g] + gcnt[g])
+  int* gcnt = nullptr;        // device, [n]
+  int* gcnt_h = nullptr;      // pinned, [n]
+  std::vector<int> gstart;
+  int ngroups = 0;
+  int layout = 0;             // bumped whenever the work list is rebuilt
+  int layout_model = -1;      // the model whose footprint sized the groups
   int max_tiles = 0;
   double* partials = nullptr; // [max_tiles][5]
   double* obs = nullptr;      // [n][5]
@@ -369,22 +378,55 @@ struct om_batch {
 
 namespace {
 
-// work list of all tiles of the items flagged active; ranges per active item
-int build_work(om_batch* b, const std::vector<int>& active) {
+// L2 budget of a group: the populations (and per-node fields) of the items
+// of one group stay on chip across the steps of a check window, as a single
+// small structure's do when it is solved alone.
+constexpr double kGroupBytes = 80e6;
+
+// bytes per node a sweep of the model touches (populations, omega and
+// reference concentration for the diffusion, packed coordinates)
+double node_bytes(const om_batch* b, int model) {
+  const Model& m = b->m[model];
+  double per = (double)m.q * stg_bytes(m.prec) + 4.0;
+  if (model == 1) per += (m.prec == OM_F64 ? 8.0 : 4.0) + (m.cr ? 4.0 : 0.0);
+  return per;
+}
+
+// Work list of all tiles of the items flagged active, ordered by group
+// (consecutive items packed while their footprint fits kGroupBytes);
+// ranges per active item; the layout counter moves on.
+int build_work(om_batch* b, const std::vector<int>& active, int model) {
+  const double per = node_bytes(b, model);
   int w = 0;
+  b->gstart.clear();
+  b->ngroups = 0;
+  double fill = 0.0;
   for (size_t a = 0; a < active.size(); ++a) {
     const int k = active[a];
+    const double bytes = per * (double)b->items_h[k].nf;
+    if (b->ngroups == 0 || (fill > 0.0 && fill + bytes > kGroupBytes)) {
+      b->gstart.push_back(w);
+      b->gcnt_h[b->ngroups] = 0;
+      ++b->ngroups;
+      fill = 0.0;
+    }
+    fill += bytes;
     const int w0 = w;
     for (uint32_t s = 0; s < b->items_h[k].nf; s += kTile) b->work_h[w++] = make_uint2((unsigned)k, s);
+    b->gcnt_h[b->ngroups - 1] += w - w0;
     b->range_h[a] = make_int2(w0, w);
   }
   *b->nwork_h = w;
+  ++b->layout;
+  b->layout_model = model;
   return w;
 }
 
 om_status upload_work(om_batch* b, int nw, int nact, cudaStream_t s) {
   if (nw > 0) OM_CUDA(cudaMemcpyAsync(b->work, b->work_h, sizeof(uint2) * nw, cudaMemcpyHostToDevice, s));
   if (nact > 0) OM_CUDA(cudaMemcpyAsync(b->range, b->range_h, sizeof(int2) * nact, cudaMemcpyHostToDevice, s));
+  if (b->ngroups > 0)
+    OM_CUDA(cudaMemcpyAsync(b->gcnt, b->gcnt_h, sizeof(int) * b->ngroups, cudaMemcpyHostToDevice, s));
   OM_CUDA(cudaMemcpyAsync(b->nwork, b->nwork_h, sizeof(int), cudaMemcpyHostToDevice, s));
   return OM_OK;
 }
@@ -420,40 +462,60 @@ DiffArgs<T> bdiff_args(const om_batch* b) {
 }
 
 template <class T, int MINB>
-void launch_flow(const om_batch* b, bool odd, int grid, cudaStream_t s) {
+void launch_flow(const om_batch* b, bool odd, int grid, const uint2* work, const int* cnt, cudaStream_t s) {
   FlowArgs<T> a = bflow_args<T>(b);
-  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
-  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
+  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
+  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
 }
 
 template <class T, int MINB>
-void launch_diff(const om_batch* b, bool odd, int grid, cudaStream_t s) {
+void launch_diff(const om_batch* b, bool odd, int grid, const uint2* work, const int* cnt, cudaStream_t s) {
   DiffArgs<T> a = bdiff_args<T>(b);
-  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
-  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork);
+  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
+  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
 }
 
 // variant 0: no residency hint; variant 1: capped for 4 (flow; 3 in FP64) / 8
 // (diffusion) CTAs per SM
 template <class T>
-void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, cudaStream_t s) {
+void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, const uint2* work, const int* cnt,
+                 cudaStream_t s) {
   if (model == 0) {
-    if (variant == 0) launch_flow<T, 0>(b, odd, grid, s);
-    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, s);
+    if (variant == 0) launch_flow<T, 0>(b, odd, grid, work, cnt, s);
+    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, work, cnt, s);
   } else {
-    if (variant == 0) launch_diff<T, 0>(b, odd, grid, s);
-    else launch_diff<T, 8>(b, odd, grid, s);
+    if (variant == 0) launch_diff<T, 0>(b, odd, grid, work, cnt, s);
+    else launch_diff<T, 8>(b, odd, grid, work, cnt, s);
+  }
+}
+
+// n steps of every item, group after group (each group's n steps run while
+// its populations sit in L2); launches onto s in that order
+template <class T>
+void launch_steps_grouped(const om_batch* b, int model, int64_t t0, int64_t n, cudaStream_t s) {
+  const Model& m = b->m[model];
+  for (int g = 0; g < b->ngroups; ++g) {
+    const int tiles = b->gcnt_h[g];
+    if (tiles == 0) continue;
+    for (int64_t k = 0; k < n; ++k) {
+      const bool odd = (t0 + k) & 1;
+      launch_step<T>(b, model, odd, m.var[odd], std::min(m.grid[odd], tiles), b->work + b->gstart[g], b->gcnt + g, s);
+    }
   }
 }
 
 template <class T>
 om_status steps_t(om_batch* b, int model, int64_t n, cudaStream_t s) {
   Model& m = b->m[model];
-  for (int64_t k = 0; k < n; ++k) {
-    const bool odd = m.t & 1;
-    launch_step<T>(b, model, odd, m.var[odd], m.grid[odd], s);
-    ++m.t;
+  if (b->layout_model != model) {  // groups sized for this model's footprint, every item
+    std::vector<int> all;
+    for (int k = 0; k < b->n; ++k)
+      if (b->items_h[k].nf > 0) all.push_back(k);
+    const int nw = build_work(b, all, model);
+    OM_TRY(upload_work(b, nw, (int)all.size(), s));
   }
+  launch_steps_grouped<T>(b, model, m.t, n, s);
+  m.t += n;
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
@@ -497,9 +559,9 @@ om_status tune_t(om_batch* b, int model, cudaStream_t s) {
     float tot[2] = {0.f, 0.f};
     for (int r = 0; r < 7; ++r) {
       OM_CUDA(cudaEventRecord(ev[0], s));
-      launch_step<T>(b, model, false, sh[0], grid, s);
+      launch_step<T>(b, model, false, sh[0], grid, b->work, b->nwork, s);
       OM_CUDA(cudaEventRecord(ev[1], s));
-      launch_step<T>(b, model, true, sh[0], grid, s);
+      launch_step<T>(b, model, true, sh[0], grid, b->work, b->nwork, s);
       OM_CUDA(cudaEventRecord(ev[2], s));
       OM_CUDA(cudaEventSynchronize(ev[2]));
       if (r == 0) continue;
@@ -525,20 +587,21 @@ om_status tune_t(om_batch* b, int model, cudaStream_t s) {
 template <class T>
 om_status capture_t(om_batch* b, int model, int K) {
   Model& m = b->m[model];
-  if (m.exec && m.graph_k == K) return OM_OK;
+  if (m.exec && m.graph_k == K && m.graph_layout == b->layout) return OM_OK;
   if (m.exec) {
     cudaGraphExecDestroy(m.exec);
     m.exec = nullptr;
   }
   cudaGraph_t g = nullptr;
   OM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) launch_step<T>(b, model, k & 1, m.var[k & 1], m.grid[k & 1], b->cap);
+  launch_steps_grouped<T>(b, model, 0, K, b->cap);
   cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
   e = cudaGraphInstantiate(&m.exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
   m.graph_k = K;
+  m.graph_layout = b->layout;
   return OM_OK;
 }
 
@@ -572,7 +635,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
     if (b->items_h[k].nf > 0 && (model == 1 || b->ns[k]->wrap_links > 0)) active.push_back(k);
   }
   std::vector<double> sj_prev(b->n, 0.0);
-  int nw = build_work(b, active);
+  int nw = build_work(b, active, model);
   OM_TRY(upload_work(b, nw, (int)active.size(), s));
   OM_TRY(observe_t<T>(b, model, (int)active.size(), s));  // reference state
   for (size_t a = 0; a < active.size(); ++a) sj_prev[active[a]] = b->obs_h[a * nv + 0];
@@ -625,7 +688,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
     }
     if (keep.size() != active.size()) {
       active.swap(keep);
-      nw = build_work(b, active);
+      nw = build_work(b, active, model);
       OM_TRY(upload_work(b, nw, (int)active.size(), s));
     }
   }
@@ -644,7 +707,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
   std::vector<int> all;
   for (int k = 0; k < b->n; ++k)
     if (b->items_h[k].nf > 0) all.push_back(k);
-  nw = build_work(b, all);
+  nw = build_work(b, all, model);
   OM_TRY(upload_work(b, nw, (int)all.size(), s));
   OM_CUDA(cudaStreamSynchronize(s));
   return OM_OK;
@@ -677,12 +740,14 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
   cudaFree(b->items);
   cudaFree(b->work);
   cudaFree(b->nwork);
+  cudaFree(b->gcnt);
   cudaFree(b->range);
   cudaFree(b->partials);
   cudaFree(b->obs);
   if (b->work_h) cudaFreeHost(b->work_h);
   if (b->range_h) cudaFreeHost(b->range_h);
   if (b->nwork_h) cudaFreeHost(b->nwork_h);
+  if (b->gcnt_h) cudaFreeHost(b->gcnt_h);
   if (b->obs_h) cudaFreeHost(b->obs_h);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -762,12 +827,14 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if ((st = dalloc((void**)&b->items, sizeof(BatchItem) * n)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->work, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->nwork, sizeof(int))) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->gcnt, sizeof(int) * n)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->range, sizeof(int2) * n)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->partials, sizeof(double) * 5 * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->obs, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->work_h, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->range_h, sizeof(int2) * n)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->nwork_h, sizeof(int))) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->gcnt_h, sizeof(int) * n)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->obs_h, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
   if (cudaMemcpyAsync(b->items, b->items_h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return bail(fail(OM_ECUDA, "om_batch_create: copy of the item table failed"));
@@ -812,7 +879,7 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     std::vector<int> all;
     for (int k = 0; k < n; ++k)
       if (b->items_h[k].nf > 0) all.push_back(k);
-    const int nw = build_work(b, all);
+    const int nw = build_work(b, all, model);
     if ((st = upload_work(b, nw, (int)all.size(), s)) != OM_OK) return bail(st);
     if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
     const int variant = model == 0 ? fp->variant : dp->variant;

@@ -92,6 +92,37 @@ def _structures(orc):
     return out
 
 
+@pytest.mark.timeout(600)
+def test_batch_in_l2_groups_steps_match_oracle(orc, om):
+    # three structures of ~6e5 nodes: their FP64 flow populations take ~93 MB
+    # and their FP64 diffusion fields ~41 MB each, so no two fit in one L2
+    # group (80 MB) and every item runs in a group of its own; a window of 5
+    # steps is taken group after group and must equal the oracle's steps
+    masks = [S.random_mask((72, 96, 96), 0.9, 40 + k) for k in range(3)]
+    tau, g = 0.9, 2e-4
+    rng = np.random.default_rng(5)
+    d = [(10 + 50 * rng.random(m.shape) * m).astype(np.float32) for m in masks]
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks], [_dev(x) for x in d],
+                 flow=om.flow_params(tau=tau, body_force=g, precision=om.OM_F64),
+                 diff=om.diff_params(precision=om.OM_F64, c_in=0.9, c_out=0.1))
+    f0 = [_rand_flow(orc, m, 70 + k) for k, m in enumerate(masks)]
+    g0 = [_rand_diff(m, 80 + k) for k, m in enumerate(masks)]
+    for k in range(3):
+        b.set_populations(0, k, _dev(f0[k]))
+        b.set_populations(1, k, _dev(g0[k]))
+    b.step(0, 5)
+    b.step(1, 5)
+    for k, m in enumerate(masks):
+        out = torch.empty(19 * m.size, dtype=torch.float64, device="cuda")
+        b.get_populations(0, k, out)
+        ref = orc.flow_step(m, f0[k], tau, g, 5)
+        assert np.abs(out.cpu().numpy().reshape(ref.shape) - ref).max() <= 5e-13, k
+        out = torch.empty(7 * m.size, dtype=torch.float64, device="cuda")
+        b.get_populations(1, k, out)
+        ref = orc.diff_step(m, g0[k], orc.omega_field(m, d[k]), 0.9, 0.1, 5)
+        assert np.abs(out.cpu().numpy().reshape(ref.shape) - ref).max() <= 5e-13, k
+
+
 @pytest.mark.timeout(900)
 def test_batch_solves_match_oracle(orc, om):
     st = _structures(orc)
