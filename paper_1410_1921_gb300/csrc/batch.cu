@@ -38,14 +38,33 @@ __global__ void rebase_columns(uint2* col, int64_t nw, uint32_t off) {
 }
 
 // ------------------------------------------------------------------ sweeps
+// A sweep launch covers one group of items.  The group's item geometry
+// travels in the kernel parameters (the constant bank, like the arguments
+// of the single-structure sweeps): per tile a thread reads one work entry
+// {item within the group, first node} and finds the rest there, so the
+// geometry costs no registers and no dependent global loads.
+constexpr int kGroupItems = 32;
+
+struct GroupItem {
+  const uint2* col;       // rebased column map (global node numbers)
+  const uint32_t* coord;  // structure-local packed coordinates
+  uint32_t off, nf;
+  int nx, ny, nz, W;
+  float slope;  // diffusion: (c_out - c_in) / nx
+};
+
+struct GroupDesc {
+  GroupItem it[kGroupItems];
+};
+
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(kTile, MINB)
-    flow_batch_sweep(FlowArgs<T> a, const BatchItem* __restrict__ items, const uint2* __restrict__ work,
+    flow_batch_sweep(FlowArgs<T> a, const __grid_constant__ GroupDesc g, const uint2* __restrict__ work,
                      const int* __restrict__ nwork) {
   const int nw = *nwork;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
     const uint2 t = work[w];
-    const BatchItem& it = items[t.x];
+    const GroupItem& it = g.it[t.x];
     const uint32_t ln = t.y + threadIdx.x;
     if (ln >= it.nf) continue;
     if (ODD) {
@@ -65,12 +84,12 @@ __global__ void __launch_bounds__(kTile, MINB)
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(kTile, MINB)
-    diff_batch_sweep(DiffArgs<T> a, const BatchItem* __restrict__ items, const uint2* __restrict__ work,
+    diff_batch_sweep(DiffArgs<T> a, const __grid_constant__ GroupDesc g, const uint2* __restrict__ work,
                      const int* __restrict__ nwork) {
   const int nw = *nwork;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
     const uint2 t = work[w];
-    const BatchItem& it = items[t.x];
+    const GroupItem& it = g.it[t.x];
     const uint32_t ln = t.y + threadIdx.x;
     if (ln >= it.nf) continue;
     DiffArgs<T> b = a;
@@ -357,11 +376,15 @@ struct om_batch {
   int2* range = nullptr;      // device per-active-item tile ranges
   int2* range_h = nullptr;    // pinned
   int* nwork_h = nullptr;     // pinned
-  // the work list in groups of items whose populations fit in L2 together:
-  // group g's tiles are work[gstart[g] .. gstart[g] + gcnt[g])
+  // the work list in groups of items whose populations fit in L2 together
+  // (at most kGroupItems each): group g's tiles are gwork[gstart[g] ..
+  // gstart[g] + gcnt[g]), entries {item within the group, first node}
+  uint2* gwork = nullptr;     // device, [max_tiles]
+  uint2* gwork_h = nullptr;   // pinned
   int* gcnt = nullptr;        // device, [n]
   int* gcnt_h = nullptr;      // pinned, [n]
   std::vector<int> gstart;
+  std::vector<GroupDesc> gdesc;
   int ngroups = 0;
   int layout = 0;             // bumped whenever the work list is rebuilt
   int layout_model = -1;      // the model whose footprint sized the groups
@@ -401,18 +424,30 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
   b->gstart.clear();
   b->ngroups = 0;
   double fill = 0.0;
+  b->gdesc.clear();
+  int in_group = 0;
   for (size_t a = 0; a < active.size(); ++a) {
     const int k = active[a];
-    const double bytes = per * (double)b->items_h[k].nf;
-    if (b->ngroups == 0 || (fill > 0.0 && fill + bytes > kGroupBytes)) {
+    const BatchItem& bi = b->items_h[k];
+    const double bytes = per * (double)bi.nf;
+    if (b->ngroups == 0 || in_group == kGroupItems || (fill > 0.0 && fill + bytes > kGroupBytes)) {
       b->gstart.push_back(w);
       b->gcnt_h[b->ngroups] = 0;
+      b->gdesc.push_back(GroupDesc{});
       ++b->ngroups;
       fill = 0.0;
+      in_group = 0;
     }
     fill += bytes;
+    b->gdesc.back().it[in_group] =
+        GroupItem{bi.col, bi.coord, bi.off, bi.nf, bi.nx, bi.ny, bi.nz, bi.W, (float)bi.slope};
     const int w0 = w;
-    for (uint32_t s = 0; s < b->items_h[k].nf; s += kTile) b->work_h[w++] = make_uint2((unsigned)k, s);
+    for (uint32_t s = 0; s < bi.nf; s += kTile) {
+      b->work_h[w] = make_uint2((unsigned)k, s);
+      b->gwork_h[w] = make_uint2((unsigned)in_group, s);
+      ++w;
+    }
+    ++in_group;
     b->gcnt_h[b->ngroups - 1] += w - w0;
     b->range_h[a] = make_int2(w0, w);
   }
@@ -424,6 +459,7 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
 
 om_status upload_work(om_batch* b, int nw, int nact, cudaStream_t s) {
   if (nw > 0) OM_CUDA(cudaMemcpyAsync(b->work, b->work_h, sizeof(uint2) * nw, cudaMemcpyHostToDevice, s));
+  if (nw > 0) OM_CUDA(cudaMemcpyAsync(b->gwork, b->gwork_h, sizeof(uint2) * nw, cudaMemcpyHostToDevice, s));
   if (nact > 0) OM_CUDA(cudaMemcpyAsync(b->range, b->range_h, sizeof(int2) * nact, cudaMemcpyHostToDevice, s));
   if (b->ngroups > 0)
     OM_CUDA(cudaMemcpyAsync(b->gcnt, b->gcnt_h, sizeof(int) * b->ngroups, cudaMemcpyHostToDevice, s));
@@ -462,30 +498,32 @@ DiffArgs<T> bdiff_args(const om_batch* b) {
 }
 
 template <class T, int MINB>
-void launch_flow(const om_batch* b, bool odd, int grid, const uint2* work, const int* cnt, cudaStream_t s) {
+void launch_flow(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
   FlowArgs<T> a = bflow_args<T>(b);
-  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
-  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
+  const uint2* work = b->gwork + b->gstart[g];
+  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
+  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
 }
 
 template <class T, int MINB>
-void launch_diff(const om_batch* b, bool odd, int grid, const uint2* work, const int* cnt, cudaStream_t s) {
+void launch_diff(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
   DiffArgs<T> a = bdiff_args<T>(b);
-  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
-  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->items, work, cnt);
+  const uint2* work = b->gwork + b->gstart[g];
+  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
+  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
 }
 
 // variant 0: no residency hint; variant 1: capped for 4 (flow; 3 in FP64) / 8
 // (diffusion) CTAs per SM
+// one step of group g
 template <class T>
-void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, const uint2* work, const int* cnt,
-                 cudaStream_t s) {
+void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, int g, cudaStream_t s) {
   if (model == 0) {
-    if (variant == 0) launch_flow<T, 0>(b, odd, grid, work, cnt, s);
-    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, work, cnt, s);
+    if (variant == 0) launch_flow<T, 0>(b, odd, grid, g, s);
+    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, g, s);
   } else {
-    if (variant == 0) launch_diff<T, 0>(b, odd, grid, work, cnt, s);
-    else launch_diff<T, 8>(b, odd, grid, work, cnt, s);
+    if (variant == 0) launch_diff<T, 0>(b, odd, grid, g, s);
+    else launch_diff<T, 8>(b, odd, grid, g, s);
   }
 }
 
@@ -499,11 +537,17 @@ void launch_steps_grouped(const om_batch* b, int model, int64_t t0, int64_t n, c
     if (tiles == 0) continue;
     for (int64_t k = 0; k < n; ++k) {
       const bool odd = (t0 + k) & 1;
-      launch_step<T>(b, model, odd, m.var[odd], std::min(m.grid[odd], tiles), b->work + b->gstart[g], b->gcnt + g, s);
+      launch_step<T>(b, model, odd, m.var[odd], std::min(m.grid[odd], tiles), g, s);
     }
   }
 }
 
+template <class T>
+om_status capture_t(om_batch* b, int model, int K);
+
+// Advance n steps: whole check windows from even times replay the captured
+// window graph (and, for rebased diffusion storage, move the reference after
+// it, as a solve does); anything else is launched step by step.
 template <class T>
 om_status steps_t(om_batch* b, int model, int64_t n, cudaStream_t s) {
   Model& m = b->m[model];
@@ -514,8 +558,20 @@ om_status steps_t(om_batch* b, int model, int64_t n, cudaStream_t s) {
     const int nw = build_work(b, all, model);
     OM_TRY(upload_work(b, nw, (int)all.size(), s));
   }
-  launch_steps_grouped<T>(b, model, m.t, n, s);
-  m.t += n;
+  const int K = model == 0 ? b->fp.check_every : b->dp.check_every;
+  while (n > 0) {
+    if (K >= 2 && !(K & 1) && !(m.t & 1) && n >= K) {
+      OM_TRY(capture_t<T>(b, model, K));
+      OM_CUDA(cudaGraphLaunch(m.exec, s));
+      m.t += K;
+      n -= K;
+      if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
+      continue;
+    }
+    launch_steps_grouped<T>(b, model, m.t, 1, s);
+    ++m.t;
+    --n;
+  }
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
@@ -559,9 +615,9 @@ om_status tune_t(om_batch* b, int model, cudaStream_t s) {
     float tot[2] = {0.f, 0.f};
     for (int r = 0; r < 7; ++r) {
       OM_CUDA(cudaEventRecord(ev[0], s));
-      launch_step<T>(b, model, false, sh[0], grid, b->work, b->nwork, s);
+      for (int gi = 0; gi < b->ngroups; ++gi) launch_step<T>(b, model, false, sh[0], grid, gi, s);
       OM_CUDA(cudaEventRecord(ev[1], s));
-      launch_step<T>(b, model, true, sh[0], grid, b->work, b->nwork, s);
+      for (int gi = 0; gi < b->ngroups; ++gi) launch_step<T>(b, model, true, sh[0], grid, gi, s);
       OM_CUDA(cudaEventRecord(ev[2], s));
       OM_CUDA(cudaEventSynchronize(ev[2]));
       if (r == 0) continue;
@@ -741,6 +797,7 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
   cudaFree(b->work);
   cudaFree(b->nwork);
   cudaFree(b->gcnt);
+  cudaFree(b->gwork);
   cudaFree(b->range);
   cudaFree(b->partials);
   cudaFree(b->obs);
@@ -748,6 +805,7 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
   if (b->range_h) cudaFreeHost(b->range_h);
   if (b->nwork_h) cudaFreeHost(b->nwork_h);
   if (b->gcnt_h) cudaFreeHost(b->gcnt_h);
+  if (b->gwork_h) cudaFreeHost(b->gwork_h);
   if (b->obs_h) cudaFreeHost(b->obs_h);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -828,6 +886,7 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if ((st = dalloc((void**)&b->work, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->nwork, sizeof(int))) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->gcnt, sizeof(int) * n)) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->gwork, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->range, sizeof(int2) * n)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->partials, sizeof(double) * 5 * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->obs, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
@@ -835,6 +894,7 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if ((st = halloc((void**)&b->range_h, sizeof(int2) * n)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->nwork_h, sizeof(int))) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->gcnt_h, sizeof(int) * n)) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->gwork_h, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->obs_h, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
   if (cudaMemcpyAsync(b->items, b->items_h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return bail(fail(OM_ECUDA, "om_batch_create: copy of the item table failed"));
