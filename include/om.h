@@ -276,10 +276,14 @@ om_status om_diff_destroy(om_diff* df);
 
 /* ---------------------------------------------------------------- batches
  * Many independent structures (the paper's 150 reconstructions) solved
- * together: one persistent launch per LB step advances every structure not
- * yet converged, a check window is replayed from a captured CUDA graph, and
- * each structure leaves the work list when it converges.  Launch shapes are
- * timed at creation.  Both models share the parameters given; pass NULL for a
+ * together.  The structures not yet converged are packed into groups whose
+ * sweep footprint fits in L2 (at most 32 structures each); one launch per LB
+ * step advances a whole group over a work list of 256-node tiles, a check
+ * window runs its steps group after group from a captured CUDA graph, and a
+ * structure leaves the work list when it converges.  Launch shapes (register
+ * cap; one CTA per tile or a resident grid of 2-8 CTAs per SM) are timed at
+ * creation.  om_batch_step replays the window graph for whole windows from
+ * even times.  Both models share the parameters given; pass NULL for a
  * model that is not needed (d_nm_dev may then be NULL too).
  * nodes_dev[k]: uint8 N_k node mask (normally the transport set) of
  * doms[k]; d_nm_dev[k]: float N_k pore sizes (nm).  All device pointers. */

@@ -50,7 +50,7 @@ struct GroupItem {
   const uint32_t* coord;  // structure-local packed coordinates
   uint32_t off, nf;
   int nx, ny, nz, W;
-  float slope;  // diffusion: (c_out - c_in) / nx
+  double slope;  // diffusion: (c_out - c_in) / nx
 };
 
 struct GroupDesc {
@@ -440,7 +440,7 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
     }
     fill += bytes;
     b->gdesc.back().it[in_group] =
-        GroupItem{bi.col, bi.coord, bi.off, bi.nf, bi.nx, bi.ny, bi.nz, bi.W, (float)bi.slope};
+        GroupItem{bi.col, bi.coord, bi.off, bi.nf, bi.nx, bi.ny, bi.nz, bi.W, bi.slope};
     const int w0 = w;
     for (uint32_t s = 0; s < bi.nf; s += kTile) {
       b->work_h[w] = make_uint2((unsigned)k, s);
@@ -537,7 +537,8 @@ void launch_steps_grouped(const om_batch* b, int model, int64_t t0, int64_t n, c
     if (tiles == 0) continue;
     for (int64_t k = 0; k < n; ++k) {
       const bool odd = (t0 + k) & 1;
-      launch_step<T>(b, model, odd, m.var[odd], std::min(m.grid[odd], tiles), g, s);
+      const int grid = m.grid[odd] > 0 ? std::min(m.grid[odd], tiles) : tiles;  // 0: one CTA per tile
+      launch_step<T>(b, model, odd, m.var[odd], grid, g, s);
     }
   }
 }
@@ -606,18 +607,22 @@ template <class T>
 om_status tune_t(om_batch* b, int model, cudaStream_t s) {
   Model& m = b->m[model];
   if (b->total == 0) return OM_OK;
-  const int shapes[4][2] = {{0, 2}, {0, 4}, {1, 4}, {1, 8}};  // {variant, CTAs per SM}
+  // {variant, CTAs per SM}; 0 CTAs per SM: one CTA per 256-node tile, the
+  // hardware scheduler balancing the tiles, instead of a resident grid
+  const int shapes[6][2] = {{0, 0}, {1, 0}, {0, 2}, {0, 4}, {1, 4}, {1, 8}};
   cudaEvent_t ev[3];
   for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
   float best[2] = {1e30f, 1e30f};
   for (const auto& sh : shapes) {
-    const int grid = sh[1] * b->sms;
+    const int grid = sh[1] * b->sms;  // 0: one CTA per tile
     float tot[2] = {0.f, 0.f};
     for (int r = 0; r < 7; ++r) {
       OM_CUDA(cudaEventRecord(ev[0], s));
-      for (int gi = 0; gi < b->ngroups; ++gi) launch_step<T>(b, model, false, sh[0], grid, gi, s);
+      for (int gi = 0; gi < b->ngroups; ++gi)
+        launch_step<T>(b, model, false, sh[0], grid > 0 ? std::min(grid, b->gcnt_h[gi]) : b->gcnt_h[gi], gi, s);
       OM_CUDA(cudaEventRecord(ev[1], s));
-      for (int gi = 0; gi < b->ngroups; ++gi) launch_step<T>(b, model, true, sh[0], grid, gi, s);
+      for (int gi = 0; gi < b->ngroups; ++gi)
+        launch_step<T>(b, model, true, sh[0], grid > 0 ? std::min(grid, b->gcnt_h[gi]) : b->gcnt_h[gi], gi, s);
       OM_CUDA(cudaEventRecord(ev[2], s));
       OM_CUDA(cudaEventSynchronize(ev[2]));
       if (r == 0) continue;
