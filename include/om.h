@@ -215,6 +215,31 @@ om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om_domain d,
 om_status om_apparent_permeability(double k_m2, double D_eff_m2s, double mu_Pa_s, double p_Pa,
                                    double* k_app_m2, double* f_c);
 
+/* The correction factors f_c (k_app = k f_c) of Sec. 4.4 for a medium of
+ * intrinsic permeability k_m2, porosity and effective Knudsen diffusivity
+ * D_eff_m2s, for a gas of molar mass M at temperature T, pressure p and
+ * viscosity mu (SI units):
+ *   lambda_m     Eq. 29, lambda = (mu / p) sqrt(pi R T / (2 M));
+ *   r_m          Eq. 30, r = 8.886e-2 (k / eps)^0.5 with k in mD and r in
+ *                micrometres (the capillary-bundle radius sqrt(8 k / eps);
+ *                the nm printed with Eq. 30 is read as a misprint);
+ *   Kn           lambda / r;
+ *   dgm          Eq. 26 (the dusty-gas form of this method);
+ *   klinkenberg  Eqs. 18-19 with c = 1: 1 + 4 Kn;
+ *   beskok_civan Eq. 20 with Eq. 21 and b = -1;
+ *   heid, jones_owens, sampath_keighin, florence: Eq. 18 with the slippage
+ *                factors of Table 1 (b_k in psi from k in mD; Florence et al.
+ *                with the membrane beta = 32.766).
+ * 1 mD = 9.869233e-16 m^2, 1 psi = 6894.757293168361 Pa.  OM_EINVAL unless
+ * k, porosity, T, M, mu, p > 0, porosity <= 1 and D_eff >= 0. */
+typedef struct {
+  double lambda_m, r_m, Kn;
+  double dgm, klinkenberg, beskok_civan;
+  double heid, jones_owens, sampath_keighin, florence;
+} om_slip_corrections;
+om_status om_slip_correction_factors(double k_m2, double porosity, double D_eff_m2s, double T_K, double M_kg_per_mol,
+                                     double mu_Pa_s, double p_Pa, om_slip_corrections* out);
+
 /* ---------------------------------------------------------------- node set and solver objects
  * The hot loop.  A node set holds the transport voxels in lexicographic order
  * with a per-column bit map and prefix count, from which every neighbour's

@@ -73,3 +73,48 @@ def mean_free_path(mu, p, T_K, M):
 def cylinder_fc(Kn):
     """Eq. 28: f_c = 1 + (64 / (3 pi)) Kn."""
     return 1.0 + 64.0 / (3.0 * math.pi) * Kn
+
+
+# ------------------------------------------------------------------ slip corrections (Sec. 4.4.1, 4.4.3)
+PA_PER_PSI = 6894.757293168361      # NIST
+M2_PER_MILLIDARCY = 9.869233e-16    # 1 D = 9.869233e-13 m^2 (NIST)
+
+
+def klinkenberg_fc(Kn):
+    """Eqs. 18-19 with c = 1: f_c = 1 + b_k/P = 1 + 4 Kn."""
+    return 1.0 + 4.0 * Kn
+
+
+def civan_alpha(Kn):
+    """Eq. 21: alpha(Kn) = 1.358 / (1 + 0.170 Kn^-0.4348)."""
+    return 1.358 / (1.0 + 0.170 * Kn ** -0.4348)
+
+
+def beskok_civan_fc(Kn, b=-1.0):
+    """Eq. 20 with Eq. 21: f_c = (1 + alpha Kn)(1 + 4 Kn / (1 - b Kn)), b = -1 (slip flow)."""
+    return (1.0 + civan_alpha(Kn) * Kn) * (1.0 + 4.0 * Kn / (1.0 - b * Kn))
+
+
+def table1_bk_psi(name, k_md, porosity):
+    """Table 1: Klinkenberg slippage factor b_k (psi) from k_d (mD) and porosity."""
+    if name == "heid":
+        return 11.419 * k_md ** -0.39
+    if name == "jones_owens":
+        return 12.639 * k_md ** -0.33
+    if name == "sampath_keighin":
+        return 13.85 * (k_md / porosity) ** -0.53
+    if name == "florence":
+        return 32.766 * (k_md / porosity) ** -0.5  # membrane beta
+    raise ValueError(name)
+
+
+def table1_fc(name, k_m2, porosity, p_Pa):
+    """Eq. 18 with a Table 1 slippage factor: f_c = 1 + b_k / P (b_k, P in psi)."""
+    return 1.0 + table1_bk_psi(name, k_m2 / M2_PER_MILLIDARCY, porosity) / (p_Pa / PA_PER_PSI)
+
+
+def characteristic_pore_size(k_m2, porosity):
+    """Eq. 30: r = 8.886e-2 (k / eps)^0.5 with k in mD, read with r in
+    micrometres (the capillary-bundle radius sqrt(8 k / eps) in those units;
+    the printed nm is off by 1000); returned in m."""
+    return 8.886e-2 * (k_m2 / M2_PER_MILLIDARCY / porosity) ** 0.5 * 1e-6

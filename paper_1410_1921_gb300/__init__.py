@@ -56,6 +56,11 @@ class om_diff_params(C.Structure):
                 ("precision", C.c_int32), ("variant", C.c_int32), ("lattice", C.c_int32)]
 
 
+class om_slip_corrections(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("lambda_m", "r_m", "Kn", "dgm", "klinkenberg", "beskok_civan", "heid",
+                                           "jones_owens", "sampath_keighin", "florence")]
+
+
 class om_run_info(C.Structure):
     _fields_ = [("steps", C.c_int64), ("n_nodes", C.c_int64), ("rel_change", C.c_double),
                 ("mass", C.c_double), ("seconds", C.c_double), ("mlups", C.c_double)]
@@ -82,6 +87,7 @@ _SIGS = {
     "om_solve_knudsen": [_vp, _vp, om_domain, C.POINTER(om_diff_params), _f64p, _f64p,
                          C.POINTER(om_run_info), _vp],
     "om_apparent_permeability": [C.c_double, C.c_double, C.c_double, C.c_double, _f64p, _f64p],
+    "om_slip_correction_factors": [C.c_double] * 7 + [C.POINTER(om_slip_corrections)],
     "om_nodeset_create": [_vp, om_domain, _vp, C.POINTER(_vp)],
     "om_nodeset_count": [_vp, _i64p],
     "om_nodeset_voxels": [_vp, _vp, _vp],
@@ -290,6 +296,15 @@ def om_solve_knudsen(mask, d_nm, dom, params, want_c=False):
     st = _call("om_solve_knudsen", _ptr(mask), _ptr(d_nm), dom, C.byref(params), C.byref(D), C.byref(tau),
                C.byref(info), _ptr(c), ok=(OM_OK, OM_ENOTCONVERGED))
     return st, D.value, tau.value, info, c
+
+
+def om_slip_correction_factors(k_m2, porosity, D_eff_m2s, T_K=323.0, M_kg_per_mol=0.016, mu_Pa_s=1.73e-5,
+                               p_Pa=17236893.0):
+    """The correction factors of Sec. 4.4 as a dict (defaults: the operating
+    point of Sec. 4.4.3, methane)."""
+    out = om_slip_corrections()
+    _call("om_slip_correction_factors", k_m2, porosity, D_eff_m2s, T_K, M_kg_per_mol, mu_Pa_s, p_Pa, C.byref(out))
+    return {n: getattr(out, n) for n, _ in om_slip_corrections._fields_}
 
 
 def om_apparent_permeability(k_m2, D_eff_m2s, mu_Pa_s, p_Pa):

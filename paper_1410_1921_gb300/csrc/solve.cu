@@ -139,3 +139,32 @@ extern "C" om_status om_apparent_permeability(double k_m2, double D_eff_m2s, dou
   if (k_app_m2) *k_app_m2 = k_m2 * fc;
   return OM_OK;
 }
+
+extern "C" om_status om_slip_correction_factors(double k_m2, double porosity, double D_eff_m2s, double T_K,
+                                                double M_kg_per_mol, double mu_Pa_s, double p_Pa,
+                                                om_slip_corrections* out) {
+  if (!out) return fail(OM_EINVAL, "om_slip_correction_factors: null pointer");
+  if (!(k_m2 > 0.0) || !(porosity > 0.0) || !(porosity <= 1.0) || !(D_eff_m2s >= 0.0) || !(T_K > 0.0) ||
+      !(M_kg_per_mol > 0.0) || !(mu_Pa_s > 0.0) || !(p_Pa > 0.0))
+    return fail(OM_EINVAL, "om_slip_correction_factors: need k, porosity, T, M, mu, p > 0, porosity <= 1, D_eff >= 0");
+  constexpr double kR = 8.314462618;             // J / (mol K)
+  constexpr double kPi = 3.14159265358979323846;
+  constexpr double kPsi = 6894.757293168361;      // Pa per psi
+  constexpr double kMilliDarcy = 9.869233e-16;    // m^2 per mD
+  om_slip_corrections c{};
+  c.lambda_m = (mu_Pa_s / p_Pa) * std::sqrt(kPi * kR * T_K / (2.0 * M_kg_per_mol));  // Eq. 29
+  const double k_md = k_m2 / kMilliDarcy;
+  c.r_m = 8.886e-2 * std::sqrt(k_md / porosity) * 1e-6;  // Eq. 30: micrometres from mD (sqrt(8 k / eps))
+  c.Kn = c.lambda_m / c.r_m;
+  c.dgm = 1.0 + D_eff_m2s * mu_Pa_s / (k_m2 * p_Pa);  // Eq. 26
+  c.klinkenberg = 1.0 + 4.0 * c.Kn;                   // Eqs. 18-19, c = 1
+  const double alpha = 1.358 / (1.0 + 0.170 * std::pow(c.Kn, -0.4348));  // Eq. 21
+  c.beskok_civan = (1.0 + alpha * c.Kn) * (1.0 + 4.0 * c.Kn / (1.0 + c.Kn));  // Eq. 20, b = -1
+  const double p_psi = p_Pa / kPsi;
+  c.heid = 1.0 + 11.419 * std::pow(k_md, -0.39) / p_psi;  // Table 1 with Eq. 18
+  c.jones_owens = 1.0 + 12.639 * std::pow(k_md, -0.33) / p_psi;
+  c.sampath_keighin = 1.0 + 13.85 * std::pow(k_md / porosity, -0.53) / p_psi;
+  c.florence = 1.0 + 32.766 * std::pow(k_md / porosity, -0.5) / p_psi;
+  *out = c;
+  return OM_OK;
+}

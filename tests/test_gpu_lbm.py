@@ -429,6 +429,23 @@ def test_step_cap_reports_not_converged(om):
     assert st == om.OM_ENOTCONVERGED and info.steps == 200 and kl > 0
 
 
+@pytest.mark.parametrize("k,eps,D", [(1e-21, 0.1, 1e-8), (2e-19, 0.3, 3e-7), (1e-17, 0.5, 1e-6)])
+def test_slip_correction_factors_match_oracle(om, k, eps, D):
+    from oracle import physics as PH
+    T, M, mu, p = 323.0, 0.016, 1.73e-5, 17236893.0
+    c = om.om_slip_correction_factors(k, eps, D, T, M, mu, p)
+    lam = PH.mean_free_path(mu, p, T, M)
+    r = PH.characteristic_pore_size(k, eps)
+    Kn = lam / r
+    ref = {"lambda_m": lam, "r_m": r, "Kn": Kn, "dgm": PH.apparent_permeability(k, D, mu, p)[1],
+           "klinkenberg": PH.klinkenberg_fc(Kn), "beskok_civan": PH.beskok_civan_fc(Kn),
+           **{n: PH.table1_fc(n, k, eps, p) for n in ("heid", "jones_owens", "sampath_keighin", "florence")}}
+    for name, v in ref.items():
+        assert c[name] == pytest.approx(v, rel=1e-12), name
+    with pytest.raises(om.OmError):
+        om.om_slip_correction_factors(k, 0.0, D)
+
+
 def test_apparent_permeability_eq26(om):
     from oracle import physics as PH
     ka, fc = om.om_apparent_permeability(2e-19, 3e-7, 1.73e-5, 17236893.0)

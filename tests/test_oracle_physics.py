@@ -57,3 +57,49 @@ def test_kozeny_carman_and_bruggeman():
     assert P.kozeny_carman(1.0, 0.5) == pytest.approx(1 / 180 * 0.125 / 0.25)
     assert P.bruggeman_alpha(0.4 ** 1.5, 1.0, 0.4) == pytest.approx(1.5)
     assert P.tortuosity(0.4, 1.0, 0.4 / 2.0) == pytest.approx(2.0)
+
+
+# ------------------------------------------------------------------ slip corrections (Sec. 4.4)
+def test_knudsen_corrections_agree_at_low_kn_and_part_above():
+    # Sec. 4.4.3 / Fig. 10: in the Darcy regime (Kn < 0.01) the Klinkenberg,
+    # Beskok-Karniadakis-Civan and cylinder (Eq. 28) corrections nearly
+    # coincide; as Kn grows Klinkenberg falls away and Eq. 28 stays with
+    # Beskok-Karniadakis-Civan
+    for Kn in (1e-4, 1e-3, 1e-2):
+        k, bk, cyl = P.klinkenberg_fc(Kn), P.beskok_civan_fc(Kn), P.cylinder_fc(Kn)
+        assert abs(k - 1) < 0.05 and abs(bk - 1) < 0.05 and abs(cyl - 1) < 0.1
+        assert bk == pytest.approx(k, rel=2 * Kn)
+    prev = 1.0
+    for Kn in (1.0, 3.0, 10.0):
+        k, bk, cyl = P.klinkenberg_fc(Kn), P.beskok_civan_fc(Kn), P.cylinder_fc(Kn)
+        assert abs(cyl - bk) < abs(k - bk) and abs(cyl - bk) < 0.25 * bk
+        assert bk / k > prev  # Klinkenberg falls further behind as Kn grows
+        prev = bk / k
+
+
+def test_civan_alpha_limits():
+    # Eq. 21: alpha -> 0 as Kn -> 0 (no rarefaction) and -> 1.358 as Kn -> inf
+    assert P.civan_alpha(1e-12) < 1e-4
+    assert P.civan_alpha(1e12) == pytest.approx(1.358, rel=1e-5)
+    # Eq. 20 with b = -1 reduces to 1 + 4 Kn / (1 + Kn) when alpha is dropped
+    assert P.beskok_civan_fc(1e-12) == pytest.approx(1.0, abs=1e-11)
+
+
+def test_table1_units_and_limits():
+    # Table 1 works in psi and mD: 1 mD, porosity 1, P = b_k psi gives f_c = 2
+    k = P.M2_PER_MILLIDARCY
+    for name, bk in (("heid", 11.419), ("jones_owens", 12.639), ("sampath_keighin", 13.85), ("florence", 32.766)):
+        assert P.table1_bk_psi(name, 1.0, 1.0) == pytest.approx(bk)
+        assert P.table1_fc(name, k, 1.0, bk * P.PA_PER_PSI) == pytest.approx(2.0)
+    # the porosity forms depend on k / eps only
+    assert P.table1_bk_psi("florence", 0.2, 0.2) == pytest.approx(32.766)
+    # tighter rock slips more
+    assert P.table1_fc("heid", 1e-21, 0.3, 1e7) > P.table1_fc("heid", 1e-18, 0.3, 1e7)
+
+
+def test_eq30_characteristic_pore_size_is_the_capillary_bundle_radius():
+    # a bundle of capillaries of radius r at porosity eps has k = eps r^2 / 8,
+    # i.e. r = sqrt(8 k / eps): Eq. 30's constant is that relation with k in
+    # mD and r in micrometres (the unit that fixes the reading of Eq. 30)
+    for k, eps in ((1e-21, 0.1), (1e-19, 0.3), (1e-17, 0.5)):
+        assert P.characteristic_pore_size(k, eps) == pytest.approx(math.sqrt(8 * k / eps), rel=1e-3)
