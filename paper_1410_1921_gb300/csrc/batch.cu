@@ -38,11 +38,12 @@ __global__ void rebase_columns(uint2* col, int64_t nw, uint32_t off) {
 }
 
 // ------------------------------------------------------------------ sweeps
-// A sweep launch covers one group of items.  The group's item geometry
-// travels in the kernel parameters (the constant bank, like the arguments
-// of the single-structure sweeps): per tile a thread reads one work entry
-// {item within the group, first node} and finds the rest there, so the
-// geometry costs no registers and no dependent global loads.
+// A sweep launch covers one group of items.  The whole group travels in the
+// kernel parameters (the constant bank, like the arguments of the
+// single-structure sweeps): its items' geometry and the first tile of each
+// item within the group, so a block finds its tile's item by a binary
+// search over at most kGroupItems constant-bank entries -- no work-list load
+// and no dependent global read before the node's own loads.
 constexpr int kGroupItems = 32;
 
 struct GroupItem {
@@ -55,17 +56,28 @@ struct GroupItem {
 
 struct GroupDesc {
   GroupItem it[kGroupItems];
+  int tile0[kGroupItems + 1];  // first tile of item k within the group; tile0[n] = tiles
+  int n;                       // items
 };
 
+// item of tile w of the group (tile0[k] <= w < tile0[k + 1]); warp-uniform
+__device__ __forceinline__ int group_item(const GroupDesc& g, int w) {
+  int lo = 0, hi = g.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.tile0[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <class T, bool ODD, int MINB>
-__global__ void __launch_bounds__(kTile, MINB)
-    flow_batch_sweep(FlowArgs<T> a, const __grid_constant__ GroupDesc g, const uint2* __restrict__ work,
-                     const int* __restrict__ nwork) {
-  const int nw = *nwork;
+__global__ void __launch_bounds__(kTile, MINB) flow_batch_sweep(FlowArgs<T> a, const __grid_constant__ GroupDesc g) {
+  const int nw = g.tile0[g.n];
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-    const uint2 t = work[w];
-    const GroupItem& it = g.it[t.x];
-    const uint32_t ln = t.y + threadIdx.x;
+    const int k = group_item(g, w);
+    const GroupItem& it = g.it[k];
+    const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
     if (ln >= it.nf) continue;
     if (ODD) {
       FlowArgs<T> b = a;
@@ -83,14 +95,12 @@ __global__ void __launch_bounds__(kTile, MINB)
 }
 
 template <class T, bool ODD, int MINB>
-__global__ void __launch_bounds__(kTile, MINB)
-    diff_batch_sweep(DiffArgs<T> a, const __grid_constant__ GroupDesc g, const uint2* __restrict__ work,
-                     const int* __restrict__ nwork) {
-  const int nw = *nwork;
+__global__ void __launch_bounds__(kTile, MINB) diff_batch_sweep(DiffArgs<T> a, const __grid_constant__ GroupDesc g) {
+  const int nw = g.tile0[g.n];
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-    const uint2 t = work[w];
-    const GroupItem& it = g.it[t.x];
-    const uint32_t ln = t.y + threadIdx.x;
+    const int k = group_item(g, w);
+    const GroupItem& it = g.it[k];
+    const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
     if (ln >= it.nf) continue;
     DiffArgs<T> b = a;
     b.nx = it.nx;
@@ -377,11 +387,8 @@ struct om_batch {
   int2* range_h = nullptr;    // pinned
   int* nwork_h = nullptr;     // pinned
   // the work list in groups of items whose populations fit in L2 together
-  // (at most kGroupItems each): group g's tiles are gwork[gstart[g] ..
-  // gstart[g] + gcnt[g]), entries {item within the group, first node}
-  uint2* gwork = nullptr;     // device, [max_tiles]
-  uint2* gwork_h = nullptr;   // pinned
-  int* gcnt = nullptr;        // device, [n]
+  // (at most kGroupItems each): group g holds the tiles work[gstart[g] ..
+  // gstart[g] + gcnt_h[g]); its sweeps take the descriptor gdesc[g]
   int* gcnt_h = nullptr;      // pinned, [n]
   std::vector<int> gstart;
   std::vector<GroupDesc> gdesc;
@@ -439,16 +446,15 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
       in_group = 0;
     }
     fill += bytes;
-    b->gdesc.back().it[in_group] =
-        GroupItem{bi.col, bi.coord, bi.off, bi.nf, bi.nx, bi.ny, bi.nz, bi.W, bi.slope};
+    GroupDesc& gd = b->gdesc.back();
+    gd.it[in_group] = GroupItem{bi.col, bi.coord, bi.off, bi.nf, bi.nx, bi.ny, bi.nz, bi.W, bi.slope};
+    gd.tile0[in_group] = w - b->gstart.back();
+    gd.n = in_group + 1;
     const int w0 = w;
-    for (uint32_t s = 0; s < bi.nf; s += kTile) {
-      b->work_h[w] = make_uint2((unsigned)k, s);
-      b->gwork_h[w] = make_uint2((unsigned)in_group, s);
-      ++w;
-    }
+    for (uint32_t s = 0; s < bi.nf; s += kTile) b->work_h[w++] = make_uint2((unsigned)k, s);
     ++in_group;
     b->gcnt_h[b->ngroups - 1] += w - w0;
+    gd.tile0[in_group] = w - b->gstart.back();
     b->range_h[a] = make_int2(w0, w);
   }
   *b->nwork_h = w;
@@ -459,10 +465,7 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
 
 om_status upload_work(om_batch* b, int nw, int nact, cudaStream_t s) {
   if (nw > 0) OM_CUDA(cudaMemcpyAsync(b->work, b->work_h, sizeof(uint2) * nw, cudaMemcpyHostToDevice, s));
-  if (nw > 0) OM_CUDA(cudaMemcpyAsync(b->gwork, b->gwork_h, sizeof(uint2) * nw, cudaMemcpyHostToDevice, s));
   if (nact > 0) OM_CUDA(cudaMemcpyAsync(b->range, b->range_h, sizeof(int2) * nact, cudaMemcpyHostToDevice, s));
-  if (b->ngroups > 0)
-    OM_CUDA(cudaMemcpyAsync(b->gcnt, b->gcnt_h, sizeof(int) * b->ngroups, cudaMemcpyHostToDevice, s));
   OM_CUDA(cudaMemcpyAsync(b->nwork, b->nwork_h, sizeof(int), cudaMemcpyHostToDevice, s));
   return OM_OK;
 }
@@ -500,17 +503,15 @@ DiffArgs<T> bdiff_args(const om_batch* b) {
 template <class T, int MINB>
 void launch_flow(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
   FlowArgs<T> a = bflow_args<T>(b);
-  const uint2* work = b->gwork + b->gstart[g];
-  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
-  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
+  if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
+  else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
 }
 
 template <class T, int MINB>
 void launch_diff(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
   DiffArgs<T> a = bdiff_args<T>(b);
-  const uint2* work = b->gwork + b->gstart[g];
-  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
-  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g], work, b->gcnt + g);
+  if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
+  else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
 }
 
 // variant 0: no residency hint; variant 1: capped for 4 (flow; 3 in FP64) / 8
@@ -801,8 +802,6 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
   cudaFree(b->items);
   cudaFree(b->work);
   cudaFree(b->nwork);
-  cudaFree(b->gcnt);
-  cudaFree(b->gwork);
   cudaFree(b->range);
   cudaFree(b->partials);
   cudaFree(b->obs);
@@ -810,7 +809,6 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
   if (b->range_h) cudaFreeHost(b->range_h);
   if (b->nwork_h) cudaFreeHost(b->nwork_h);
   if (b->gcnt_h) cudaFreeHost(b->gcnt_h);
-  if (b->gwork_h) cudaFreeHost(b->gwork_h);
   if (b->obs_h) cudaFreeHost(b->obs_h);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
@@ -890,8 +888,6 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if ((st = dalloc((void**)&b->items, sizeof(BatchItem) * n)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->work, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->nwork, sizeof(int))) != OM_OK) return bail(st);
-  if ((st = dalloc((void**)&b->gcnt, sizeof(int) * n)) != OM_OK) return bail(st);
-  if ((st = dalloc((void**)&b->gwork, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->range, sizeof(int2) * n)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->partials, sizeof(double) * 5 * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = dalloc((void**)&b->obs, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
@@ -899,7 +895,6 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if ((st = halloc((void**)&b->range_h, sizeof(int2) * n)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->nwork_h, sizeof(int))) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->gcnt_h, sizeof(int) * n)) != OM_OK) return bail(st);
-  if ((st = halloc((void**)&b->gwork_h, sizeof(uint2) * b->max_tiles)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->obs_h, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
   if (cudaMemcpyAsync(b->items, b->items_h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return bail(fail(OM_ECUDA, "om_batch_create: copy of the item table failed"));
