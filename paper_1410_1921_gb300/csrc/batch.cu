@@ -116,6 +116,23 @@ __global__ void __launch_bounds__(kTile, MINB) diff_batch_sweep(DiffArgs<T> a, c
   }
 }
 
+// An item large enough to fill the GPU alone (a "solo" group) runs the
+// single-structure sweep body: its geometry is in the scalar arguments, its
+// nodes are [off, off + nf) of the arena, one thread per node.
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(kTile, MINB) flow_solo_sweep(FlowArgs<T> a, uint32_t off) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  flow_node<T, ODD>(a, off + ln, ln);
+}
+
+template <class T, bool ODD, int MINB>
+__global__ void __launch_bounds__(kTile, MINB) diff_solo_sweep(DiffArgs<T> a, uint32_t off) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  diff_node<T, ODD>(a, off + ln, ln);
+}
+
 // ------------------------------------------------------------------ observables
 // partials[w][NV] for every tile w of the work list
 template <class T, bool ODD>
@@ -392,6 +409,7 @@ struct om_batch {
   int* gcnt_h = nullptr;      // pinned, [n]
   std::vector<int> gstart;
   std::vector<GroupDesc> gdesc;
+  std::vector<int> gsolo;     // item of a solo group (one large item), else -1
   int ngroups = 0;
   int layout = 0;             // bumped whenever the work list is rebuilt
   int layout_model = -1;      // the model whose footprint sized the groups
@@ -422,9 +440,14 @@ double node_bytes(const om_batch* b, int model) {
   return per;
 }
 
+// Items with at least this many nodes fill the GPU alone: they form a group
+// of their own and run the single-structure sweep body.
+constexpr uint32_t kSoloNodes = 1u << 19;
+
 // Work list of all tiles of the items flagged active, ordered by group
-// (consecutive items packed while their footprint fits kGroupBytes);
-// ranges per active item; the layout counter moves on.
+// (consecutive small items packed while their footprint fits kGroupBytes;
+// every large item alone); ranges per active item; the layout counter
+// moves on.
 int build_work(om_batch* b, const std::vector<int>& active, int model) {
   const double per = node_bytes(b, model);
   int w = 0;
@@ -432,15 +455,19 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
   b->ngroups = 0;
   double fill = 0.0;
   b->gdesc.clear();
+  b->gsolo.clear();
   int in_group = 0;
   for (size_t a = 0; a < active.size(); ++a) {
     const int k = active[a];
     const BatchItem& bi = b->items_h[k];
     const double bytes = per * (double)bi.nf;
-    if (b->ngroups == 0 || in_group == kGroupItems || (fill > 0.0 && fill + bytes > kGroupBytes)) {
+    const bool solo = bi.nf >= kSoloNodes;
+    if (b->ngroups == 0 || solo || b->gsolo.back() >= 0 || in_group == kGroupItems ||
+        (fill > 0.0 && fill + bytes > kGroupBytes)) {
       b->gstart.push_back(w);
       b->gcnt_h[b->ngroups] = 0;
       b->gdesc.push_back(GroupDesc{});
+      b->gsolo.push_back(solo ? k : -1);
       ++b->ngroups;
       fill = 0.0;
       in_group = 0;
@@ -503,6 +530,21 @@ DiffArgs<T> bdiff_args(const om_batch* b) {
 template <class T, int MINB>
 void launch_flow(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
   FlowArgs<T> a = bflow_args<T>(b);
+  const int solo = b->gsolo[g];
+  if (solo >= 0) {
+    const BatchItem& it = b->items_h[solo];
+    a.nf = it.nf;
+    a.col = it.col;
+    a.coord = it.coord;
+    a.nx = it.nx;
+    a.ny = it.ny;
+    a.nz = it.nz;
+    a.W = it.W;
+    const unsigned nb = (it.nf + kTile - 1) / kTile;
+    if (odd) flow_solo_sweep<T, true, MINB><<<nb, kTile, 0, s>>>(a, it.off);
+    else flow_solo_sweep<T, false, MINB><<<nb, kTile, 0, s>>>(a, it.off);
+    return;
+  }
   if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
   else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
 }
@@ -510,6 +552,22 @@ void launch_flow(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
 template <class T, int MINB>
 void launch_diff(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
   DiffArgs<T> a = bdiff_args<T>(b);
+  const int solo = b->gsolo[g];
+  if (solo >= 0) {
+    const BatchItem& it = b->items_h[solo];
+    a.nf = it.nf;
+    a.col = it.col;
+    a.coord = it.coord;
+    a.nx = it.nx;
+    a.ny = it.ny;
+    a.nz = it.nz;
+    a.W = it.W;
+    a.s = (typename Stg<T>::C)it.slope;
+    const unsigned nb = (it.nf + kTile - 1) / kTile;
+    if (odd) diff_solo_sweep<T, true, MINB><<<nb, kTile, 0, s>>>(a, it.off);
+    else diff_solo_sweep<T, false, MINB><<<nb, kTile, 0, s>>>(a, it.off);
+    return;
+  }
   if (odd) diff_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
   else diff_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
 }
