@@ -71,6 +71,22 @@ def batch_structures(n=150, seed=7):
     return out
 
 
+def campaign_structures(means=(30.0, 45.0, 60.0), porosities=None, xis=(0.1, 0.2, 0.3), seeds=5, edge=200,
+                        dx_nm=1.5):
+    """The paper's reconstruction campaign (Sec. 2): pore diameters uniform in
+    <d> +- 15 nm, <d> in {30, 45, 60} nm, porosity 0.10 .. 0.55 in steps of
+    0.05, overlap tolerance in {0.1, 0.2, 0.3}, five structures per
+    configuration, 200^3 voxels of 1.5 nm.  Any sub-grid (and a smaller box
+    for tests) can be asked for."""
+    porosities = porosities if porosities is not None else tuple(round(0.10 + 0.05 * k, 2) for k in range(10))
+    out = []
+    for i, (mean, eps, xi) in enumerate((m, e, x) for m in means for e in porosities for x in xis):
+        for s in range(seeds):
+            out.append(Recon(100_000 + 100 * i + s, (edge, edge, edge), dx_nm, mean, 15.0, mean - 15.0,
+                             mean + 15.0, eps, xi, dist=1))
+    return out
+
+
 # ------------------------------------------------------------------ geometric masks
 def slit(nx, H, nz=1):
     """Two plane walls normal to y: pore rows y = 1..H, solid rows y = 0, H+1."""
