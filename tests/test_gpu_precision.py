@@ -1,0 +1,64 @@
+"""Stated error bounds of the storage formats (row a7 "precision"): the
+converged k and D_eff with FP32, FP16 and BF16 population storage against
+the FP64 solve of the same structure (which the LB parity tests tie to the
+oracle to ~1e-9).
+
+Bounds (relative): FP32 1e-5 for both models (the FP32-vs-FP64 target);
+16-bit diffusion (rebased deviations) 2e-3 (FP16) and 1e-2 (BF16); 16-bit
+flow (deviations from the weights, FP16 scaled by 2^10) 1e-2 (FP16) and
+2e-2 (BF16).  16-bit runs may end on the step cap: their rounding noise
+floors the relative-change test; the field they reach is compared.  Run with
+-s to print the measured errors."""
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {"OM_F32": (1e-5, 1e-5), "OM_F16DEV": (1e-2, 2e-3), "OM_BF16DEV": (2e-2, 1e-2)}  # (flow, diffusion)
+CASES = [S.small_structure(), S.sweep_structure(0.35, edge=64)]
+
+
+def _setup(om, cfg):
+    from paper_1410_1921_gb300 import warmstart as W
+    return W.structure(cfg)
+
+
+@pytest.mark.timeout(900)
+@pytest.mark.parametrize("cfg", CASES, ids=["48cube_2nm", "64cube_1nm"])
+def test_storage_formats_within_stated_bounds(om, cfg):
+    dom, mask, tr, d = _setup(om, cfg)
+    ns = om.NodeSet(tr, dom)
+
+    def flow(prec, tol, K, cap):
+        fl = om.Flow(ns, om.flow_params(precision=prec, conv_tol=tol, check_every=K, max_steps=cap))
+        st, kl, info = fl.solve()
+        fl.close()
+        return st, kl
+
+    def diff(prec, tol, K, cap):
+        df = om.Diffusion(ns, d, om.diff_params(precision=prec, conv_tol=tol, check_every=K, max_steps=cap))
+        st, Dl, info = df.solve()
+        df.close()
+        return st, Dl
+
+    st, k64 = flow(om.OM_F64, 1e-10, 100, 2_000_000)
+    assert st in (om.OM_OK, om.OM_ENOPERC)
+    has_flow = st == om.OM_OK  # ENOPERC: no link across the periodic x boundary, k = 0 in every format
+    st, D64 = diff(om.OM_F64, 1e-10, 100, 4_000_000)
+    assert st == om.OM_OK
+    for name, (bk, bd) in BOUNDS.items():
+        prec = getattr(om, name)
+        if name == "OM_F32":
+            stk, k = flow(prec, 1e-7, 2000, 2_000_000)
+            std, D = diff(prec, 1e-7, 2000, 4_000_000)
+            assert stk == (om.OM_OK if has_flow else om.OM_ENOPERC) and std == om.OM_OK
+        else:
+            stk, k = flow(prec, 1e-7, 2000, 400_000)
+            std, D = diff(prec, 1e-7, 2000, 1_000_000)
+            assert stk in (om.OM_OK, om.OM_ENOTCONVERGED, om.OM_ENOPERC) and std in (om.OM_OK, om.OM_ENOTCONVERGED)
+        ek = abs(k / k64 - 1) if has_flow else abs(k)
+        eD = abs(D / D64 - 1)
+        print(f"{cfg.shape} {name}: k {ek:.2e} (status {stk}), D_eff {eD:.2e} (status {std})")
+        assert ek <= bk and eD <= bd, (name, ek, eD)
+    ns.close()
