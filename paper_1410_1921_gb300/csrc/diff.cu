@@ -19,7 +19,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "diff_core.cuh"
+#include "solvers.cuh"
 
 namespace om {
 
@@ -207,49 +207,9 @@ __global__ void diff_omega(const int64_t* vox, const float* d_nm, int64_t nf, do
 
 using namespace om;
 
-struct om_diff {
-  const om_nodeset* ns = nullptr;
-  om_diff_params p{};
-  void* g = nullptr;
-  void* omega = nullptr;
-  float* cr = nullptr;  // per-node reference concentration (16-bit storage)
-  int q = 7;            // lattice: 7 (D3Q7) or 19 (D3Q19)
-  double* prev = nullptr;
-  double* partials = nullptr;
-  double* obs_dev = nullptr;
-  double* obs_host = nullptr;
-  int64_t t = 0;
-  double up = 1.0;      // storage scale (stored = deviation * up)
-  int var[2] = {0, 0};  // launch variant of the even and odd sweeps
-  // a captured window of graph_k steps starting at an even time (replayed by *_step)
-  cudaGraphExec_t exec = nullptr;
-  int graph_k = 0;
-  cudaStream_t cap = nullptr;
-};
 
 namespace {
 
-template <class T, class L>
-DiffArgs<T, L> diff_args(const om_diff* df) {
-  DiffArgs<T, L> a;
-  const om_nodeset* ns = df->ns;
-  for (int i = 0; i < L::Q; ++i) a.q[i] = (T*)df->g + (size_t)i * ns->pitch;
-  a.nf = (uint32_t)ns->nf;
-  a.col = ns->col;
-  a.coord = ns->coord;
-  a.omega = (const typename Stg<T>::C*)df->omega;
-  a.nx = ns->dom.nx;
-  a.ny = ns->dom.ny;
-  a.nz = ns->dom.nz;
-  a.W = ns->W;
-  a.s = (typename Stg<T>::C)((df->p.c_out - df->p.c_in) / (double)ns->dom.nx);
-  a.up = (typename Stg<T>::C)df->up;
-  a.down = (typename Stg<T>::C)(1.0 / df->up);
-  a.cin = df->p.c_in;
-  a.cout = df->p.c_out;
-  a.cr = df->cr;
-  return a;
-}
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -459,11 +419,22 @@ om_status diff_omega_t(om_diff* df, const float* d_nm, cudaStream_t s) {
 
 size_t storage_bytes(int prec) { return prec == OM_F64 ? 8 : (prec == OM_F32 ? 4 : 2); }
 
+template <class T, class L>
+om_status diff_rebase_t(om_diff* df, cudaStream_t s) {
+  if (!kRebased<T> || df->ns->nf == 0) return OM_OK;
+  DiffArgs<T, L> a = diff_args<T, L>(df);
+  diff_rebase<T, L><<<blocks_for(a.nf), 256, 0, s>>>(a);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
 om_status diff_observe_any(om_diff* df, double* out, cudaStream_t s) {
   OM_DIFF_DISPATCH(df, diff_observe_t, df, out, s);
 }
 
 }  // namespace
+
+om_status om::diff_rebase_any(om_diff* df, cudaStream_t s) { OM_DIFF_DISPATCH(df, diff_rebase_t, df, s); }
 
 extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
                                     const om_diff_params* p, void* stream, om_diff** out) {

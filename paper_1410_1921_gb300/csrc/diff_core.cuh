@@ -126,20 +126,15 @@ __device__ __forceinline__ void diff_load(const DiffArgs<T, L>& a, uint32_t n, c
   diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
 }
 
-// One fused collide-stream update of node n (global slot index) with packed
-// coordinates c (read on odd steps only); the AA read/write pattern of
-// flow_node_at with the anti-bounce-back inlet/outlet and the reference shift.
+// One fused collide-stream update of node n (global slot index) at x whose
+// neighbours are nb (used on odd steps only); the AA read/write pattern of
+// flow_node_nb with the anti-bounce-back inlet/outlet and the reference shift.
 template <class T, class L, bool ODD>
-__device__ __forceinline__ void diff_node_at(const DiffArgs<T, L>& a, uint32_t n, uint32_t c) {
+__device__ __forceinline__ void diff_node_nb(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q]) {
   using S = Stg<T>;
   using C = typename S::C;
-  uint32_t nb[L::Q];
-  int x = 0;
   DiffRefs<T, L> r{};
-  if (ODD) {
-    diff_neighbours(a, c, nb, x);
-    diff_refs(a, n, nb, r);
-  }
+  if (ODD) diff_refs(a, n, nb, r);
   C g[L::Q];
   diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
   const C om = a.omega[n];
@@ -179,6 +174,15 @@ __device__ __forceinline__ void diff_node_at(const DiffArgs<T, L>& a, uint32_t n
       S::st(p, v, a.up);
     }
   }
+}
+
+// diff_node_nb after the neighbour lookup of the node's coordinates c
+template <class T, class L, bool ODD>
+__device__ __forceinline__ void diff_node_at(const DiffArgs<T, L>& a, uint32_t n, uint32_t c) {
+  uint32_t nb[L::Q];
+  int x = 0;
+  if (ODD) diff_neighbours(a, c, nb, x);
+  diff_node_nb<T, L, ODD>(a, n, x, nb);
 }
 
 // diff_node_at for node n whose coordinates are coord[ln]

@@ -36,7 +36,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "flow_core.cuh"
+#include "solvers.cuh"
 
 namespace om {
 
@@ -260,56 +260,9 @@ __global__ void d3q19_rest(FlowArgs<T> a) {
 
 using namespace om;
 
-struct om_flow {
-  const om_nodeset* ns = nullptr;
-  om_flow_params p{};
-  void* f = nullptr;
-  double* prev = nullptr;
-  double* partials = nullptr;
-  double* obs_dev = nullptr;
-  double* obs_host = nullptr;  // pinned
-  int64_t t = 0;
-  double up = 1.0;  // storage scale of reduced-precision formats (stored = deviation * up)
-  int var[2] = {0, 0};  // launch variant of the even and odd sweeps
-  // pressure drive: boundary nodes [0, n_in) and [nf - n_out, nf), their
-  // extrapolated populations (storage arithmetic type, [19][n_in + n_out])
-  uint32_t n_in = 0, n_out = 0;
-  void* bc = nullptr;
-  // a captured window of graph_k steps starting at an even time (replayed by *_step)
-  cudaGraphExec_t exec = nullptr;
-  int graph_k = 0;
-  cudaStream_t cap = nullptr;
-};
 
 namespace {
 
-template <class T>
-FlowArgs<T> flow_args(const om_flow* fl) {
-  FlowArgs<T> a;
-  const om_nodeset* ns = fl->ns;
-  for (int i = 0; i < 19; ++i) a.s[i] = (T*)fl->f + (size_t)i * ns->pitch;
-  a.nf = (uint32_t)ns->nf;
-  a.col = ns->col;
-  a.coord = ns->coord;
-  a.nx = ns->dom.nx;
-  a.ny = ns->dom.ny;
-  a.nz = ns->dom.nz;
-  a.W = ns->W;
-  const double tau = fl->p.tau;
-  a.wp = (typename Stg<T>::C)(1.0 / tau);
-  a.wm = (typename Stg<T>::C)(8.0 * (2.0 * tau - 1.0) / (8.0 * tau - 1.0));
-  a.g = (typename Stg<T>::C)fl->p.body_force;
-  a.up = (typename Stg<T>::C)fl->up;
-  a.down = (typename Stg<T>::C)(1.0 / fl->up);
-  if (fl->p.drive == OM_DRIVE_PRESSURE) {
-    a.g = 0;
-    a.px = 0;
-    a.n_in = fl->n_in;
-    a.n_out = fl->n_out;
-    a.bc = (const typename Stg<T>::C*)fl->bc;
-  }
-  return a;
-}
 
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }

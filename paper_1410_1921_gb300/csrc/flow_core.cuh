@@ -91,18 +91,16 @@ __device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
 }
 
 
-// One fused collide-stream update of node n (global slot index) with packed
-// coordinates c (read on odd steps only).  Even steps: read and write the
+// One fused collide-stream update of node n (global slot index) whose
+// neighbours are nb (used on odd steps only).  Even steps: read and write the
 // node's own slots (post-collision f*_i to slot opposite(i)).  Odd steps:
 // read slot opposite(i) of x - e_i, write slot i of x + e_i; a missing
 // neighbour is halfway bounce-back (own slot i read, own slot opposite(i)
 // written).
 template <class T, bool ODD>
-__device__ __forceinline__ void flow_node_at(const FlowArgs<T>& a, uint32_t n, uint32_t c) {
+__device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19]) {
   using S = Stg<T>;
   using C = typename S::C;
-  uint32_t nb[19];
-  if (ODD) flow_neighbours(a, c, nb);
   C f[19];
   flow_load<T, ODD>(a, n, nb, f);
   if (a.n_in + a.n_out) {  // pressure drive: boundary nodes take the extrapolated populations
@@ -125,6 +123,14 @@ __device__ __forceinline__ void flow_node_at(const FlowArgs<T>& a, uint32_t n, u
     }
     S::st(p, f[i], a.up);
   }
+}
+
+// flow_node_nb after the neighbour lookup of the node's coordinates c
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_node_at(const FlowArgs<T>& a, uint32_t n, uint32_t c) {
+  uint32_t nb[19];
+  if (ODD) flow_neighbours(a, c, nb);
+  flow_node_nb<T, ODD>(a, n, nb);
 }
 
 // flow_node_at for node n whose coordinates are coord[ln]

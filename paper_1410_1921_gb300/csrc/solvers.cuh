@@ -1,0 +1,106 @@
+// solvers.cuh -- the state of the single-structure solver objects of
+// include/om.h (om_flow, om_diff) and the kernel arguments built from it,
+// shared by the translation units that launch their sweeps.
+#pragma once
+
+#include "diff_core.cuh"
+#include "flow_core.cuh"
+
+struct om_flow {
+  const om_nodeset* ns = nullptr;
+  om_flow_params p{};
+  void* f = nullptr;
+  double* prev = nullptr;
+  double* partials = nullptr;
+  double* obs_dev = nullptr;
+  double* obs_host = nullptr;  // pinned
+  int64_t t = 0;
+  double up = 1.0;  // storage scale of reduced-precision formats (stored = deviation * up)
+  int var[2] = {0, 0};  // launch variant of the even and odd sweeps
+  // pressure drive: boundary nodes [0, n_in) and [nf - n_out, nf), their
+  // extrapolated populations (storage arithmetic type, [19][n_in + n_out])
+  uint32_t n_in = 0, n_out = 0;
+  void* bc = nullptr;
+  // a captured window of graph_k steps starting at an even time (replayed by *_step)
+  cudaGraphExec_t exec = nullptr;
+  int graph_k = 0;
+  cudaStream_t cap = nullptr;
+};
+
+struct om_diff {
+  const om_nodeset* ns = nullptr;
+  om_diff_params p{};
+  void* g = nullptr;
+  void* omega = nullptr;
+  float* cr = nullptr;  // per-node reference concentration (16-bit storage)
+  int q = 7;            // lattice: 7 (D3Q7) or 19 (D3Q19)
+  double* prev = nullptr;
+  double* partials = nullptr;
+  double* obs_dev = nullptr;
+  double* obs_host = nullptr;
+  int64_t t = 0;
+  double up = 1.0;      // storage scale (stored = deviation * up)
+  int var[2] = {0, 0};  // launch variant of the even and odd sweeps
+  // a captured window of graph_k steps starting at an even time (replayed by *_step)
+  cudaGraphExec_t exec = nullptr;
+  int graph_k = 0;
+  cudaStream_t cap = nullptr;
+};
+
+namespace om {
+
+template <class T>
+inline FlowArgs<T> flow_args(const om_flow* fl) {
+  FlowArgs<T> a;
+  const om_nodeset* ns = fl->ns;
+  for (int i = 0; i < 19; ++i) a.s[i] = (T*)fl->f + (size_t)i * ns->pitch;
+  a.nf = (uint32_t)ns->nf;
+  a.col = ns->col;
+  a.coord = ns->coord;
+  a.nx = ns->dom.nx;
+  a.ny = ns->dom.ny;
+  a.nz = ns->dom.nz;
+  a.W = ns->W;
+  const double tau = fl->p.tau;
+  a.wp = (typename Stg<T>::C)(1.0 / tau);
+  a.wm = (typename Stg<T>::C)(8.0 * (2.0 * tau - 1.0) / (8.0 * tau - 1.0));
+  a.g = (typename Stg<T>::C)fl->p.body_force;
+  a.up = (typename Stg<T>::C)fl->up;
+  a.down = (typename Stg<T>::C)(1.0 / fl->up);
+  if (fl->p.drive == OM_DRIVE_PRESSURE) {
+    a.g = 0;
+    a.px = 0;
+    a.n_in = fl->n_in;
+    a.n_out = fl->n_out;
+    a.bc = (const typename Stg<T>::C*)fl->bc;
+  }
+  return a;
+}
+
+template <class T, class L>
+inline DiffArgs<T, L> diff_args(const om_diff* df) {
+  DiffArgs<T, L> a;
+  const om_nodeset* ns = df->ns;
+  for (int i = 0; i < L::Q; ++i) a.q[i] = (T*)df->g + (size_t)i * ns->pitch;
+  a.nf = (uint32_t)ns->nf;
+  a.col = ns->col;
+  a.coord = ns->coord;
+  a.omega = (const typename Stg<T>::C*)df->omega;
+  a.nx = ns->dom.nx;
+  a.ny = ns->dom.ny;
+  a.nz = ns->dom.nz;
+  a.W = ns->W;
+  a.s = (typename Stg<T>::C)((df->p.c_out - df->p.c_in) / (double)ns->dom.nx);
+  a.up = (typename Stg<T>::C)df->up;
+  a.down = (typename Stg<T>::C)(1.0 / df->up);
+  a.cin = df->p.c_in;
+  a.cout = df->p.c_out;
+  a.cr = df->cr;
+  return a;
+}
+
+// move the rebased diffusion's per-node reference to the current
+// concentration (diff.cu); OM_OK without work for FP64 storage
+om_status diff_rebase_any(om_diff* df, cudaStream_t s);
+
+}  // namespace om

@@ -3,12 +3,17 @@ converged k and D_eff with FP32, FP16 and BF16 population storage against
 the FP64 solve of the same structure (which the LB parity tests tie to the
 oracle to ~1e-9).
 
-Bounds (relative): FP32 1e-5 for both models (the FP32-vs-FP64 target);
-16-bit diffusion (rebased deviations) 2e-3 (FP16) and 1e-2 (BF16); 16-bit
-flow (deviations from the weights, FP16 scaled by 2^10) 1e-2 (FP16) and
-2e-2 (BF16).  16-bit runs may end on the step cap: their rounding noise
-floors the relative-change test; the field they reach is compared.  Run with
--s to print the measured errors."""
+Bounds (relative): FP32 1e-5 for both models (the FP32-vs-FP64 target),
+against the FP64 solve under the same stopping rule (relative change below
+1e-6 over 100 steps), so that what is compared is the storage rounding
+alone and not the distance of the stopping point from the steady state,
+which both formats share; FP32 rounding noise keeps much tighter tests from
+being met reliably.  16-bit diffusion (rebased deviations) 2e-3 (FP16) and
+1e-2 (BF16); 16-bit flow (deviations from the weights, FP16 scaled by 2^10)
+1e-2 (FP16) and 2e-2 (BF16), against the FP64 solve at 1e-10: 16-bit runs
+may end on the step cap, their rounding noise flooring the relative-change
+test, and the field they reach is compared.  Run with -s to print the
+measured errors."""
 import pytest
 
 import synthetic as S
@@ -50,13 +55,19 @@ def test_storage_formats_within_stated_bounds(om, cfg):
     for name, (bk, bd) in BOUNDS.items():
         prec = getattr(om, name)
         if name == "OM_F32":
-            stk, k = flow(prec, 1e-7, 2000, 2_000_000)
-            std, D = diff(prec, 1e-7, 2000, 4_000_000)
+            stk, k = flow(prec, 1e-6, 100, 2_000_000)
+            std, D = diff(prec, 1e-6, 100, 4_000_000)
             assert stk == (om.OM_OK if has_flow else om.OM_ENOPERC) and std == om.OM_OK
-        else:
-            stk, k = flow(prec, 1e-7, 2000, 400_000)
-            std, D = diff(prec, 1e-7, 2000, 1_000_000)
-            assert stk in (om.OM_OK, om.OM_ENOTCONVERGED, om.OM_ENOPERC) and std in (om.OM_OK, om.OM_ENOTCONVERGED)
+            st, k64s = flow(om.OM_F64, 1e-6, 100, 2_000_000)
+            st, D64s = diff(om.OM_F64, 1e-6, 100, 4_000_000)
+            ek = abs(k / k64s - 1) if has_flow else abs(k)
+            eD = abs(D / D64s - 1)
+            print(f"{cfg.shape} {name} (same test as FP64): k {ek:.2e} (status {stk}), D_eff {eD:.2e} (status {std})")
+            assert ek <= bk and eD <= bd, (name, ek, eD)
+            continue
+        stk, k = flow(prec, 1e-7, 2000, 400_000)
+        std, D = diff(prec, 1e-7, 2000, 1_000_000)
+        assert stk in (om.OM_OK, om.OM_ENOTCONVERGED, om.OM_ENOPERC) and std in (om.OM_OK, om.OM_ENOTCONVERGED)
         ek = abs(k / k64 - 1) if has_flow else abs(k)
         eD = abs(D / D64 - 1)
         print(f"{cfg.shape} {name}: k {ek:.2e} (status {stk}), D_eff {eD:.2e} (status {std})")
