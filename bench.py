@@ -497,6 +497,32 @@ def _window_mlups(step, nodes, steps, reps):
     return nodes * steps * reps / (ms * 1e-3) / 1e6, ms / reps
 
 
+def _parity_us(model, nodes, bytes_per_node, peak, reps=20):
+    """Mean CUDA-event time of single even and odd sweeps of `model` (one
+    step() call each, outside any captured window) and the fraction of the
+    measured HBM bandwidth that the algorithmic bytes make of it."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    if model.time & 1:
+        model.step(1)
+    model.step(2)
+    torch.cuda.synchronize()
+    te = to = 0.0
+    for _ in range(reps):
+        ev[0].record()
+        model.step(1)
+        ev[1].record()
+        model.step(1)
+        ev[2].record()
+        torch.cuda.synchronize()
+        te += ev[0].elapsed_time(ev[1])
+        to += ev[1].elapsed_time(ev[2])
+    out = {}
+    for k, ms in (("even", te / reps), ("odd", to / reps)):
+        out[k] = {"us": ms * 1e3, "frac_hbm": nodes * bytes_per_node / (ms * 1e-3) / 1e9 / peak}
+    return out
+
+
 def run_batch(a):
     """The 150-structure set (edges {64..200}^3, porosity U[0.10, 0.50], <d>
     U[10, 60] nm, tolerance U[0, 0.8], 1.5 nm voxels) advanced together: one
@@ -567,8 +593,9 @@ def run_batch(a):
 def run_precision(a):
     """A 512^3 structure (porosity 0.30, <d> 40 nm, sd 10, tolerance 0.5, 1 nm
     voxels): device MLUPS of both sweeps with FP32, FP16 and BF16 population
-    storage over 100-step windows (the errors of each format against FP64 are
-    measured on smaller structures by the precision study)."""
+    storage over 100-step windows, and the time of single even and odd sweeps
+    against the HBM roofline of their algorithmic bytes (the errors of each
+    format against FP64 are the subject of tests/test_gpu_precision.py)."""
     import torch
 
     from paper_1410_1921_gb300 import build as B
@@ -580,14 +607,18 @@ def run_precision(a):
     dom, tr, d = _device_structure(P, W, S.large_structure())
     ns = P.NodeSet(tr, dom)
     out = {}
+    peak, _ = _peak_hbm()
     for name, prec in (("f32", P.OM_F32), ("f16", P.OM_F16DEV), ("bf16", P.OM_BF16DEV)):
+        bf, bd = (BYTES_FLOW_F32, BYTES_DIFF_F32) if prec == P.OM_F32 else (BYTES_FLOW_F32 // 2, 32)
         fl = P.Flow(ns, P.flow_params(precision=prec, check_every=WINDOW))
         fm, fms = _window_mlups(lambda: fl.step(WINDOW), ns.n_nodes, WINDOW, 3)
+        fpar = _parity_us(fl, ns.n_nodes, bf, peak)
         fl.close()
         df = P.Diffusion(ns, d, P.diff_params(precision=prec, check_every=WINDOW))
         dm, dms = _window_mlups(lambda: df.step(WINDOW), ns.n_nodes, WINDOW, 3)
+        dpar = _parity_us(df, ns.n_nodes, bd, peak)
         df.close()
-        out[name] = {"flow_mlups": fm, "diffusion_mlups": dm}
+        out[name] = {"flow_mlups": fm, "diffusion_mlups": dm, "flow_sweeps": fpar, "diffusion_sweeps": dpar}
     line = {"metric": "fluid MLUPS by population storage, 512^3", "value": out["f16"]["flow_mlups"], "unit": "MLUPS",
             "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "nodes": ns.n_nodes, "by_storage": out,
             "gain_over_f32": {k: {"flow": v["flow_mlups"] / out["f32"]["flow_mlups"],

@@ -4,11 +4,13 @@ the FP64 solve of the same structure (which the LB parity tests tie to the
 oracle to ~1e-9).
 
 Bounds (relative): FP32 1e-5 for both models (the FP32-vs-FP64 target),
-against the FP64 solve under the same stopping rule (relative change below
-1e-6 over 100 steps), so that what is compared is the storage rounding
-alone and not the distance of the stopping point from the steady state,
-which both formats share; FP32 rounding noise keeps much tighter tests from
-being met reliably.  16-bit diffusion (rebased deviations) 2e-3 (FP16) and
+against the FP64 solve after the same number of steps: the FP64 solve runs
+to the usual test (relative change below 1e-6 over 100 steps) and the FP32
+one is stopped at that step, so that what is compared is the storage
+rounding alone and not where each run's stopping test happens to fire (near
+the threshold the two can stop some windows apart, and the result still
+moves by up to ~1e-6 per window there).  The FP32 solve must also meet the
+same test on its own.  16-bit diffusion (rebased deviations) 2e-3 (FP16) and
 1e-2 (BF16); 16-bit flow (deviations from the weights, FP16 scaled by 2^10)
 1e-2 (FP16) and 2e-2 (BF16), against the FP64 solve at 1e-10: 16-bit runs
 may end on the step cap, their rounding noise flooring the relative-change
@@ -35,16 +37,20 @@ def test_storage_formats_within_stated_bounds(om, cfg):
     dom, mask, tr, d = _setup(om, cfg)
     ns = om.NodeSet(tr, dom)
 
-    def flow(prec, tol, K, cap):
+    def flow(prec, tol, K, cap, steps=None):
         fl = om.Flow(ns, om.flow_params(precision=prec, conv_tol=tol, check_every=K, max_steps=cap))
         st, kl, info = fl.solve()
         fl.close()
+        if steps is not None:
+            steps.append(info.steps)
         return st, kl
 
-    def diff(prec, tol, K, cap):
+    def diff(prec, tol, K, cap, steps=None):
         df = om.Diffusion(ns, d, om.diff_params(precision=prec, conv_tol=tol, check_every=K, max_steps=cap))
         st, Dl, info = df.solve()
         df.close()
+        if steps is not None:
+            steps.append(info.steps)
         return st, Dl
 
     st, k64 = flow(om.OM_F64, 1e-10, 100, 2_000_000)
@@ -55,14 +61,17 @@ def test_storage_formats_within_stated_bounds(om, cfg):
     for name, (bk, bd) in BOUNDS.items():
         prec = getattr(om, name)
         if name == "OM_F32":
-            stk, k = flow(prec, 1e-6, 100, 2_000_000)
-            std, D = diff(prec, 1e-6, 100, 4_000_000)
+            stk, _ = flow(prec, 1e-6, 100, 2_000_000)
+            std, _ = diff(prec, 1e-6, 100, 4_000_000)
             assert stk == (om.OM_OK if has_flow else om.OM_ENOPERC) and std == om.OM_OK
-            st, k64s = flow(om.OM_F64, 1e-6, 100, 2_000_000)
-            st, D64s = diff(om.OM_F64, 1e-6, 100, 4_000_000)
+            sf, sd = [], []
+            st, k64s = flow(om.OM_F64, 1e-6, 100, 2_000_000, sf)
+            st, D64s = diff(om.OM_F64, 1e-6, 100, 4_000_000, sd)
+            stk, k = flow(prec, 0.0, 100, max(sf[0], 100))  # stopped at the FP64 run's step
+            std, D = diff(prec, 0.0, 100, sd[0])
             ek = abs(k / k64s - 1) if has_flow else abs(k)
             eD = abs(D / D64s - 1)
-            print(f"{cfg.shape} {name} (same test as FP64): k {ek:.2e} (status {stk}), D_eff {eD:.2e} (status {std})")
+            print(f"{cfg.shape} {name} (at FP64's {sf[0]} / {sd[0]} steps): k {ek:.2e}, D_eff {eD:.2e}")
             assert ek <= bk and eD <= bd, (name, ek, eD)
             continue
         stk, k = flow(prec, 1e-7, 2000, 400_000)
