@@ -85,11 +85,12 @@ typedef struct {
   /* sweep launch variant, the same arithmetic in every one: -1 = time them
    * all at creation and keep the fastest per parity (solvers whose node
    * count lies in the same power-of-two octave as one timed before in this
-   * process, with the same precision and device, reuse its choice); 0..5 =
+   * process, with the same precision and device, reuse its choice); 0..6 =
    * force one (0/1 one thread per node without/with a register cap, 2/3 the
    * same on a resident grid striding over nodes, 4 a tighter cap, 5 the
    * resident grid two nodes deep with the next node's column-map words
-   * prefetched); larger values clamp to 5 */
+   * prefetched, 6 even steps two consecutive nodes per thread with vector
+   * loads and stores, odd steps as 0); larger values clamp to 6 */
   int32_t variant;
   /* OM_DRIVE_FORCE: body_force along x, x periodic.  OM_DRIVE_PRESSURE
    * (Sec. 3.3): no force, x not periodic, densities 1 + delta_rho/2 and
@@ -117,7 +118,7 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
-  int32_t variant; /* as om_flow_params.variant: 0..3 as there, 4 = its 5 (larger values clamp to 4) */
+  int32_t variant; /* as om_flow_params.variant: 0..3 as there, 4 = its 5, 5 = its 6 (larger values clamp to 5) */
   int32_t lattice;
 } om_diff_params;
 

@@ -23,7 +23,7 @@
 namespace om {
 
 struct BatchItem {
-  const uint2* col;       // rebased column map (global node numbers)
+  const uint4* col;       // rebased column map (global node numbers)
   const uint32_t* coord;  // structure-local packed coordinates
   uint32_t off, nf;
   int nx, ny, nz, W;
@@ -32,9 +32,14 @@ struct BatchItem {
 
 constexpr int kTile = 256;
 
-__global__ void rebase_columns(uint2* col, int64_t nw, uint32_t off) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (int64_t)gridDim.x * blockDim.x)
-    col[k].y += off;
+__global__ void rebase_columns(uint4* col, int64_t nw, uint32_t off) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += (int64_t)gridDim.x * blockDim.x) {
+    uint4 w = col[k];
+    w.y += off;
+    if (w.z != kNoNode) w.z += off;
+    if (w.w != kNoNode) w.w += off;
+    col[k] = w;
+  }
 }
 
 // ------------------------------------------------------------------ sweeps
@@ -47,7 +52,7 @@ __global__ void rebase_columns(uint2* col, int64_t nw, uint32_t off) {
 constexpr int kGroupItems = 32;
 
 struct GroupItem {
-  const uint2* col;       // rebased column map (global node numbers)
+  const uint4* col;       // rebased column map (global node numbers)
   const uint32_t* coord;  // structure-local packed coordinates
   uint32_t off, nf;
   int nx, ny, nz, W;

@@ -151,7 +151,9 @@ struct om_nodeset {
   int64_t N = 0;        // voxels
   int64_t nf = 0;       // nodes
   int64_t pitch = 0;    // population array stride (nodes, padded to 64)
-  uint2* col = nullptr;       // [nx*ny*W]: {node bits, nodes before this word}
+  // [nx*ny*W]: {node bits, nodes before this word, node number of the voxel
+  // below the word's first and above its last (periodic in z; kNoNode if none)}
+  uint4* col = nullptr;
   uint32_t* coord = nullptr;  // [nf] packed x, y, z
   int64_t* vox = nullptr;     // [nf] voxel index
   int64_t wrap_links = 0;     // D3Q19 links from node voxels at x = nx-1 to node voxels at x = 0

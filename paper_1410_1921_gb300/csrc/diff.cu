@@ -29,8 +29,10 @@ namespace om {
 // threads stride over nodes, loading the next node's coordinates before
 // updating the current one (the flow sweep's variants 2 and 3); 4 = variant
 // 2 two nodes deep with the next node's column-map words prefetched into L1
-// (the flow sweep's variant 5).
-constexpr int kDiffVariants = 5;
+// (the flow sweep's variant 5); 5 = even steps two consecutive nodes per
+// thread with vector loads and stores (the flow sweep's variant 6), odd
+// steps as variant 0.
+constexpr int kDiffVariants = 6;
 
 template <class T, class L, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) diff_sweep(DiffArgs<T, L> a) {
@@ -78,6 +80,14 @@ __global__ void __launch_bounds__(256, MINB) diff_sweep_pipelined(DiffArgs<T, L>
     c0 = c1;
     c1 = c2;
   }
+}
+
+template <class T, class L>
+__global__ void __launch_bounds__(256) diff_sweep_pair(DiffArgs<T, L> a) {
+  const uint32_t n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (n >= a.nf) return;
+  if (n + 1 == a.nf) diff_node_at<T, L, false>(a, n, 0u);
+  else diff_pair_even<T, L>(a, n);
 }
 
 // Observables: sum J_x, sum |C - prev|, sum |C|, sum C, sum D_L; prev <- C.
@@ -237,6 +247,12 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const DiffArgs<T, 
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
+    case 5:
+      if (!ODD) {
+        diff_sweep_pair<T, L><<<blocks_for((a.nf + 1) / 2), 256, 0, s>>>(a);
+        break;
+      }
+      [[fallthrough]];
     default: diff_sweep<T, L, ODD, 0><<<nb, 256, 0, s>>>(a); break;
   }
 }

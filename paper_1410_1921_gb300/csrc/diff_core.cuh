@@ -12,7 +12,7 @@ template <class T, class L = D3Q7>
 struct DiffArgs {
   T* q[L::Q];  // population i of node n is q[i][n]
   uint32_t nf;
-  const uint2* col;
+  const uint4* col;
   const uint32_t* coord;
   const typename Stg<T>::C* omega;
   int nx, ny, nz, W;
@@ -45,15 +45,15 @@ __device__ __forceinline__ void diff_neighbours(const DiffArgs<T, L>& a, uint32_
     q19_neighbours(a.col, a.nx, a.ny, a.nz, a.W, 0, c, nb);
   } else {
     const int yp = y + 1 == a.ny ? 0 : y + 1, ym = y == 0 ? a.ny - 1 : y - 1;
-    const int zp = z + 1 == a.nz ? 0 : z + 1, zm = z == 0 ? a.nz - 1 : z - 1;
+    const ZPos p = zpos(z, a.nz);
     const uint32_t ny = (uint32_t)a.ny, W = (uint32_t)a.W;
     auto base = [&](int xx, int yy) { return ((uint32_t)xx * ny + (uint32_t)yy) * W; };
     uint32_t self;
-    column3(a.col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
-    nb[1] = x + 1 < a.nx ? column1(a.col, base(x + 1, y), z) : kNoNode;
-    nb[2] = x > 0 ? column1(a.col, base(x - 1, y), z) : kNoNode;
-    nb[3] = column1(a.col, base(x, yp), z);
-    nb[4] = column1(a.col, base(x, ym), z);
+    column3(a.col, base(x, y), p, nb[6], self, nb[5]);
+    nb[1] = x + 1 < a.nx ? column1(a.col, base(x + 1, y), p) : kNoNode;
+    nb[2] = x > 0 ? column1(a.col, base(x - 1, y), p) : kNoNode;
+    nb[3] = column1(a.col, base(x, yp), p);
+    nb[4] = column1(a.col, base(x, ym), p);
     (void)self;
   }
 }
@@ -126,6 +126,17 @@ __device__ __forceinline__ void diff_load(const DiffArgs<T, L>& a, uint32_t n, c
   diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
 }
 
+// BGK relaxation of a node's deviations g toward a_i times their sum (the
+// reference's own equilibrium part cancels: it is at rest).
+template <class L, class C>
+__device__ __forceinline__ void diff_relax(C (&g)[L::Q], C om) {
+  C cc = g[0];
+#pragma unroll
+  for (int i = 1; i < L::Q; ++i) cc += g[i];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) g[i] = g[i] - om * (g[i] - C(L::w(i)) * cc);
+}
+
 // One fused collide-stream update of node n (global slot index) at x whose
 // neighbours are nb (used on odd steps only); the AA read/write pattern of
 // flow_node_nb with the anti-bounce-back inlet/outlet and the reference shift.
@@ -137,12 +148,7 @@ __device__ __forceinline__ void diff_node_nb(const DiffArgs<T, L>& a, uint32_t n
   if (ODD) diff_refs(a, n, nb, r);
   C g[L::Q];
   diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
-  const C om = a.omega[n];
-  C cc = g[0];
-#pragma unroll
-  for (int i = 1; i < L::Q; ++i) cc += g[i];
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) g[i] = g[i] - om * (g[i] - C(L::w(i)) * cc);
+  diff_relax<L>(g, a.omega[n]);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const int o = L::opp(i);
@@ -174,6 +180,23 @@ __device__ __forceinline__ void diff_node_nb(const DiffArgs<T, L>& a, uint32_t n
       S::st(p, v, a.up);
     }
   }
+}
+
+// Even-step update of the two nodes n, n + 1 (n even, n + 1 < nf): each
+// population of both moved as one vector (Pair<T>), the relaxations those of
+// diff_node_nb.
+template <class T, class L>
+__device__ __forceinline__ void diff_pair_even(const DiffArgs<T, L>& a, uint32_t n) {
+  using C = typename Stg<T>::C;
+  C g0[L::Q], g1[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) Pair<T>::ld(a.q[i] + n, a.down, g0[i], g1[i]);
+  C om0, om1;
+  Pair<C>::ld(a.omega + n, C(1), om0, om1);
+  diff_relax<L>(g0, om0);
+  diff_relax<L>(g1, om1);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) Pair<T>::st(a.q[L::opp(i)] + n, g0[i], g1[i], a.up);
 }
 
 // diff_node_nb after the neighbour lookup of the node's coordinates c

@@ -52,10 +52,14 @@ namespace om {
 //   4  one thread per node with a tighter cap (MINB + 1 blocks);
 //   5  variant 2 two nodes deep: the coordinates of the node after next are
 //      loaded, and the column-map words of the next node prefetched into
-//      L1, while the current node is updated (odd steps).
+//      L1, while the current node is updated (odd steps);
+//   6  even steps: two consecutive nodes per thread, each population of both
+//      loaded and stored as one vector of two (twice the bytes per load
+//      instruction and per register in flight, which the 16-bit formats
+//      need to approach the bandwidth roofline); odd steps as variant 0.
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
-constexpr int kSweepVariants = 6;
+constexpr int kSweepVariants = 7;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
@@ -103,6 +107,14 @@ __global__ void __launch_bounds__(256, MINB) d3q19_sweep_pipelined(FlowArgs<T> a
     c0 = c1;
     c1 = c2;
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) d3q19_sweep_pair(FlowArgs<T> a) {
+  const uint32_t n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (n >= a.nf) return;
+  if (n + 1 == a.nf) flow_node_at<T, false>(a, n, 0u);
+  else flow_pair_even<T>(a, n);
 }
 
 // Observables (FP64, fixed grid): sum u_x, sum |u_x - prev|, sum |u_x|,
@@ -288,6 +300,12 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>&
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
+    case 6:
+      if (!ODD) {
+        d3q19_sweep_pair<T><<<blocks_for((a.nf + 1) / 2), 256, 0, s>>>(a);
+        break;
+      }
+      [[fallthrough]];
     default: d3q19_sweep<T, ODD, 0><<<nb, 256, 0, s>>>(a); break;
   }
 }
@@ -496,12 +514,12 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   fl->p = *p;
   if (p->drive == OM_DRIVE_PRESSURE && ns->nf > 0) {
     // nodes before column (1, 0) lie at x = 0; from column (nx - 1, 0) on, at x = nx - 1
-    uint2 w[2];
+    uint4 w[2];
     const om_domain& d = ns->dom;
-    cudaError_t e = cudaMemcpyAsync(&w[0], ns->col + (size_t)1 * d.ny * ns->W, sizeof(uint2),
+    cudaError_t e = cudaMemcpyAsync(&w[0], ns->col + (size_t)1 * d.ny * ns->W, sizeof(uint4),
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&w[1], ns->col + (size_t)(d.nx - 1) * d.ny * ns->W, sizeof(uint2),
+      e = cudaMemcpyAsync(&w[1], ns->col + (size_t)(d.nx - 1) * d.ny * ns->W, sizeof(uint4),
                           cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -14,7 +14,7 @@ template <class T>
 struct FlowArgs {
   T* s[19];  // population i of node n is s[i][n] (kernel parameters: no per-slot registers)
   uint32_t nf;
-  const uint2* col;
+  const uint4* col;
   const uint32_t* coord;
   int nx, ny, nz, W;
   typename Stg<T>::C wp, wm, g, up, down;
@@ -91,6 +91,21 @@ __device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
 }
 
 
+// Collision of node n's pre-collision deviations f; under the pressure drive
+// a boundary node first takes its extrapolated populations.
+template <class T>
+__device__ __forceinline__ void flow_collide(const FlowArgs<T>& a, uint32_t n, typename Stg<T>::C (&f)[19]) {
+  if (a.n_in + a.n_out) {
+    const int64_t k = flow_boundary_index(a, n);
+    if (k >= 0) {
+      const uint32_t nbt = a.n_in + a.n_out;
+#pragma unroll
+      for (int i = 0; i < 19; ++i) f[i] = a.bc[(size_t)i * nbt + k];
+    }
+  }
+  trt_collide(f, a.wp, a.wm, a.g);
+}
+
 // One fused collide-stream update of node n (global slot index) whose
 // neighbours are nb (used on odd steps only).  Even steps: read and write the
 // node's own slots (post-collision f*_i to slot opposite(i)).  Odd steps:
@@ -103,15 +118,7 @@ __device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, c
   using C = typename S::C;
   C f[19];
   flow_load<T, ODD>(a, n, nb, f);
-  if (a.n_in + a.n_out) {  // pressure drive: boundary nodes take the extrapolated populations
-    const int64_t k = flow_boundary_index(a, n);
-    if (k >= 0) {
-      const uint32_t nbt = a.n_in + a.n_out;
-#pragma unroll
-      for (int i = 0; i < 19; ++i) f[i] = a.bc[(size_t)i * nbt + k];
-    }
-  }
-  trt_collide(f, a.wp, a.wm, a.g);
+  flow_collide(a, n, f);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     T* p = a.s[q19_opp(i)] + n;
@@ -131,6 +138,21 @@ __device__ __forceinline__ void flow_node_at(const FlowArgs<T>& a, uint32_t n, u
   uint32_t nb[19];
   if (ODD) flow_neighbours(a, c, nb);
   flow_node_nb<T, ODD>(a, n, nb);
+}
+
+// Even-step update of the two nodes n, n + 1 (n even, n + 1 < nf): each
+// population of both moved as one vector (Pair<T>), the collisions those of
+// flow_node_nb.
+template <class T>
+__device__ __forceinline__ void flow_pair_even(const FlowArgs<T>& a, uint32_t n) {
+  using C = typename Stg<T>::C;
+  C f0[19], f1[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) Pair<T>::ld(a.s[i] + n, a.down, f0[i], f1[i]);
+  flow_collide(a, n, f0);
+  flow_collide(a, n + 1, f1);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) Pair<T>::st(a.s[q19_opp(i)] + n, f0[i], f1[i], a.up);
 }
 
 // flow_node_at for node n whose coordinates are coord[ln]

@@ -45,80 +45,140 @@ struct Stg<__nv_bfloat16> {
   }
 };
 
+// Two consecutive nodes' values of one population as one vector access (the
+// even sweeps that update two nodes per thread): the same conversions and
+// rounding as Stg<T>::ld / st, element by element.  p must be 2-element
+// aligned (an even node number in a slot array of even pitch).
+template <class T>
+struct Pair;
+template <>
+struct Pair<double> {
+  __device__ __forceinline__ static void ld(const double* p, double, double& a, double& b) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+  }
+  __device__ __forceinline__ static void st(double* p, double a, double b, double) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  }
+};
+template <>
+struct Pair<float> {
+  __device__ __forceinline__ static void ld(const float* p, float, float& a, float& b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+  }
+  __device__ __forceinline__ static void st(float* p, float a, float b, float) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  }
+};
+template <>
+struct Pair<__half> {
+  __device__ __forceinline__ static void ld(const __half* p, float down, float& a, float& b) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+    a = v.x * down;
+    b = v.y * down;
+  }
+  __device__ __forceinline__ static void st(__half* p, float a, float b, float up) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * up, b * up);
+  }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+  __device__ __forceinline__ static void ld(const __nv_bfloat16* p, float down, float& a, float& b) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    a = v.x * down;
+    b = v.y * down;
+  }
+  __device__ __forceinline__ static void st(__nv_bfloat16* p, float a, float b, float up) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a * up, b * up);
+  }
+};
+
 // Node number of voxel (x, y, z) from its column's bit map, or kNoNode.
 // Column-map indices fit 32 bits (nx*ny*W <= 1024*2048*64).
-__device__ __forceinline__ uint32_t node_at(const uint2* __restrict__ col, int ny, int W, int x,
+__device__ __forceinline__ uint32_t node_at(const uint4* __restrict__ col, int ny, int W, int x,
                                             int y, int z) {
   const uint32_t k = ((uint32_t)x * (uint32_t)ny + (uint32_t)y) * (uint32_t)W + ((uint32_t)z >> 5);
-  const uint2 b = __ldg(col + k);
+  const uint2 b = __ldg(reinterpret_cast<const uint2*>(col + k));
   const uint32_t bit = 1u << (z & 31);
   return (b.x & bit) ? b.y + __popc(b.x & (bit - 1u)) : kNoNode;
 }
 
-// Node numbers of the voxels z-1, z, z+1 of one (x, y) column.  The three
-// usually share one 32-voxel word of the column map, so one load and a
-// popcount serve all of them; a neighbour across a word edge or the periodic
-// wrap takes its own word.
-__device__ __forceinline__ void column3(const uint2* __restrict__ col, uint32_t base, int z, int zp, int zm,
-                                        uint32_t& rm, uint32_t& r0, uint32_t& rp) {
-  const int zb = z & 31;
-  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
-  const uint32_t b0 = (w.x >> zb) & 1u;
-  const uint32_t rank0 = w.y + __popc(w.x & ((1u << zb) - 1u));
-  r0 = b0 ? rank0 : kNoNode;
-  if (zb != 31 && zp == z + 1) {
-    rp = ((w.x >> (zb + 1)) & 1u) ? rank0 + b0 : kNoNode;
-  } else {
-    const uint2 v = __ldg(col + base + ((uint32_t)zp >> 5));
-    const uint32_t bit = 1u << (zp & 31);
-    rp = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
-  }
-  if (zb != 0 && zm == z - 1) {
-    rm = ((w.x >> (zb - 1)) & 1u) ? rank0 - 1u : kNoNode;
-  } else {
-    const uint2 v = __ldg(col + base + ((uint32_t)zm >> 5));
-    const uint32_t bit = 1u << (zm & 31);
-    rm = (v.x & bit) ? v.y + __popc(v.x & (bit - 1u)) : kNoNode;
-  }
+// Where z sits in its 32-voxel column word, worked out once per node and
+// shared by the lookups in all neighbour columns: first / last say that
+// z - 1 / z + 1 (periodic in z) lies outside the word, where the word's own
+// prev / next fields give its node number.
+struct ZPos {
+  uint32_t w;      // word index within the column
+  uint32_t zb;     // bit of z within the word
+  uint32_t below;  // bits of the word below z
+  bool first, last;
+};
+
+__device__ __forceinline__ ZPos zpos(int z, int nz) {
+  ZPos p;
+  p.w = (uint32_t)z >> 5;
+  p.zb = (uint32_t)z & 31u;
+  p.below = (1u << p.zb) - 1u;
+  p.first = p.zb == 0;
+  p.last = p.zb == 31 || z == nz - 1;
+  return p;
 }
 
-__device__ __forceinline__ uint32_t column1(const uint2* __restrict__ col, uint32_t base, int z) {
-  const uint2 w = __ldg(col + base + ((uint32_t)z >> 5));
-  const uint32_t bit = 1u << (z & 31);
-  return (w.x & bit) ? w.y + __popc(w.x & (bit - 1u)) : kNoNode;
+// Node numbers of the voxels z - 1, z, z + 1 (periodic) of one (x, y) column
+// from one 16-byte word: a popcount gives z's rank, its neighbours inside
+// the word are one rank away, and the word's prev / next fields hold the
+// node numbers across the word edge and the periodic wrap.  Branch-free.
+__device__ __forceinline__ void column3(const uint4* __restrict__ col, uint32_t base, const ZPos& p,
+                                        uint32_t& rm, uint32_t& r0, uint32_t& rp) {
+  const uint4 w = __ldg(col + base + p.w);
+  const uint32_t rank0 = w.y + __popc(w.x & p.below);
+  const uint32_t b0 = (w.x >> p.zb) & 1u;
+  const uint32_t bp = ((w.x >> p.zb) >> 1) & 1u;  // z + 1 inside the word
+  const uint32_t bm = ((w.x << 1) >> p.zb) & 1u;  // z - 1 inside the word
+  r0 = b0 ? rank0 : kNoNode;
+  rp = p.last ? w.w : (bp ? rank0 + b0 : kNoNode);
+  rm = p.first ? w.z : (bm ? rank0 - 1u : kNoNode);
+}
+
+__device__ __forceinline__ uint32_t column1(const uint4* __restrict__ col, uint32_t base, const ZPos& p) {
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(col + base + p.w));
+  return ((w.x >> p.zb) & 1u) ? w.y + __popc(w.x & p.below) : kNoNode;
 }
 
 // nb[i] = node number of x + e_i for the D3Q19 velocities (kNoNode off the
 // node set) of the node with packed coordinates c; periodic y, z, and x when
 // px (else no neighbour beyond the x faces).
-__device__ __forceinline__ void q19_neighbours(const uint2* __restrict__ col, int nx, int ny, int nz, int W,
+__device__ __forceinline__ void q19_neighbours(const uint4* __restrict__ col, int nx, int ny, int nz, int W,
                                                int px, uint32_t c, uint32_t (&nb)[19]) {
   int x, y, z;
   unpack_xyz(c, x, y, z);
   const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
   const bool hp = px || x + 1 < nx, hm = px || x > 0;
   const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
-  const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+  const ZPos p = zpos(z, nz);
   const uint32_t uy = (uint32_t)ny, uW = (uint32_t)W;
   auto base = [&](int xx, int yy) { return ((uint32_t)xx * uy + (uint32_t)yy) * uW; };
   uint32_t self;
-  column3(col, base(x, y), z, zp, zm, nb[6], self, nb[5]);
+  column3(col, base(x, y), p, nb[6], self, nb[5]);
   if (hp) {
-    column3(col, base(xp, y), z, zp, zm, nb[13], nb[1], nb[11]);
-    nb[7] = column1(col, base(xp, yp), z);
-    nb[9] = column1(col, base(xp, ym), z);
+    column3(col, base(xp, y), p, nb[13], nb[1], nb[11]);
+    nb[7] = column1(col, base(xp, yp), p);
+    nb[9] = column1(col, base(xp, ym), p);
   } else {
     nb[13] = nb[1] = nb[11] = nb[7] = nb[9] = kNoNode;
   }
   if (hm) {
-    column3(col, base(xm, y), z, zp, zm, nb[14], nb[2], nb[12]);
-    nb[8] = column1(col, base(xm, yp), z);
-    nb[10] = column1(col, base(xm, ym), z);
+    column3(col, base(xm, y), p, nb[14], nb[2], nb[12]);
+    nb[8] = column1(col, base(xm, yp), p);
+    nb[10] = column1(col, base(xm, ym), p);
   } else {
     nb[14] = nb[2] = nb[12] = nb[8] = nb[10] = kNoNode;
   }
-  column3(col, base(x, yp), z, zp, zm, nb[17], nb[3], nb[15]);
-  column3(col, base(x, ym), z, zp, zm, nb[18], nb[4], nb[16]);
+  column3(col, base(x, yp), p, nb[17], nb[3], nb[15]);
+  column3(col, base(x, ym), p, nb[18], nb[4], nb[16]);
   (void)self;
 }
 
@@ -128,7 +188,7 @@ __device__ __forceinline__ void q19_neighbours(const uint2* __restrict__ col, in
 // that a node's lookup finds them on chip when its turn comes.  No register
 // holds the result; x wraps only when px.
 template <int Q>
-__device__ __forceinline__ void prefetch_columns(const uint2* col, int nx, int ny, int W, int px, uint32_t c) {
+__device__ __forceinline__ void prefetch_columns(const uint4* col, int nx, int ny, int W, int px, uint32_t c) {
   int x, y, z;
   unpack_xyz(c, x, y, z);
   const uint32_t w = (uint32_t)z >> 5;
@@ -143,7 +203,7 @@ __device__ __forceinline__ void prefetch_columns(const uint2* col, int nx, int n
     for (int dy = -1; dy <= 1; ++dy) {
       if (Q == 7 && dx != 0 && dy != 0) continue;
       const int yy = y + dy < 0 ? y + dy + ny : (y + dy >= ny ? y + dy - ny : y + dy);
-      const uint2* p = col + ((uint32_t)xx * (uint32_t)ny + (uint32_t)yy) * (uint32_t)W + w;
+      const uint4* p = col + ((uint32_t)xx * (uint32_t)ny + (uint32_t)yy) * (uint32_t)W + w;
       asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));  // in bounds: xx, yy, w valid
     }
   }

@@ -135,7 +135,7 @@ def test_diffusion_steps_fp32(orc, om, geom, steps):
 # Every launch variant of the sweeps does the same arithmetic per node: each
 # matches the oracle, and on a structure with more nodes than one resident
 # grid has threads (so the striding variants loop) all give identical bits.
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_flow_variants_match_oracle(orc, om, variant):
     node = GEOMS["blobs"]()
     f0 = _rand_pops(orc, node, 7)
@@ -144,7 +144,7 @@ def test_flow_variants_match_oracle(orc, om, variant):
     assert np.abs(got - ref).max() <= 1e-13 * 7
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_diffusion_variants_match_oracle(orc, om, variant):
     node = GEOMS["ragged"]()
     g0 = _rand_diff(node, 8)
@@ -154,19 +154,35 @@ def test_diffusion_variants_match_oracle(orc, om, variant):
     assert np.abs(got - ref).max() <= 1e-13 * 7
 
 
+# The even sweeps of two nodes per thread (flow variant 6, diffusion 5) on
+# node sets of odd and even size (the last node of an odd count alone), in
+# every storage format, against the one-node-per-thread sweep.
+@pytest.mark.parametrize("geom", ["tiny", "line", "blobs", "ragged"])
+@pytest.mark.parametrize("prec", ["OM_F64", "OM_F32", "OM_F16DEV", "OM_BF16DEV"])
+def test_pair_sweeps_identical_bits(orc, om, geom, prec):
+    node = GEOMS[geom]()
+    P = getattr(om, prec)
+    f0 = _rand_pops(orc, node, 12, amp=0.05)
+    assert np.array_equal(_flow_run(om, node, f0, 0.9, 1e-5, 3, P, 6), _flow_run(om, node, f0, 0.9, 1e-5, 3, P, 0))
+    d = _rand_d(node, 14)
+    for q in (7, 19):
+        g0 = _rand_diff(node, 13, q=q)
+        assert np.array_equal(_diff_run(om, node, d, g0, 3, P, 0.9, 0.2, 5), _diff_run(om, node, d, g0, 3, P, 0.9, 0.2, 0)), q
+
+
 @pytest.mark.parametrize("prec", ["OM_F32", "OM_F16DEV"])
 def test_sweep_variants_identical_bits(orc, om, prec):
     node = S.random_mask((64, 96, 112), 0.7, 21)  # ~4.8e5 nodes: > SMs x resident threads
     P = getattr(om, prec)
     f0 = _rand_pops(orc, node, 22, amp=0.05)
     first = _flow_run(om, node, f0, 1.0, 1e-5, 5, P, 0)
-    for v in range(1, 6):
+    for v in range(1, 7):
         assert np.array_equal(_flow_run(om, node, f0, 1.0, 1e-5, 5, P, v), first), v
     d = _rand_d(node, 24)
     for q in (7, 19):
         g0 = _rand_diff(node, 23, q=q)
         first = _diff_run(om, node, d, g0, 5, P, 1.0, 0.0, 0)
-        for v in range(1, 5):
+        for v in range(1, 6):
             assert np.array_equal(_diff_run(om, node, d, g0, 5, P, 1.0, 0.0, v), first), (q, v)
 
 
