@@ -118,7 +118,7 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
-  int32_t variant; /* as om_flow_params.variant: 0..3 as there, 4 = its 5, 5 = its 6 (larger values clamp to 5) */
+  int32_t variant; /* as om_flow_params.variant: 0..3 as there, 4, 5 = its 5, 6 (larger values clamp to 5) */
   int32_t lattice;
 } om_diff_params;
 

@@ -141,14 +141,25 @@ __device__ __forceinline__ void diff_relax(C (&g)[L::Q], C om) {
 // neighbours are nb (used on odd steps only); the AA read/write pattern of
 // flow_node_nb with the anti-bounce-back inlet/outlet and the reference shift.
 template <class T, class L, bool ODD>
+__device__ __forceinline__ void diff_store(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q],
+                                           const DiffRefs<T, L>& r, const typename Stg<T>::C (&g)[L::Q]);
+
+template <class T, class L, bool ODD>
 __device__ __forceinline__ void diff_node_nb(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q]) {
-  using S = Stg<T>;
-  using C = typename S::C;
   DiffRefs<T, L> r{};
   if (ODD) diff_refs(a, n, nb, r);
-  C g[L::Q];
+  typename Stg<T>::C g[L::Q];
   diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
   diff_relax<L>(g, a.omega[n]);
+  diff_store<T, L, ODD>(a, n, x, nb, r, g);
+}
+
+// post-collision deviations of node n at x to their slots (see diff_node_nb)
+template <class T, class L, bool ODD>
+__device__ __forceinline__ void diff_store(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q],
+                                           const DiffRefs<T, L>& r, const typename Stg<T>::C (&g)[L::Q]) {
+  using S = Stg<T>;
+  using C = typename S::C;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const int o = L::opp(i);

@@ -57,6 +57,9 @@ namespace om {
 //      loaded and stored as one vector of two (twice the bytes per load
 //      instruction and per register in flight, which the 16-bit formats
 //      need to approach the bandwidth roofline); odd steps as variant 0.
+// (Odd steps of two nodes per thread, a grid apart, with both lookups and
+// all 38 loads issued before either update, were measured slower than
+// variant 2: the registers they need halve the resident threads.)
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
 constexpr int kSweepVariants = 7;

@@ -106,19 +106,10 @@ __device__ __forceinline__ void flow_collide(const FlowArgs<T>& a, uint32_t n, t
   trt_collide(f, a.wp, a.wm, a.g);
 }
 
-// One fused collide-stream update of node n (global slot index) whose
-// neighbours are nb (used on odd steps only).  Even steps: read and write the
-// node's own slots (post-collision f*_i to slot opposite(i)).  Odd steps:
-// read slot opposite(i) of x - e_i, write slot i of x + e_i; a missing
-// neighbour is halfway bounce-back (own slot i read, own slot opposite(i)
-// written).
+// post-collision populations of node n to their slots (see flow_node_nb)
 template <class T, bool ODD>
-__device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19]) {
-  using S = Stg<T>;
-  using C = typename S::C;
-  C f[19];
-  flow_load<T, ODD>(a, n, nb, f);
-  flow_collide(a, n, f);
+__device__ __forceinline__ void flow_store(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
+                                           const typename Stg<T>::C (&f)[19]) {
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     T* p = a.s[q19_opp(i)] + n;
@@ -128,8 +119,22 @@ __device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, c
     } else if (ODD) {
       p = a.s[0] + n;
     }
-    S::st(p, f[i], a.up);
+    Stg<T>::st(p, f[i], a.up);
   }
+}
+
+// One fused collide-stream update of node n (global slot index) whose
+// neighbours are nb (used on odd steps only).  Even steps: read and write the
+// node's own slots (post-collision f*_i to slot opposite(i)).  Odd steps:
+// read slot opposite(i) of x - e_i, write slot i of x + e_i; a missing
+// neighbour is halfway bounce-back (own slot i read, own slot opposite(i)
+// written).
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19]) {
+  typename Stg<T>::C f[19];
+  flow_load<T, ODD>(a, n, nb, f);
+  flow_collide(a, n, f);
+  flow_store<T, ODD>(a, n, nb, f);
 }
 
 // flow_node_nb after the neighbour lookup of the node's coordinates c

@@ -154,20 +154,23 @@ def test_diffusion_variants_match_oracle(orc, om, variant):
     assert np.abs(got - ref).max() <= 1e-13 * 7
 
 
-# The even sweeps of two nodes per thread (flow variant 6, diffusion 5) on
-# node sets of odd and even size (the last node of an odd count alone), in
-# every storage format, against the one-node-per-thread sweep.
+# The even sweeps of two consecutive nodes per thread (flow variant 6,
+# diffusion 5) on node sets of odd and even size (the last node of an odd
+# count alone), in every storage format, against the one-node-per-thread
+# sweep.
 @pytest.mark.parametrize("geom", ["tiny", "line", "blobs", "ragged"])
 @pytest.mark.parametrize("prec", ["OM_F64", "OM_F32", "OM_F16DEV", "OM_BF16DEV"])
 def test_pair_sweeps_identical_bits(orc, om, geom, prec):
     node = GEOMS[geom]()
     P = getattr(om, prec)
     f0 = _rand_pops(orc, node, 12, amp=0.05)
-    assert np.array_equal(_flow_run(om, node, f0, 0.9, 1e-5, 3, P, 6), _flow_run(om, node, f0, 0.9, 1e-5, 3, P, 0))
+    ref = _flow_run(om, node, f0, 0.9, 1e-5, 3, P, 0)
+    assert np.array_equal(_flow_run(om, node, f0, 0.9, 1e-5, 3, P, 6), ref)
     d = _rand_d(node, 14)
     for q in (7, 19):
         g0 = _rand_diff(node, 13, q=q)
-        assert np.array_equal(_diff_run(om, node, d, g0, 3, P, 0.9, 0.2, 5), _diff_run(om, node, d, g0, 3, P, 0.9, 0.2, 0)), q
+        ref = _diff_run(om, node, d, g0, 3, P, 0.9, 0.2, 0)
+        assert np.array_equal(_diff_run(om, node, d, g0, 3, P, 0.9, 0.2, 5), ref), q
 
 
 @pytest.mark.parametrize("prec", ["OM_F32", "OM_F16DEV"])
