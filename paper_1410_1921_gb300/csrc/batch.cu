@@ -507,6 +507,7 @@ FlowArgs<T> bflow_args(const om_batch* b) {
   FlowArgs<T> a{};
   const Model& m = b->m[0];
   for (int i = 0; i < 19; ++i) a.s[i] = (T*)m.pop + (size_t)i * b->pitch;
+  a.P = (uint32_t)b->pitch;
   a.nf = b->total;
   const double tau = b->fp.tau;
   a.wp = (typename Stg<T>::C)(1.0 / tau);
@@ -927,9 +928,10 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     tiles += (int)((ns->nf + kTile - 1) / kTile);
     b->items_h.push_back(it);
   }
-  if (total >= 0xFFFFFFF0ull) return bail(fail(OM_EINVAL, "om_batch_create: more than 2^32 nodes"));
-  b->total = (uint32_t)total;
   b->pitch = ((int64_t)total + 63) / 64 * 64;
+  if (19 * b->pitch > (int64_t)UINT32_MAX)
+    return bail(fail(OM_EINVAL, "om_batch_create: more than 226 M nodes (slot offsets are 32-bit)"));
+  b->total = (uint32_t)total;
   b->max_tiles = std::max(1, tiles);
   auto dalloc = [&](void** p, size_t bytes) -> om_status {
     if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {

@@ -501,6 +501,8 @@ om_status flow_observe_any(om_flow* fl, double* out, cudaStream_t s) {
 extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* p, void* stream,
                                     om_flow** out) {
   if (!ns || !p || !out) return fail(OM_EINVAL, "om_flow_create: null pointer");
+  if (19 * ns->pitch > (int64_t)UINT32_MAX)
+    return fail(OM_EINVAL, "om_flow_create: more than 226 M nodes (slot offsets are 32-bit)");
   if (!(p->tau > 0.5)) return fail(OM_EINVAL, "om_flow_create: tau must exceed 1/2");
   if (p->precision < OM_F64 || p->precision > OM_BF16DEV)
     return fail(OM_EINVAL, "om_flow_create: unknown precision");

@@ -13,6 +13,7 @@ namespace om {
 template <class T>
 struct FlowArgs {
   T* s[19];  // population i of node n is s[i][n] (kernel parameters: no per-slot registers)
+  uint32_t P;  // slot pitch: s[i] == s[0] + i * P, and 19 * P < 2^32
   uint32_t nf;
   const uint4* col;
   const uint32_t* coord;
@@ -42,18 +43,34 @@ __device__ __forceinline__ int64_t flow_boundary_index(const FlowArgs<T>& a, uin
   return -1;
 }
 
+// Odd steps: off[i] = element offset from s[0] of the slot that population i
+// of node n is read from -- slot opposite(i) of the neighbour x - e_i, or
+// the node's own slot i where that neighbour is missing (halfway
+// bounce-back).  In the AA pattern the post-collision population
+// opposite(i) is written to the same slot, so one offset serves both.
+template <class T>
+__device__ __forceinline__ void flow_slots_odd(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
+                                               uint32_t (&off)[19]) {
+  off[0] = n;
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    const uint32_t o = (uint32_t)q19_opp(i), src = nb[o];
+    off[i] = src != kNoNode ? o * a.P + src : (uint32_t)i * a.P + n;
+  }
+}
+
 // pre-collision populations of node n at the current time
 template <class T, bool ODD>
 __device__ __forceinline__ void flow_load(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
                                           typename Stg<T>::C (&f)[19]) {
+  if constexpr (ODD) {
+    uint32_t off[19];
+    flow_slots_odd(a, n, nb, off);
 #pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    const T* p = a.s[i] + n;
-    if (ODD && i > 0) {
-      const uint32_t src = nb[q19_opp(i)];
-      if (src != kNoNode) p = a.s[q19_opp(i)] + src;
-    }
-    f[i] = Stg<T>::ld(p, a.down);
+    for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[0] + off[i], a.down);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[i] + n, a.down);
   }
 }
 
@@ -106,22 +123,6 @@ __device__ __forceinline__ void flow_collide(const FlowArgs<T>& a, uint32_t n, t
   trt_collide(f, a.wp, a.wm, a.g);
 }
 
-// post-collision populations of node n to their slots (see flow_node_nb)
-template <class T, bool ODD>
-__device__ __forceinline__ void flow_store(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19],
-                                           const typename Stg<T>::C (&f)[19]) {
-#pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    T* p = a.s[q19_opp(i)] + n;
-    if (ODD && i > 0) {
-      const uint32_t dst = nb[i];
-      if (dst != kNoNode) p = a.s[i] + dst;
-    } else if (ODD) {
-      p = a.s[0] + n;
-    }
-    Stg<T>::st(p, f[i], a.up);
-  }
-}
 
 // One fused collide-stream update of node n (global slot index) whose
 // neighbours are nb (used on odd steps only).  Even steps: read and write the
@@ -132,9 +133,21 @@ __device__ __forceinline__ void flow_store(const FlowArgs<T>& a, uint32_t n, con
 template <class T, bool ODD>
 __device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, const uint32_t (&nb)[19]) {
   typename Stg<T>::C f[19];
-  flow_load<T, ODD>(a, n, nb, f);
-  flow_collide(a, n, f);
-  flow_store<T, ODD>(a, n, nb, f);
+  if constexpr (ODD) {
+    uint32_t off[19];
+    flow_slots_odd(a, n, nb, off);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[0] + off[i], a.down);
+    flow_collide(a, n, f);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Stg<T>::st(a.s[0] + off[q19_opp(i)], f[i], a.up);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[i] + n, a.down);
+    flow_collide(a, n, f);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Stg<T>::st(a.s[q19_opp(i)] + n, f[i], a.up);
+  }
 }
 
 // flow_node_nb after the neighbour lookup of the node's coordinates c

@@ -54,6 +54,7 @@ inline FlowArgs<T> flow_args(const om_flow* fl) {
   FlowArgs<T> a;
   const om_nodeset* ns = fl->ns;
   for (int i = 0; i < 19; ++i) a.s[i] = (T*)fl->f + (size_t)i * ns->pitch;
+  a.P = (uint32_t)ns->pitch;
   a.nf = (uint32_t)ns->nf;
   a.col = ns->col;
   a.coord = ns->coord;
