@@ -344,7 +344,9 @@ def run_gpu(a):
                        "setup_s": t_setup},
             "flow_mlups": flow_updates / (flow_ms * 1e-3) / 1e6,
             "roofline": roofline, "clocks": ck, "e2e": e2e,
-            "gpu_launches": a.steps * len(solvers) * 2 * (WINDOW + 2)}
+            # per structure and step: two windows, each model's observe and
+            # fixed-order reduction, the diffusion's reference move
+            "gpu_launches": a.steps * len(solvers) * (2 * (WINDOW + 2) + 1)}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
             step, desc = _oracle_sample(a.edge)
@@ -526,10 +528,13 @@ def _parity_us(model, nodes, bytes_per_node, peak, reps=20):
 def run_batch(a):
     """The 150-structure set (edges {64..200}^3, porosity U[0.10, 0.50], <d>
     U[10, 60] nm, tolerance U[0, 0.8], 1.5 nm voxels) advanced together: one
-    persistent launch per LB step over every structure's nodes, check windows
-    replayed as CUDA graphs, launch shape autotuned.  Aggregate MLUPS of each
-    model over 100-step windows (FP32), and the plain form for comparison:
-    the same structures one solver each, the same windows."""
+    launch per LB step and L2-sized group over a work list of tiles, check
+    windows replayed as CUDA graphs, launch shape autotuned.  Aggregate MLUPS
+    of each model over 100-step windows (FP32), and the plain form for
+    comparison: the same structures one solver each, the same windows.
+    Also the two window modes of a batch solve (graph of per-step launches,
+    one persistent grid-barrier launch per group), each over 4 windows with
+    their convergence checks."""
     import torch
 
     from paper_1410_1921_gb300 import build as B
@@ -559,6 +564,18 @@ def run_batch(a):
         mlups, ms = _window_mlups(lambda: b.step(model, WINDOW), total, WINDOW, 3)
         out[name] = {"mlups": mlups, "ms_per_window": ms}
     b.close()
+    modes = {}
+    for mode, mname in ((0, "graph"), (1, "persistent")):
+        fp0 = P.flow_params(precision=P.OM_F32, conv_tol=0.0, check_every=WINDOW, max_steps=4 * WINDOW)
+        dp0 = P.diff_params(precision=P.OM_F32, conv_tol=0.0, check_every=WINDOW, max_steps=4 * WINDOW)
+        bm = P.Batch([i[0] for i in items], [i[1] for i in items], [i[2] for i in items], flow=fp0, diff=dp0)
+        modes[mname] = {}
+        for model, name in ((0, "flow"), (1, "diffusion")):
+            bm.set_window_mode(model, mode)
+            res, _, info, st = bm.solve(model)
+            moved = sum(nodes[k] * info[k].steps for k in range(len(nodes)) if st[k] != P.OM_ENOPERC)
+            modes[mname][name] = {"mlups": moved / info[0].seconds / 1e6, "s": info[0].seconds}
+        bm.close()
     # plain: one solver per structure, the same windows one after the other
     plain = {}
     for name in ("flow", "diffusion"):
@@ -579,7 +596,7 @@ def run_batch(a):
             ns.close()
     line = {"metric": "aggregate fluid MLUPS, batched structures", "value": out["flow"]["mlups"],
             "unit": "MLUPS", "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "batched": out, "plain": plain, "structures": len(items), "nodes": total,
+            "batched": out, "plain": plain, "window_modes": modes, "structures": len(items), "nodes": total,
             "setup_s": t_setup, "batch_create_s": t_create,
             "config": {"workload": ("150 structures, edges {64,96,128,160,200}^3 at 1.5 nm, porosity U[0.10,0.50]"
                                     if a.batch_set == "150" else

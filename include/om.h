@@ -326,9 +326,29 @@ om_status om_batch_step(om_batch* b, int32_t model, int64_t nsteps, void* stream
  * info (nullable; seconds and mlups are those of the whole batch); status
  * (nullable) = OM_OK, OM_ENOTCONVERGED or OM_ENOPERC (no nodes; flow: or
  * no link across the periodic x boundary, result 0) per structure.  Returns
- * OM_OK unless a call fails. */
+ * OM_OK unless a call fails; OM_ETIMEOUT if a grid-barrier wait of a
+ * persistent window gave up (see om_batch_set_window_mode; the batch's
+ * state is then undefined).
+ * Check windows run in one of two modes with identical results: the
+ * captured graph of per-step launches, or one persistent cooperative launch
+ * per group whose blocks meet at a grid barrier between steps (every wait
+ * bounded, ~2 s).  Unless a mode was set, the first two whole windows of the
+ * first solve are run one in each mode, timed, and the faster is kept. */
 om_status om_batch_solve(om_batch* b, int32_t model, double* result, double* aux, om_run_info* info,
                          int32_t* status, void* stream);
+/* Window mode of om_batch_solve for a model: -1 = time both (default), 0 =
+ * graph of per-step launches, 1 = persistent launches.  om_batch_step always
+ * replays the graph. */
+om_status om_batch_set_window_mode(om_batch* b, int32_t model, int32_t mode);
+/* Self-test of the bounded grid barrier: one cooperative launch of `blocks`
+ * 256-thread blocks (at most what fits on the GPU at once, else OM_EINVAL)
+ * meets `rounds` times at the barrier of the persistent windows, which is
+ * told to expect `blocks + extra` arrivals; each wait gives up after
+ * max_polls polls of ~100 ns.  *status = OM_OK when every barrier completed,
+ * OM_ETIMEOUT when a wait gave up (always so for extra > 0: the barrier can
+ * never complete, and the launch still ends).  Synchronises. */
+om_status om_barrier_selftest(int32_t blocks, int32_t rounds, int32_t extra, int64_t max_polls, int32_t* status,
+                              void* stream);
 /* populations of structure `item` in the dense layout of om_flow_get_populations /
  * om_diff_get_populations (double q*N_k, device) */
 om_status om_batch_get_populations(om_batch* b, int32_t model, int32_t item, double* dense_dev,

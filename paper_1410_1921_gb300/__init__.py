@@ -114,6 +114,8 @@ _SIGS = {
                         C.POINTER(om_flow_params), C.POINTER(om_diff_params), _vp, C.POINTER(_vp)],
     "om_batch_step": [_vp, C.c_int32, C.c_int64, _vp],
     "om_batch_solve": [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp],
+    "om_batch_set_window_mode": [_vp, C.c_int32, C.c_int32],
+    "om_barrier_selftest": [C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.POINTER(C.c_int32), _vp],
     "om_batch_get_populations": [_vp, C.c_int32, C.c_int32, _vp, _vp],
     "om_batch_set_populations": [_vp, C.c_int32, C.c_int32, _vp, _vp],
     "om_batch_reset": [_vp, C.c_int32, _vp],
@@ -476,6 +478,11 @@ class Batch:
         _call("om_batch_solve", self.h, model, _ptr(res), _ptr(aux), info, _ptr(st), _stream(stream))
         return res, aux, list(info), st
 
+    def set_window_mode(self, model, mode):
+        """-1: time both window modes in the first solve; 0: graph of
+        per-step launches; 1: persistent grid-barrier launches."""
+        _call("om_batch_set_window_mode", self.h, model, mode)
+
     def get_populations(self, model, item, out_dev, stream=None):
         _call("om_batch_get_populations", self.h, model, item, _ptr(out_dev), _stream(stream))
 
@@ -499,6 +506,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def om_barrier_selftest(blocks, rounds, extra, max_polls, stream=None):
+    """Status (OM_OK or OM_ETIMEOUT) of `rounds` bounded grid barriers among
+    `blocks` co-resident blocks that expect `blocks + extra` arrivals."""
+    st = C.c_int32()
+    _call("om_barrier_selftest", blocks, rounds, extra, max_polls, C.byref(st), _stream(stream))
+    return st.value
 
 
 def om_unet_pack_structure(mask_dev, d_nm_dev, d_scale, x_dev, stream=None):

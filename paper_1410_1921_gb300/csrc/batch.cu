@@ -14,6 +14,7 @@
 // tile order (deterministic).  Launch shapes (residency cap, CTAs per SM) are
 // picked per parity by timing them on the batch itself.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <vector>
 
@@ -76,49 +77,142 @@ __device__ __forceinline__ int group_item(const GroupDesc& g, int w) {
   return lo;
 }
 
+// one step of the nodes of tile w of group g
+template <class T, bool ODD>
+__device__ __forceinline__ void flow_group_tile(const FlowArgs<T>& a, const GroupDesc& g, int w) {
+  const int k = group_item(g, w);
+  const GroupItem& it = g.it[k];
+  const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
+  if (ln >= it.nf) return;
+  if (ODD) {
+    FlowArgs<T> b = a;
+    b.col = it.col;
+    b.coord = it.coord;
+    b.nx = it.nx;
+    b.ny = it.ny;
+    b.nz = it.nz;
+    b.W = it.W;
+    flow_node<T, true>(b, it.off + ln, ln);
+  } else {
+    flow_node<T, false>(a, it.off + ln, ln);
+  }
+}
+
+template <class T, bool ODD>
+__device__ __forceinline__ void diff_group_tile(const DiffArgs<T>& a, const GroupDesc& g, int w) {
+  const int k = group_item(g, w);
+  const GroupItem& it = g.it[k];
+  const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
+  if (ln >= it.nf) return;
+  DiffArgs<T> b = a;
+  b.nx = it.nx;
+  b.s = (typename Stg<T>::C)it.slope;
+  if (ODD) {
+    b.col = it.col;
+    b.coord = it.coord;
+    b.ny = it.ny;
+    b.nz = it.nz;
+    b.W = it.W;
+  }
+  diff_node<T, ODD>(b, it.off + ln, ln);
+}
+
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(kTile, MINB) flow_batch_sweep(FlowArgs<T> a, const __grid_constant__ GroupDesc g) {
   const int nw = g.tile0[g.n];
-  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-    const int k = group_item(g, w);
-    const GroupItem& it = g.it[k];
-    const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
-    if (ln >= it.nf) continue;
-    if (ODD) {
-      FlowArgs<T> b = a;
-      b.col = it.col;
-      b.coord = it.coord;
-      b.nx = it.nx;
-      b.ny = it.ny;
-      b.nz = it.nz;
-      b.W = it.W;
-      flow_node<T, true>(b, it.off + ln, ln);
-    } else {
-      flow_node<T, false>(a, it.off + ln, ln);
-    }
-  }
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) flow_group_tile<T, ODD>(a, g, w);
 }
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(kTile, MINB) diff_batch_sweep(DiffArgs<T> a, const __grid_constant__ GroupDesc g) {
   const int nw = g.tile0[g.n];
-  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-    const int k = group_item(g, w);
-    const GroupItem& it = g.it[k];
-    const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
-    if (ln >= it.nf) continue;
-    DiffArgs<T> b = a;
-    b.nx = it.nx;
-    b.s = (typename Stg<T>::C)it.slope;
-    if (ODD) {
-      b.col = it.col;
-      b.coord = it.coord;
-      b.ny = it.ny;
-      b.nz = it.nz;
-      b.W = it.W;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) diff_group_tile<T, ODD>(a, g, w);
+}
+
+// ------------------------------------------------------------------ persistent windows
+// A window of K steps of one group in a single cooperative launch (all its
+// blocks co-resident): the blocks stride over the group's tiles for a step,
+// meet at a grid barrier, and go on to the next step.  The barrier waits are
+// bounded: a block that waits more than `limit` polls (about 100 ns each)
+// records OM_ETIMEOUT in the barrier's status word and returns, and every
+// other block leaves at its next wait once it sees the status, so the
+// launch always ends and the host reads the status instead of a hang.
+struct GridBar {
+  unsigned count;  // arrivals at the current barrier
+  unsigned gen;    // barriers completed (only ever incremented)
+  int status;      // OM_OK, or OM_ETIMEOUT once a wait gave up
+  int pad;
+};
+
+constexpr unsigned long long kBarrierPolls = 20000000ull;  // ~2 s of polling
+
+// Barrier of `expected` blocks; false when a wait gave up (the caller
+// returns).
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned expected, unsigned long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    volatile unsigned* gen = &bar->gen;
+    volatile int* status = &bar->status;
+    const unsigned g0 = *gen;
+    __threadfence();  // this block's stores of the step before its arrival
+    if (atomicAdd(&bar->count, 1u) == expected - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned long long polls = 0;
+      while (*gen == g0) {
+        if (*status != OM_OK || ++polls > limit) {
+          atomicCAS(&bar->status, OM_OK, OM_ETIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
     }
-    diff_node<T, ODD>(b, it.off + ln, ln);
+    __threadfence();  // the other blocks' stores before this block reads
+    ok = good;
   }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class T, int MINB>
+__global__ void __launch_bounds__(kTile, MINB) flow_batch_window(FlowArgs<T> a, const __grid_constant__ GroupDesc g,
+                                                                 int odd0, int K, GridBar* bar) {
+  const int nw = g.tile0[g.n];
+  for (int k = 0; k < K; ++k) {
+    if ((odd0 + k) & 1) {
+      for (int w = blockIdx.x; w < nw; w += gridDim.x) flow_group_tile<T, true>(a, g, w);
+    } else {
+      for (int w = blockIdx.x; w < nw; w += gridDim.x) flow_group_tile<T, false>(a, g, w);
+    }
+    if (k + 1 < K && !grid_barrier(bar, gridDim.x, kBarrierPolls)) return;
+  }
+}
+
+template <class T, int MINB>
+__global__ void __launch_bounds__(kTile, MINB) diff_batch_window(DiffArgs<T> a, const __grid_constant__ GroupDesc g,
+                                                                 int odd0, int K, GridBar* bar) {
+  const int nw = g.tile0[g.n];
+  for (int k = 0; k < K; ++k) {
+    if ((odd0 + k) & 1) {
+      for (int w = blockIdx.x; w < nw; w += gridDim.x) diff_group_tile<T, true>(a, g, w);
+    } else {
+      for (int w = blockIdx.x; w < nw; w += gridDim.x) diff_group_tile<T, false>(a, g, w);
+    }
+    if (k + 1 < K && !grid_barrier(bar, gridDim.x, kBarrierPolls)) return;
+  }
+}
+
+// Self-test of the bounded barrier: `rounds` barriers among the launch's
+// blocks, expecting `extra` more blocks than the launch has (extra > 0: a
+// barrier that can never complete, so every wait runs out).
+__global__ void barrier_selftest(GridBar* bar, int rounds, unsigned extra, unsigned long long limit) {
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_barrier(bar, gridDim.x + extra, limit)) return;
 }
 
 // An item large enough to fill the GPU alone (a "solo" group) runs the
@@ -387,6 +481,11 @@ struct Model {
   double up = 1.0;
   int var[2] = {0, 0};   // launch variant per parity
   int grid[2] = {152, 152};
+  // check windows: 0 = replay of the captured per-step launches, 1 = one
+  // persistent cooperative launch per group (grid-barrier steps); -1 = not
+  // chosen yet (the first windows time both)
+  int mode = -1;
+  float trial_ms[2] = {-1.f, -1.f};  // time of the window timed in each mode
   cudaGraphExec_t exec = nullptr;
   int graph_k = 0;
   int graph_layout = -1;  // work-list layout the graph was captured for
@@ -427,6 +526,8 @@ struct om_batch {
   Model m[2];
   cudaStream_t cap = nullptr;  // capture stream
   int sms = 152;
+  GridBar* bar = nullptr;      // grid barrier of the persistent windows
+  int* bar_h = nullptr;        // pinned copy of its status
 };
 
 namespace {
@@ -611,6 +712,67 @@ void launch_steps_grouped(const om_batch* b, int model, int64_t t0, int64_t n, c
 template <class T>
 om_status capture_t(om_batch* b, int model, int K);
 
+// Largest grid of the window kernel of a model whose blocks are all
+// resident at once (the cooperative-launch limit).
+template <class T>
+int window_grid(const om_batch* b, int model) {
+  static int cache[2] = {0, 0};
+  if (cache[model] <= 0) {
+    int per = 0;
+    if (model == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flow_batch_window<T, 0>, kTile, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, diff_batch_window<T, 0>, kTile, 0);
+    cache[model] = std::max(1, per) * b->sms;
+  }
+  return cache[model];
+}
+
+// K steps (from time t0) of every group, each group in one persistent
+// cooperative launch.  The barrier's status is cleared once per window (a
+// timeout in one group stays visible, and the later groups' waits then give
+// up at once); its counters before every launch.
+template <class T>
+om_status launch_window_persistent(om_batch* b, int model, int64_t t0, int K, cudaStream_t s) {
+  const int cap = window_grid<T>(b, model);
+  int odd0 = (int)(t0 & 1);
+  OM_CUDA(cudaMemsetAsync(b->bar, 0, sizeof(GridBar), s));
+  for (int g = 0; g < b->ngroups; ++g) {
+    const int tiles = b->gcnt_h[g];
+    if (tiles == 0) continue;
+    unsigned grid = (unsigned)std::min(tiles, cap);
+    OM_CUDA(cudaMemsetAsync(b->bar, 0, offsetof(GridBar, status), s));
+    GridBar* bar = b->bar;
+    if (model == 0) {
+      FlowArgs<T> a = bflow_args<T>(b);
+      void* args[] = {&a, &b->gdesc[g], &odd0, &K, &bar};
+      OM_CUDA(cudaLaunchCooperativeKernel((const void*)flow_batch_window<T, 0>, dim3(grid), dim3(kTile), args, 0, s));
+    } else {
+      DiffArgs<T> a = bdiff_args<T>(b);
+      void* args[] = {&a, &b->gdesc[g], &odd0, &K, &bar};
+      OM_CUDA(cudaLaunchCooperativeKernel((const void*)diff_batch_window<T, 0>, dim3(grid), dim3(kTile), args, 0, s));
+    }
+  }
+  return OM_OK;
+}
+
+// one check window of K steps from an even time: mode 0 replays the
+// captured per-step launches, mode 1 runs each group as one persistent
+// launch and queues a copy of the barrier status to the host (read after the
+// caller's next synchronisation)
+template <class T>
+om_status window_t(om_batch* b, int model, int K, int mode, cudaStream_t s) {
+  Model& m = b->m[model];
+  if (mode == 1) {
+    OM_TRY(launch_window_persistent<T>(b, model, m.t, K, s));
+    OM_CUDA(cudaMemcpyAsync(b->bar_h, &b->bar->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  } else {
+    OM_TRY(capture_t<T>(b, model, K));
+    OM_CUDA(cudaGraphLaunch(m.exec, s));
+  }
+  m.t += K;
+  if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
+  return OM_OK;
+}
+
 // Advance n steps: whole check windows from even times replay the captured
 // window graph (and, for rebased diffusion storage, move the reference after
 // it, as a solve does); anything else is launched step by step.
@@ -627,11 +789,8 @@ om_status steps_t(om_batch* b, int model, int64_t n, cudaStream_t s) {
   const int K = model == 0 ? b->fp.check_every : b->dp.check_every;
   while (n > 0) {
     if (K >= 2 && !(K & 1) && !(m.t & 1) && n >= K) {
-      OM_TRY(capture_t<T>(b, model, K));
-      OM_CUDA(cudaGraphLaunch(m.exec, s));
-      m.t += K;
+      OM_TRY(window_t<T>(b, model, K, 0, s));
       n -= K;
-      if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
       continue;
     }
     launch_steps_grouped<T>(b, model, m.t, 1, s);
@@ -765,24 +924,41 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
   OM_TRY(upload_work(b, nw, (int)active.size(), s));
   OM_TRY(observe_t<T>(b, model, (int)active.size(), s));  // reference state
   for (size_t a = 0; a < active.size(); ++a) sj_prev[active[a]] = b->obs_h[a * nv + 0];
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0, e1, w0, w1;
   OM_CUDA(cudaEventCreate(&e0));
   OM_CUDA(cudaEventCreate(&e1));
+  OM_CUDA(cudaEventCreate(&w0));
+  OM_CUDA(cudaEventCreate(&w1));
   OM_CUDA(cudaEventRecord(e0, s));
   const int64_t t0 = m.t;
   int64_t updates = 0;
   while (!active.empty() && m.t - t0 < max_steps) {
     const int64_t k = std::min<int64_t>(K, max_steps - (m.t - t0));
+    // a whole window: in the model's mode, or, until both modes have been
+    // timed on a window of this solve, the one not timed yet
+    int mode = -1;
     if (k == K) {
-      OM_TRY(capture_t<T>(b, model, K));
-      OM_CUDA(cudaGraphLaunch(m.exec, s));
-      m.t += K;
-      if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
+      mode = m.mode >= 0 ? m.mode : (m.trial_ms[0] < 0.f ? 0 : 1);
+      *b->bar_h = OM_OK;
+      if (mode == 0) OM_TRY(capture_t<T>(b, model, K));  // host work outside the timed window
+      OM_CUDA(cudaEventRecord(w0, s));
+      OM_TRY(window_t<T>(b, model, K, mode, s));
+      OM_CUDA(cudaEventRecord(w1, s));
     } else {
       OM_TRY(steps_t<T>(b, model, k, s));
     }
     for (int a : active) updates += (int64_t)b->items_h[a].nf * k;
-    OM_TRY(observe_t<T>(b, model, (int)active.size(), s));
+    OM_TRY(observe_t<T>(b, model, (int)active.size(), s));  // synchronises
+    if (mode == 1 && *b->bar_h != OM_OK) {
+      for (cudaEvent_t e : {e0, e1, w0, w1}) cudaEventDestroy(e);
+      return fail(OM_ETIMEOUT, "om_batch_solve: a grid-barrier wait of a persistent window gave up");
+    }
+    if (mode >= 0 && m.mode < 0) {
+      float ms = 0.f;
+      OM_CUDA(cudaEventElapsedTime(&ms, w0, w1));
+      m.trial_ms[mode] = ms;
+      if (m.trial_ms[0] >= 0.f && m.trial_ms[1] >= 0.f) m.mode = m.trial_ms[1] < m.trial_ms[0] ? 1 : 0;
+    }
     std::vector<int> keep;
     for (size_t a = 0; a < active.size(); ++a) {
       const int it = active[a];
@@ -824,6 +1000,8 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
   OM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(w0);
+  cudaEventDestroy(w1);
   if (info)
     for (int k = 0; k < b->n; ++k) {
       info[k].seconds = ms * 1e-3;
@@ -869,6 +1047,8 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
   cudaFree(b->range);
   cudaFree(b->partials);
   cudaFree(b->obs);
+  cudaFree(b->bar);
+  if (b->bar_h) cudaFreeHost(b->bar_h);
   if (b->work_h) cudaFreeHost(b->work_h);
   if (b->range_h) cudaFreeHost(b->range_h);
   if (b->nwork_h) cudaFreeHost(b->nwork_h);
@@ -961,6 +1141,9 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if ((st = halloc((void**)&b->nwork_h, sizeof(int))) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->gcnt_h, sizeof(int) * n)) != OM_OK) return bail(st);
   if ((st = halloc((void**)&b->obs_h, sizeof(double) * 5 * n)) != OM_OK) return bail(st);
+  if ((st = dalloc((void**)&b->bar, sizeof(GridBar))) != OM_OK) return bail(st);
+  if ((st = halloc((void**)&b->bar_h, sizeof(int))) != OM_OK) return bail(st);
+  *b->bar_h = OM_OK;
   if (cudaMemcpyAsync(b->items, b->items_h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return bail(fail(OM_ECUDA, "om_batch_create: copy of the item table failed"));
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
@@ -1025,6 +1208,46 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
 extern "C" om_status om_batch_step(om_batch* b, int32_t model, int64_t nsteps, void* stream) {
   if (!b || model < 0 || model > 1 || !b->m[model].on || nsteps < 0) return fail(OM_EINVAL, "om_batch_step: bad arguments");
   OM_BATCH_DISPATCH(b->m[model].prec, steps_t, b, model, nsteps, as_stream(stream));
+}
+
+extern "C" om_status om_batch_set_window_mode(om_batch* b, int32_t model, int32_t mode) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on || mode < -1 || mode > 1)
+    return fail(OM_EINVAL, "om_batch_set_window_mode: bad arguments");
+  Model& m = b->m[model];
+  m.mode = mode;
+  m.trial_ms[0] = m.trial_ms[1] = -1.f;
+  return OM_OK;
+}
+
+extern "C" om_status om_barrier_selftest(int32_t blocks, int32_t rounds, int32_t extra, int64_t max_polls,
+                                         int32_t* status, void* stream) {
+  if (blocks <= 0 || rounds < 0 || extra < 0 || max_polls <= 0 || !status)
+    return fail(OM_EINVAL, "om_barrier_selftest: bad arguments");
+  int dev = 0, sms = 0, per = 0;
+  OM_CUDA(cudaGetDevice(&dev));
+  OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  OM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, barrier_selftest, kTile, 0));
+  if ((int64_t)blocks > (int64_t)per * sms)
+    return fail(OM_EINVAL, "om_barrier_selftest: more blocks than can be resident at once");
+  cudaStream_t s = as_stream(stream);
+  GridBar* bar = nullptr;
+  if (cudaMalloc((void**)&bar, sizeof(GridBar)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(OM_ENOMEM, "om_barrier_selftest: device allocation failed");
+  }
+  unsigned ex = (unsigned)extra;
+  unsigned long long lim = (unsigned long long)max_polls;
+  void* args[] = {&bar, &rounds, &ex, &lim};
+  int st = OM_OK;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void*)barrier_selftest, dim3(blocks), dim3(kTile), args, 0, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, &bar->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(bar);
+  if (e != cudaSuccess) return cuda_fail(e, "om_barrier_selftest", __FILE__, __LINE__);
+  *status = st;
+  return OM_OK;
 }
 
 extern "C" om_status om_batch_solve(om_batch* b, int32_t model, double* result, double* aux, om_run_info* info,

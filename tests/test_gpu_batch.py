@@ -1,7 +1,10 @@
-"""Batched solves (om_batch_*): many structures advanced together by one
-persistent launch per step, a graph-replayed check window and per-structure
-early retirement.  Parity with the oracle per step (random populations, FP64
-and FP32) and at convergence, plus structures without nodes."""
+"""Batched solves (om_batch_*): many structures advanced together over a
+work list of tiles, a check window replayed from a captured graph of
+per-step launches or run as one persistent cooperative launch per group
+with grid barriers between steps, and per-structure early retirement.
+Parity with the oracle per step (random populations, FP64 and FP32) and at
+convergence, identical bits in both window modes, structures without nodes,
+and the bounded barrier wait."""
 import numpy as np
 import pytest
 import torch
@@ -166,3 +169,73 @@ def test_batch_matches_single_structure_solver(orc, om):
         assert status[k] == om.OM_OK and s1 == om.OM_OK
         assert kl[k] == pytest.approx(k1, rel=1e-6)
         assert abs(info[k].steps - i1.steps) <= 100
+
+
+# ------------------------------------------------------------------ persistent windows
+def _window_run(om, masks, d, prec, mode, K=100, windows=12):
+    """Populations of both models after a solve that runs `windows` whole
+    windows (a test of 0 is never met) in window mode `mode`."""
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks], [_dev(x) for x in d],
+                 flow=om.flow_params(conv_tol=0.0, check_every=K, max_steps=K * windows, precision=prec),
+                 diff=om.diff_params(conv_tol=0.0, check_every=K, max_steps=K * windows, precision=prec))
+    b.set_window_mode(0, mode)
+    b.set_window_mode(1, mode)
+    kl, _, _, st_f = b.solve(0)
+    dl, _, _, st_d = b.solve(1)
+    pops = []
+    for model, q in ((0, 19), (1, 7)):
+        for k, m in enumerate(masks):
+            out = torch.empty(q * m.size, dtype=torch.float64, device="cuda")
+            b.get_populations(model, k, out)
+            pops.append(out.cpu().numpy())
+    b.close()
+    return kl, dl, st_f, st_d, pops
+
+
+# A persistent window (one cooperative launch per group, grid barriers
+# between steps) does per step exactly the node updates of the per-step
+# launches, so both modes give the same bits, in every storage format, for
+# small items packed into one group and for items of a group of their own
+# with more tiles than the grid has blocks.
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("prec", ["OM_F64", "OM_F32", "OM_F16DEV"])
+def test_persistent_windows_equal_graph_windows(orc, om, prec):
+    st = _structures(orc)
+    masks = [t for t, _ in st] + [S.random_mask((72, 96, 96), 0.9, 41)]
+    rng = np.random.default_rng(9)
+    d = [x for _, x in st] + [(10 + 50 * rng.random(masks[-1].shape) * masks[-1]).astype(np.float32)]
+    P = getattr(om, prec)
+    a = _window_run(om, masks, d, P, 0)
+    b = _window_run(om, masks, d, P, 1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert list(a[2]) == list(b[2]) and list(a[3]) == list(b[3])
+    assert a[2][-2] == om.OM_ENOPERC  # the item without nodes stays out of both
+    for x, y in zip(a[4], b[4]):
+        assert np.array_equal(x, y)
+
+
+def test_default_window_mode_times_both_and_matches(orc, om):
+    # mode -1: the first two windows of the first solve run one in each mode
+    st = _structures(orc)
+    masks = [t for t, _ in st]
+    d = [x for _, x in st]
+    a = _window_run(om, masks, d, om.OM_F32, 0, windows=6)
+    b = _window_run(om, masks, d, om.OM_F32, -1, windows=6)
+    for x, y in zip(a[4], b[4]):
+        assert np.array_equal(x, y)
+
+
+# The grid barrier's waits are bounded: a barrier that expects one block more
+# than the launch has can never complete, every wait gives up after its poll
+# limit, the status reports it, the launch ends and the context stays usable.
+def test_grid_barrier_wait_is_bounded(om):
+    import time
+    assert om.om_barrier_selftest(2 * 152, 200, 0, 20_000_000) == om.OM_OK
+    t = time.perf_counter()
+    assert om.om_barrier_selftest(8, 3, 1, 20_000) == om.OM_ETIMEOUT
+    assert time.perf_counter() - t < 10.0
+    x = torch.arange(10, device="cuda", dtype=torch.float32)
+    assert float(x.sum()) == 45.0
+    assert om.om_barrier_selftest(64, 10, 0, 20_000_000) == om.OM_OK
+    with pytest.raises(om.OmError):
+        om.om_barrier_selftest(10 ** 6, 1, 0, 1000)  # more blocks than can be resident
