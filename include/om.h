@@ -300,6 +300,23 @@ om_status om_diff_get_fields(const om_diff* df, float* c_dev, float* jx_dev, voi
 om_status om_diff_time(const om_diff* df, int64_t* t);
 om_status om_diff_destroy(om_diff* df);
 
+/* ---------------------------------------------------------------- checkpoint and resume
+ * A solver's evolving state -- its populations exactly as stored, the
+ * diffusion's per-node reference concentration (FP32 and 16-bit storage),
+ * the previous observables of its convergence test and its step counter --
+ * as an opaque host byte image of *_state_size bytes.  Loaded into a solver
+ * of the same node set, kind, precision and lattice (else OM_EINVAL, nothing
+ * changed), the solver continues bit for bit as the saved one would have:
+ * long diffusion runs can stop and resume.  host: caller-owned host memory
+ * (pinned or pageable) of at least the size given; both calls synchronise
+ * the stream. */
+om_status om_flow_state_size(const om_flow* fl, int64_t* bytes);
+om_status om_flow_save_state(const om_flow* fl, void* host, int64_t bytes, void* stream);
+om_status om_flow_load_state(om_flow* fl, const void* host, int64_t bytes, void* stream);
+om_status om_diff_state_size(const om_diff* df, int64_t* bytes);
+om_status om_diff_save_state(const om_diff* df, void* host, int64_t bytes, void* stream);
+om_status om_diff_load_state(om_diff* df, const void* host, int64_t bytes, void* stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent structures (the paper's 150 reconstructions) solved
  * together.  The structures not yet converged are packed into groups whose

@@ -110,6 +110,12 @@ _SIGS = {
     "om_diff_get_fields": [_vp, _vp, _vp, _vp],
     "om_diff_time": [_vp, _i64p],
     "om_diff_destroy": [_vp],
+    "om_flow_state_size": [_vp, _i64p],
+    "om_flow_save_state": [_vp, _vp, C.c_int64, _vp],
+    "om_flow_load_state": [_vp, _vp, C.c_int64, _vp],
+    "om_diff_state_size": [_vp, _i64p],
+    "om_diff_save_state": [_vp, _vp, C.c_int64, _vp],
+    "om_diff_load_state": [_vp, _vp, C.c_int64, _vp],
     "om_batch_create": [C.c_int32, C.POINTER(om_domain), C.POINTER(_vp), C.POINTER(_vp),
                         C.POINTER(om_flow_params), C.POINTER(om_diff_params), _vp, C.POINTER(_vp)],
     "om_batch_step": [_vp, C.c_int32, C.c_int64, _vp],
@@ -380,6 +386,19 @@ class Flow:
     def init_velocity(self, ux_dev, stride=1, scale=1.0, stream=None):
         _call("om_flow_init_velocity", self.h, _ptr(ux_dev), stride, scale, _stream(stream))
 
+    def save_state(self, stream=None):
+        """The solver's whole evolving state as a host byte array (om_flow_save_state)."""
+        n = C.c_int64()
+        _call("om_flow_state_size", self.h, C.byref(n))
+        buf = np.empty(n.value, np.uint8)
+        _call("om_flow_save_state", self.h, _ptr(buf), n.value, _stream(stream))
+        return buf
+
+    def load_state(self, buf, stream=None):
+        """Continue from a state saved by save_state (om_flow_load_state)."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _call("om_flow_load_state", self.h, _ptr(buf), buf.size, _stream(stream))
+
     @property
     def time(self):
         t = C.c_int64()
@@ -432,6 +451,19 @@ class Diffusion:
 
     def init_concentration(self, c_dev, stride=1, from_linear=False, stream=None):
         _call("om_diff_init_concentration", self.h, _ptr(c_dev), stride, int(from_linear), _stream(stream))
+
+    def save_state(self, stream=None):
+        """The solver's whole evolving state as a host byte array (om_diff_save_state)."""
+        n = C.c_int64()
+        _call("om_diff_state_size", self.h, C.byref(n))
+        buf = np.empty(n.value, np.uint8)
+        _call("om_diff_save_state", self.h, _ptr(buf), n.value, _stream(stream))
+        return buf
+
+    def load_state(self, buf, stream=None):
+        """Continue from a state saved by save_state (om_diff_load_state)."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _call("om_diff_load_state", self.h, _ptr(buf), buf.size, _stream(stream))
 
     @property
     def time(self):
