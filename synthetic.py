@@ -133,6 +133,20 @@ def sphere_in_cube(L):
     return (~solid).astype(np.uint8)
 
 
+def bcc_array(L, porosity):
+    """Cube of side L holding one cell of a body-centred cubic array of equal
+    solid spheres (at the corners, with their periodic images, and at the
+    centre), their diameter set by the porosity of the continuous array,
+    1 - 2 (pi/6) d^3 / L^3; the pore space is the rest."""
+    d = L * ((1.0 - porosity) * 6.0 / (2.0 * np.pi)) ** (1.0 / 3.0)
+    x = np.arange(L) + 0.5
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    solid = np.zeros((L, L, L), bool)
+    for cx, cy, cz in [(a, b, c) for a in (0.0, L) for b in (0.0, L) for c in (0.0, L)] + [(L / 2.0,) * 3]:
+        solid |= ((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) <= (d / 2.0) ** 2
+    return (~solid).astype(np.uint8), d
+
+
 def offset_channel(nx=12, ny=10, nz=3, shift=4):
     """Two half-length slits along x, rows y = 1, 2 for x < nx/2 and rows
     y = 1+shift, 2+shift for x >= nx/2, joined by a riser at x = nx/2 - 1,
