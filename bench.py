@@ -636,6 +636,12 @@ def run_precision(a):
         dpar = _parity_us(df, ns.n_nodes, bd, peak)
         df.close()
         out[name] = {"flow_mlups": fm, "diffusion_mlups": dm, "flow_sweeps": fpar, "diffusion_sweeps": dpar}
+        if prec == P.OM_F32:  # the paper's diffusion lattice, for comparison (not a bench line)
+            d19 = P.Diffusion(ns, d, P.diff_params(precision=prec, check_every=WINDOW, lattice=19))
+            m19, _ = _window_mlups(lambda: d19.step(WINDOW), ns.n_nodes, WINDOW, 3)
+            out[name]["diffusion_d3q19_mlups"] = m19
+            out[name]["diffusion_d3q19_sweeps"] = _parity_us(d19, ns.n_nodes, 19 * 4 * 2 + 4, peak)
+            d19.close()
     line = {"metric": "fluid MLUPS by population storage, 512^3", "value": out["f16"]["flow_mlups"], "unit": "MLUPS",
             "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "nodes": ns.n_nodes, "by_storage": out,
             "gain_over_f32": {k: {"flow": v["flow_mlups"] / out["f32"]["flow_mlups"],
