@@ -300,6 +300,27 @@ om_status om_diff_get_fields(const om_diff* df, float* c_dev, float* jx_dev, voi
 om_status om_diff_time(const om_diff* df, int64_t* t);
 om_status om_diff_destroy(om_diff* df);
 
+/* ---------------------------------------------------------------- two-level warm start
+ * Not in the paper: an initial state for a fine diffusion solve from a solve
+ * on the structure coarsened 2x per axis; the fine LB then iterates to its
+ * own convergence test, so the result stays the fine method's.
+ * om_coarse_domain: the coarse domain, ceil(n/2) per axis, voxel 2 dx.
+ * om_coarsen2_dev: coarse voxel (X, Y, Z) covers fine voxels 2X..2X+1 per
+ * axis (clipped at an odd edge); nodes_c = 1 where at least half of those
+ * are nodes of nodes_dev; d_c = mean pore size (nm) over those nodes (0 if
+ * none).  d_nm_dev and d_c_dev both NULL to skip pore sizes.  uint8 / float
+ * arrays of N (fine) and N_c (coarse) voxels, device, caller-owned.
+ * om_prolong2_dev: fine concentration c_dev (float N) from the coarse dense
+ * populations g_c_dev (double q x N_c, the layout of om_diff_get_populations
+ * / om_batch_get_populations): the sum over i at the covering coarse voxel
+ * where nodes_c is 1, else the linear profile between c_in and c_out.
+ * Both asynchronous on stream. */
+om_status om_coarse_domain(om_domain d, om_domain* dc);
+om_status om_coarsen2_dev(const uint8_t* nodes_dev, const float* d_nm_dev, om_domain d, uint8_t* nodes_c_dev,
+                          float* d_c_dev, void* stream);
+om_status om_prolong2_dev(const double* g_c_dev, int32_t q, const uint8_t* nodes_c_dev, om_domain d, double c_in,
+                          double c_out, float* c_dev, void* stream);
+
 /* ---------------------------------------------------------------- checkpoint and resume
  * A solver's evolving state -- its populations exactly as stored, the
  * diffusion's per-node reference concentration (FP32 and 16-bit storage),

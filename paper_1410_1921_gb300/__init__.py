@@ -110,6 +110,9 @@ _SIGS = {
     "om_diff_get_fields": [_vp, _vp, _vp, _vp],
     "om_diff_time": [_vp, _i64p],
     "om_diff_destroy": [_vp],
+    "om_coarse_domain": [om_domain, C.POINTER(om_domain)],
+    "om_coarsen2_dev": [_vp, _vp, om_domain, _vp, _vp, _vp],
+    "om_prolong2_dev": [_vp, C.c_int32, _vp, om_domain, C.c_double, C.c_double, _vp, _vp],
     "om_flow_state_size": [_vp, _i64p],
     "om_flow_save_state": [_vp, _vp, C.c_int64, _vp],
     "om_flow_load_state": [_vp, _vp, C.c_int64, _vp],
@@ -538,6 +541,28 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def om_coarse_domain(dom):
+    dc = om_domain()
+    _call("om_coarse_domain", dom, C.byref(dc))
+    return dc
+
+
+def om_coarsen2_dev(nodes_dev, dom, d_nm_dev=None, stream=None):
+    """(coarse domain, coarse node mask, coarse pore sizes or None) of a
+    device node mask (and pore sizes), coarsened 2x per axis."""
+    import torch
+    dc = om_coarse_domain(dom)
+    nc = dc.nx * dc.ny * dc.nz
+    nodes_c = torch.empty(nc, dtype=torch.uint8, device=nodes_dev.device)
+    d_c = torch.empty(nc, dtype=torch.float32, device=nodes_dev.device) if d_nm_dev is not None else None
+    _call("om_coarsen2_dev", _ptr(nodes_dev), _ptr(d_nm_dev), dom, _ptr(nodes_c), _ptr(d_c), _stream(stream))
+    return dc, nodes_c, d_c
+
+
+def om_prolong2_dev(g_c_dev, q, nodes_c_dev, dom, c_in, c_out, c_dev, stream=None):
+    _call("om_prolong2_dev", _ptr(g_c_dev), q, _ptr(nodes_c_dev), dom, c_in, c_out, _ptr(c_dev), _stream(stream))
 
 
 def om_barrier_selftest(blocks, rounds, extra, max_polls, stream=None):
