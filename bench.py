@@ -58,10 +58,11 @@ def _args():
     ap.add_argument("--n-train", type=int, default=96, help="converge mode: training structures")
     ap.add_argument("--epochs", type=int, default=60, help="converge mode: U-Net epochs")
     ap.add_argument("--max-steps", type=int, default=500_000, help="converge mode: step cap per solve")
-    ap.add_argument("--warm", default="diffusion", choices=["both", "diffusion", "none", "coarse"],
+    ap.add_argument("--warm", default="diffusion", choices=["both", "diffusion", "none", "coarse", "coarse+net"],
                     help="converge mode: which models the network warm-starts (velocity warm starts "
                          "measured to slow the flow's convergence); 'coarse': the diffusion starts from a "
-                         "batched solve of the structures coarsened 2x per axis instead of the network")
+                         "batched solve of the structures coarsened 2x per axis instead of the network; "
+                         "'coarse+net': from that solve refined by the network")
     return ap.parse_args()
 
 
@@ -406,13 +407,18 @@ def run_converge(a):
     fp = P.flow_params(precision=P.OM_F32, conv_tol=tol, check_every=K, max_steps=cap)
     dp = P.diff_params(precision=P.OM_F32, conv_tol=tol, check_every=K, max_steps=cap)
     fields = ("ux", "c") if a.warm == "both" else ("c",)
-    learned = a.warm in ("both", "diffusion")
+    learned = a.warm in ("both", "diffusion", "coarse+net")
+    refine = a.warm == "coarse+net"
+    # the coarse level: FP16 storage and a 10x looser test (the coarse field
+    # only has to carry the structure-scale modes)
+    dpc = P.diff_params(precision=P.OM_F16DEV, conv_tol=10 * tol, check_every=K, max_steps=cap)
     data, hist, t_data, t_train = [], [None], 0.0, 0.0
     if learned:
         t0 = time.perf_counter()
-        data = W.make_dataset(_converge_set(a.n_train, 11, (64,)), fp, dp, fields=fields)
+        data = W.make_dataset(_converge_set(a.n_train, 11, (64,)), fp, dp, fields=fields, coarse=refine,
+                              dp_coarse=dpc)
         t_data = time.perf_counter() - t0
-        net = P.UNet(2, len(fields), (16, 32, 64, 128), seed=5)
+        net = P.UNet(3 if refine else 2, len(fields), (16, 32, 64, 128), seed=5)
         t0 = time.perf_counter()
         hist = W.train(net, data, epochs=a.epochs, lr=1e-3, lr_end=5e-5)
         torch.cuda.synchronize()
@@ -434,30 +440,28 @@ def run_converge(a):
     t0 = time.perf_counter()
     b = P.Batch([s[1] for s in structs], [s[3] for s in structs], [s[4] for s in structs], flow=fp, diff=fp16)
     coarse_steps = 0
-    if a.warm == "coarse":
-        # the structures coarsened 2x per axis, solved together (FP16 storage,
-        # a 10x looser test: the coarse field only has to carry the
-        # structure-scale modes), their concentration carried to the fine nodes
-        cs = []
-        for _, dom, mask, tr, d in structs:
-            dc, mc, d_c = P.om_coarsen2_dev(tr, dom, d)
-            tr_c = torch.empty_like(mc)
-            P.om_label_connectivity_dev(mc, dc, None, tr_c)
-            cs.append((dc, tr_c, d_c))
-        keep = [k for k, c in enumerate(cs) if bool(c[1].any())]
+    if a.warm in ("coarse", "coarse+net"):
+        # the structures coarsened 2x per axis, solved together, their
+        # concentration carried to the fine nodes (refined by the network)
+        cs = [W.coarse_level(dom, tr, d) for _, dom, mask, tr, d in structs]
+        keep = [k for k, c in enumerate(cs) if c[1] is not None]
+        bc = None
         if keep:
-            dpc = P.diff_params(precision=P.OM_F16DEV, conv_tol=10 * tol, check_every=K, max_steps=cap)
             bc = P.Batch([cs[k][0] for k in keep], [cs[k][1] for k in keep], [cs[k][2] for k in keep], diff=dpc)
             _, _, info_c, _ = bc.solve(1)
             coarse_steps = int(sum(i.steps for i in info_c))
-            for j, k in enumerate(keep):
-                dc = cs[k][0]
-                g = torch.empty(7 * dc.nx * dc.ny * dc.nz, dtype=torch.float64, device="cuda")
-                bc.get_populations(1, j, g)
-                dom = structs[k][1]
-                c = torch.empty(dom.nx * dom.ny * dom.nz, dtype=torch.float32, device="cuda")
-                P.om_prolong2_dev(g, 7, cs[k][1], dom, dpc.c_in, dpc.c_out, c)
-                b.init_fields(1, k, c, stride=1, from_linear=False)
+        for k, (_, dom, mask, tr, d) in enumerate(structs):
+            if k not in keep:
+                if refine:  # no coarse level: the network on a zero coarse departure
+                    zero = torch.zeros(dom.nx * dom.ny * dom.nz, dtype=torch.float32, device="cuda")
+                    b.init_fields(1, k, W.predict(net, mask, d, dom, zero), stride=1, from_linear=True)
+                continue
+            dc, tr_c, _ = cs[k]
+            g = torch.empty(7 * dc.nx * dc.ny * dc.nz, dtype=torch.float64, device="cuda")
+            bc.get_populations(1, keep.index(k), g)
+            y = W.predict(net, mask, d, dom, W.prolonged(g, tr_c, dom, dpc, departure=True)) if refine else None
+            b.init_fields(1, k, W.prolonged(g, tr_c, dom, dpc, corr=y), stride=1, from_linear=False)
+        if bc is not None:
             bc.close()
     elif a.warm != "none":
         nch, ci = len(fields), fields.index("c")
@@ -485,8 +489,8 @@ def run_converge(a):
     resolved = (P.OM_OK, P.OM_ENOPERC)  # ENOPERC: k = 0 exactly, on both sides
     dk = max(rel(kl[i], p["k_lattice"]) for i, p in enumerate(plain))
     dD = max(rel(dl[i], p["D_lattice"]) for i, p in enumerate(plain))
-    warm_name = {"coarse": "two-level (2x coarsened solve) warm start", "none": "no warm start"}.get(
-        a.warm, "U-Net warm start")
+    warm_name = {"coarse": "two-level (2x coarsened solve) warm start", "none": "no warm start",
+                 "coarse+net": "two-level warm start refined by the U-Net"}.get(a.warm, "U-Net warm start")
     line = {"metric": f"time to converged k, D_eff: plain / (batched + FP16 diffusion + {warm_name})",
             "value": t_plain / t_fast, "unit": "x", "higher_is_better": True, "n_gpus": 1,
             "plain_s": t_plain, "fast_s": t_fast, "structures": len(structs),

@@ -313,13 +313,20 @@ om_status om_diff_destroy(om_diff* df);
  * om_prolong2_dev: fine concentration c_dev (float N) from the coarse dense
  * populations g_c_dev (double q x N_c, the layout of om_diff_get_populations
  * / om_batch_get_populations): the sum over i at the covering coarse voxel
- * where nodes_c is 1, else the linear profile between c_in and c_out.
- * Both asynchronous on stream. */
+ * where nodes_c is 1, else the linear profile C_lin(x) between c_in and
+ * c_out; minus C_lin when departure != 0; plus corr_dev[v * corr_stride]
+ * when corr_dev is not NULL (a learned correction).
+ * om_unet_pack_structure3: the network input of the refining warm start,
+ * float [N][3] = (node mask, d * d_scale, extra), extra = the prolonged
+ * coarse departure.  All asynchronous on stream. */
 om_status om_coarse_domain(om_domain d, om_domain* dc);
 om_status om_coarsen2_dev(const uint8_t* nodes_dev, const float* d_nm_dev, om_domain d, uint8_t* nodes_c_dev,
                           float* d_c_dev, void* stream);
 om_status om_prolong2_dev(const double* g_c_dev, int32_t q, const uint8_t* nodes_c_dev, om_domain d, double c_in,
-                          double c_out, float* c_dev, void* stream);
+                          double c_out, const float* corr_dev, int64_t corr_stride, int32_t departure, float* c_dev,
+                          void* stream);
+om_status om_unet_pack_structure3(const uint8_t* mask_dev, const float* d_nm_dev, double d_scale,
+                                  const float* extra_dev, int64_t n, float* x_dev, void* stream);
 
 /* ---------------------------------------------------------------- checkpoint and resume
  * A solver's evolving state -- its populations exactly as stored, the

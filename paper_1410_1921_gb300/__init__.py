@@ -112,7 +112,8 @@ _SIGS = {
     "om_diff_destroy": [_vp],
     "om_coarse_domain": [om_domain, C.POINTER(om_domain)],
     "om_coarsen2_dev": [_vp, _vp, om_domain, _vp, _vp, _vp],
-    "om_prolong2_dev": [_vp, C.c_int32, _vp, om_domain, C.c_double, C.c_double, _vp, _vp],
+    "om_prolong2_dev": [_vp, C.c_int32, _vp, om_domain, C.c_double, C.c_double, _vp, C.c_int64, C.c_int32, _vp, _vp],
+    "om_unet_pack_structure3": [_vp, _vp, C.c_double, _vp, C.c_int64, _vp, _vp],
     "om_flow_state_size": [_vp, _i64p],
     "om_flow_save_state": [_vp, _vp, C.c_int64, _vp],
     "om_flow_load_state": [_vp, _vp, C.c_int64, _vp],
@@ -561,8 +562,15 @@ def om_coarsen2_dev(nodes_dev, dom, d_nm_dev=None, stream=None):
     return dc, nodes_c, d_c
 
 
-def om_prolong2_dev(g_c_dev, q, nodes_c_dev, dom, c_in, c_out, c_dev, stream=None):
-    _call("om_prolong2_dev", _ptr(g_c_dev), q, _ptr(nodes_c_dev), dom, c_in, c_out, _ptr(c_dev), _stream(stream))
+def om_prolong2_dev(g_c_dev, q, nodes_c_dev, dom, c_in, c_out, c_dev, corr_dev=None, corr_stride=1, departure=False,
+                    stream=None):
+    _call("om_prolong2_dev", _ptr(g_c_dev), q, _ptr(nodes_c_dev), dom, c_in, c_out, _ptr(corr_dev), corr_stride,
+          int(departure), _ptr(c_dev), _stream(stream))
+
+
+def om_unet_pack_structure3(mask_dev, d_nm_dev, d_scale, extra_dev, x_dev, stream=None):
+    _call("om_unet_pack_structure3", _ptr(mask_dev), _ptr(d_nm_dev), d_scale, _ptr(extra_dev), mask_dev.numel(),
+          _ptr(x_dev), _stream(stream))
 
 
 def om_barrier_selftest(blocks, rounds, extra, max_polls, stream=None):

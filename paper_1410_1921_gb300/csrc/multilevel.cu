@@ -13,7 +13,9 @@
 // voxels it covers are nodes, and its pore size is the mean of theirs.
 // Prolongation: a fine node takes the concentration of the coarse voxel
 // that covers it when that is a coarse node, else the linear inlet-outlet
-// profile C_lin(x).
+// profile C_lin(x); optionally as the departure from C_lin (an input of the
+// warm-start network) and plus a per-voxel correction (the network's
+// output), so that the network refines the coarse solution.
 #include "common.cuh"
 
 namespace om {
@@ -46,19 +48,23 @@ __global__ void coarsen2(const uint8_t* __restrict__ nodes, const float* __restr
 }
 
 __global__ void prolong2(const double* __restrict__ g_c, int q, const uint8_t* __restrict__ nodes_c, int cx, int cy,
-                         int cz, int nx, int ny, int nz, double c_in, double c_out, float* __restrict__ c) {
+                         int cz, int nx, int ny, int nz, double c_in, double c_out, const float* __restrict__ corr,
+                         int64_t corr_stride, int departure, float* __restrict__ c) {
   const int64_t n = (int64_t)nx * ny * nz, nc = (int64_t)cx * cy * cz;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(v / ((int64_t)ny * nz));
     const int y = (int)((v / nz) % ny);
     const int z = (int)(v % nz);
     const int64_t k = ((int64_t)(x / 2) * cy + y / 2) * cz + z / 2;
-    double val = c_in + (c_out - c_in) * ((double)x + 0.5) / (double)nx;  // C_lin(x)
+    const double clin = c_in + (c_out - c_in) * ((double)x + 0.5) / (double)nx;  // C_lin(x)
+    double val = clin;
     if (nodes_c[k]) {
       double s = 0.0;
       for (int i = 0; i < q; ++i) s += g_c[(int64_t)i * nc + k];
       val = s;
     }
+    if (departure) val -= clin;
+    if (corr) val += (double)corr[v * corr_stride];
     c[v] = (float)val;
   }
 }
@@ -100,12 +106,15 @@ extern "C" om_status om_coarsen2_dev(const uint8_t* nodes_dev, const float* d_nm
 }
 
 extern "C" om_status om_prolong2_dev(const double* g_c_dev, int32_t q, const uint8_t* nodes_c_dev, om_domain d,
-                                     double c_in, double c_out, float* c_dev, void* stream) {
-  if (!g_c_dev || !nodes_c_dev || !c_dev || q < 1 || q > 27) return fail(OM_EINVAL, "om_prolong2_dev: bad argument");
+                                     double c_in, double c_out, const float* corr_dev, int64_t corr_stride,
+                                     int32_t departure, float* c_dev, void* stream) {
+  if (!g_c_dev || !nodes_c_dev || !c_dev || q < 1 || q > 27 || (corr_dev && corr_stride < 1))
+    return fail(OM_EINVAL, "om_prolong2_dev: bad argument");
   OM_TRY(check_domain(d));
   const om_domain c = coarse_domain(d);
   prolong2<<<grid_for(voxels(d)), 256, 0, as_stream(stream)>>>(g_c_dev, q, nodes_c_dev, c.nx, c.ny, c.nz, d.nx, d.ny,
-                                                              d.nz, c_in, c_out, c_dev);
+                                                              d.nz, c_in, c_out, corr_dev, corr_stride, departure,
+                                                              c_dev);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }

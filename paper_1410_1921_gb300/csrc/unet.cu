@@ -667,6 +667,14 @@ __global__ void pack_structure(const uint8_t* mask, const float* d, int64_t n, f
     x[2 * v + 1] = d[v] * ds;
   }
 }
+
+__global__ void pack_structure3(const uint8_t* mask, const float* d, const float* e, int64_t n, float ds, float* x) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    x[3 * v] = mask[v] ? 1.f : 0.f;
+    x[3 * v + 1] = d[v] * ds;
+    x[3 * v + 2] = e[v];
+  }
+}
 }  // namespace nn
 }  // namespace om
 
@@ -676,6 +684,17 @@ extern "C" om_status om_unet_pack_structure(const uint8_t* mask_dev, const float
   if (n == 0) return OM_OK;
   om::nn::pack_structure<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1 << 20), 256, 0, as_stream(stream)>>>(
       mask_dev, d_nm_dev, n, (float)d_scale, x_dev);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+extern "C" om_status om_unet_pack_structure3(const uint8_t* mask_dev, const float* d_nm_dev, double d_scale,
+                                            const float* extra_dev, int64_t n, float* x_dev, void* stream) {
+  if (!mask_dev || !d_nm_dev || !extra_dev || !x_dev || n < 0)
+    return fail(OM_EINVAL, "om_unet_pack_structure3: bad argument");
+  if (n == 0) return OM_OK;
+  om::nn::pack_structure3<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1 << 20), 256, 0, as_stream(stream)>>>(
+      mask_dev, d_nm_dev, extra_dev, n, (float)d_scale, x_dev);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }

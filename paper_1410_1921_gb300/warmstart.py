@@ -9,6 +9,11 @@ Targets per voxel, the network's output channels in the order of `fields`:
 "ux" = u_x / U0 with U0 = g L0^2 / nu (L0 = 10 lattice units), "c" = C -
 C_lin(x), the concentration's departure from the linear inlet-outlet profile;
 the loss is taken over the node set.  Inputs: pore mask and d / 60 nm.
+
+Refining form (coarse=True): a third input channel holds the departure of
+the structure's 2x-coarsened diffusion solution (solved, then carried to the
+fine voxels), and the network predicts the fine solution's difference from
+it; the warm start is the coarse solution plus the prediction.
 """
 import time
 
@@ -16,8 +21,8 @@ import numpy as np
 import torch
 
 from . import (OM_ENOPERC, OM_F32, OM_OK, OM_PORE_CHORD13, Diffusion, Flow, NodeSet, UNet, diff_params, domain,
-               flow_params, om_label_connectivity_dev, om_local_pore_diameter_dev, om_reconstruct_dev,
-               om_unet_pack_structure, recon_params)
+               flow_params, om_coarsen2_dev, om_label_connectivity_dev, om_local_pore_diameter_dev,
+               om_prolong2_dev, om_reconstruct_dev, om_unet_pack_structure, om_unet_pack_structure3, recon_params)
 
 D_SCALE = 1.0 / 60.0
 L0 = 10.0
@@ -45,10 +50,48 @@ def structure(cfg, stream=None):
     return dom, mask, tr, d
 
 
-def net_input(mask, d, dom):
-    x = torch.empty(mask.numel() * 2, dtype=torch.float32, device="cuda")
-    om_unet_pack_structure(mask, d, D_SCALE, x)
-    return x.view(1, dom.nx, dom.ny, dom.nz, 2)
+def net_input(mask, d, dom, extra=None):
+    if extra is None:
+        x = torch.empty(mask.numel() * 2, dtype=torch.float32, device="cuda")
+        om_unet_pack_structure(mask, d, D_SCALE, x)
+        return x.view(1, dom.nx, dom.ny, dom.nz, 2)
+    x = torch.empty(mask.numel() * 3, dtype=torch.float32, device="cuda")
+    om_unet_pack_structure3(mask, d, D_SCALE, extra, x)
+    return x.view(1, dom.nx, dom.ny, dom.nz, 3)
+
+
+def coarse_level(dom, tr, d):
+    """The structure coarsened 2x per axis: (coarse domain, coarse transport
+    set, coarse pore sizes); the transport set is None when nothing of the
+    coarse structure spans x."""
+    dc, mc, d_c = om_coarsen2_dev(tr, dom, d)
+    tr_c = torch.empty_like(mc)
+    om_label_connectivity_dev(mc, dc, None, tr_c)
+    return dc, (tr_c if bool(tr_c.any()) else None), d_c
+
+
+def prolonged(g_c, tr_c, dom, dp, departure=False, corr=None):
+    """Fine float [N] field from the coarse dense populations g_c: the coarse
+    concentration (or its departure from C_lin), plus corr if given."""
+    c = torch.empty(dom.nx * dom.ny * dom.nz, dtype=torch.float32, device="cuda")
+    om_prolong2_dev(g_c, 7, tr_c, dom, dp.c_in, dp.c_out, c, corr_dev=corr, departure=departure)
+    return c
+
+
+def coarse_departure(dom, tr, d, dp):
+    """Departure from C_lin of the coarse-level diffusion solution carried to
+    the fine voxels (zeros where the coarse structure does not span x)."""
+    dc, tr_c, d_c = coarse_level(dom, tr, d)
+    if tr_c is None:
+        return torch.zeros(dom.nx * dom.ny * dom.nz, dtype=torch.float32, device="cuda")
+    ns = NodeSet(tr_c, dc)
+    df = Diffusion(ns, d_c, dp)
+    df.solve()
+    g = torch.empty(7 * dc.nx * dc.ny * dc.nz, dtype=torch.float64, device="cuda")
+    df.get_populations(g)
+    df.close()
+    ns.close()
+    return prolonged(g, tr_c, dom, dp, departure=True)
 
 
 def solve(dom, tr, d, fp, dp, prediction=None, warm_flow=False, fields=FIELDS, flow=True):
@@ -107,14 +150,19 @@ def targets(res, dom, fp, dp, fields=FIELDS):
     return torch.from_numpy(t).cuda()
 
 
-def make_dataset(cfgs, fp=None, dp=None, log=None, fields=FIELDS):
+def make_dataset(cfgs, fp=None, dp=None, log=None, fields=FIELDS, coarse=False, dp_coarse=None):
     """Solve every structure (cold, FP32) and keep (input, target, mask) of
     those whose solves reached the convergence test (a flow with no link
     across the periodic x boundary counts: its field is exactly u = 0).  The
-    flow is solved only when "ux" is among the fields."""
+    flow is solved only when "ux" is among the fields.  coarse: the refining
+    form (fields must be ("c",)): the input carries the coarse-level
+    departure (solved with dp_coarse) and the target is the fine departure
+    minus it."""
     fp = fp or flow_params(precision=OM_F32)
     dp = dp or diff_params(precision=OM_F32)
     flow = "ux" in fields
+    if coarse and tuple(fields) != ("c",):
+        raise ValueError("the refining form predicts the concentration only")
     data = []
     for cfg in cfgs:
         dom, mask, tr, d = structure(cfg)
@@ -123,7 +171,13 @@ def make_dataset(cfgs, fp=None, dp=None, log=None, fields=FIELDS):
         res = solve(dom, tr, d, fp, dp, flow=flow)
         if (flow and res["flow_status"] not in (OM_OK, OM_ENOPERC)) or res["diff_status"] != OM_OK:
             continue
-        data.append((net_input(mask, d, dom), targets(res, dom, fp, dp, fields), tr.view(1, dom.nx, dom.ny, dom.nz)))
+        t = targets(res, dom, fp, dp, fields)
+        extra = None
+        if coarse:
+            extra = coarse_departure(dom, tr, d, dp_coarse or dp)
+            # host-side target assembly: the fine departure minus the coarse one
+            t = torch.from_numpy(t.cpu().numpy() - extra.cpu().numpy().reshape(t.shape)).cuda()
+        data.append((net_input(mask, d, dom, extra), t, tr.view(1, dom.nx, dom.ny, dom.nz)))
         if log:
             log(f"sample {len(data)}: {cfg.shape} eps={cfg.porosity:.2f} nodes={res['nodes']} "
                 f"flow {res.get('flow_steps', 0)} diff {res['diff_steps']} steps")
@@ -150,9 +204,10 @@ def train(net, data, epochs, lr=1e-3, lr_end=1e-4, seed=0, log=None):
     return hist
 
 
-def predict(net, mask, d, dom):
-    """Network output, flat float [N][net.out_ch] on the device."""
-    x = net_input(mask, d, dom)
+def predict(net, mask, d, dom, extra=None):
+    """Network output, flat float [N][net.out_ch] on the device (extra: the
+    coarse departure input of the refining form)."""
+    x = net_input(mask, d, dom, extra)
     y = torch.empty(mask.numel() * net.out_ch, dtype=torch.float32, device="cuda")
     net.forward(x, y)
     return y

@@ -72,6 +72,26 @@ def test_prolong_matches_definition(om, shape, seed, q):
                 else:
                     ref[x, y, z] = np.float32(0.9 + (0.1 - 0.9) * (x + 0.5) / shape[0])
     assert np.array_equal(got, ref)
+    # departure from C_lin, plus a strided correction
+    corr = S.random_field((int(np.prod(shape)), 2), seed + 2, -0.05, 0.05).astype(np.float32)
+    om.om_prolong2_dev(_dev(g), q, _dev(mc), dom, 0.9, 0.1, out, corr_dev=_dev(corr), corr_stride=2, departure=True)
+    # the FP64 value of the same steps, rounded once
+    exact = np.zeros(shape)
+    for xx in range(shape[0]):
+        for y in range(shape[1]):
+            for z in range(shape[2]):
+                X, Y, Z = xx // 2, y // 2, z // 2
+                cl = 0.9 + (0.1 - 0.9) * (xx + 0.5) / shape[0]
+                if mc[X, Y, Z]:
+                    s = 0.0
+                    for i in range(q):
+                        s += float(g[i, X, Y, Z])
+                    v = s - cl
+                else:
+                    v = cl - cl
+                v += float(corr[(xx * shape[1] + y) * shape[2] + z, 0])
+                exact[xx, y, z] = v
+    assert np.array_equal(out.cpu().numpy().reshape(shape), exact.astype(np.float32))
 
 
 @pytest.mark.timeout(600)
