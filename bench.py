@@ -470,7 +470,11 @@ def run_converge(a):
             if a.warm == "both":
                 b.init_fields(0, k, y[fields.index("ux"):], stride=nch, scale=W.velocity_scale(fp))
             b.init_fields(1, k, y[ci:], stride=nch, from_linear=True)
+    torch.cuda.synchronize()
+    t_warm = time.perf_counter() - t0
     kl, _, info_f, st_f = b.solve(0)
+    torch.cuda.synchronize()
+    t_flow = time.perf_counter() - t0 - t_warm
     dl, _, info_d, st_d = b.solve(1)
     torch.cuda.synchronize()
     t_fast = time.perf_counter() - t0
@@ -493,7 +497,9 @@ def run_converge(a):
                  "coarse+net": "two-level warm start refined by the U-Net"}.get(a.warm, "U-Net warm start")
     line = {"metric": f"time to converged k, D_eff: plain / (batched + FP16 diffusion + {warm_name})",
             "value": t_plain / t_fast, "unit": "x", "higher_is_better": True, "n_gpus": 1,
-            "plain_s": t_plain, "fast_s": t_fast, "structures": len(structs),
+            "plain_s": t_plain, "fast_s": t_fast,
+            "fast_split_s": {"batch_and_warm_start": t_warm, "flow": t_flow, "diffusion": t_fast - t_warm - t_flow},
+            "structures": len(structs),
             "max_rel_diff_k": dk, "max_rel_diff_D_eff": dD,
             "plain_steps": {"flow": int(sum(p["flow_steps"] for p in plain)),
                             "diffusion": int(sum(p["diff_steps"] for p in plain))},
