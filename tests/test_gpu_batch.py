@@ -239,3 +239,56 @@ def test_grid_barrier_wait_is_bounded(om):
     assert om.om_barrier_selftest(64, 10, 0, 20_000_000) == om.OM_OK
     with pytest.raises(om.OmError):
         om.om_barrier_selftest(10 ** 6, 1, 0, 1000)  # more blocks than can be resident
+
+
+# ------------------------------------------------------------------ the 150-structure set at full size
+# The batched configuration bench.py times (all structures of the
+# 150-structure set with transport pores in one batch, L2 groups and solo
+# groups, tuned launch shapes, FP32): random states in three items of
+# different sizes, three steps of the whole batch, and nodes sampled in
+# those items against the oracle on periodic crops around them (the state of
+# a node after s steps depends only on nodes within s cells).
+@pytest.mark.timeout(1200)
+def test_150_set_batch_sampled(orc, om):
+    from paper_1410_1921_gb300 import warmstart as W
+    items = []
+    for cfg in S.batch_structures():
+        dom, mask, tr, d = W.structure(cfg)
+        if int(tr.sum().item()) > 0:
+            items.append((cfg, dom, tr, d))
+    doms = [it[1] for it in items]
+    tau, gforce = 1.0, 1e-6
+    b = om.Batch(doms, [it[2] for it in items], [it[3] for it in items],
+                 flow=om.flow_params(tau=tau, body_force=gforce, precision=om.OM_F32),
+                 diff=om.diff_params(precision=om.OM_F32))
+    sizes = np.array([int(it[2].sum().item()) for it in items])
+    picks = [int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(np.argmax(sizes))]
+    w = torch.tensor(orc.weights19(), dtype=torch.float64, device="cuda")
+    f0s = {}
+    for k in picks:
+        tr = items[k][2]
+        gen = torch.Generator(device="cuda").manual_seed(100 + k)
+        dev = (1e-3 * (torch.rand(19, tr.numel(), generator=gen, device="cuda", dtype=torch.float32) - 0.5)).double()
+        f0s[k] = (w[:, None] + dev) * tr.double()[None]
+        b.set_populations(0, k, f0s[k].reshape(-1))
+    steps = 3
+    b.step(0, steps)
+    h = steps + 1
+    for k in picks:
+        cfg, dom, tr, _ = items[k]
+        shape = cfg.shape
+        out = torch.empty(19 * tr.numel(), dtype=torch.float64, device="cuda")
+        b.get_populations(0, k, out)
+        got = out.view(19, *shape)
+        tr_np = tr.cpu().numpy().reshape(shape)
+        f0v = f0s[k].view(19, *shape)
+        pts = np.argwhere(tr_np)
+        pts = pts[np.random.default_rng(k).choice(len(pts), min(12, len(pts)), replace=False)]
+        for p in pts:
+            idx = [torch.arange(p[a] - h, p[a] + h + 1, device="cuda") % shape[a] for a in range(3)]
+            fc = f0v[:, idx[0][:, None, None], idx[1][None, :, None], idx[2][None, None, :]].cpu().numpy()
+            mc = tr_np[np.ix_(*[np.arange(p[a] - h, p[a] + h + 1) % shape[a] for a in range(3)])]
+            ref = orc.flow_step(mc, fc, tau, gforce, steps)[:, h, h, h]
+            gv = got[:, p[0], p[1], p[2]].cpu().numpy()
+            assert np.abs(gv - ref).max() <= 64 * U32 * 1e-3 * steps + 1e-12, (k, p)
+    b.close()
