@@ -299,8 +299,12 @@ om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
   const int K = df->p.check_every;
   while (nsteps > 0) {
     if (K >= 2 && !(K & 1) && !(df->t & 1) && nsteps >= K) {
-      OM_TRY((diff_capture_t<T, L>(df, K)));
-      OM_CUDA(cudaGraphLaunch(df->exec, s));
+      if (df->windows++ > 0) {  // the first whole window as plain launches (see om_flow)
+        OM_TRY((diff_capture_t<T, L>(df, K)));
+        OM_CUDA(cudaGraphLaunch(df->exec, s));
+      } else {
+        for (int k = 0; k < K; ++k) launch_sweep<T, L>(k & 1, df->var[k & 1], nb, s, a);
+      }
       df->t += K;
       nsteps -= K;
       if (kRebased<T>) diff_rebase<T, L><<<nb, 256, 0, s>>>(a);  // once per window

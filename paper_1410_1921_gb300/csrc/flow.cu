@@ -368,8 +368,12 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
   const int K = fl->p.check_every;
   while (nsteps > 0) {
     if (K >= 2 && !(K & 1) && !(fl->t & 1) && nsteps >= K) {
-      OM_TRY(flow_capture_t<T>(fl, K));
-      OM_CUDA(cudaGraphLaunch(fl->exec, s));
+      if (fl->windows++ > 0) {
+        OM_TRY(flow_capture_t<T>(fl, K));
+        OM_CUDA(cudaGraphLaunch(fl->exec, s));
+      } else {  // the first whole window as plain launches: one-window calls capture nothing
+        for (int k = 0; k < K; ++k) launch_step<T>(fl, k & 1, fl->var[k & 1], nb, s, a);
+      }
       fl->t += K;
       nsteps -= K;
       continue;

@@ -21,9 +21,12 @@ struct om_flow {
   // extrapolated populations (storage arithmetic type, [19][n_in + n_out])
   uint32_t n_in = 0, n_out = 0;
   void* bc = nullptr;
-  // a captured window of graph_k steps starting at an even time (replayed by *_step)
+  // a captured window of graph_k steps starting at an even time (replayed by
+  // *_step); the first whole window runs as plain launches and the graph is
+  // captured at the second, so that single-window calls pay no capture
   cudaGraphExec_t exec = nullptr;
   int graph_k = 0;
+  int64_t windows = 0;
   cudaStream_t cap = nullptr;
 };
 
@@ -41,9 +44,10 @@ struct om_diff {
   int64_t t = 0;
   double up = 1.0;      // storage scale (stored = deviation * up)
   int var[2] = {0, 0};  // launch variant of the even and odd sweeps
-  // a captured window of graph_k steps starting at an even time (replayed by *_step)
+  // as om_flow's
   cudaGraphExec_t exec = nullptr;
   int graph_k = 0;
+  int64_t windows = 0;
   cudaStream_t cap = nullptr;
 };
 
