@@ -58,10 +58,12 @@ def _args():
     ap.add_argument("--n-train", type=int, default=96, help="converge mode: training structures")
     ap.add_argument("--epochs", type=int, default=60, help="converge mode: U-Net epochs")
     ap.add_argument("--max-steps", type=int, default=500_000, help="converge mode: step cap per solve")
-    ap.add_argument("--warm", default="diffusion", choices=["both", "diffusion", "none", "coarse", "coarse+net"],
+    ap.add_argument("--warm", default="diffusion",
+                    choices=["both", "diffusion", "none", "coarse", "coarse-both", "coarse+net"],
                     help="converge mode: which models the network warm-starts (velocity warm starts "
                          "measured to slow the flow's convergence); 'coarse': the diffusion starts from a "
                          "batched solve of the structures coarsened 2x per axis instead of the network; "
+                         "'coarse-both': the flow too, from a coarse flow solve; "
                          "'coarse+net': from that solve refined by the network")
     return ap.parse_args()
 
@@ -440,16 +442,33 @@ def run_converge(a):
     t0 = time.perf_counter()
     b = P.Batch([s[1] for s in structs], [s[3] for s in structs], [s[4] for s in structs], flow=fp, diff=fp16)
     coarse_steps = 0
-    if a.warm in ("coarse", "coarse+net"):
+    if a.warm in ("coarse", "coarse-both", "coarse+net"):
         # the structures coarsened 2x per axis, solved together, their
         # concentration carried to the fine nodes (refined by the network)
         cs = [W.coarse_level(dom, tr, d) for _, dom, mask, tr, d in structs]
         keep = [k for k, c in enumerate(cs) if c[1] is not None]
         bc = None
         if keep:
-            bc = P.Batch([cs[k][0] for k in keep], [cs[k][1] for k in keep], [cs[k][2] for k in keep], diff=dpc)
+            fpc = None
+            if a.warm == "coarse-both":  # 4x the force: about the fine lattice's velocities (k ~ spacing^2)
+                fpc = P.flow_params(precision=P.OM_F32, body_force=4 * fp.body_force, conv_tol=10 * tol,
+                                    check_every=K, max_steps=cap)
+            bc = P.Batch([cs[k][0] for k in keep], [cs[k][1] for k in keep], [cs[k][2] for k in keep], flow=fpc,
+                         diff=dpc)
             _, _, info_c, _ = bc.solve(1)
             coarse_steps = int(sum(i.steps for i in info_c))
+            if fpc is not None:
+                _, _, _, stc = bc.solve(0)
+                for j, k in enumerate(keep):
+                    if stc[j] != P.OM_OK:
+                        continue
+                    dc, tr_c = cs[k][0], cs[k][1]
+                    fcd = torch.empty(19 * dc.nx * dc.ny * dc.nz, dtype=torch.float64, device="cuda")
+                    bc.get_populations(0, j, fcd)
+                    dom = structs[k][1]
+                    u = torch.empty(dom.nx * dom.ny * dom.nz, dtype=torch.float32, device="cuda")
+                    P.om_prolong2_ux_dev(fcd, tr_c, dom, fpc.body_force, 1.0, u)
+                    b.init_fields(0, k, u, stride=1, scale=1.0)
         for k, (_, dom, mask, tr, d) in enumerate(structs):
             if k not in keep:
                 if refine:  # no coarse level: the network on a zero coarse departure
@@ -494,6 +513,7 @@ def run_converge(a):
     dk = max(rel(kl[i], p["k_lattice"]) for i, p in enumerate(plain))
     dD = max(rel(dl[i], p["D_lattice"]) for i, p in enumerate(plain))
     warm_name = {"coarse": "two-level (2x coarsened solve) warm start", "none": "no warm start",
+                 "coarse-both": "two-level warm start of both models",
                  "coarse+net": "two-level warm start refined by the U-Net"}.get(a.warm, "U-Net warm start")
     line = {"metric": f"time to converged k, D_eff: plain / (batched + FP16 diffusion + {warm_name})",
             "value": t_plain / t_fast, "unit": "x", "higher_is_better": True, "n_gpus": 1,

@@ -327,6 +327,13 @@ om_status om_prolong2_dev(const double* g_c_dev, int32_t q, const uint8_t* nodes
                           void* stream);
 om_status om_unet_pack_structure3(const uint8_t* mask_dev, const float* d_nm_dev, double d_scale,
                                   const float* extra_dev, int64_t n, float* x_dev, void* stream);
+/* Fine u_x (float N) from the coarse flow's dense populations f_c_dev (double
+ * 19 x N_c, body force body_force_c along x on the coarse lattice):
+ * scale * (sum_i e_ix f_i + body_force_c / 2) at the covering coarse voxel
+ * where nodes_c is 1, else 0 -- the flow's initial velocity for
+ * om_batch_init_fields / om_flow_init_velocity. */
+om_status om_prolong2_ux_dev(const double* f_c_dev, const uint8_t* nodes_c_dev, om_domain d, double body_force_c,
+                             double scale, float* ux_dev, void* stream);
 
 /* ---------------------------------------------------------------- checkpoint and resume
  * A solver's evolving state -- its populations exactly as stored, the

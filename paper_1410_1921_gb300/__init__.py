@@ -114,6 +114,7 @@ _SIGS = {
     "om_coarsen2_dev": [_vp, _vp, om_domain, _vp, _vp, _vp],
     "om_prolong2_dev": [_vp, C.c_int32, _vp, om_domain, C.c_double, C.c_double, _vp, C.c_int64, C.c_int32, _vp, _vp],
     "om_unet_pack_structure3": [_vp, _vp, C.c_double, _vp, C.c_int64, _vp, _vp],
+    "om_prolong2_ux_dev": [_vp, _vp, om_domain, C.c_double, C.c_double, _vp, _vp],
     "om_flow_state_size": [_vp, _i64p],
     "om_flow_save_state": [_vp, _vp, C.c_int64, _vp],
     "om_flow_load_state": [_vp, _vp, C.c_int64, _vp],
@@ -566,6 +567,11 @@ def om_prolong2_dev(g_c_dev, q, nodes_c_dev, dom, c_in, c_out, c_dev, corr_dev=N
                     stream=None):
     _call("om_prolong2_dev", _ptr(g_c_dev), q, _ptr(nodes_c_dev), dom, c_in, c_out, _ptr(corr_dev), corr_stride,
           int(departure), _ptr(c_dev), _stream(stream))
+
+
+def om_prolong2_ux_dev(f_c_dev, nodes_c_dev, dom, body_force_c, scale, ux_dev, stream=None):
+    _call("om_prolong2_ux_dev", _ptr(f_c_dev), _ptr(nodes_c_dev), dom, body_force_c, scale, _ptr(ux_dev),
+          _stream(stream))
 
 
 def om_unet_pack_structure3(mask_dev, d_nm_dev, d_scale, extra_dev, x_dev, stream=None):

@@ -69,6 +69,28 @@ __global__ void prolong2(const double* __restrict__ g_c, int q, const uint8_t* _
   }
 }
 
+// fine u_x from the coarse flow populations: scale * (sum_i e_ix f_i + g/2)
+// at the covering coarse voxel where it is a node, else 0 (Guo's half-force
+// velocity, Sec. 3.1)
+__global__ void prolong2_ux(const double* __restrict__ f_c, const uint8_t* __restrict__ nodes_c, int cx, int cy,
+                            int cz, int nx, int ny, int nz, double half_g, double scale, float* __restrict__ u) {
+  const int64_t n = (int64_t)nx * ny * nz, nc = (int64_t)cx * cy * cz;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(v / ((int64_t)ny * nz));
+    const int y = (int)((v / nz) % ny);
+    const int z = (int)(v % nz);
+    const int64_t k = ((int64_t)(x / 2) * cy + y / 2) * cz + z / 2;
+    double val = 0.0;
+    if (nodes_c[k]) {
+      double jx = 0.0;
+      for (int i = 1; i < 19; ++i)
+        if (q19_e(i, 0)) jx += q19_e(i, 0) > 0 ? f_c[(int64_t)i * nc + k] : -f_c[(int64_t)i * nc + k];
+      val = scale * (jx + half_g);
+    }
+    u[v] = (float)val;
+  }
+}
+
 om_domain coarse_domain(const om_domain& d) {
   om_domain c = d;
   c.nx = (d.nx + 1) / 2;
@@ -115,6 +137,17 @@ extern "C" om_status om_prolong2_dev(const double* g_c_dev, int32_t q, const uin
   prolong2<<<grid_for(voxels(d)), 256, 0, as_stream(stream)>>>(g_c_dev, q, nodes_c_dev, c.nx, c.ny, c.nz, d.nx, d.ny,
                                                               d.nz, c_in, c_out, corr_dev, corr_stride, departure,
                                                               c_dev);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+extern "C" om_status om_prolong2_ux_dev(const double* f_c_dev, const uint8_t* nodes_c_dev, om_domain d,
+                                        double body_force_c, double scale, float* ux_dev, void* stream) {
+  if (!f_c_dev || !nodes_c_dev || !ux_dev) return fail(OM_EINVAL, "om_prolong2_ux_dev: null pointer");
+  OM_TRY(check_domain(d));
+  const om_domain c = coarse_domain(d);
+  prolong2_ux<<<grid_for(voxels(d)), 256, 0, as_stream(stream)>>>(f_c_dev, nodes_c_dev, c.nx, c.ny, c.nz, d.nx, d.ny,
+                                                                 d.nz, 0.5 * body_force_c, scale, ux_dev);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }

@@ -121,3 +121,34 @@ def test_two_level_warm_start_keeps_result_and_saves_steps(om):
     assert st0 == st1 == st_c == om.OM_OK
     assert D1 == pytest.approx(D0, rel=2e-3)  # both stop on the same test, from different sides
     assert info1.steps < 0.8 * info0.steps  # measured 92k against 134k
+
+
+@pytest.mark.timeout(600)
+def test_two_level_flow_warm_start_keeps_result(om):
+    # the coarse flow with 4x the body force has about the fine lattice's
+    # velocities (k scales with the square of the lattice spacing); its u_x
+    # carried to the fine nodes starts the fine solve, which iterates to the
+    # same test and the same permeability
+    from paper_1410_1921_gb300 import warmstart as W
+    cfg = S.sweep_structure(0.35, edge=64)
+    dom, mask, tr, d = W.structure(cfg)
+    g = 1e-6
+    fp = om.flow_params(body_force=g, precision=om.OM_F32, conv_tol=1e-5, check_every=1000, max_steps=1_000_000)
+    ns = om.NodeSet(tr, dom)
+    st0, k0, info0 = om.Flow(ns, fp).solve()
+    dc, tr_c, _ = W.coarse_level(dom, tr, d)
+    ns_c = om.NodeSet(tr_c, dc)
+    flc = om.Flow(ns_c, om.flow_params(body_force=4 * g, precision=om.OM_F32, conv_tol=1e-4, check_every=1000,
+                                       max_steps=1_000_000))
+    st_c, _, info_c = flc.solve()
+    nc = dc.nx * dc.ny * dc.nz
+    f_c = torch.empty(19 * nc, dtype=torch.float64, device="cuda")
+    flc.get_populations(f_c)
+    u = torch.empty(dom.nx * dom.ny * dom.nz, dtype=torch.float32, device="cuda")
+    om.om_prolong2_ux_dev(f_c, tr_c, dom, 4 * g, 1.0, u)
+    fl = om.Flow(ns, fp)
+    fl.init_velocity(u)
+    st1, k1, info1 = fl.solve()
+    print(f"flow cold {info0.steps} steps, coarse {info_c.steps}, warm {info1.steps}; k {k0:.6e} {k1:.6e}")
+    assert st0 == st1 == st_c == om.OM_OK
+    assert k1 == pytest.approx(k0, rel=2e-3)
