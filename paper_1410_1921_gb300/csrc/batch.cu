@@ -712,6 +712,14 @@ void launch_steps_grouped(const om_batch* b, int model, int64_t t0, int64_t n, c
 template <class T>
 om_status capture_t(om_batch* b, int model, int K);
 
+// whether the current device takes cooperative launches
+inline bool cooperative_ok() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return false;
+  return v != 0;
+}
+
 // Largest grid of the window kernel of a model whose blocks are all
 // resident at once (the cooperative-launch limit).
 template <class T>
@@ -938,6 +946,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
     // timed on a window of this solve, the one not timed yet
     int mode = -1;
     if (k == K) {
+      if (m.mode < 0 && !cooperative_ok()) m.mode = 0;  // no cooperative launches here: graphs only
       mode = m.mode >= 0 ? m.mode : (m.trial_ms[0] < 0.f ? 0 : 1);
       *b->bar_h = OM_OK;
       if (mode == 0) OM_TRY(capture_t<T>(b, model, K));  // host work outside the timed window
