@@ -546,18 +546,23 @@ def _device_structure(P, W, cfg):
     return dom, tr, d
 
 
-def _window_mlups(step, nodes, steps, reps):
+def _window_mlups(step, nodes, steps, reps, nvtx=None):
     """Device MLUPS of `reps` calls of step() (each `steps` LB steps over
-    `nodes` nodes), CUDA events around the calls after one warm-up call."""
+    `nodes` nodes), CUDA events around the calls after one warm-up call;
+    nvtx names an NVTX range around the timed calls (for a profiler)."""
     import torch
     step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     e0.record()
     for _ in range(reps):
         step()
     e1.record()
     torch.cuda.synchronize()
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     return nodes * steps * reps / (ms * 1e-3) / 1e6, ms / reps
 
@@ -624,7 +629,7 @@ def run_batch(a):
     total = sum(nodes)
     out = {}
     for model, name in ((0, "flow"), (1, "diffusion")):
-        mlups, ms = _window_mlups(lambda: b.step(model, WINDOW), total, WINDOW, 3)
+        mlups, ms = _window_mlups(lambda: b.step(model, WINDOW), total, WINDOW, 3, nvtx="timed")
         out[name] = {"mlups": mlups, "ms_per_window": ms}
     b.close()
     modes = {}
