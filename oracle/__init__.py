@@ -336,3 +336,16 @@ def diff_solve(node, omega, cin=1.0, cout=0.0, tol=1e-6, K=100, max_steps=1_000_
     rc = lib().orc_diffq_solve(q, _p(n, _u8p), *n.shape, _p(om, _f64p), cin, cout, tol, K, max_steps,
                                _p(g, _f64p), _p(out, _f64p))
     return rc, out[0], out[1], int(out[2]), out[3], out[4], g.reshape((q,) + n.shape)
+
+
+# ---------------------------------------------------------------- results in physical units (Eqs. 15, 16)
+def tortuosity_eq16(pore_mask, transport, d_nm, D_eff_m2s, T_K, M_kg_per_mol):
+    """Eq. 16, tortuosity = eps D / D_eff, with eps the total porosity (pore
+    voxels over all voxels, dead-end and isolated pores included) and D the
+    local Knudsen diffusivity of Eq. 11 averaged over the transport nodes (the
+    nodes the diffusion runs on), d in nm."""
+    pore = np.asarray(pore_mask) != 0
+    tr = np.asarray(transport) != 0
+    eps = float(pore.sum()) / pore.size
+    D_mean = physics.mean_knudsen_diffusivity(np.asarray(d_nm, np.float64)[tr], T_K, M_kg_per_mol)
+    return physics.tortuosity(eps, D_mean, D_eff_m2s)

@@ -18,9 +18,25 @@ def tau_knudsen(d_nm, d_ref_nm=60.0, tau_ref=1.0):
     return (d_nm / d_ref_nm) * (tau_ref - 0.5) + 0.5
 
 
+def lattice_cs2(q):
+    """Squared lattice sound speed of the diffusion lattice: D3Q7 with rest
+    weight 1/4 has c_s^2 = 1/4; the paper's D3Q19 (Sec. 3.2, the weights
+    below Eq. 3) has c_s^2 = 1/3."""
+    if q == 7:
+        return 0.25
+    if q == 19:
+        return 1.0 / 3.0
+    raise ValueError(f"no diffusion lattice D3Q{q}")
+
+
+def lattice_diffusivity(tau, q):
+    """BGK diffusion: D_L = c_s^2 (tau - 1/2) on D3Q7 or D3Q19."""
+    return (tau - 0.5) * lattice_cs2(q)
+
+
 def d3q7_lattice_diffusivity(tau):
     """BGK diffusion on D3Q7 with rest weight 1/4: c_s^2 = 1/4, D_L = (tau - 1/2)/4."""
-    return (tau - 0.5) * 0.25
+    return lattice_diffusivity(tau, 7)
 
 
 def d3q19_viscosity(tau):
@@ -33,15 +49,28 @@ def permeability_physical(k_lattice, dx_m):
     return k_lattice * dx_m * dx_m
 
 
-def diffusivity_physical(D_lattice, d_ref_m, T_K, M, tau_ref=1.0):
-    """Eq. 15 with the time step fixed by the reference pore: D_L,ref maps to
-    D_K(d_ref) (Eqs. 11-12), so D_P = D_L * D_K,ref / D_L,ref."""
-    return D_lattice * knudsen_diffusivity(d_ref_m, T_K, M) / d3q7_lattice_diffusivity(tau_ref)
+def diffusivity_physical(D_lattice, d_ref_m, T_K, M, q, tau_ref=1.0):
+    """Eq. 15 with the time step fixed by the reference pore: D_L,ref of the
+    lattice q maps to D_K(d_ref) (Eqs. 11-12), so D_P = D_L * D_K,ref / D_L,ref.
+    The lattice must be named: D_L,ref = c_s^2 (tau_ref - 1/2) depends on it."""
+    return D_lattice * knudsen_diffusivity(d_ref_m, T_K, M) / lattice_diffusivity(tau_ref, q)
 
 
 def tortuosity(porosity, D_mean, D_eff):
     """Eq. 16: D_eff = D eps / tortuosity."""
     return porosity * D_mean / D_eff
+
+
+def mean_knudsen_diffusivity(d_nm_values, T_K, M):
+    """The D of Eq. 16 for a structure with local pore sizes: Eq. 11 applied
+    node by node (d in nm) and averaged over the nodes given -- the transport
+    nodes, the ones the diffusion runs on."""
+    n = 0
+    acc = 0.0
+    for d in d_nm_values:
+        acc += knudsen_diffusivity(float(d) * 1e-9, T_K, M)
+        n += 1
+    return acc / n
 
 
 def bruggeman_alpha(D_eff, D_ref, porosity):

@@ -335,6 +335,59 @@ def test_d3q19_diffusion_open_box_exact(orc):
         assert np.allclose(C, (1 - x / 9)[:, None, None], atol=1e-11)
 
 
+def test_physical_diffusivity_open_box_both_lattices(orc):
+    # an open box of uniform pore size d conducts with the local Knudsen
+    # diffusivity of Eq. 11 whatever the lattice: Eq. 15's time step, fixed by
+    # the reference pore through Eq. 12, must use the lattice's own c_s^2
+    from oracle import physics as PH
+    m = np.ones((9, 4, 3), np.uint8)
+    d = 33.0
+    om = orc.omega_field(m, np.full(m.shape, d))
+    for q in (7, 19):
+        rc, DL, *_ = orc.diff_solve(m, om, 1.0, 0.0, tol=1e-14, K=100, max_steps=200_000, q=q)
+        assert rc == 0
+        D = PH.diffusivity_physical(DL, 60e-9, 300.0, 0.016, q)
+        assert D == pytest.approx(PH.knudsen_diffusivity(d * 1e-9, 300.0, 0.016), rel=1e-10)
+
+
+def layered_slit_with_pocket():
+    """A plane channel along x whose four pore rows have different pore sizes,
+    and an isolated pore pocket (no 18-neighbour path to the channel, not
+    spanning x) with another size.  Returns (pore mask, d_nm, transport)."""
+    nx, ny, nz = 8, 10, 3
+    m = np.zeros((nx, ny, nz), np.uint8)
+    d = np.zeros(m.shape)
+    for y, dl in zip(range(1, 5), (60.0, 30.0, 45.0, 12.0)):
+        m[:, y, :] = 1
+        d[:, y, :] = dl
+    m[2:5, 7:9, :] = 1  # rows y = 6 and y = 9 stay solid
+    d[2:5, 7:9, :] = 20.0
+    tr = np.zeros_like(m)
+    tr[:, 1:5, :] = 1
+    return m, d, tr
+
+
+def test_tortuosity_averages_over_transport_nodes(orc):
+    # Eq. 16 on a layered channel: the layers are parallel conductors, so
+    # D_eff = sum of the transport nodes' D_K / N and, with eps the total
+    # porosity and D their mean D_K, tortuosity = (pore voxels)/(transport
+    # nodes) exactly.  Averaging D over every pore voxel (the pocket has
+    # another size) or taking eps over the transport nodes fails this.
+    from oracle import physics as PH
+    m, d, tr = layered_slit_with_pocket()
+    _, tr_o, _ = orc.label18(m)
+    assert np.array_equal(tr_o, tr)
+    T, M = 300.0, 0.016
+    rc, DL, *_ = orc.diff_solve(tr, orc.omega_field(tr, d), 1.0, 0.0, tol=1e-14, K=100, max_steps=400_000)
+    assert rc == 0
+    D_eff = PH.diffusivity_physical(DL, 60e-9, T, M, 7)
+    DK = [PH.knudsen_diffusivity(v * 1e-9, T, M) for v in d[tr == 1]]
+    assert D_eff == pytest.approx(sum(DK) / m.size, rel=1e-10)
+    tau = orc.tortuosity_eq16(m, tr, d, D_eff, T, M)
+    assert tau == pytest.approx(m.sum() / tr.sum(), rel=1e-10)
+    assert m.sum() > tr.sum()
+
+
 def test_d3q19_diffusion_mass_conservation_closed(orc):
     m = S.closed_box((6, 6, 6))
     rng = np.random.default_rng(2)

@@ -46,10 +46,19 @@ def test_tau_knudsen_eq12_limits():
 
 
 def test_unit_conversion_round_trip():
-    # D_L,ref maps to D_K(d_ref): Eq. 15 with the time step fixed by Eq. 12
+    # D_L,ref maps to D_K(d_ref) on either lattice: Eq. 15 with the time step
+    # fixed by Eq. 12
     T, M = 300.0, 0.016
-    D = P.diffusivity_physical(P.d3q7_lattice_diffusivity(1.0), 60e-9, T, M)
-    assert D == pytest.approx(P.knudsen_diffusivity(60e-9, T, M), rel=1e-15)
+    for q in (7, 19):
+        D = P.diffusivity_physical(P.lattice_diffusivity(1.0, q), 60e-9, T, M, q)
+        assert D == pytest.approx(P.knudsen_diffusivity(60e-9, T, M), rel=1e-15)
+    # c_s^2 of the two lattices: D3Q7 with rest weight 1/4, the D3Q19 weights
+    # printed below Eq. 3 (sum of w_i e_ix^2)
+    w = GOLD["weights_d3q19"]
+    assert P.lattice_cs2(19) == pytest.approx(2 * w["axis"] + 8 * w["diagonal"], rel=1e-15)
+    assert P.lattice_cs2(7) == 2 * 0.125
+    with pytest.raises(ValueError):
+        P.lattice_cs2(15)
     assert P.permeability_physical(2.0, 1.5e-9) == pytest.approx(2.0 * 2.25e-18)
 
 
