@@ -165,7 +165,10 @@ om_status om_label_connectivity_dev(const uint8_t* mask_dev, om_domain d, int32_
  * is a static device array of 4 MiB + 256 B that every GPU loading the
  * library holds until exit, which limits the box to 2^24 voxels (larger ->
  * OM_EINVAL).  The first call on a device (with it current) looks up the
- * array's device address; make that first call before any stream capture.
+ * array's device address and keeps it for that CUDA context; a call under
+ * another context (after a device reset, or with a caller-made context
+ * current) looks it up again.  Make the first call on a device, and in each
+ * new context, before any stream capture.
  * All calls share the array: calls that overlap on the GPU race. */
 om_status om_label_connectivity_noalloc(const uint8_t* mask_dev, om_domain d, int32_t* labels_dev,
                                         uint8_t* transport_dev, double* connectivity_out, void* stream);

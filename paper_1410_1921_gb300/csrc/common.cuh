@@ -113,21 +113,15 @@ __host__ __device__ inline void unpack_xyz(uint32_t c, int& x, int& y, int& z) {
 constexpr int kObsBlocks = 1216;  // 8 x 152 SMs: fixed grid of reductions
 constexpr int kObsThreads = 256;
 
-// Blocks of `threads` threads of `kernel` that fit on the device at once
-// (SMs x resident blocks per SM), capped at nb: the grid of a kernel whose
-// threads stride over their work.  Cached per kernel and device.
+// Blocks of `threads` threads of `kernel` (with `smem` bytes of dynamic
+// shared memory) that fit on the device at once (SMs x resident blocks per
+// SM), capped at nb: the grid of a kernel whose threads stride over their
+// work.  Cached per kernel, launch shape and device.
+unsigned resident_blocks(const void* kernel, int threads, size_t smem);
 template <class K>
-inline unsigned resident_grid(K kernel, unsigned nb, int threads = 256) {
-  static int cache[64] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-  if (cache[dev] <= 0) {
-    int sms = 0, per = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
-    cache[dev] = sms * per > 0 ? sms * per : 1;
-  }
-  return nb < (unsigned)cache[dev] ? nb : (unsigned)cache[dev];
+inline unsigned resident_grid(K kernel, unsigned nb, int threads = 256, size_t smem = 0) {
+  const unsigned r = resident_blocks((const void*)kernel, threads, smem);
+  return nb < r ? nb : r;
 }
 
 // Launch variants the autotuner chose, remembered for the life of the
@@ -157,4 +151,15 @@ struct om_nodeset {
   uint32_t* coord = nullptr;  // [nf] packed x, y, z
   int64_t* vox = nullptr;     // [nf] voxel index
   int64_t wrap_links = 0;     // D3Q19 links from node voxels at x = nx-1 to node voxels at x = 0
+  // Neighbour records (lattice.cuh, "neighbour records"): per node the
+  // D3Q7 part rec7[n] and the rest of the D3Q19 neighbourhood rec19[n], from
+  // which an odd sweep derives its neighbours' node numbers without the
+  // column map; nodes on a face of the box (where neighbours wrap or an x
+  // face is crossed) carry the "slow" mark and are listed in slow[n_slow]
+  // (ascending), updated through the column map instead.  rec7 == nullptr
+  // when the box is too large for the record fields (then no sweep uses them).
+  uint2* rec7 = nullptr;
+  uint2* rec19 = nullptr;
+  uint32_t* slow = nullptr;
+  int64_t n_slow = 0;
 };

@@ -31,8 +31,11 @@ namespace om {
 // 2 two nodes deep with the next node's column-map words prefetched into L1
 // (the flow sweep's variant 5); 5 = even steps two consecutive nodes per
 // thread with vector loads and stores (the flow sweep's variant 6), odd
-// steps as variant 0.
-constexpr int kDiffVariants = 6;
+// steps as variant 0; 6, 7, 8 = odd steps from the neighbour records with
+// the slow nodes in the same grid (the flow sweep's variants 7, 8, 9: one
+// thread per node, capped, and a resident grid loading the next node's
+// records ahead), even steps as variant 5.  Without records 6-8 run as 5.
+constexpr int kDiffVariants = 9;
 
 template <class T, class L, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) diff_sweep(DiffArgs<T, L> a) {
@@ -79,6 +82,34 @@ __global__ void __launch_bounds__(256, MINB) diff_sweep_pipelined(DiffArgs<T, L>
     n = (uint32_t)nn;
     c0 = c1;
     c1 = c2;
+  }
+}
+
+template <class T, class L, int MINB>
+__global__ void __launch_bounds__(256, MINB) diff_sweep_rec(DiffArgs<T, L> a) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nf + a.nslow) return;
+  uint2 r, q;
+  diff_rec_load<L>(a.rec7, a.rec19, t, a.nf, r, q);
+  diff_odd_rec<T, L>(a, t, r, q);
+}
+
+template <class T, class L>
+__global__ void __launch_bounds__(256) diff_sweep_rec_strided(DiffArgs<T, L> a) {
+  const uint32_t stride = gridDim.x * blockDim.x, total = a.nf + a.nslow;
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  uint2 r, q;
+  diff_rec_load<L>(a.rec7, a.rec19, t, a.nf, r, q);
+  for (;;) {
+    const uint64_t tn = (uint64_t)t + stride;
+    uint2 rn, qn;
+    diff_rec_load<L>(a.rec7, a.rec19, tn < a.nf ? (uint32_t)tn : a.nf, a.nf, rn, qn);
+    diff_odd_rec<T, L>(a, t, r, q);
+    if (tn >= total) break;
+    t = (uint32_t)tn;
+    r = rn;
+    q = qn;
   }
 }
 
@@ -247,6 +278,20 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const DiffArgs<T, 
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
+    case 6:
+    case 7:
+    case 8:
+      if (ODD && a.rec7) {
+        const unsigned nbr = blocks_for((int64_t)a.nf + a.nslow);
+        if (variant == 6) diff_sweep_rec<T, L, 0><<<nbr, 256, 0, s>>>(a);
+        else if (variant == 7) diff_sweep_rec<T, L, M><<<nbr, 256, 0, s>>>(a);
+        else {
+          auto k = diff_sweep_rec_strided<T, L>;
+          k<<<resident_grid(k, nbr), 256, 0, s>>>(a);
+        }
+        break;
+      }
+      [[fallthrough]];
     case 5:
       if (!ODD) {
         diff_sweep_pair<T, L><<<blocks_for((a.nf + 1) / 2), 256, 0, s>>>(a);

@@ -20,6 +20,12 @@ struct DiffArgs {
   typename Stg<T>::C up, down;  // storage scale
   double cin, cout;
   float* cr;  // 16-bit storage: per-node reference concentration (see kRebased)
+  // neighbour records of the node set and its slow nodes (lattice.cuh);
+  // rec7 == nullptr when the node set has none
+  const uint2* rec7 = nullptr;
+  const uint2* rec19 = nullptr;
+  const uint32_t* slow = nullptr;
+  uint32_t nslow = 0;
 };
 
 // Reference state of the stored deviations.  FP64 storage: a_i C_lin(x),
@@ -85,8 +91,9 @@ template <class L>
 __device__ __forceinline__ bool from_outlet(int i, int x, int nx) { return L::e(i, 0) == -1 && x == nx - 1; }
 
 // pre-collision deviations of node n at the current time (odd steps: with
-// the reference concentrations r of diff_refs)
-template <class T, class L, bool ODD>
+// the reference concentrations r of diff_refs).  FACES = false: the node is
+// known to lie off both x faces (x is not used).
+template <class T, class L, bool ODD, bool FACES = true>
 __device__ __forceinline__ void diff_load_r(const DiffArgs<T, L>& a, uint32_t n, const uint32_t (&nb)[L::Q], int x,
                                             const DiffRefs<T, L>& r, typename Stg<T>::C (&g)[L::Q]) {
   using S = Stg<T>;
@@ -98,7 +105,7 @@ __device__ __forceinline__ void diff_load_r(const DiffArgs<T, L>& a, uint32_t n,
     } else {
       const int o = L::opp(i);
       const uint32_t src = nb[o];  // x - e_i
-      const bool inlet = from_inlet<L>(i, x), outlet = from_outlet<L>(i, x, a.nx);
+      const bool inlet = FACES && from_inlet<L>(i, x), outlet = FACES && from_outlet<L>(i, x, a.nx);
       const T* p = (src != kNoNode && !inlet && !outlet) ? a.q[o] + src : a.q[i] + n;
       const C v = S::ld(p, a.down);
       const C w = C(L::w(i));
@@ -140,22 +147,22 @@ __device__ __forceinline__ void diff_relax(C (&g)[L::Q], C om) {
 // One fused collide-stream update of node n (global slot index) at x whose
 // neighbours are nb (used on odd steps only); the AA read/write pattern of
 // flow_node_nb with the anti-bounce-back inlet/outlet and the reference shift.
-template <class T, class L, bool ODD>
+template <class T, class L, bool ODD, bool FACES = true>
 __device__ __forceinline__ void diff_store(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q],
                                            const DiffRefs<T, L>& r, const typename Stg<T>::C (&g)[L::Q]);
 
-template <class T, class L, bool ODD>
+template <class T, class L, bool ODD, bool FACES = true>
 __device__ __forceinline__ void diff_node_nb(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q]) {
   DiffRefs<T, L> r{};
   if (ODD) diff_refs(a, n, nb, r);
   typename Stg<T>::C g[L::Q];
-  diff_load_r<T, L, ODD>(a, n, nb, x, r, g);
+  diff_load_r<T, L, ODD, FACES>(a, n, nb, x, r, g);
   diff_relax<L>(g, a.omega[n]);
-  diff_store<T, L, ODD>(a, n, x, nb, r, g);
+  diff_store<T, L, ODD, FACES>(a, n, x, nb, r, g);
 }
 
 // post-collision deviations of node n at x to their slots (see diff_node_nb)
-template <class T, class L, bool ODD>
+template <class T, class L, bool ODD, bool FACES>
 __device__ __forceinline__ void diff_store(const DiffArgs<T, L>& a, uint32_t n, int x, const uint32_t (&nb)[L::Q],
                                            const DiffRefs<T, L>& r, const typename Stg<T>::C (&g)[L::Q]) {
   using S = Stg<T>;
@@ -169,7 +176,7 @@ __device__ __forceinline__ void diff_store(const DiffArgs<T, L>& a, uint32_t n, 
       S::st(a.q[0] + n, g[0], a.up);
     } else {
       // leaves through the outlet (e_ix = +1 at nx-1) or the inlet half link
-      const bool outlet = L::e(i, 0) == 1 && x == a.nx - 1, inlet = L::e(i, 0) == -1 && x == 0;
+      const bool outlet = FACES && L::e(i, 0) == 1 && x == a.nx - 1, inlet = FACES && L::e(i, 0) == -1 && x == 0;
       T* p = a.q[o] + n;
       C v = g[i];
       const C w = C(L::w(i));
@@ -217,6 +224,35 @@ __device__ __forceinline__ void diff_node_at(const DiffArgs<T, L>& a, uint32_t n
   int x = 0;
   if (ODD) diff_neighbours(a, c, nb, x);
   diff_node_nb<T, L, ODD>(a, n, x, nb);
+}
+
+// Odd step of node t from its records (a node off every face of the box:
+// no inlet or outlet link), or of slow node slow[t - nf] through the column
+// map; r, q are node t's records (t < nf)
+template <class T, class L>
+__device__ __forceinline__ void diff_odd_rec(const DiffArgs<T, L>& a, uint32_t t, uint2 r, uint2 q) {
+  if (t < a.nf) {
+    if (rec_slow(r)) return;  // updated from the slow list
+    uint32_t nb[L::Q];
+    if constexpr (L::Q == 19) rec_neighbours19(r, q, t, nb);
+    else rec_axis<L::Q>(r, t, nb);
+    diff_node_nb<T, L, true, false>(a, t, 0, nb);
+  } else {
+    const uint32_t n = __ldg(a.slow + (t - a.nf));
+    diff_node_at<T, L, true>(a, n, __ldg(a.coord + n));
+  }
+}
+
+// node t's records (the D3Q19 part only for that lattice)
+template <class L>
+__device__ __forceinline__ void diff_rec_load(const uint2* rec7, const uint2* rec19, uint32_t t, uint32_t nf, uint2& r,
+                                              uint2& q) {
+  r = make_uint2(0u, 0u);
+  q = make_uint2(0u, 0u);
+  if (t < nf) {
+    r = __ldg(rec7 + t);
+    if constexpr (L::Q == 19) q = __ldg(rec19 + t);
+  }
 }
 
 // diff_node_at for node n whose coordinates are coord[ln]

@@ -56,13 +56,24 @@ namespace om {
 //   6  even steps: two consecutive nodes per thread, each population of both
 //      loaded and stored as one vector of two (twice the bytes per load
 //      instruction and per register in flight, which the 16-bit formats
-//      need to approach the bandwidth roofline); odd steps as variant 0.
+//      need to approach the bandwidth roofline); odd steps as variant 0;
+//   7  odd steps from the neighbour records (lattice.cuh): one thread per
+//      node reads its two record words and derives its 18 neighbours' node
+//      numbers with integer adds, no column-map lookup between the record
+//      and the population loads; the slow nodes (faces of the box) follow
+//      in the same grid, one thread each, through the column map; even
+//      steps as variant 6;
+//   8  variant 7 with the register cap of variant 1;
+//   9  variant 7 on a resident grid whose threads stride over the nodes
+//      (then the slow list) and load the next node's records before
+//      updating the current one.
+//   Without records (a box beyond their fields) 7-9 run as 6.
 // (Odd steps of two nodes per thread, a grid apart, with both lookups and
 // all 38 loads issued before either update, were measured slower than
 // variant 2: the registers they need halve the resident threads.)
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
-constexpr int kSweepVariants = 7;
+constexpr int kSweepVariants = 10;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
@@ -109,6 +120,57 @@ __global__ void __launch_bounds__(256, MINB) d3q19_sweep_pipelined(FlowArgs<T> a
     n = (uint32_t)nn;
     c0 = c1;
     c1 = c2;
+  }
+}
+
+// Odd step of node t from its records, or of slow node slow[t - nf]
+template <class T>
+__device__ __forceinline__ void flow_odd_rec(const FlowArgs<T>& a, uint32_t t, uint2 r, uint2 q) {
+  if (t < a.nf) {
+    if (rec_slow(r)) return;  // updated from the slow list
+    uint32_t nb[19];
+    rec_neighbours19(r, q, t, nb);
+    flow_node_nb<T, true>(a, t, nb);
+  } else {
+    const uint32_t n = __ldg(a.slow + (t - a.nf));
+    flow_node_at<T, true>(a, n, __ldg(a.coord + n));
+  }
+}
+
+template <class T, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q19_sweep_rec(FlowArgs<T> a) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nf + a.nslow) return;
+  uint2 r = make_uint2(0u, 0u), q = make_uint2(0u, 0u);
+  if (t < a.nf) {
+    r = __ldg(a.rec7 + t);
+    q = __ldg(a.rec19 + t);
+  }
+  flow_odd_rec<T>(a, t, r, q);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) d3q19_sweep_rec_strided(FlowArgs<T> a) {
+  const uint32_t stride = gridDim.x * blockDim.x, total = a.nf + a.nslow;
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  uint2 r = make_uint2(0u, 0u), q = make_uint2(0u, 0u);
+  if (t < a.nf) {
+    r = __ldg(a.rec7 + t);
+    q = __ldg(a.rec19 + t);
+  }
+  for (;;) {
+    const uint64_t tn = (uint64_t)t + stride;
+    uint2 rn = make_uint2(0u, 0u), qn = make_uint2(0u, 0u);
+    if (tn < a.nf) {
+      rn = __ldg(a.rec7 + tn);
+      qn = __ldg(a.rec19 + tn);
+    }
+    flow_odd_rec<T>(a, t, r, q);
+    if (tn >= total) break;
+    t = (uint32_t)tn;
+    r = rn;
+    q = qn;
   }
 }
 
@@ -303,6 +365,20 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>&
       k<<<resident_grid(k, nb), 256, 0, s>>>(a);
       break;
     }
+    case 7:
+    case 8:
+    case 9:
+      if (ODD && a.rec7) {
+        const unsigned nbr = blocks_for((int64_t)a.nf + a.nslow);
+        if (variant == 7) d3q19_sweep_rec<T, 0><<<nbr, 256, 0, s>>>(a);
+        else if (variant == 8) d3q19_sweep_rec<T, M><<<nbr, 256, 0, s>>>(a);
+        else {
+          auto k = d3q19_sweep_rec_strided<T>;
+          k<<<resident_grid(k, nbr), 256, 0, s>>>(a);
+        }
+        break;
+      }
+      [[fallthrough]];
     case 6:
       if (!ODD) {
         d3q19_sweep_pair<T><<<blocks_for((a.nf + 1) / 2), 256, 0, s>>>(a);

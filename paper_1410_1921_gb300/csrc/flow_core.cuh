@@ -26,6 +26,12 @@ struct FlowArgs {
   int px = 1;
   uint32_t n_in = 0, n_out = 0;
   const typename Stg<T>::C* bc = nullptr;
+  // neighbour records of the node set and its slow nodes (lattice.cuh);
+  // rec7 == nullptr when the node set has none
+  const uint2* rec7 = nullptr;
+  const uint2* rec19 = nullptr;
+  const uint32_t* slow = nullptr;
+  uint32_t nslow = 0;
 };
 
 // nb[i] = node number of x + e_i (kNoNode off the node set); periodic y, z,

@@ -20,14 +20,20 @@
 // Host code cannot use the array's name as a device address (in host code
 // it names a host-side stand-in), so the first call on each device, with
 // that device current, asks the runtime for the address with
-// cudaGetSymbolAddress and keeps it.  That first call on a device should
-// come before any stream capture on it.  Device code below still names the
-// array only through the pointer it is given.
+// cudaGetSymbolAddress and keeps it, together with the unique id of the
+// CUDA context that was current.  A later call under another context (the
+// device was reset and its primary context recreated, or the caller made a
+// context of its own current) looks the address up again for that context.
+// That first call on a device (or in a new context) should come before any
+// stream capture on it.  Device code below still names the array only
+// through the pointer it is given.
 //
 // Every call shares the one array and leaves its contents behind: each call
 // clears the flag words and counters it uses before its kernels run.  Calls
 // whose work overlaps on the GPU (on different streams, or from different
 // host threads) race on the array; serialise them.
+#include <cuda.h>  // driver types only: the two driver calls are fetched through the runtime
+
 #include <mutex>
 
 #include "common.cuh"
@@ -45,21 +51,55 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_label_scratch[kScratchBytes];
 
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+  unsigned long long ctx_id;  // unique id of the context the address belongs to
+  void* addr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
 
-// device address of g_label_scratch on the current device (set up once)
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// unique id of the context current on this thread (0 if none is current);
+// the driver functions come through the runtime, so nothing links libcuda
+om_status current_context_id(unsigned long long* id) {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa{}, qb{};
+    OM_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa));
+    OM_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb));
+    if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+      return fail(OM_ECUDA, "om_label_connectivity_noalloc: driver context queries unavailable");
+    g_ctx_get_current = (CtxGetCurrentFn)a;
+    g_ctx_get_id = (CtxGetIdFn)b;
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return fail(OM_ECUDA, "cuCtxGetCurrent failed");
+  *id = 0;
+  if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return fail(OM_ECUDA, "cuCtxGetId failed");
+  return OM_OK;
+}
+
+// device address of g_label_scratch on the current device, looked up once
+// per device and context
 om_status scratch_address(void** out) {
   int dev = 0;
   OM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(OM_EINVAL, "om_label_connectivity_noalloc: device ordinal too large");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  OM_TRY(current_context_id(&id));
+  if (id == 0 || !g_scratch[dev].addr || g_scratch[dev].ctx_id != id) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_label_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_label_scratch);  // makes the device's context current if none is
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_label_scratch)", __FILE__, __LINE__);
-    g_scratch_addr[dev] = p;
+    OM_TRY(current_context_id(&id));
+    g_scratch[dev] = ScratchSlot{id, p};
   }
-  *out = g_scratch_addr[dev];
+  *out = g_scratch[dev].addr;
   return OM_OK;
 }
 

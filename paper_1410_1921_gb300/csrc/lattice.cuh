@@ -182,6 +182,68 @@ __device__ __forceinline__ void q19_neighbours(const uint4* __restrict__ col, in
   (void)self;
 }
 
+// Neighbour records.  For a node n at (x, y, z) away from every face of the
+// box, R_c(z) = the number of nodes that precede voxel (c, z) in voxel order
+// (its node number if it is a node) differs from n by a bounded amount for
+// each of the eight columns c = (x +- 1, y), (x, y +- 1), (x +- 1, y +- 1),
+// and the neighbours at z +- 1 of a column are R_c(z) + [voxel (c, z) is a
+// node] and R_c(z) - 1.  Two 8-byte words per node hold those differences and
+// the node bits of the 18 neighbour voxels, so an odd sweep gets every
+// neighbour's node number from its own coalesced record with integer adds:
+//   rec7.x : [0,19) R(x+1,y) - n - 1 (all ones: "slow" node), [19,29)
+//            R(x,y+1) - n - 1, bit 29 (x+1,y,z), 30 (x,y+1,z), 31 (x,y,z+1)
+//   rec7.y : [0,19) n - R(x-1,y), [19,29) n - R(x,y-1), bit 29 (x-1,y,z),
+//            30 (x,y-1,z), 31 (x,y,z-1)
+//   rec19.x: [0,10) R(x+1,y+1) - R(x+1,y), [10,20) R(x+1,y) - R(x+1,y-1),
+//            [20,30) R(x-1,y+1) - R(x-1,y), bit 30 (x+1,y+1,z), 31 (x+1,y-1,z)
+//   rec19.y: [0,10) R(x-1,y) - R(x-1,y-1), bit 10 (x-1,y+1,z),
+//            11 (x-1,y-1,z), 12/13 (x+1,y,z-+1), 14/15 (x-1,y,z-+1),
+//            16/17 (x,y+1,z-+1), 18/19 (x,y-1,z-+1)
+// The fields bound the box: nz <= kRecMaxNz, ny nz <= kRecMaxPlane.  Nodes on
+// a face (x, y or z = 0 or the last; their neighbours wrap or cross an x
+// face) are "slow": their sweeps use the column map.  The differences are
+// invariant under a shift of all node numbers, so a batch, whose node
+// numbers are offset per structure, uses the records as they are.
+constexpr uint32_t kRecSlow = 0x7FFFFu;
+constexpr int kRecMaxNz = 1023;
+constexpr int64_t kRecMaxPlane = 0x7FFFF;
+
+__device__ __forceinline__ bool rec_slow(uint2 r7) { return (r7.x & kRecSlow) == kRecSlow; }
+
+// nb[1..6] of a node that is not slow (nb[0] untouched)
+template <int Q>
+__device__ __forceinline__ void rec_axis(uint2 r, uint32_t n, uint32_t (&nb)[Q]) {
+  const uint32_t ap = n + (r.x & 0x7FFFFu) + 1u, am = n - (r.y & 0x7FFFFu);
+  const uint32_t bp = n + ((r.x >> 19) & 0x3FFu) + 1u, bm = n - ((r.y >> 19) & 0x3FFu);
+  nb[1] = (r.x >> 29) & 1u ? ap : kNoNode;
+  nb[2] = (r.y >> 29) & 1u ? am : kNoNode;
+  nb[3] = (r.x >> 30) & 1u ? bp : kNoNode;
+  nb[4] = (r.y >> 30) & 1u ? bm : kNoNode;
+  nb[5] = (r.x >> 31) ? n + 1u : kNoNode;
+  nb[6] = (r.y >> 31) ? n - 1u : kNoNode;
+}
+
+// the D3Q19 neighbours nb[1..18] of a node that is not slow
+__device__ __forceinline__ void rec_neighbours19(uint2 r, uint2 q, uint32_t n, uint32_t (&nb)[19]) {
+  rec_axis<19>(r, n, nb);
+  const uint32_t ap = n + (r.x & 0x7FFFFu) + 1u, am = n - (r.y & 0x7FFFFu);
+  const uint32_t bp = n + ((r.x >> 19) & 0x3FFu) + 1u, bm = n - ((r.y >> 19) & 0x3FFu);
+  const uint32_t a0 = (r.x >> 29) & 1u, am0 = (r.y >> 29) & 1u, b0 = (r.x >> 30) & 1u, bm0 = (r.y >> 30) & 1u;
+  const uint32_t e1 = q.x & 0x3FFu, e2 = (q.x >> 10) & 0x3FFu, e3 = (q.x >> 20) & 0x3FFu, e4 = q.y & 0x3FFu;
+  nb[7] = (q.x >> 30) & 1u ? ap + e1 : kNoNode;   // (1, 1, 0)
+  nb[8] = (q.y >> 10) & 1u ? am + e3 : kNoNode;   // (-1, 1, 0)
+  nb[9] = (q.x >> 31) ? ap - e2 : kNoNode;        // (1, -1, 0)
+  nb[10] = (q.y >> 11) & 1u ? am - e4 : kNoNode;  // (-1, -1, 0)
+  nb[11] = (q.y >> 13) & 1u ? ap + a0 : kNoNode;  // (1, 0, 1)
+  nb[12] = (q.y >> 15) & 1u ? am + am0 : kNoNode; // (-1, 0, 1)
+  nb[13] = (q.y >> 12) & 1u ? ap - 1u : kNoNode;  // (1, 0, -1)
+  nb[14] = (q.y >> 14) & 1u ? am - 1u : kNoNode;  // (-1, 0, -1)
+  nb[15] = (q.y >> 17) & 1u ? bp + b0 : kNoNode;  // (0, 1, 1)
+  nb[16] = (q.y >> 19) & 1u ? bm + bm0 : kNoNode; // (0, -1, 1)
+  nb[17] = (q.y >> 16) & 1u ? bp - 1u : kNoNode;  // (0, 1, -1)
+  nb[18] = (q.y >> 18) & 1u ? bm - 1u : kNoNode;  // (0, -1, -1)
+}
+
 // Ask L1 for the column-map words the neighbour lookup of the node with
 // packed coordinates c will read (z's 32-voxel word of the columns (x + dx,
 // y + dy): all nine for D3Q19, the five with |dx| + |dy| <= 1 for D3Q7), so

@@ -11,7 +11,7 @@
 // above its last (periodic in z), so that z - 1, z, z + 1 of any column come
 // from one 16-byte word without branches.  16 bytes per 32 voxels (the whole
 // map sits in L2) instead of an 18-entry neighbour table per node.
-#include "common.cuh"
+#include "lattice.cuh"
 
 namespace om {
 
@@ -81,9 +81,104 @@ __global__ void ns_wrap_links(const uint8_t* nodes, int nx, int ny, int nz, unsi
   if (c) atomicAdd(count, c);
 }
 
+// R_c(z) (nodes before voxel (x, y, z)) and whether that voxel is a node
+__device__ __forceinline__ void ns_rank_bit(const uint4* col, int ny, int W, int x, int y, int z, uint32_t& r,
+                                            uint32_t& bit) {
+  const uint4 w = col[((int64_t)x * ny + y) * W + (z >> 5)];
+  r = w.y + __popc(w.x & ((1u << (z & 31)) - 1u));
+  bit = (w.x >> (z & 31)) & 1u;
+}
+
+// The neighbour records of lattice.cuh for every node, and a 0/1 "slow" flag
+// per node (a face of the box, or a box beyond the record fields: !fit).
+__global__ void ns_records(const uint4* col, const uint32_t* coord, int64_t nf, int nx, int ny, int nz, int W,
+                           int fit, uint2* rec7, uint2* rec19, uint32_t* slow) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nf) return;
+  int x, y, z;
+  unpack_xyz(coord[n], x, y, z);
+  if (!fit || x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1) {
+    rec7[n] = make_uint2(kRecSlow, 0u);
+    rec19[n] = make_uint2(0u, 0u);
+    slow[n] = 1u;
+    return;
+  }
+  const uint32_t nn = (uint32_t)n;
+  uint32_t rxp, bxp, rxm, bxm, ryp, byp, rym, bym, r;
+  ns_rank_bit(col, ny, W, x + 1, y, z, rxp, bxp);
+  ns_rank_bit(col, ny, W, x - 1, y, z, rxm, bxm);
+  ns_rank_bit(col, ny, W, x, y + 1, z, ryp, byp);
+  ns_rank_bit(col, ny, W, x, y - 1, z, rym, bym);
+  uint32_t szp, szm;
+  ns_rank_bit(col, ny, W, x, y, z + 1, r, szp);
+  ns_rank_bit(col, ny, W, x, y, z - 1, r, szm);
+  uint2 a;
+  a.x = (rxp - nn - 1u) | ((ryp - nn - 1u) << 19) | (bxp << 29) | (byp << 30) | (szp << 31);
+  a.y = (nn - rxm) | ((nn - rym) << 19) | (bxm << 29) | (bym << 30) | (szm << 31);
+  uint32_t r1, b1, r2, b2, r3, b3, r4, b4;
+  ns_rank_bit(col, ny, W, x + 1, y + 1, z, r1, b1);
+  ns_rank_bit(col, ny, W, x + 1, y - 1, z, r2, b2);
+  ns_rank_bit(col, ny, W, x - 1, y + 1, z, r3, b3);
+  ns_rank_bit(col, ny, W, x - 1, y - 1, z, r4, b4);
+  uint32_t zb[8];
+  ns_rank_bit(col, ny, W, x + 1, y, z - 1, r, zb[0]);
+  ns_rank_bit(col, ny, W, x + 1, y, z + 1, r, zb[1]);
+  ns_rank_bit(col, ny, W, x - 1, y, z - 1, r, zb[2]);
+  ns_rank_bit(col, ny, W, x - 1, y, z + 1, r, zb[3]);
+  ns_rank_bit(col, ny, W, x, y + 1, z - 1, r, zb[4]);
+  ns_rank_bit(col, ny, W, x, y + 1, z + 1, r, zb[5]);
+  ns_rank_bit(col, ny, W, x, y - 1, z - 1, r, zb[6]);
+  ns_rank_bit(col, ny, W, x, y - 1, z + 1, r, zb[7]);
+  uint2 q;
+  q.x = (r1 - rxp) | ((rxp - r2) << 10) | ((r3 - rxm) << 20) | (b1 << 30) | (b2 << 31);
+  q.y = (rxm - r4) | (b3 << 10) | (b4 << 11);
+  for (int k = 0; k < 8; ++k) q.y |= zb[k] << (12 + k);
+  rec7[n] = a;
+  rec19[n] = q;
+  slow[n] = 0u;
+}
+
+__global__ void ns_slow_list(const uint32_t* flag, const uint32_t* pos, int64_t nf, uint32_t* list) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nf && flag[n]) list[pos[n]] = (uint32_t)n;
+}
+
 }  // namespace om
 
 using namespace om;
+
+namespace {
+// The neighbour records and the list of slow nodes (see lattice.cuh).
+om_status build_records(om_nodeset* ns, cudaStream_t s) {
+  const om_domain& d = ns->dom;
+  const int64_t nf = ns->nf;
+  const int fit = d.nz <= kRecMaxNz && (int64_t)d.ny * d.nz <= kRecMaxPlane;
+  DevBuf<uint2> r7, r19;
+  DevBuf<uint32_t> flag, pos, list;
+  DevBuf<uint64_t> total;
+  OM_TRY(r7.alloc(nf));
+  OM_TRY(r19.alloc(nf));
+  OM_TRY(flag.alloc(nf));
+  OM_TRY(pos.alloc(nf));
+  OM_TRY(total.alloc(1));
+  const unsigned nb = (unsigned)((nf + 255) / 256);
+  ns_records<<<nb, 256, 0, s>>>(ns->col, ns->coord, nf, d.nx, d.ny, d.nz, ns->W, fit, r7.p, r19.p, flag.p);
+  OM_CUDA(cudaGetLastError());
+  OM_TRY(exclusive_scan_u32(flag.p, pos.p, nf, total.p, s));
+  uint64_t nslow = 0;
+  OM_CUDA(cudaMemcpyAsync(&nslow, total.p, sizeof nslow, cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  OM_TRY(list.alloc(nslow));
+  ns_slow_list<<<nb, 256, 0, s>>>(flag.p, pos.p, nf, list.p);
+  OM_CUDA(cudaGetLastError());
+  OM_CUDA(cudaStreamSynchronize(s));
+  ns->rec7 = fit ? r7.take() : nullptr;
+  ns->rec19 = fit ? r19.take() : nullptr;
+  ns->slow = list.take();
+  ns->n_slow = (int64_t)nslow;
+  return OM_OK;
+}
+}  // namespace
 
 extern "C" om_status om_nodeset_create(const uint8_t* nodes_dev, om_domain d, void* stream,
                                        om_nodeset** out) {
@@ -140,6 +235,13 @@ extern "C" om_status om_nodeset_create(const uint8_t* nodes_dev, om_domain d, vo
   ns->col = col.take();
   ns->coord = coord.take();
   ns->vox = vox.take();
+  if (nf > 0) {
+    om_status rs = build_records(ns, s);
+    if (rs != OM_OK) {
+      om_nodeset_destroy(ns);
+      return rs;
+    }
+  }
   *out = ns;
   return OM_OK;
 }
@@ -163,6 +265,9 @@ extern "C" om_status om_nodeset_destroy(om_nodeset* ns) {
   cudaFree(ns->col);
   cudaFree(ns->coord);
   cudaFree(ns->vox);
+  cudaFree(ns->rec7);
+  cudaFree(ns->rec19);
+  cudaFree(ns->slow);
   delete ns;
   return OM_OK;
 }

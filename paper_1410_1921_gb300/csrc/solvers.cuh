@@ -62,6 +62,10 @@ inline FlowArgs<T> flow_args(const om_flow* fl) {
   a.nf = (uint32_t)ns->nf;
   a.col = ns->col;
   a.coord = ns->coord;
+  a.rec7 = ns->rec7;
+  a.rec19 = ns->rec19;
+  a.slow = ns->slow;
+  a.nslow = (uint32_t)ns->n_slow;
   a.nx = ns->dom.nx;
   a.ny = ns->dom.ny;
   a.nz = ns->dom.nz;
@@ -101,6 +105,10 @@ inline DiffArgs<T, L> diff_args(const om_diff* df) {
   a.cin = df->p.c_in;
   a.cout = df->p.c_out;
   a.cr = df->cr;
+  a.rec7 = ns->rec7;
+  a.rec19 = ns->rec19;
+  a.slow = ns->slow;
+  a.nslow = (uint32_t)ns->n_slow;
   return a;
 }
 

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 
 namespace om {
 
@@ -181,6 +182,23 @@ bool tuned_lookup(int kind, int prec, int64_t nf, int var[2]) {
 void tuned_store(int kind, int prec, int64_t nf, const int var[2]) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[tune_key(kind, prec, nf)] = {var[0], var[1]};
+}
+
+unsigned resident_blocks(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, unsigned> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const auto key = std::make_tuple(kernel, threads, smem, dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  const unsigned r = sms * per > 0 ? (unsigned)(sms * per) : 1u;
+  cache[key] = r;
+  return r;
 }
 
 void launch_finalize(const double* partials, int nblk, int nval, double* out, cudaStream_t s) {

@@ -32,7 +32,7 @@ def _both(om, m):
     return (lab_a.cpu().numpy(), tr_a.cpu().numpy(), conn_a), (lab_b.cpu().numpy(), tr_b.cpu().numpy(), conn_b)
 
 
-def test_noalloc_matches_allocating_entry_point_twice(om):
+def test_noalloc_matches_allocating_entry_point_twice(om, orc):
     first = S.blob_mask((40, 33, 29), 3, n=9, rmin=2.0, rmax=6.0)
     second = S.random_mask((24, 20, 36), 0.55, 8)  # different shape and components
     for m in (first, second):
@@ -40,6 +40,18 @@ def test_noalloc_matches_allocating_entry_point_twice(om):
         assert np.array_equal(la, lb)
         assert np.array_equal(ta, tb)
         assert ca == cb
+        # and the oracle's 18-neighbour labelling (Sec. 4.1), directly
+        lo, to, co = orc.label18(m)
+        assert np.array_equal(lb, lo.reshape(-1)) and np.array_equal(tb, to.reshape(-1)) and cb == co
+    assert ta.sum() > 0
+
+
+def test_noalloc_at_the_largest_box_it_accepts(om):
+    # 256^3 = 2^24 voxels: the packed flags fill every word of the static
+    # array and the counters sit right behind them
+    m = S.random_mask((256, 256, 256), 0.6, 11)
+    (la, ta, ca), (lb, tb, cb) = _both(om, m)
+    assert np.array_equal(la, lb) and np.array_equal(ta, tb) and ca == cb
     assert ta.sum() > 0
 
 
