@@ -118,9 +118,21 @@ typedef struct {
   int32_t check_every;
   int64_t max_steps;
   int32_t precision;
-  int32_t variant; /* as om_flow_params.variant: 0..3 as there, 4, 5 = its 5, 6 (larger values clamp to 5) */
+  int32_t variant; /* launch variant, -1 = autotune (see diff.cu; larger values clamp to the last) */
   int32_t lattice;
+  /* OM_ACCEL_EXTRAPOLATE (not in the paper): om_diff_solve and
+   * om_batch_solve restart the iteration from an extrapolated state when the
+   * decay of the concentration change has settled on one mode: after three
+   * consecutive check windows whose ratios rho = sum|dC| / sum|dC|_previous
+   * agree to 2 % of 1 - rho, every node's concentration moves by
+   * dC rho / (1 - rho) (dC its change over the last window; the stored
+   * non-equilibrium parts are kept).  The LB then iterates on to the same
+   * convergence test, so the fixed point and the test are those of the
+   * plain solve.  OM_ACCEL_NONE: the plain iteration. */
+  int32_t accel;
 } om_diff_params;
+
+enum { OM_ACCEL_NONE = 0, OM_ACCEL_EXTRAPOLATE = 1 };
 
 typedef struct {
   int64_t steps;        /* LB steps taken */

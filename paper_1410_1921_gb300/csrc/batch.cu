@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(kTile) flow_batch_observe(FlowArgs<T> a, const
 
 template <class T, bool ODD>
 __global__ void __launch_bounds__(kTile) diff_batch_observe(DiffArgs<T> a, const BatchItem* items, const uint2* work,
-                                                            const int* nwork, double* prev, double* partials) {
+                                                            const int* nwork, double* prev, double* partials,
+                                                            double* dprev) {
   using C = typename Stg<T>::C;
   const int nw = *nwork;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
@@ -310,9 +311,29 @@ __global__ void __launch_bounds__(kTile) diff_batch_observe(DiffArgs<T> a, const
       acc[2] = fabs(c);
       acc[3] = c;
       acc[4] = 0.25 * (1.0 / om - 0.5);
+      if (dprev) dprev[n] = c - prev[n];
       prev[n] = c;
     }
     block_reduce_write<5>(acc, partials + (int64_t)w * 5);
+  }
+}
+
+// Extrapolated restart of one item (om_diff_params.accel; see
+// diff_extrapolate in diff.cu): nodes [off, off + nf) move by f dC.
+template <class T>
+__global__ void diff_batch_extrapolate(DiffArgs<T> a, uint32_t off, uint32_t nf, double* prev, const double* dprev,
+                                       double f) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf) return;
+  const uint32_t n = off + k;
+  const double dc = f * dprev[n];
+  prev[n] += dc;
+  if constexpr (kRebased<T>) {
+    a.cr[n] = (float)((double)a.cr[n] + dc);
+  } else {
+    using S = Stg<T>;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) S::st(a.q[i] + n, S::ld(a.q[i] + n, a.down) + (typename S::C)(q7_w(i) * dc), a.up);
   }
 }
 
@@ -477,6 +498,7 @@ struct Model {
   void* omega = nullptr; // diffusion only, compute type, [pitch]
   float* cr = nullptr;   // diffusion with 16-bit storage: per-node reference concentration
   double* prev = nullptr;
+  double* dprev = nullptr;  // diffusion with OM_ACCEL_EXTRAPOLATE: each node's change over the last window
   int64_t t = 0;
   double up = 1.0;
   int var[2] = {0, 0};   // launch variant per parity
@@ -821,8 +843,10 @@ om_status observe_t(om_batch* b, int model, int nact, cudaStream_t s) {
     if (nact > 0) batch_finalize<4><<<nact, 256, 0, s>>>(b->partials, b->range, b->obs);
   } else {
     DiffArgs<T> a = bdiff_args<T>(b);
-    if (m.t & 1) diff_batch_observe<T, true><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials);
-    else diff_batch_observe<T, false><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials);
+    if (m.t & 1)
+      diff_batch_observe<T, true><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials, m.dprev);
+    else
+      diff_batch_observe<T, false><<<grid, kTile, 0, s>>>(a, b->items, b->work, b->nwork, m.prev, b->partials, m.dprev);
     if (nact > 0) batch_finalize<5><<<nact, 256, 0, s>>>(b->partials, b->range, b->obs);
   }
   OM_CUDA(cudaGetLastError());
@@ -928,6 +952,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
     if (b->items_h[k].nf > 0 && (model == 1 || b->ns[k]->wrap_links > 0)) active.push_back(k);
   }
   std::vector<double> sj_prev(b->n, 0.0);
+  std::vector<ExtrapolationTrack> track(b->n);
   int nw = build_work(b, active, model);
   OM_TRY(upload_work(b, nw, (int)active.size(), s));
   OM_TRY(observe_t<T>(b, model, (int)active.size(), s));  // reference state
@@ -996,6 +1021,14 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
       const bool diverged = !std::isfinite(o[0]) || !std::isfinite(o[2]);
       if (status) status[it] = done && !diverged ? OM_OK : OM_ENOTCONVERGED;
       if (!done && !diverged) keep.push_back(it);
+      if (!done && !diverged && model == 1 && m.dprev) {
+        const double f = track[it].observe(o[1]);
+        if (f > 0.0) {
+          diff_batch_extrapolate<T><<<(bi.nf + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b), bi.off, bi.nf, m.prev,
+                                                                         m.dprev, std::min(f, 1e3));
+          OM_CUDA(cudaGetLastError());
+        }
+      }
     }
     if (keep.size() != active.size()) {
       active.swap(keep);
@@ -1049,6 +1082,7 @@ extern "C" om_status om_batch_destroy(om_batch* b) {
     cudaFree(m.omega);
     cudaFree(m.cr);
     cudaFree(m.prev);
+    cudaFree(m.dprev);
   }
   cudaFree(b->items);
   cudaFree(b->work);
@@ -1074,6 +1108,8 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if (n <= 0 || !doms || !nodes_dev || !out || (!fp && !dp)) return fail(OM_EINVAL, "om_batch_create: bad arguments");
   if (dp && !d_nm_dev) return fail(OM_EINVAL, "om_batch_create: diffusion needs pore sizes");
   if (dp && dp->lattice != 7) return fail(OM_EINVAL, "om_batch_create: batches take the D3Q7 diffusion lattice");
+  if (dp && dp->accel != OM_ACCEL_NONE && dp->accel != OM_ACCEL_EXTRAPOLATE)
+    return fail(OM_EINVAL, "om_batch_create: unknown accel");
   if (fp && !(fp->tau > 0.5)) return fail(OM_EINVAL, "om_batch_create: tau must exceed 1/2");
   if (fp && fp->drive != OM_DRIVE_FORCE) return fail(OM_EINVAL, "om_batch_create: batches take the body-force drive");
   if (dp && (!(dp->d_ref_nm > 0.0) || !(dp->tau_ref > 0.5) || !(dp->c_in != dp->c_out)))
@@ -1168,6 +1204,9 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     m.up = m.prec == OM_F16DEV ? (model == 0 ? 1024.0 : 64.0) : 1.0;
     if ((st = dalloc(&m.pop, (size_t)m.q * b->pitch * stg_bytes(m.prec))) != OM_OK) return bail(st);
     if ((st = dalloc((void**)&m.prev, sizeof(double) * b->pitch)) != OM_OK) return bail(st);
+    if (model == 1 && dp->accel == OM_ACCEL_EXTRAPOLATE &&
+        (st = dalloc((void**)&m.dprev, sizeof(double) * b->pitch)) != OM_OK)
+      return bail(st);
     if (model == 1) {
       const size_t cb = m.prec == OM_F64 ? 8 : 4;
       if ((st = dalloc(&m.omega, cb * b->pitch)) != OM_OK) return bail(st);

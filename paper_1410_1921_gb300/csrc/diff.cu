@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) diff_sweep_pair(DiffArgs<T, L> a) {
 // Observables: sum J_x, sum |C - prev|, sum |C|, sum C, sum D_L; prev <- C.
 template <class T, class L, bool ODD>
 __global__ void __launch_bounds__(kObsThreads) diff_observe(DiffArgs<T, L> a, double* prev,
-                                                            double* partials) {
+                                                            double* partials, double* dprev) {
   using C = typename Stg<T>::C;
   double acc[5] = {0, 0, 0, 0, 0};
   for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < a.nf; n += gridDim.x * blockDim.x) {
@@ -148,9 +148,33 @@ __global__ void __launch_bounds__(kObsThreads) diff_observe(DiffArgs<T, L> a, do
     acc[2] += fabs(c);
     acc[3] += c;
     acc[4] += L::cs2 * (1.0 / om - 0.5);
+    if (dprev) dprev[n] = c - prev[n];
     prev[n] = c;
   }
   block_reduce_store<5>(acc, partials);
+}
+
+// Extrapolated restart (om_diff_params.accel): node n's concentration
+// moves by f dC(n); the stored non-equilibrium parts stay.  Rebased storage
+// moves the node's reference (every population of the node shifts by a_i
+// times it, in either parity's slots); FP64 storage shifts each slot by
+// a_i f dC (the weights are symmetric, so slot i and slot opposite(i) take
+// the same shift).  prev follows, so the next window's change is measured
+// from the new state.
+template <class T, class L>
+__global__ void diff_extrapolate(DiffArgs<T, L> a, double* prev, const double* dprev, double f) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  const double dc = f * dprev[n];
+  prev[n] += dc;
+  if constexpr (kRebased<T>) {
+    a.cr[n] = (float)((double)a.cr[n] + dc);
+  } else {
+    using S = Stg<T>;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      S::st(a.q[i] + n, S::ld(a.q[i] + n, a.down) + (typename S::C)(L::w(i) * dc), a.up);
+  }
 }
 
 template <class T, class L, bool ODD>
@@ -407,13 +431,22 @@ om_status diff_tune_t(om_diff* df, cudaStream_t s) {
 template <class T, class L>
 om_status diff_observe_t(om_diff* df, double* out, cudaStream_t s) {
   DiffArgs<T, L> a = diff_args<T, L>(df);
-  if (df->t & 1) diff_observe<T, L, true><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
-  else diff_observe<T, L, false><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials);
+  if (df->t & 1) diff_observe<T, L, true><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials, df->dprev);
+  else diff_observe<T, L, false><<<kObsBlocks, kObsThreads, 0, s>>>(a, df->prev, df->partials, df->dprev);
   launch_finalize(df->partials, kObsBlocks, 5, df->obs_dev, s);
   OM_CUDA(cudaGetLastError());
   OM_CUDA(cudaMemcpyAsync(df->obs_host, df->obs_dev, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
   OM_CUDA(cudaStreamSynchronize(s));
   for (int k = 0; k < 5; ++k) out[k] = df->obs_host[k];
+  return OM_OK;
+}
+
+template <class T, class L>
+om_status diff_extrapolate_t(om_diff* df, double f, cudaStream_t s) {
+  if (df->ns->nf == 0 || !df->dprev) return OM_OK;
+  DiffArgs<T, L> a = diff_args<T, L>(df);
+  diff_extrapolate<T, L><<<blocks_for(a.nf), 256, 0, s>>>(a, df->prev, df->dprev, f);
+  OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
 
@@ -509,6 +542,8 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   if (!(p->d_ref_nm > 0.0) || !(p->tau_ref > 0.5) || !(p->c_in != p->c_out))
     return fail(OM_EINVAL, "om_diff_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");
   if (p->lattice != 7 && p->lattice != 19) return fail(OM_EINVAL, "om_diff_create: lattice must be 7 or 19");
+  if (p->accel != OM_ACCEL_NONE && p->accel != OM_ACCEL_EXTRAPOLATE)
+    return fail(OM_EINVAL, "om_diff_create: unknown accel");
   cudaStream_t s = as_stream(stream);
   om_diff* df = new om_diff();
   df->ns = ns;
@@ -523,6 +558,8 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   if (st == OM_OK && storage_bytes(p->precision) <= 4) st = cr.alloc(ns->pitch);
   if (st == OM_OK) st = om.alloc((size_t)ns->pitch * cb);
   if (st == OM_OK) st = prev.alloc(ns->nf);
+  DevBuf<double> dprev;
+  if (st == OM_OK && p->accel == OM_ACCEL_EXTRAPOLATE) st = dprev.alloc(ns->nf);
   if (st == OM_OK) st = part.alloc((size_t)kObsBlocks * 8);
   if (st == OM_OK) st = obs.alloc(8);
   double* host = nullptr;
@@ -538,6 +575,7 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   df->omega = om.take();
   df->cr = cr.take();
   df->prev = prev.take();
+  df->dprev = p->accel == OM_ACCEL_EXTRAPOLATE ? dprev.take() : nullptr;
   df->partials = part.take();
   df->obs_dev = obs.take();
   df->obs_host = host;
@@ -592,6 +630,7 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
   om_status rc = OM_ENOTCONVERGED;
   double rel = 1.0;
   bool diverged = false;
+  ExtrapolationTrack track;
   while (df->t - t0 < p.max_steps) {
     int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (df->t - t0));
     OM_TRY(om_diff_step(df, k, stream));
@@ -609,6 +648,13 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
     if (rel < p.conv_tol) {
       rc = OM_OK;
       break;
+    }
+    if (df->dprev) {
+      const double f = track.observe(o[1]);
+      if (f > 0.0) {
+        auto ex = [&]() -> om_status { OM_DIFF_DISPATCH(df, diff_extrapolate_t, df, std::min(f, 1e3), s); };
+        OM_TRY(ex());
+      }
     }
   }
   OM_CUDA(cudaEventRecord(e1, s));
@@ -679,6 +725,7 @@ extern "C" om_status om_diff_destroy(om_diff* df) {
   cudaFree(df->omega);
   cudaFree(df->cr);
   cudaFree(df->prev);
+  cudaFree(df->dprev);
   cudaFree(df->partials);
   cudaFree(df->obs_dev);
   if (df->obs_host) cudaFreeHost(df->obs_host);

@@ -4,6 +4,8 @@
 // See diff.cu for the scheme.
 #pragma once
 
+#include <cmath>
+
 #include "lattice.cuh"
 
 namespace om {
@@ -287,5 +289,32 @@ __device__ __forceinline__ void diff_rebase_node(const DiffArgs<T, L>& a, uint32
     for (int i = 0; i < L::Q; ++i) S::st(a.q[i] + n, d[i] + (float)L::w(i) * (old - now), a.up);
   }
 }
+
+// Extrapolated restarts (om_diff_params.accel): the host side of the test
+// that the decay of the window-to-window change has settled on one mode.
+struct ExtrapolationTrack {
+  double last = -1.0;  // sum |dC| of the last window (< 0: none since the start or the last jump)
+  double rho[3] = {0.0, 0.0, 0.0};
+  int n = 0;           // ratios recorded since then
+  // record this window's sum |dC|; returns the factor rho / (1 - rho) to
+  // move every node's C by (times its dC) when the last three ratios agree,
+  // else 0
+  double observe(double sum_abs_dc) {
+    if (last > 0.0 && sum_abs_dc > 0.0) {
+      rho[0] = rho[1];
+      rho[1] = rho[2];
+      rho[2] = sum_abs_dc / last;
+      ++n;
+    }
+    last = sum_abs_dc;
+    if (n < 3) return 0.0;
+    const double r = rho[2];
+    if (!(r > 0.0 && r < 0.999)) return 0.0;
+    const double tol = 0.02 * (1.0 - r);
+    if (std::fabs(rho[2] - rho[1]) > tol || std::fabs(rho[1] - rho[0]) > 0.02 * (1.0 - rho[1])) return 0.0;
+    *this = ExtrapolationTrack{};  // start over after the jump
+    return r / (1.0 - r);
+  }
+};
 
 }  // namespace om

@@ -3,6 +3,8 @@
 // shared by the translation units that launch their sweeps.
 #pragma once
 
+#include <cmath>
+
 #include "diff_core.cuh"
 #include "flow_core.cuh"
 
@@ -38,6 +40,7 @@ struct om_diff {
   float* cr = nullptr;  // per-node reference concentration (16-bit storage)
   int q = 7;            // lattice: 7 (D3Q7) or 19 (D3Q19)
   double* prev = nullptr;
+  double* dprev = nullptr;  // OM_ACCEL_EXTRAPOLATE: each node's change of C over the last window
   double* partials = nullptr;
   double* obs_dev = nullptr;
   double* obs_host = nullptr;

@@ -292,3 +292,31 @@ def test_150_set_batch_sampled(orc, om):
             gv = got[:, p[0], p[1], p[2]].cpu().numpy()
             assert np.abs(gv - ref).max() <= 64 * U32 * 1e-3 * steps + 1e-12, (k, p)
     b.close()
+
+
+@pytest.mark.timeout(900)
+def test_batch_extrapolated_restarts_match_oracle(orc, om):
+    # the batch's per-structure extrapolated restarts (OM_ACCEL_EXTRAPOLATE):
+    # each structure lands on the oracle's tightly converged D_eff, in fewer
+    # steps than the plain batch, in FP64 and FP32 storage
+    st = _structures(orc)
+    doms = [om.domain(t.shape, 2.0) for t, _ in st]
+    ref = []
+    for tr, d in st[:-1]:
+        rc, D, *_ = orc.diff_solve(tr, orc.omega_field(tr, d), 1.0, 0.0, tol=1e-11, K=100, max_steps=3_000_000)
+        assert rc == 0
+        ref.append(D)
+    for P, tol, rel in ((om.OM_F64, 1e-10, 1e-8), (om.OM_F32, 1e-7, 1e-5)):
+        total = {}
+        for accel in (om.OM_ACCEL_NONE, om.OM_ACCEL_EXTRAPOLATE):
+            b = om.Batch(doms, [_dev(t) for t, _ in st], [_dev(d) for _, d in st],
+                         diff=om.diff_params(conv_tol=tol, check_every=1000, max_steps=3_000_000, precision=P,
+                                             accel=accel))
+            dl, _, info, status = b.solve(1)
+            b.close()
+            assert status[-1] == om.OM_ENOPERC
+            for k, D in enumerate(ref):
+                assert status[k] == om.OM_OK
+                assert dl[k] == pytest.approx(D, rel=rel), (P, accel, k)
+            total[accel] = sum(i.steps for i in info[:-1])
+        assert total[om.OM_ACCEL_EXTRAPOLATE] < 0.8 * total[om.OM_ACCEL_NONE], total
