@@ -1000,11 +1000,12 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
       const BatchItem& bi = b->items_h[it];
       const double N = (double)b->dom[it].nx * b->dom[it].ny * b->dom[it].nz;
       double rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
-      if (model == 1) {
-        const double relj = o[0] != 0.0 ? std::fabs(o[0] - sj_prev[it]) / std::fabs(o[0]) : 0.0;
-        rel = std::max(rel, relj);
-        sj_prev[it] = o[0];
-      }
+      // relative change of the net flux (sum u_x, or sum J_x)
+      const double relf = o[0] != 0.0 ? std::fabs(o[0] - sj_prev[it]) / std::fabs(o[0]) : 0.0;
+      sj_prev[it] = o[0];
+      const int test = model == 0 ? b->fp.conv_test : b->dp.conv_test;
+      if (test == OM_TEST_FLUX) rel = relf;
+      else if (model == 1) rel = std::max(rel, relf);
       if (result) {
         if (model == 0) result[it] = ((b->fp.tau - 0.5) / 3.0) * (o[0] / N) / b->fp.body_force;
         else result[it] = (o[0] / N) * (double)bi.nx / (b->dp.c_in - b->dp.c_out);
@@ -1110,6 +1111,9 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if (dp && dp->lattice != 7) return fail(OM_EINVAL, "om_batch_create: batches take the D3Q7 diffusion lattice");
   if (dp && dp->accel != OM_ACCEL_NONE && dp->accel != OM_ACCEL_EXTRAPOLATE)
     return fail(OM_EINVAL, "om_batch_create: unknown accel");
+  if ((dp && dp->conv_test != OM_TEST_FIELD && dp->conv_test != OM_TEST_FLUX) ||
+      (fp && fp->conv_test != OM_TEST_FIELD && fp->conv_test != OM_TEST_FLUX))
+    return fail(OM_EINVAL, "om_batch_create: unknown conv_test");
   if (fp && !(fp->tau > 0.5)) return fail(OM_EINVAL, "om_batch_create: tau must exceed 1/2");
   if (fp && fp->drive != OM_DRIVE_FORCE) return fail(OM_EINVAL, "om_batch_create: batches take the body-force drive");
   if (dp && (!(dp->d_ref_nm > 0.0) || !(dp->tau_ref > 0.5) || !(dp->c_in != dp->c_out)))

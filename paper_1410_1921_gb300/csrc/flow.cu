@@ -588,6 +588,8 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
     return fail(OM_EINVAL, "om_flow_create: unknown precision");
   if (p->drive != OM_DRIVE_FORCE && p->drive != OM_DRIVE_PRESSURE)
     return fail(OM_EINVAL, "om_flow_create: unknown drive");
+  if (p->conv_test != OM_TEST_FIELD && p->conv_test != OM_TEST_FLUX)
+    return fail(OM_EINVAL, "om_flow_create: unknown conv_test");
   if (p->drive == OM_DRIVE_PRESSURE) {
     if (ns->dom.nx < 4) return fail(OM_EINVAL, "om_flow_create: the pressure drive needs nx >= 4");
     if (!(std::fabs(p->delta_rho) > 0.0 && std::fabs(p->delta_rho) < 0.1))
@@ -694,6 +696,7 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
   OM_CUDA(cudaEventCreate(&e1));
   double o[4];
   OM_TRY(flow_observe_any(fl, o, s));  // reference for the first check
+  double flux_prev = o[0];
   const int64_t t0 = fl->t;
   OM_CUDA(cudaEventRecord(e0, s));
   om_status rc = OM_ENOTCONVERGED;
@@ -707,7 +710,9 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
       diverged = true;
       break;
     }
-    rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+    if (p.conv_test == OM_TEST_FLUX) rel = o[0] != 0.0 ? std::fabs(o[0] - flux_prev) / std::fabs(o[0]) : 0.0;
+    else rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+    flux_prev = o[0];
     if (rel < p.conv_tol) {
       rc = OM_OK;
       break;
