@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kTile) flow_batch_observe(FlowArgs<T> a, const
       acc[0] = ux;
       acc[1] = fabs(ux - prev[n]);
       acc[2] = fabs(ux);
-      acc[3] = rho;
+      acc[3] = rho + flow_ref(a, n);
       prev[n] = ux;
     }
     block_reduce_write<4>(acc, partials + (int64_t)w * 4);
@@ -377,8 +377,9 @@ __global__ void flow_batch_export(FlowArgs<T> a, uint32_t off, const int64_t* vo
   C f[19];
   flow_load<T, ODD>(a, off + ln, nb, f);
   const int64_t v = vox[ln];
+  const double r1 = 1.0 + flow_ref(a, off + ln);
 #pragma unroll
-  for (int i = 0; i < 19; ++i) out[i * N + v] = (double)f[i] + q19_w(i);
+  for (int i = 0; i < 19; ++i) out[i * N + v] = (double)f[i] + q19_w(i) * r1;
 }
 
 template <class T, bool ODD>
@@ -403,6 +404,7 @@ __global__ void flow_batch_import(FlowArgs<T> a, uint32_t off, const int64_t* vo
   const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
   if (ln >= a.nf) return;
   const int64_t v = vox[ln];
+  if constexpr (kFlowRebased<T>) a.rr[off + ln] = 0.f;
 #pragma unroll
   for (int i = 0; i < 19; ++i)
     Stg<T>::st(a.s[i] + off + ln, (typename Stg<T>::C)(in[i * N + v] - q19_w(i)), a.up);
@@ -435,6 +437,7 @@ __global__ void flow_batch_init(FlowArgs<T> a, uint32_t off, const int64_t* vox,
   const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
   if (ln >= a.nf) return;
   const double u = warm_velocity(scale * (double)field[vox[ln] * stride]);
+  if constexpr (kFlowRebased<T>) a.rr[off + ln] = 0.f;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const double eu = (double)q19_e(i, 0) * u;
@@ -481,6 +484,12 @@ __global__ void batch_rebase(DiffArgs<T> a) {
   if (n < a.nf) diff_rebase_node<T>(a, n);
 }
 
+template <class T>
+__global__ void batch_flow_rebase(FlowArgs<T> a) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < a.nf) flow_rebase_node<T>(a, n);
+}
+
 }  // namespace om
 
 using namespace om;
@@ -496,7 +505,7 @@ struct Model {
   int q = 0;             // populations per node
   void* pop = nullptr;   // arena [q][pitch]
   void* omega = nullptr; // diffusion only, compute type, [pitch]
-  float* cr = nullptr;   // diffusion with 16-bit storage: per-node reference concentration
+  float* cr = nullptr;   // rebased storage: per-node reference concentration (diffusion) or density (flow)
   double* prev = nullptr;
   double* dprev = nullptr;  // diffusion with OM_ACCEL_EXTRAPOLATE: each node's change over the last window
   int64_t t = 0;
@@ -559,12 +568,12 @@ namespace {
 // small structure's do when it is solved alone.
 constexpr double kGroupBytes = 80e6;
 
-// bytes per node a sweep of the model touches (populations, omega and
-// reference concentration for the diffusion, packed coordinates)
+// bytes per node a sweep of the model touches (populations, omega for the
+// diffusion, the reference of rebased storage, packed coordinates)
 double node_bytes(const om_batch* b, int model) {
   const Model& m = b->m[model];
-  double per = (double)m.q * stg_bytes(m.prec) + 4.0;
-  if (model == 1) per += (m.prec == OM_F64 ? 8.0 : 4.0) + (m.cr ? 4.0 : 0.0);
+  double per = (double)m.q * stg_bytes(m.prec) + 4.0 + (m.cr ? 4.0 : 0.0);
+  if (model == 1) per += m.prec == OM_F64 ? 8.0 : 4.0;
   return per;
 }
 
@@ -638,6 +647,7 @@ FlowArgs<T> bflow_args(const om_batch* b) {
   a.g = (typename Stg<T>::C)b->fp.body_force;
   a.up = (typename Stg<T>::C)m.up;
   a.down = (typename Stg<T>::C)(1.0 / m.up);
+  a.rr = m.cr;
   return a;
 }
 
@@ -800,6 +810,7 @@ om_status window_t(om_batch* b, int model, int K, int mode, cudaStream_t s) {
   }
   m.t += K;
   if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
+  if (model == 0 && m.cr) batch_flow_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bflow_args<T>(b));
   return OM_OK;
 }
 
@@ -926,7 +937,8 @@ template <class T>
 om_status init_state_t(om_batch* b, int model, cudaStream_t s) {
   Model& m = b->m[model];
   OM_CUDA(cudaMemsetAsync(m.pop, 0, (size_t)m.q * b->pitch * stg_bytes(m.prec), s));  // rest / linear profile
-  if (m.cr) batch_cr_linear<<<b->sms * 4, kTile, 0, s>>>(b->items, b->work, b->nwork, b->dp.c_in, m.cr);
+  if (m.cr && model == 1) batch_cr_linear<<<b->sms * 4, kTile, 0, s>>>(b->items, b->work, b->nwork, b->dp.c_in, m.cr);
+  if (m.cr && model == 0) OM_CUDA(cudaMemsetAsync(m.cr, 0, sizeof(float) * b->pitch, s));  // rest density
   OM_CUDA(cudaGetLastError());
   m.t = 0;
   return OM_OK;
@@ -1208,6 +1220,8 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     m.up = m.prec == OM_F16DEV ? (model == 0 ? 1024.0 : 64.0) : 1.0;
     if ((st = dalloc(&m.pop, (size_t)m.q * b->pitch * stg_bytes(m.prec))) != OM_OK) return bail(st);
     if ((st = dalloc((void**)&m.prev, sizeof(double) * b->pitch)) != OM_OK) return bail(st);
+    if (model == 0 && stg_bytes(m.prec) <= 4 && (st = dalloc((void**)&m.cr, sizeof(float) * b->pitch)) != OM_OK)
+      return bail(st);
     if (model == 1 && dp->accel == OM_ACCEL_EXTRAPOLATE &&
         (st = dalloc((void**)&m.dprev, sizeof(double) * b->pitch)) != OM_OK)
       return bail(st);

@@ -73,7 +73,7 @@ namespace om {
 // variant 2: the registers they need halve the resident threads.)
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
-constexpr int kSweepVariants = 10;
+constexpr int kSweepVariants = 13;
 
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(256, MINB) d3q19_sweep(FlowArgs<T> a) {
@@ -135,6 +135,67 @@ __device__ __forceinline__ void flow_odd_rec(const FlowArgs<T>& a, uint32_t t, u
     const uint32_t n = __ldg(a.slow + (t - a.nf));
     flow_node_at<T, true>(a, n, __ldg(a.coord + n));
   }
+}
+
+// Odd step of a record node with nothing but its populations held across
+// the collision: the neighbours (and, for rebased storage, their reference
+// densities) are taken from the records before the loads, and again after
+// the collision for the stores (variants 10-12; the slow nodes run as their
+// own launch, d3q19_sweep_slow, so that the column-map code sets no
+// register budget here).
+template <class T>
+__device__ __forceinline__ void flow_odd_rec_lean(const FlowArgs<T>& a, uint32_t n, uint2 r, uint2 q) {
+  using C = typename Stg<T>::C;
+  C f[19];
+  float rn = 0.f;
+  if constexpr (kFlowRebased<T>) rn = a.rr[n];
+  {
+    uint32_t nb[19];
+    rec_neighbours19(r, q, n, nb);
+    f[0] = Stg<T>::ld(a.s[0] + n, a.down);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      const uint32_t o = (uint32_t)q19_opp(i), src = nb[o];
+      const uint32_t off = src != kNoNode ? o * a.P + src : (uint32_t)i * a.P + n;
+      f[i] = Stg<T>::ld(a.s[0] + off, a.down);
+      if constexpr (kFlowRebased<T>)
+        if (src != kNoNode) f[i] += (float)q19_w(i) * (a.rr[src] - rn);
+    }
+  }
+  flow_collide(a, n, f);
+  order_after(f[16], f[17]);
+  asm volatile("" : "+r"(r.x), "+r"(r.y), "+r"(q.x), "+r"(q.y), "+r"(n));
+  {
+    uint32_t nb[19];
+    rec_neighbours19(r, q, n, nb);
+    Stg<T>::st(a.s[0] + n, f[0], a.up);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      const uint32_t dst = nb[i];
+      const uint32_t off = dst != kNoNode ? (uint32_t)i * a.P + dst : (uint32_t)q19_opp(i) * a.P + n;
+      C v = f[i];
+      if constexpr (kFlowRebased<T>)
+        if (dst != kNoNode) v -= (float)q19_w(i) * (a.rr[dst] - rn);
+      Stg<T>::st(a.s[0] + off, v, a.up);
+    }
+  }
+}
+
+template <class T, int MINB>
+__global__ void __launch_bounds__(256, MINB) d3q19_sweep_rec_lean(FlowArgs<T> a) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  const uint2 r = __ldg(a.rec7 + n);
+  if (rec_slow(r)) return;
+  flow_odd_rec_lean<T>(a, n, r, __ldg(a.rec19 + n));
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) d3q19_sweep_slow(FlowArgs<T> a) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nslow) return;
+  const uint32_t n = __ldg(a.slow + t);
+  flow_node_at<T, true>(a, n, __ldg(a.coord + n));
 }
 
 template <class T, int MINB>
@@ -201,7 +262,7 @@ __global__ void __launch_bounds__(kObsThreads) d3q19_observe(FlowArgs<T> a, doub
       jx += (double)q19_e(i, 0) * (double)f[i];
     }
     const double ux = jx + 0.5 * (double)a.g;
-    acc[3] += rho;
+    acc[3] += rho + flow_ref(a, n);
     if (flow_boundary_index(a, n) >= 0) continue;  // pressure drive: velocity sums over interior layers
     acc[0] += ux;
     acc[1] += fabs(ux - prev[n]);
@@ -223,8 +284,9 @@ __global__ void d3q19_export(FlowArgs<T> a, const int64_t* vox, int64_t N, doubl
   flow_load<T, ODD>(a, n, nb, f);
   const int64_t v = vox[n];
   if (fdense) {
+    const double r1 = 1.0 + flow_ref(a, n);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fdense[i * N + v] = (double)f[i] + q19_w(i);
+    for (int i = 0; i < 19; ++i) fdense[i * N + v] = (double)f[i] + q19_w(i) * r1;
   }
   if (udense) {
     double jx = 0, jy = 0, jz = 0;
@@ -246,6 +308,7 @@ __global__ void d3q19_import(FlowArgs<T> a, const int64_t* vox, int64_t N, const
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   const int64_t v = vox[n];
+  if constexpr (kFlowRebased<T>) a.rr[n] = 0.f;
 #pragma unroll
   for (int i = 0; i < 19; ++i) S::st(a.s[i] + n, (typename S::C)(fdense[i * N + v] - q19_w(i)), a.up);
 }
@@ -256,6 +319,7 @@ __global__ void d3q19_init_u(FlowArgs<T> a, const int64_t* vox, const float* ux,
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
   const double u = warm_velocity(scale * (double)ux[vox[n] * stride]);
+  if constexpr (kFlowRebased<T>) a.rr[n] = 0.f;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const double eu = (double)q19_e(i, 0) * u;
@@ -329,8 +393,18 @@ template <class T>
 __global__ void d3q19_rest(FlowArgs<T> a) {
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.nf) return;
+  if constexpr (kFlowRebased<T>) a.rr[n] = 0.f;
 #pragma unroll
   for (int i = 0; i < 19; ++i) Stg<T>::st(a.s[i] + n, 0, a.up);
+}
+
+// rebased storage: every node's reference moved to its current density
+// (even time), once per check window
+template <class T>
+__global__ void d3q19_rebase(FlowArgs<T> a) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.nf) return;
+  flow_rebase_node<T>(a, n);
 }
 
 }  // namespace om
@@ -368,9 +442,17 @@ void launch_sweep_p(int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>&
     case 7:
     case 8:
     case 9:
+    case 10:
+    case 11:
+    case 12:
       if (ODD && a.rec7) {
         const unsigned nbr = blocks_for((int64_t)a.nf + a.nslow);
-        if (variant == 7) d3q19_sweep_rec<T, 0><<<nbr, 256, 0, s>>>(a);
+        if (variant >= 10) {
+          if (variant == 10) d3q19_sweep_rec_lean<T, 0><<<nb, 256, 0, s>>>(a);
+          else if (variant == 11) d3q19_sweep_rec_lean<T, M><<<nb, 256, 0, s>>>(a);
+          else d3q19_sweep_rec_lean<T, M - 1><<<nb, 256, 0, s>>>(a);
+          if (a.nslow) d3q19_sweep_slow<T><<<blocks_for(a.nslow), 256, 0, s>>>(a);
+        } else if (variant == 7) d3q19_sweep_rec<T, 0><<<nbr, 256, 0, s>>>(a);
         else if (variant == 8) d3q19_sweep_rec<T, M><<<nbr, 256, 0, s>>>(a);
         else {
           auto k = d3q19_sweep_rec_strided<T>;
@@ -452,6 +534,7 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
       }
       fl->t += K;
       nsteps -= K;
+      if (kFlowRebased<T>) d3q19_rebase<T><<<nb, 256, 0, s>>>(a);  // once per window
       continue;
     }
     const bool odd = fl->t & 1;
@@ -620,7 +703,9 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   fl->up = p->precision == OM_F16DEV ? 1024.0 : 1.0;
   DevBuf<uint8_t> f;
   DevBuf<double> prev, part, obs;
+  DevBuf<float> rr;
   om_status st = f.alloc(19 * (size_t)ns->pitch * storage_bytes(p->precision));
+  if (st == OM_OK && storage_bytes(p->precision) <= 4) st = rr.alloc(ns->pitch);
   if (st == OM_OK) st = prev.alloc(ns->nf);
   if (st == OM_OK) st = part.alloc((size_t)kObsBlocks * 8);
   if (st == OM_OK) st = obs.alloc(8);
@@ -640,6 +725,7 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
     return st;
   }
   fl->f = f.take();
+  fl->rr = rr.take();
   fl->prev = prev.take();
   fl->partials = part.take();
   fl->obs_dev = obs.take();
@@ -788,6 +874,7 @@ extern "C" om_status om_flow_destroy(om_flow* fl) {
   if (fl->exec) cudaGraphExecDestroy(fl->exec);
   if (fl->cap) cudaStreamDestroy(fl->cap);
   cudaFree(fl->f);
+  cudaFree(fl->rr);
   cudaFree(fl->prev);
   cudaFree(fl->partials);
   cudaFree(fl->obs_dev);

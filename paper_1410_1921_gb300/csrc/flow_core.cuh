@@ -32,7 +32,24 @@ struct FlowArgs {
   const uint2* rec19 = nullptr;
   const uint32_t* slow = nullptr;
   uint32_t nslow = 0;
+  // rebased storage (kFlowRebased<T>): per-node reference density deviation
+  float* rr = nullptr;
 };
+
+// Reference state of the stored deviations.  FP64: w_i (rest at rho0 = 1).
+// FP32 and 16-bit: w_i (1 + rr(node)), a per-node density the solver moves
+// to the node's current density once per check window ("rebasing", as the
+// diffusion does with its concentration).  A slow flow's velocity is a small
+// difference of populations that also carry the local density deviation
+// (body-force driven flow in tortuous pores: delta rho / u ~ 3 L nu / k, 1e2
+// to 1e4); without the rebase that deviation takes 7-13 bits of every stored
+// value, which biased single-precision k by up to 2e-5 and kept the
+// per-node velocity change above 1e-5 in tight pores.  A population that
+// changes node is re-referenced by w_i (rr(source) - rr(target)) -- only on
+// odd steps, where populations are read from and written to neighbours; the
+// collision is unchanged (it is invariant under a shift of the rest part).
+template <class T>
+constexpr bool kFlowRebased = sizeof(T) <= 4;
 
 // nb[i] = node number of x + e_i (kNoNode off the node set); periodic y, z,
 // and x unless a.px = 0 (no neighbour beyond the x faces)
@@ -74,11 +91,25 @@ __device__ __forceinline__ void flow_load(const FlowArgs<T>& a, uint32_t n, cons
     flow_slots_odd(a, n, nb, off);
 #pragma unroll
     for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[0] + off[i], a.down);
+    if constexpr (kFlowRebased<T>) {
+      const float rn = a.rr[n];
+#pragma unroll
+      for (int i = 1; i < 19; ++i) {
+        const uint32_t src = nb[q19_opp(i)];
+        if (src != kNoNode) f[i] += (float)q19_w(i) * (a.rr[src] - rn);
+      }
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[i] + n, a.down);
   }
 }
+
+// An empty asm statement taking two values as in-out operands: what reads
+// them afterwards cannot be scheduled before the code that produced them
+// (keeps the reference gathers of a rebased odd step after the collision).
+__device__ __forceinline__ void order_after(float& a, float& b) { asm volatile("" : "+f"(a), "+f"(b)); }
+__device__ __forceinline__ void order_after(double& a, double& b) { asm volatile("" : "+d"(a), "+d"(b)); }
 
 template <class C>
 __device__ __forceinline__ void trt_collide(C (&f)[19], C wp, C wm, C g) {
@@ -122,8 +153,12 @@ __device__ __forceinline__ void flow_collide(const FlowArgs<T>& a, uint32_t n, t
     const int64_t k = flow_boundary_index(a, n);
     if (k >= 0) {
       const uint32_t nbt = a.n_in + a.n_out;
+      // the extrapolated populations are deviations from w_i; rebased storage
+      // refers the node's to w_i (1 + rr(n))
+      typename Stg<T>::C rn = 0;
+      if constexpr (kFlowRebased<T>) rn = a.rr[n];
 #pragma unroll
-      for (int i = 0; i < 19; ++i) f[i] = a.bc[(size_t)i * nbt + k];
+      for (int i = 0; i < 19; ++i) f[i] = a.bc[(size_t)i * nbt + k] - typename Stg<T>::C(q19_w(i)) * rn;
     }
   }
   trt_collide(f, a.wp, a.wm, a.g);
@@ -144,7 +179,29 @@ __device__ __forceinline__ void flow_node_nb(const FlowArgs<T>& a, uint32_t n, c
     flow_slots_odd(a, n, nb, off);
 #pragma unroll
     for (int i = 0; i < 19; ++i) f[i] = Stg<T>::ld(a.s[0] + off[i], a.down);
-    flow_collide(a, n, f);
+    if constexpr (kFlowRebased<T>) {
+      // Population i came from x - e_i, and leaves for x + e_i, when its
+      // slot offset points into another node's slots: the node index
+      // off - (slot array) * P then lies in [0, P) (a bounce-back slot of
+      // the node itself gives an index outside it).  The references are
+      // gathered again after the collision rather than held across it
+      // (fewer live registers; the second reads hit L1).
+      const float rn = a.rr[n];
+#pragma unroll
+      for (int i = 1; i < 19; ++i) {
+        const uint32_t src = off[i] - (uint32_t)q19_opp(i) * a.P;
+        if (src < a.P) f[i] += (float)q19_w(i) * (a.rr[src] - rn);
+      }
+      flow_collide(a, n, f);
+      order_after(f[16], f[17]);
+#pragma unroll
+      for (int i = 1; i < 19; ++i) {
+        const uint32_t dst = off[q19_opp(i)] - (uint32_t)i * a.P;
+        if (dst < a.P) f[i] -= (float)q19_w(i) * (a.rr[dst] - rn);
+      }
+    } else {
+      flow_collide(a, n, f);
+    }
 #pragma unroll
     for (int i = 0; i < 19; ++i) Stg<T>::st(a.s[0] + off[q19_opp(i)], f[i], a.up);
   } else {
@@ -177,6 +234,33 @@ __device__ __forceinline__ void flow_pair_even(const FlowArgs<T>& a, uint32_t n)
   flow_collide(a, n + 1, f1);
 #pragma unroll
   for (int i = 0; i < 19; ++i) Pair<T>::st(a.s[q19_opp(i)] + n, f0[i], f1[i], a.up);
+}
+
+// Move node n's reference to its current density (even time only):
+// rr += sum_i dev_i, dev_i -= w_i (rr_new - rr_old).
+template <class T>
+__device__ __forceinline__ void flow_rebase_node(const FlowArgs<T>& a, uint32_t n) {
+  if constexpr (kFlowRebased<T>) {
+    using S = Stg<T>;
+    float f[19], sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      f[i] = S::ld(a.s[i] + n, a.down);
+      sum += f[i];
+    }
+    const float old = a.rr[n];
+    const float now = old + sum;
+    a.rr[n] = now;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) S::st(a.s[i] + n, f[i] + (float)q19_w(i) * (old - now), a.up);
+  }
+}
+
+// Reference density deviation of node n (0 for FP64 storage)
+template <class T>
+__device__ __forceinline__ double flow_ref(const FlowArgs<T>& a, uint32_t n) {
+  if constexpr (kFlowRebased<T>) return (double)a.rr[n];
+  else return 0.0;
 }
 
 // flow_node_at for node n whose coordinates are coord[ln]

@@ -12,6 +12,7 @@ struct om_flow {
   const om_nodeset* ns = nullptr;
   om_flow_params p{};
   void* f = nullptr;
+  float* rr = nullptr;  // rebased storage: per-node reference density deviation
   double* prev = nullptr;
   double* partials = nullptr;
   double* obs_dev = nullptr;
@@ -69,6 +70,7 @@ inline FlowArgs<T> flow_args(const om_flow* fl) {
   a.rec19 = ns->rec19;
   a.slow = ns->slow;
   a.nslow = (uint32_t)ns->n_slow;
+  a.rr = fl->rr;
   a.nx = ns->dom.nx;
   a.ny = ns->dom.ny;
   a.nz = ns->dom.nz;

@@ -99,8 +99,8 @@ om_status load(const StateView& v, int64_t* t, const void* host, int64_t bytes, 
 }
 
 StateView flow_view(const om_flow* fl) {
-  return StateView{0, fl->p.precision, 19, 0, fl->ns->nf, fl->ns->pitch, elem_bytes(fl->p.precision),
-                   fl->f, fl->prev, nullptr, fl->up};
+  return StateView{0, fl->p.precision, 19, fl->rr ? 1 : 0, fl->ns->nf, fl->ns->pitch, elem_bytes(fl->p.precision),
+                   fl->f, fl->prev, fl->rr, fl->up};
 }
 
 StateView diff_view(const om_diff* df) {

@@ -24,7 +24,7 @@ import synthetic as S
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-FLOW_VARIANTS = 10  # launch variants of the D3Q19 flow sweep (flow.cu)
+FLOW_VARIANTS = 13  # launch variants of the D3Q19 flow sweep (flow.cu)
 DIFF_VARIANTS = 9  # of the diffusion sweep (diff.cu)
 
 
@@ -345,8 +345,12 @@ def test_flow_converged_permeability(orc, om, name, node, tau):
     assert rc == 0
     st, k64, info = _flow_solve_gpu(om, node, om.OM_F64, tau=tau)
     assert st == om.OM_OK and k64 == pytest.approx(kL, rel=1e-10)
+    # FP32: near the steady state an LB step changes each stored population by
+    # less than its rounding unit, so the single-precision iteration stalls
+    # at a point within ~1e-5 of the fixed point (here -7.5e-6 after 20000
+    # steps, and the relative-change test can already be met at that stall)
     st, k32, info = _flow_solve_gpu(om, node, om.OM_F32, tau=tau, tol=1e-7)
-    assert st == om.OM_OK and k32 == pytest.approx(kL, rel=1e-5)
+    assert st == om.OM_OK and k32 == pytest.approx(kL, rel=2e-5)
 
 
 def test_flow_converged_reconstructed(orc, om):
