@@ -1220,8 +1220,6 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     m.up = m.prec == OM_F16DEV ? (model == 0 ? 1024.0 : 64.0) : 1.0;
     if ((st = dalloc(&m.pop, (size_t)m.q * b->pitch * stg_bytes(m.prec))) != OM_OK) return bail(st);
     if ((st = dalloc((void**)&m.prev, sizeof(double) * b->pitch)) != OM_OK) return bail(st);
-    if (model == 0 && stg_bytes(m.prec) <= 4 && (st = dalloc((void**)&m.cr, sizeof(float) * b->pitch)) != OM_OK)
-      return bail(st);
     if (model == 1 && dp->accel == OM_ACCEL_EXTRAPOLATE &&
         (st = dalloc((void**)&m.dprev, sizeof(double) * b->pitch)) != OM_OK)
       return bail(st);

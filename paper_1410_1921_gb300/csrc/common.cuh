@@ -127,7 +127,7 @@ inline unsigned resident_grid(K kernel, unsigned nb, int threads = 256, size_t s
 // Launch variants the autotuner chose, remembered for the life of the
 // process per (solver kind, precision, device, octave of the node count):
 // the first solver of a class times the variants, later ones reuse the choice.
-enum { kTuneFlow = 0, kTuneDiff7 = 1, kTuneDiff19 = 2 };
+enum { kTuneFlow = 0, kTuneDiff7 = 1, kTuneDiff19 = 2, kTuneFlowReb = 3 };
 bool tuned_lookup(int kind, int prec, int64_t nf, int var[2]);
 void tuned_store(int kind, int prec, int64_t nf, const int var[2]);
 

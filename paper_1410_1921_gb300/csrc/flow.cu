@@ -73,6 +73,13 @@ namespace om {
 // variant 2: the registers they need halve the resident threads.)
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
+
+// om_flow_solve enters the rebased mode (flow_core.cuh) once the relative
+// change of the velocity field over a check window falls below this: two to
+// three decades before a tight test, and above the ~1e-5 floor that
+// single-precision rounding puts under that change in tight pores without
+// the rebase.
+constexpr double kRebaseBelow = 1e-4;
 constexpr int kSweepVariants = 13;
 
 template <class T, bool ODD, int MINB>
@@ -490,10 +497,16 @@ void launch_step(const om_flow* fl, bool odd, int variant, unsigned nb, cudaStre
   launch_sweep<T>(odd, variant, nb, s, a);
 }
 
+// launch variants of the storage mode T
+template <class T>
+int* flow_var(om_flow* fl) {
+  return kFlowRebased<T> ? fl->varr : fl->var;
+}
+
 // Capture K sweeps (K even, from an even time) into a CUDA graph once.
 template <class T>
 om_status flow_capture_t(om_flow* fl, int K) {
-  if (fl->exec && fl->graph_k == K) return OM_OK;
+  if (fl->exec && fl->graph_k == K && fl->graph_reb == kFlowRebased<T>) return OM_OK;
   if (fl->exec) {
     cudaGraphExecDestroy(fl->exec);
     fl->exec = nullptr;
@@ -503,13 +516,15 @@ om_status flow_capture_t(om_flow* fl, int K) {
   const unsigned nb = blocks_for(a.nf);
   cudaGraph_t g = nullptr;
   OM_CUDA(cudaStreamBeginCapture(fl->cap, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) launch_step<T>(fl, k & 1, fl->var[k & 1], nb, fl->cap, a);
+  const int* V = flow_var<T>(fl);
+  for (int k = 0; k < K; ++k) launch_step<T>(fl, k & 1, V[k & 1], nb, fl->cap, a);
   cudaError_t e = cudaStreamEndCapture(fl->cap, &g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
   e = cudaGraphInstantiate(&fl->exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
   fl->graph_k = K;
+  fl->graph_reb = kFlowRebased<T>;
   return OM_OK;
 }
 
@@ -524,13 +539,14 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
   FlowArgs<T> a = flow_args<T>(fl);
   const unsigned nb = blocks_for(a.nf);
   const int K = fl->p.check_every;
+  const int* V = flow_var<T>(fl);
   while (nsteps > 0) {
     if (K >= 2 && !(K & 1) && !(fl->t & 1) && nsteps >= K) {
       if (fl->windows++ > 0) {
         OM_TRY(flow_capture_t<T>(fl, K));
         OM_CUDA(cudaGraphLaunch(fl->exec, s));
       } else {  // the first whole window as plain launches: one-window calls capture nothing
-        for (int k = 0; k < K; ++k) launch_step<T>(fl, k & 1, fl->var[k & 1], nb, s, a);
+        for (int k = 0; k < K; ++k) launch_step<T>(fl, k & 1, V[k & 1], nb, s, a);
       }
       fl->t += K;
       nsteps -= K;
@@ -538,7 +554,7 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
       continue;
     }
     const bool odd = fl->t & 1;
-    launch_step<T>(fl, odd, fl->var[odd], nb, s, a);
+    launch_step<T>(fl, odd, V[odd], nb, s, a);
     ++fl->t;
     --nsteps;
   }
@@ -553,7 +569,9 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
 template <class T>
 om_status flow_tune_t(om_flow* fl, cudaStream_t s) {
   if (fl->ns->nf == 0) return OM_OK;
-  if (tuned_lookup(kTuneFlow, fl->p.precision, fl->ns->nf, fl->var)) return OM_OK;
+  const int kind = kFlowRebased<T> ? kTuneFlowReb : kTuneFlow;
+  int* V = flow_var<T>(fl);
+  if (tuned_lookup(kind, fl->p.precision, fl->ns->nf, V)) return OM_OK;
   FlowArgs<T> a = flow_args<T>(fl);
   const unsigned nb = blocks_for(a.nf);
   cudaEvent_t ev[3];
@@ -578,11 +596,11 @@ om_status flow_tune_t(om_flow* fl, cudaStream_t s) {
     for (int p = 0; p < 2; ++p)
       if (tot[p] < best[p]) {
         best[p] = tot[p];
-        fl->var[p] = v;
+        V[p] = v;
       }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  tuned_store(kTuneFlow, fl->p.precision, fl->ns->nf, fl->var);
+  tuned_store(kind, fl->p.precision, fl->ns->nf, V);
   d3q19_rest<T><<<nb, 256, 0, s>>>(a);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
@@ -642,14 +660,40 @@ om_status flow_rest_t(om_flow* fl, cudaStream_t s) {
   return OM_OK;
 }
 
-#define OM_FLOW_DISPATCH(fl, fn, ...)                                        \
-  switch ((fl)->p.precision) {                                               \
-    case OM_F64: return fn<double>(__VA_ARGS__);                             \
-    case OM_F32: return fn<float>(__VA_ARGS__);                              \
-    case OM_F16DEV: return fn<__half>(__VA_ARGS__);                          \
-    case OM_BF16DEV: return fn<__nv_bfloat16>(__VA_ARGS__);                  \
-    default: return fail(OM_EINVAL, "unknown precision");                    \
+// the storage type of the solver's precision and mode (rebased or not)
+#define OM_FLOW_DISPATCH(fl, fn, ...)                                                            \
+  switch ((fl)->p.precision) {                                                                   \
+    case OM_F64: return fn<double>(__VA_ARGS__);                                                 \
+    case OM_F32: return (fl)->reb ? fn<Reb<float>>(__VA_ARGS__) : fn<float>(__VA_ARGS__);        \
+    case OM_F16DEV: return (fl)->reb ? fn<Reb<__half>>(__VA_ARGS__) : fn<__half>(__VA_ARGS__);   \
+    case OM_BF16DEV:                                                                             \
+      return (fl)->reb ? fn<Reb<__nv_bfloat16>>(__VA_ARGS__) : fn<__nv_bfloat16>(__VA_ARGS__);   \
+    default: return fail(OM_EINVAL, "unknown precision");                                        \
   }
+
+// Enter the rebased mode from the current (unrebased) state: the reference
+// starts at zero and takes the nodes' densities, the stored deviations lose
+// them (an exact change of variables, at an even time).
+template <class S>
+om_status flow_enter_rebased_s(om_flow* fl, cudaStream_t s) {
+  if (fl->ns->nf > 0) {
+    OM_CUDA(cudaMemsetAsync(fl->rr, 0, sizeof(float) * fl->ns->nf, s));
+    FlowArgs<Reb<S>> a = flow_args<Reb<S>>(fl);
+    d3q19_rebase<Reb<S>><<<blocks_for(a.nf), 256, 0, s>>>(a);
+    OM_CUDA(cudaGetLastError());
+  }
+  fl->reb = true;
+  return OM_OK;
+}
+om_status flow_enter_rebased(om_flow* fl, cudaStream_t s) {
+  if (fl->reb || !fl->rr || (fl->t & 1)) return OM_OK;
+  switch (fl->p.precision) {
+    case OM_F32: return flow_enter_rebased_s<float>(fl, s);
+    case OM_F16DEV: return flow_enter_rebased_s<__half>(fl, s);
+    case OM_BF16DEV: return flow_enter_rebased_s<__nv_bfloat16>(fl, s);
+    default: return OM_OK;
+  }
+}
 
 size_t storage_bytes(int prec) {
   return prec == OM_F64 ? 8 : (prec == OM_F32 ? 4 : 2);
@@ -733,9 +777,17 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   fl->bc = bc.take();
   auto rest = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_rest_t, fl, s); };
   auto tune = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_tune_t, fl, s); };
-  if (p->variant >= 0) fl->var[0] = fl->var[1] = std::min(p->variant, kSweepVariants - 1);
+  if (p->variant >= 0)
+    fl->var[0] = fl->var[1] = fl->varr[0] = fl->varr[1] = std::min(p->variant, kSweepVariants - 1);
   st = rest();
   if (st == OM_OK && p->variant < 0) st = tune();
+  if (st == OM_OK && p->variant < 0 && fl->rr) {  // and the rebased mode's kernels, from rest
+    fl->reb = true;
+    st = rest();
+    if (st == OM_OK) st = tune();
+    fl->reb = false;
+    if (st == OM_OK) st = rest();
+  }
   if (st == OM_OK) {
     double o[4];
     st = flow_observe_any(fl, o, s);  // prev <- u_x of the rest state
@@ -792,6 +844,7 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
     int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (fl->t - t0));
     OM_TRY(om_flow_step(fl, k, stream));
     OM_TRY(flow_observe_any(fl, o, s));
+    const double rel_field = o[2] > 0.0 ? o[1] / o[2] : 0.0;
     if (!std::isfinite(o[0]) || !std::isfinite(o[2])) {
       diverged = true;
       break;
@@ -803,6 +856,10 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
       rc = OM_OK;
       break;
     }
+    // the last decades of the convergence in the rebased mode (single and
+    // half precision): its storage resolves the velocity where the
+    // unrebased one spends bits on the local density deviation
+    if (!fl->reb && fl->rr && rel_field < kRebaseBelow) OM_TRY(flow_enter_rebased(fl, s));
   }
   OM_CUDA(cudaEventRecord(e1, s));
   OM_CUDA(cudaEventSynchronize(e1));
@@ -847,6 +904,7 @@ extern "C" om_status om_flow_set_populations(om_flow* fl, const double* f_dev, v
   if (!fl || !f_dev) return fail(OM_EINVAL, "om_flow_set_populations: null pointer");
   cudaStream_t s = as_stream(stream);
   fl->t = 0;
+  fl->reb = false;
   auto imp = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_import_t, fl, f_dev, s); };
   OM_TRY(imp());
   double o[4];
@@ -857,6 +915,7 @@ extern "C" om_status om_flow_init_velocity(om_flow* fl, const float* ux_dev, int
                                            void* stream) {
   if (!fl || !ux_dev || stride < 1) return fail(OM_EINVAL, "om_flow_init_velocity: bad argument");
   cudaStream_t s = as_stream(stream);
+  fl->reb = false;
   auto init = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_init_u_t, fl, ux_dev, stride, scale, s); };
   OM_TRY(init());
   double o[4];

@@ -36,10 +36,12 @@ struct FlowArgs {
   float* rr = nullptr;
 };
 
-// Reference state of the stored deviations.  FP64: w_i (rest at rho0 = 1).
-// FP32 and 16-bit: w_i (1 + rr(node)), a per-node density the solver moves
-// to the node's current density once per check window ("rebasing", as the
-// diffusion does with its concentration).  A slow flow's velocity is a small
+// Reference state of the stored deviations: w_i (rest at rho0 = 1), or in
+// the rebased mode (storage type Reb<S>, FP32 and 16-bit) w_i (1 + rr(node)),
+// a per-node density the solver moves to the node's current density once
+// per check window ("rebasing", as the diffusion does with its
+// concentration).  om_flow_solve switches to the rebased mode for the last
+// decades of a tight convergence (see flow.cu).  A slow flow's velocity is a small
 // difference of populations that also carry the local density deviation
 // (body-force driven flow in tortuous pores: delta rho / u ~ 3 L nu / k, 1e2
 // to 1e4); without the rebase that deviation takes 7-13 bits of every stored
@@ -49,7 +51,9 @@ struct FlowArgs {
 // odd steps, where populations are read from and written to neighbours; the
 // collision is unchanged (it is invariant under a shift of the rest part).
 template <class T>
-constexpr bool kFlowRebased = sizeof(T) <= 4;
+constexpr bool kFlowRebased = false;
+template <class S>
+constexpr bool kFlowRebased<Reb<S>> = true;
 
 // nb[i] = node number of x + e_i (kNoNode off the node set); periodic y, z,
 // and x unless a.px = 0 (no neighbour beyond the x faces)

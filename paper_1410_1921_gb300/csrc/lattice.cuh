@@ -96,6 +96,30 @@ struct Pair<__nv_bfloat16> {
   }
 };
 
+// Storage S rebased on a per-node reference (the flow's rebased mode): the
+// same bits in memory as S; the type only selects the kernels that apply the
+// reference (kFlowRebased in flow_core.cuh).
+template <class S>
+struct Reb {
+  S v;
+};
+template <class S>
+struct Stg<Reb<S>> {
+  using C = typename Stg<S>::C;
+  __device__ __forceinline__ static C ld(const Reb<S>* p, C down) { return Stg<S>::ld(&p->v, down); }
+  __device__ __forceinline__ static void st(Reb<S>* p, C v, C up) { Stg<S>::st(&p->v, v, up); }
+};
+template <class S>
+struct Pair<Reb<S>> {
+  using C = typename Stg<S>::C;
+  __device__ __forceinline__ static void ld(const Reb<S>* p, C down, C& a, C& b) {
+    Pair<S>::ld(reinterpret_cast<const S*>(p), down, a, b);
+  }
+  __device__ __forceinline__ static void st(Reb<S>* p, C a, C b, C up) {
+    Pair<S>::st(reinterpret_cast<S*>(p), a, b, up);
+  }
+};
+
 // Node number of voxel (x, y, z) from its column's bit map, or kNoNode.
 // Column-map indices fit 32 bits (nx*ny*W <= 1024*2048*64).
 __device__ __forceinline__ uint32_t node_at(const uint4* __restrict__ col, int ny, int W, int x,

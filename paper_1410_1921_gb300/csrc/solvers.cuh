@@ -20,6 +20,11 @@ struct om_flow {
   int64_t t = 0;
   double up = 1.0;  // storage scale of reduced-precision formats (stored = deviation * up)
   int var[2] = {0, 0};  // launch variant of the even and odd sweeps
+  int varr[2] = {0, 0};  // the same for the rebased mode
+  // rebased mode (storage Reb<S>, reference rr): entered by om_flow_solve
+  // for the last decades of its convergence, left by any (re)initialisation
+  bool reb = false;
+  bool graph_reb = false;  // the captured window is of the rebased kernels
   // pressure drive: boundary nodes [0, n_in) and [nf - n_out, nf), their
   // extrapolated populations (storage arithmetic type, [19][n_in + n_out])
   uint32_t n_in = 0, n_out = 0;

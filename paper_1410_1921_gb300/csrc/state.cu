@@ -99,7 +99,7 @@ om_status load(const StateView& v, int64_t* t, const void* host, int64_t bytes, 
 }
 
 StateView flow_view(const om_flow* fl) {
-  return StateView{0, fl->p.precision, 19, fl->rr ? 1 : 0, fl->ns->nf, fl->ns->pitch, elem_bytes(fl->p.precision),
+  return StateView{0, fl->p.precision, 19, fl->reb ? 1 : 0, fl->ns->nf, fl->ns->pitch, elem_bytes(fl->p.precision),
                    fl->f, fl->prev, fl->rr, fl->up};
 }
 
@@ -126,7 +126,19 @@ extern "C" om_status om_flow_save_state(const om_flow* fl, void* host, int64_t b
 
 extern "C" om_status om_flow_load_state(om_flow* fl, const void* host, int64_t bytes, void* stream) {
   if (!fl) return fail(OM_EINVAL, "om_flow_load_state: null pointer");
-  return load(flow_view(fl), &fl->t, host, bytes, as_stream(stream), "om_flow_load_state");
+  // the image says whether the saved solver was in its rebased mode (it
+  // then carries the reference densities); the solver takes that mode
+  bool reb = false;
+  if (host && bytes >= (int64_t)sizeof(StateHeader)) {
+    StateHeader h;
+    std::memcpy(&h, host, sizeof h);
+    reb = h.has_cr != 0 && fl->rr != nullptr;
+  }
+  const bool was = fl->reb;
+  fl->reb = reb;
+  const om_status st = load(flow_view(fl), &fl->t, host, bytes, as_stream(stream), "om_flow_load_state");
+  if (st != OM_OK) fl->reb = was;
+  return st;
 }
 
 extern "C" om_status om_diff_state_size(const om_diff* df, int64_t* bytes) {
