@@ -392,10 +392,9 @@ def converge_leg(P, W, n_struct=6, warm="none", fast_diff_prec=None):
     structure and model) against the fast form (all structures in one batch,
     extrapolated restarts of the diffusion, and -- warm="coarse" -- the
     diffusion started from a solve of the structures coarsened 2x per axis).
-    Both stop on the same tests: the flow on the relative change of its net
-    flux (FP32 rounding noise keeps every node's u_x from settling below
-    ~1e-5 in tight pores), the diffusion on the relative change of both its
-    concentration field and its net flux, each below 1e-6 over 1000 steps.
+    Both stop on the same tests: the flow on the relative change of its
+    velocity field, the diffusion on that of both its concentration field
+    and its net flux, each below 1e-6 over 1000 steps.
     Every result is compared with an FP64 reference converged 1e4-1e5 times
     tighter.  Setup (reconstruction, labelling, pore size) is outside both
     timings; the fast form's batch creation (and coarse solve) is inside.
@@ -403,8 +402,7 @@ def converge_leg(P, W, n_struct=6, warm="none", fast_diff_prec=None):
     field test at 1e-6 (its rounding floor is ~1e-5)."""
     import torch
     fdp = P.OM_F32 if fast_diff_prec is None else fast_diff_prec
-    fp = P.flow_params(precision=P.OM_F32, conv_tol=CONV_TOL, check_every=CONV_K, max_steps=CONV_CAP,
-                       conv_test=P.OM_TEST_FLUX)
+    fp = P.flow_params(precision=P.OM_F32, conv_tol=CONV_TOL, check_every=CONV_K, max_steps=CONV_CAP)
     dp = P.diff_params(precision=P.OM_F32, conv_tol=CONV_TOL, check_every=CONV_K, max_steps=CONV_CAP)
     dpx = P.diff_params(precision=fdp, conv_tol=CONV_TOL, check_every=CONV_K, max_steps=CONV_CAP,
                         accel=P.OM_ACCEL_EXTRAPOLATE)
@@ -480,8 +478,8 @@ def converge_leg(P, W, n_struct=6, warm="none", fast_diff_prec=None):
                                 "diffusion": sum(p["diff_steps"] for p in plain)},
                       "fast": {"flow": sum(i.steps for i in info_f), "diffusion": sum(i.steps for i in info_d),
                                "coarse_diffusion": coarse_steps}},
-            "test": f"flow: relative change of the net flux, diffusion: of the concentration field and the net "
-                    f"flux, < {CONV_TOL:g} over {CONV_K} steps (both forms)",
+            "test": f"flow: relative change of the velocity field, diffusion: of the concentration field and the "
+                    f"net flux, < {CONV_TOL:g} over {CONV_K} steps (both forms)",
             "reference": "FP64; flow: sum|du_x|/sum|u_x| < 1e-10, diffusion: field and flux < 1e-11, over 1000 steps",
             "reference_s": t_ref,
             "bound": CONV_BOUND, "max_rel_err": worst,

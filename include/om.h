@@ -76,8 +76,12 @@ enum { OM_PORE_CHORD13 = 0, OM_PORE_MIS = 1 };
 
 /* D3Q19 flow (Sec. 3.1): relaxation time tau (Eq. 8), body force along x in
  * lattice units, convergence when sum|du_x| / sum|u_x| over check_every
- * steps drops below conv_tol (conv_test OM_TEST_FIELD), or the relative
- * change of the net flux sum u_x does (OM_TEST_FLUX). */
+ * steps drops below conv_tol.  Single- and half-precision solves store their
+ * populations as deviations from w_i until that change falls below 1e-4,
+ * then as deviations from w_i (1 + rho_ref(node)) with the per-node
+ * reference moved to the node's density every check window (the velocity,
+ * a small difference of populations that also carry the local density
+ * deviation, keeps its precision; see flow_core.cuh). */
 typedef struct {
   double tau, body_force, conv_tol;
   int32_t check_every;
@@ -106,26 +110,14 @@ typedef struct {
    * OM_DRIVE_FORCE. */
   int32_t drive;
   double delta_rho;
-  /* OM_TEST_FIELD (the oracle's test) or OM_TEST_FLUX: the relative change
-   * of the net flux alone.  Single-precision storage of a slow flow in tight
-   * pores carries rounding noise in every node's u_x (its velocity is a small
-   * difference of populations dominated by the local density deviation) that
-   * keeps sum|du_x| above ~1e-5 of sum|u_x|; the net flux, which alone sets
-   * k, averages that noise out. */
-  int32_t conv_test;
 } om_flow_params;
-
-enum { OM_TEST_FIELD = 0, OM_TEST_FLUX = 1 };
 
 enum { OM_DRIVE_FORCE = 0, OM_DRIVE_PRESSURE = 1 };
 
 /* Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
  * size and relaxation time of Eq. 12, inlet/outlet concentrations.
  * Convergence: every check_every steps both sum|dC| / sum|C| and the relative
- * change of the total flux sum J_x drop below conv_tol (conv_test
- * OM_TEST_FIELD), or the latter alone (OM_TEST_FLUX: D_eff is set by the
- * flux, and 16-bit storage's rounding noise keeps sum|dC| / sum|C| above
- * ~1e-5).  lattice: 7 (D3Q7,
+ * change of the total flux sum J_x drop below conv_tol.  lattice: 7 (D3Q7,
  * c_s^2 = 1/4) or 19 (the paper's D3Q19 with the flow's velocities and
  * weights, c_s^2 = 1/3); D_L = c_s^2 (tau_g - 1/2).  Batches take 7 only. */
 typedef struct {
@@ -145,7 +137,6 @@ typedef struct {
    * convergence test, so the fixed point and the test are those of the
    * plain solve.  OM_ACCEL_NONE: the plain iteration. */
   int32_t accel;
-  int32_t conv_test; /* OM_TEST_FIELD or OM_TEST_FLUX, see above */
 } om_diff_params;
 
 enum { OM_ACCEL_NONE = 0, OM_ACCEL_EXTRAPOLATE = 1 };

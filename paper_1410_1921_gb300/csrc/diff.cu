@@ -544,8 +544,6 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   if (p->lattice != 7 && p->lattice != 19) return fail(OM_EINVAL, "om_diff_create: lattice must be 7 or 19");
   if (p->accel != OM_ACCEL_NONE && p->accel != OM_ACCEL_EXTRAPOLATE)
     return fail(OM_EINVAL, "om_diff_create: unknown accel");
-  if (p->conv_test != OM_TEST_FIELD && p->conv_test != OM_TEST_FLUX)
-    return fail(OM_EINVAL, "om_diff_create: unknown conv_test");
   cudaStream_t s = as_stream(stream);
   om_diff* df = new om_diff();
   df->ns = ns;
@@ -645,7 +643,7 @@ extern "C" om_status om_diff_solve(om_diff* df, double* D_eff_lattice, om_run_in
     }
     rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
     const double relj = o[0] != 0.0 ? std::fabs(o[0] - sj_prev) / std::fabs(o[0]) : 0.0;
-    rel = p.conv_test == OM_TEST_FLUX ? relj : std::max(rel, relj);
+    rel = std::max(rel, relj);
     sj_prev = o[0];
     if (rel < p.conv_tol) {
       rc = OM_OK;

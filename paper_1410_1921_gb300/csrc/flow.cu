@@ -715,8 +715,6 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
     return fail(OM_EINVAL, "om_flow_create: unknown precision");
   if (p->drive != OM_DRIVE_FORCE && p->drive != OM_DRIVE_PRESSURE)
     return fail(OM_EINVAL, "om_flow_create: unknown drive");
-  if (p->conv_test != OM_TEST_FIELD && p->conv_test != OM_TEST_FLUX)
-    return fail(OM_EINVAL, "om_flow_create: unknown conv_test");
   if (p->drive == OM_DRIVE_PRESSURE) {
     if (ns->dom.nx < 4) return fail(OM_EINVAL, "om_flow_create: the pressure drive needs nx >= 4");
     if (!(std::fabs(p->delta_rho) > 0.0 && std::fabs(p->delta_rho) < 0.1))
@@ -834,7 +832,6 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
   OM_CUDA(cudaEventCreate(&e1));
   double o[4];
   OM_TRY(flow_observe_any(fl, o, s));  // reference for the first check
-  double flux_prev = o[0];
   const int64_t t0 = fl->t;
   OM_CUDA(cudaEventRecord(e0, s));
   om_status rc = OM_ENOTCONVERGED;
@@ -844,14 +841,12 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
     int64_t k = std::min<int64_t>(p.check_every, p.max_steps - (fl->t - t0));
     OM_TRY(om_flow_step(fl, k, stream));
     OM_TRY(flow_observe_any(fl, o, s));
-    const double rel_field = o[2] > 0.0 ? o[1] / o[2] : 0.0;
+
     if (!std::isfinite(o[0]) || !std::isfinite(o[2])) {
       diverged = true;
       break;
     }
-    if (p.conv_test == OM_TEST_FLUX) rel = o[0] != 0.0 ? std::fabs(o[0] - flux_prev) / std::fabs(o[0]) : 0.0;
-    else rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
-    flux_prev = o[0];
+    rel = o[2] > 0.0 ? o[1] / o[2] : 0.0;
     if (rel < p.conv_tol) {
       rc = OM_OK;
       break;
@@ -859,7 +854,7 @@ extern "C" om_status om_flow_solve(om_flow* fl, double* k_lattice, om_run_info* 
     // the last decades of the convergence in the rebased mode (single and
     // half precision): its storage resolves the velocity where the
     // unrebased one spends bits on the local density deviation
-    if (!fl->reb && fl->rr && rel_field < kRebaseBelow) OM_TRY(flow_enter_rebased(fl, s));
+    if (!fl->reb && fl->rr && rel < kRebaseBelow) OM_TRY(flow_enter_rebased(fl, s));
   }
   OM_CUDA(cudaEventRecord(e1, s));
   OM_CUDA(cudaEventSynchronize(e1));
