@@ -234,6 +234,37 @@ om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om_domain d,
                            const om_diff_params* params, double* D_eff_m2s, double* tortuosity,
                            om_run_info* info, float* c_out);
 
+/* A structure's results in physical units from its lattice solves (the
+ * arithmetic behind om_solve_permeability / om_solve_knudsen, for callers
+ * that solve on the device objects or in batches):
+ *   k_m2        Eq. 15: k_lattice dx^2;
+ *   D_eff_m2s   Eq. 15 with the time step fixed by the reference pore
+ *               (Eqs. 11-12): D_eff_lattice D_K(d_ref) / (c_s^2 (tau_ref - 1/2)),
+ *               c_s^2 of params->lattice (1/4 on D3Q7, 1/3 on D3Q19);
+ *   D_mean_m2s  the same conversion of D_mean_lattice, the mean lattice
+ *               diffusivity over the transport nodes: the mean local Knudsen
+ *               diffusivity D of Eqs. 11-12 over them;
+ *   tortuosity  Eq. 16: porosity D / D_eff (porosity: pore voxels over all);
+ *   alpha       Sec. 4.2: the exponent of D_eff = D porosity^alpha for this
+ *               structure, ln(D_eff / D) / ln(porosity);
+ *   k_kc_m2     Eq. 17 (Kozeny-Carman, A = d^2 / 180) with d = mean_d_nm.
+ * Non-positive D_eff_lattice gives tortuosity +inf and alpha NaN; k_lattice
+ * may be 0.  OM_EINVAL for dx_nm <= 0, porosity outside (0, 1) or a
+ * non-positive mean_d_nm. */
+typedef struct {
+  double k_m2, D_eff_m2s, D_mean_m2s, tortuosity, alpha, k_kc_m2;
+} om_structure_results;
+om_status om_structure_results_from_lattice(double dx_nm, double k_lattice, double D_eff_lattice,
+                                            double D_mean_lattice, double porosity, double mean_d_nm,
+                                            const om_diff_params* params, om_structure_results* out);
+
+/* Sec. 4.2: the Bruggeman exponent alpha of D_eff = D porosity^alpha fitted
+ * over n structures, least squares on ln(D_eff / D) = alpha ln(porosity)
+ * (a line through the origin).  Host arrays of n values; OM_EINVAL if n < 1
+ * or any value is non-positive or a porosity is not below 1. */
+om_status om_bruggeman_fit(int64_t n, const double* porosity, const double* D_eff_m2s, const double* D_mean_m2s,
+                           double* alpha);
+
 /* Eq. 26: k_app = k (1 + D_eff mu / (k p)); f_c the bracket. */
 om_status om_apparent_permeability(double k_m2, double D_eff_m2s, double mu_Pa_s, double p_Pa,
                                    double* k_app_m2, double* f_c);

@@ -78,6 +78,18 @@ def bruggeman_alpha(D_eff, D_ref, porosity):
     return math.log(D_eff / D_ref) / math.log(porosity)
 
 
+def bruggeman_fit(porosities, D_effs, D_means):
+    """Sec. 4.2: the exponent alpha of D_eff = D eps^alpha fitted over a set
+    of structures by least squares on ln(D_eff / D) = alpha ln(eps) (a line
+    through the origin)."""
+    sxy = sxx = 0.0
+    for e, De, Dm in zip(porosities, D_effs, D_means):
+        x = math.log(e)
+        sxy += x * math.log(De / Dm)
+        sxx += x * x
+    return sxy / sxx
+
+
 def kozeny_carman(d_m, porosity):
     """Eq. 17 with A = d^2/180."""
     return (d_m * d_m / 180.0) * porosity ** 3 / (1.0 - porosity) ** 2

@@ -62,6 +62,10 @@ class om_slip_corrections(C.Structure):
                                            "jones_owens", "sampath_keighin", "florence")]
 
 
+class om_structure_results(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("k_m2", "D_eff_m2s", "D_mean_m2s", "tortuosity", "alpha", "k_kc_m2")]
+
+
 class om_run_info(C.Structure):
     _fields_ = [("steps", C.c_int64), ("n_nodes", C.c_int64), ("rel_change", C.c_double),
                 ("mass", C.c_double), ("seconds", C.c_double), ("mlups", C.c_double)]
@@ -88,6 +92,9 @@ _SIGS = {
     "om_solve_knudsen": [_vp, _vp, om_domain, C.POINTER(om_diff_params), _f64p, _f64p,
                          C.POINTER(om_run_info), _vp],
     "om_apparent_permeability": [C.c_double, C.c_double, C.c_double, C.c_double, _f64p, _f64p],
+    "om_structure_results_from_lattice": [C.c_double] * 6 + [C.POINTER(om_diff_params),
+                                                             C.POINTER(om_structure_results)],
+    "om_bruggeman_fit": [C.c_int64, _vp, _vp, _vp, _f64p],
     "om_slip_correction_factors": [C.c_double] * 7 + [C.POINTER(om_slip_corrections)],
     "om_nodeset_create": [_vp, om_domain, _vp, C.POINTER(_vp)],
     "om_nodeset_count": [_vp, _i64p],
@@ -320,6 +327,24 @@ def om_slip_correction_factors(k_m2, porosity, D_eff_m2s, T_K=323.0, M_kg_per_mo
     out = om_slip_corrections()
     _call("om_slip_correction_factors", k_m2, porosity, D_eff_m2s, T_K, M_kg_per_mol, mu_Pa_s, p_Pa, C.byref(out))
     return {n: getattr(out, n) for n, _ in om_slip_corrections._fields_}
+
+
+def om_structure_results_from_lattice(dx_nm, k_lattice, D_eff_lattice, D_mean_lattice, porosity, mean_d_nm,
+                                      params):
+    """k, D_eff, D, tortuosity, alpha and the Kozeny-Carman k of a structure
+    from its lattice results (Eqs. 15-17, Sec. 4.2), as a dict."""
+    out = om_structure_results()
+    _call("om_structure_results_from_lattice", dx_nm, k_lattice, D_eff_lattice, D_mean_lattice, porosity, mean_d_nm,
+          C.byref(params), C.byref(out))
+    return {n: getattr(out, n) for n, _ in om_structure_results._fields_}
+
+
+def om_bruggeman_fit(porosity, D_eff_m2s, D_mean_m2s):
+    """Sec. 4.2: the exponent of D_eff = D eps^alpha fitted over structures."""
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (porosity, D_eff_m2s, D_mean_m2s)]
+    alpha = C.c_double()
+    _call("om_bruggeman_fit", arrs[0].size, *[_ptr(a) for a in arrs], C.byref(alpha))
+    return alpha.value
 
 
 def om_apparent_permeability(k_m2, D_eff_m2s, mu_Pa_s, p_Pa):

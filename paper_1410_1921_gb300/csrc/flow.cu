@@ -671,6 +671,12 @@ om_status flow_rest_t(om_flow* fl, cudaStream_t s) {
     default: return fail(OM_EINVAL, "unknown precision");                                        \
   }
 
+// The mode a (re)initialised solver starts in: FP32 unrebased (its fast
+// sweeps; solves enter the rebased mode for their last decades), 16-bit
+// rebased throughout (with 8 to 11 mantissa bits, unrebased storage cannot
+// resolve a slow flow's velocity at all).
+bool starts_rebased(const om_flow* fl) { return fl->rr != nullptr && fl->p.precision != OM_F32; }
+
 // Enter the rebased mode from the current (unrebased) state: the reference
 // starts at zero and takes the nodes' densities, the stored deviations lose
 // them (an exact change of variables, at an even time).
@@ -786,6 +792,10 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
     fl->reb = false;
     if (st == OM_OK) st = rest();
   }
+  if (st == OM_OK && starts_rebased(fl)) {
+    fl->reb = true;
+    st = rest();
+  }
   if (st == OM_OK) {
     double o[4];
     st = flow_observe_any(fl, o, s);  // prev <- u_x of the rest state
@@ -899,7 +909,7 @@ extern "C" om_status om_flow_set_populations(om_flow* fl, const double* f_dev, v
   if (!fl || !f_dev) return fail(OM_EINVAL, "om_flow_set_populations: null pointer");
   cudaStream_t s = as_stream(stream);
   fl->t = 0;
-  fl->reb = false;
+  fl->reb = starts_rebased(fl);
   auto imp = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_import_t, fl, f_dev, s); };
   OM_TRY(imp());
   double o[4];
@@ -910,7 +920,7 @@ extern "C" om_status om_flow_init_velocity(om_flow* fl, const float* ux_dev, int
                                            void* stream) {
   if (!fl || !ux_dev || stride < 1) return fail(OM_EINVAL, "om_flow_init_velocity: bad argument");
   cudaStream_t s = as_stream(stream);
-  fl->reb = false;
+  fl->reb = starts_rebased(fl);
   auto init = [&]() -> om_status { OM_FLOW_DISPATCH(fl, flow_init_u_t, fl, ux_dev, stride, scale, s); };
   OM_TRY(init());
   double o[4];

@@ -22,6 +22,15 @@ constexpr double kPi = 3.14159265358979323846;
 // Eq. 11: D_K = (d / 3) sqrt(8 R T / (pi M)), d in metres
 double knudsen(double d_m, double T, double M) { return d_m / 3.0 * std::sqrt(8.0 * kR * T / (kPi * M)); }
 
+// Eq. 15 for a diffusivity: lattice units to m^2/s, the time step fixed by
+// the reference pore (Eqs. 11-12) on the lattice of p
+double diffusivity_to_si(double D_lattice, const om_diff_params& p) {
+  const double cs2 = p.lattice == 19 ? 1.0 / 3.0 : 0.25;  // D3Q19 or D3Q7
+  const double DL_ref = cs2 * (p.tau_ref - 0.5);
+  const double DK_ref = knudsen(p.d_ref_nm * 1e-9, p.T_K, p.M_kg_per_mol);
+  return D_lattice * DK_ref / DL_ref;
+}
+
 struct Scope {
   cudaStream_t s = nullptr;
   om_nodeset* ns = nullptr;
@@ -110,11 +119,7 @@ extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om
   if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
   double o[5];
   OM_TRY(om_diff_observe(sc.df, o, sc.s));
-  // Eq. 15 with the time step set by the reference pore (Eqs. 11-12)
-  const double cs2 = params->lattice == 19 ? 1.0 / 3.0 : 0.25;  // D3Q19 or D3Q7
-  const double DL_ref = cs2 * (params->tau_ref - 0.5);
-  const double DK_ref = knudsen(params->d_ref_nm * 1e-9, params->T_K, params->M_kg_per_mol);
-  if (D_eff_m2s) *D_eff_m2s = Dl * DK_ref / DL_ref;
+  if (D_eff_m2s) *D_eff_m2s = diffusivity_to_si(Dl, *params);  // Eq. 15
   if (tortuosity) {
     const double porosity = (double)np / (double)N;
     const double DL_mean = o[4] / (double)nt;
@@ -128,6 +133,46 @@ extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om
     OM_CUDA(cudaStreamSynchronize(sc.s));
   }
   return st;
+}
+
+extern "C" om_status om_structure_results_from_lattice(double dx_nm, double k_lattice, double D_eff_lattice,
+                                                       double D_mean_lattice, double porosity, double mean_d_nm,
+                                                       const om_diff_params* params, om_structure_results* out) {
+  if (!params || !out) return fail(OM_EINVAL, "om_structure_results_from_lattice: null pointer");
+  if (!(dx_nm > 0.0) || !(porosity > 0.0) || !(porosity < 1.0) || !(mean_d_nm > 0.0))
+    return fail(OM_EINVAL, "om_structure_results_from_lattice: need dx > 0, 0 < porosity < 1, mean_d > 0");
+  const double dx = dx_nm * 1e-9;
+  om_structure_results r{};
+  r.k_m2 = k_lattice * dx * dx;                             // Eq. 15
+  r.D_eff_m2s = diffusivity_to_si(D_eff_lattice, *params);  // Eq. 15
+  r.D_mean_m2s = diffusivity_to_si(D_mean_lattice, *params);
+  if (D_eff_lattice > 0.0) {
+    r.tortuosity = porosity * D_mean_lattice / D_eff_lattice;               // Eq. 16
+    r.alpha = std::log(r.D_eff_m2s / r.D_mean_m2s) / std::log(porosity);  // Sec. 4.2
+  } else {
+    r.tortuosity = INFINITY;
+    r.alpha = NAN;
+  }
+  const double d = mean_d_nm * 1e-9;
+  r.k_kc_m2 = (d * d / 180.0) * porosity * porosity * porosity / ((1.0 - porosity) * (1.0 - porosity));  // Eq. 17
+  *out = r;
+  return OM_OK;
+}
+
+extern "C" om_status om_bruggeman_fit(int64_t n, const double* porosity, const double* D_eff_m2s,
+                                      const double* D_mean_m2s, double* alpha) {
+  if (n < 1 || !porosity || !D_eff_m2s || !D_mean_m2s || !alpha)
+    return fail(OM_EINVAL, "om_bruggeman_fit: need n >= 1 and four arrays");
+  double sxy = 0.0, sxx = 0.0;
+  for (int64_t k = 0; k < n; ++k) {
+    if (!(porosity[k] > 0.0) || !(porosity[k] < 1.0) || !(D_eff_m2s[k] > 0.0) || !(D_mean_m2s[k] > 0.0))
+      return fail(OM_EINVAL, "om_bruggeman_fit: porosities in (0, 1) and positive diffusivities");
+    const double x = std::log(porosity[k]);
+    sxy += x * std::log(D_eff_m2s[k] / D_mean_m2s[k]);
+    sxx += x * x;
+  }
+  *alpha = sxy / sxx;
+  return OM_OK;
 }
 
 extern "C" om_status om_apparent_permeability(double k_m2, double D_eff_m2s, double mu_Pa_s, double p_Pa,

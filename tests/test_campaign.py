@@ -1,7 +1,10 @@
-"""The paper's structure campaign (Secs. 2, 4.1-4.4): the structure grid,
-the Bruggeman and Kozeny-Carman fits, and a two-structure campaign on the
-GPU checked against single-structure solves."""
+"""The paper's structure campaign (Secs. 2, 4.1-4.4): the structure grid, the
+results-in-physical-units entry points against the oracle's formulas, and a
+campaign sub-grid solved on the GPU against the FP64 oracle's converged
+values (tests/golden/campaign_small.json, written by make_campaign.py)."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -21,43 +24,77 @@ def test_campaign_grid_follows_sec2():
     assert len({c.seed for c in cfgs}) == len(cfgs)
 
 
-def test_bruggeman_fit_recovers_the_exponent():
-    from paper_1410_1921_gb300 import campaign as CP
-    rows = [{"porosity": e, "D_mean_m2s": 2e-6, "D_eff_m2s": 2e-6 * e ** 3.3} for e in (0.2, 0.3, 0.45)]
-    assert CP.fit_bruggeman(rows) == pytest.approx(3.3, rel=1e-12)
-    assert CP.bruggeman_alpha(2e-6 * 0.3 ** 1.5, 2e-6, 0.3) == pytest.approx(1.5)
-    # the product's formulas against the oracle's
+@pytest.fixture(scope="module")
+def lib():
+    """The library's host entry points (they run on the CPU, no device)."""
+    from paper_1410_1921_gb300 import build
+    build.build()
+    import paper_1410_1921_gb300 as P
+    P.lib()
+    return P
+
+
+@pytest.mark.parametrize("lattice", [7, 19])
+def test_structure_results_match_the_oracle_formulas(lib, lattice):
     from oracle import physics as PH
-    assert CP.kozeny_carman(45e-9, 0.3) == pytest.approx(PH.kozeny_carman(45e-9, 0.3), rel=1e-15)
-    assert CP.knudsen_diffusivity(60e-9, 323.0, 0.016) == pytest.approx(PH.knudsen_diffusivity(60e-9, 323.0, 0.016),
-                                                                        rel=1e-15)
+    P = lib
+    dp = P.diff_params(T_K=323.0, lattice=lattice)
+    DL, DLm, kL, eps, dx, dmean = 0.0123, 0.0311, 0.0456, 0.37, 1.5, 45.0
+    r = P.om_structure_results_from_lattice(dx, kL, DL, DLm, eps, dmean, dp)
+    D = PH.diffusivity_physical(DL, 60e-9, 323.0, 0.016, lattice)
+    Dm = PH.diffusivity_physical(DLm, 60e-9, 323.0, 0.016, lattice)
+    assert r["k_m2"] == pytest.approx(PH.permeability_physical(kL, dx * 1e-9), rel=1e-15)
+    assert r["D_eff_m2s"] == pytest.approx(D, rel=1e-14)
+    assert r["D_mean_m2s"] == pytest.approx(Dm, rel=1e-14)
+    assert r["tortuosity"] == pytest.approx(PH.tortuosity(eps, Dm, D), rel=1e-14)
+    assert r["alpha"] == pytest.approx(PH.bruggeman_alpha(D, Dm, eps), rel=1e-13)
+    assert r["k_kc_m2"] == pytest.approx(PH.kozeny_carman(dmean * 1e-9, eps), rel=1e-14)
+    with pytest.raises(P.OmError):
+        P.om_structure_results_from_lattice(dx, kL, DL, DLm, 1.0, dmean, dp)
+
+
+def test_bruggeman_fit_matches_the_oracle(lib):
+    from oracle import physics as PH
+    eps = [0.12, 0.3, 0.45, 0.51]
+    Dm = [1e-6, 3e-6, 7e-7, 2e-6]
+    De = [d * e ** a for d, e, a in zip(Dm, eps, (3.1, 2.7, 3.6, 2.9))]
+    assert lib.om_bruggeman_fit(eps, De, Dm) == pytest.approx(PH.bruggeman_fit(eps, De, Dm), rel=1e-14)
+    with pytest.raises(lib.OmError):
+        lib.om_bruggeman_fit([0.3], [1e-7], [0.0])
 
 
 @pytest.mark.gpu
 @pytest.mark.timeout(600)
-def test_small_campaign_matches_single_solves(om):
-    import torch
+def test_campaign_subgrid_matches_the_oracle(om):
+    # the campaign driver (batched diffusion, pressure-driven flow per
+    # structure, FP32) on the oracle's sub-grid: porosity and connectivity
+    # exactly; k, D_eff, D, tortuosity, Kozeny-Carman k within the FP32
+    # bound 1e-5 relative, alpha and the fitted alpha within 1e-5 absolute
     from paper_1410_1921_gb300 import campaign as CP
-    from paper_1410_1921_gb300 import warmstart as W
-    cfgs = S.campaign_structures(means=(30.0,), porosities=(0.40, 0.50), xis=(0.3,), seeds=1, edge=48)
-    fp = om.flow_params(conv_tol=1e-6, check_every=200, max_steps=400_000, drive=om.OM_DRIVE_PRESSURE)
-    dp = om.diff_params(conv_tol=1e-6, check_every=200, max_steps=400_000)
-    rows = CP.run(cfgs, fp, dp)
-    solved = [r for r in rows if "k_m2" in r]
-    assert solved
-    for r, cfg in zip(rows, cfgs):
-        if "k_m2" not in r:
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "campaign_small.json")))
+    g = gold["grid"]
+    cfgs = [c for c in S.campaign_structures(means=(g["mean_d_nm"],), porosities=tuple(g["porosities"]),
+                                             xis=(g["xi"],), seeds=3, edge=g["edge"])
+            if c.seed in {r["seed"] for r in gold["structures"]}]
+    fg, dg = gold["flow"], gold["diffusion"]
+    fp = om.flow_params(tau=fg["tau"], conv_tol=fg["conv_tol"], check_every=fg["check_every"], max_steps=2_000_000,
+                        drive=om.OM_DRIVE_PRESSURE, delta_rho=fg["delta_rho"])
+    dp = om.diff_params(T_K=dg["T_K"], M_kg_per_mol=dg["M_kg_per_mol"], conv_tol=dg["conv_tol"],
+                        check_every=dg["check_every"], max_steps=3_000_000)
+    rows = {r["seed"]: r for r in CP.run(cfgs, fp, dp)}
+    solved = []
+    for want in gold["structures"]:
+        got = rows[want["seed"]]
+        assert got["porosity"] == want["porosity"]
+        assert got["connectivity"] == want["connectivity"]
+        if "k_m2" not in want:
+            assert "k_m2" not in got  # nothing percolates
             continue
-        assert r["flow_status"] == om.OM_OK and r["diff_status"] == om.OM_OK
-        assert r["k_m2"] > 0 and r["D_eff_m2s"] > 0 and r["tortuosity"] > 0.5
-        assert 0 < r["connectivity"] <= 1 and abs(r["porosity"] - cfg.porosity) < 0.02
-        # the batched diffusion equals a single solve of the same structure
-        dom, mask, tr, d = W.structure(cfg)
-        ns = om.NodeSet(tr, dom)
-        df = om.Diffusion(ns, d, dp)
-        st, Dl, _ = df.solve()
-        cs2 = 0.25
-        DK = CP.knudsen_diffusivity(60e-9, dp.T_K, dp.M_kg_per_mol)
-        assert st == om.OM_OK and r["D_eff_m2s"] == pytest.approx(Dl * DK / (cs2 * 0.5), rel=1e-6)
-        assert math.isfinite(r["alpha"]) and r["alpha"] > 1.0
-        assert set(r["corrections"]) >= {"dgm", "klinkenberg", "beskok_civan", "heid"}
+        assert got["flow_status"] == om.OM_OK and got["diff_status"] == om.OM_OK
+        for key in ("k_m2", "D_eff_m2s", "D_mean_m2s", "tortuosity", "k_kc_m2"):
+            assert got[key] == pytest.approx(want[key], rel=1e-5), key
+        assert got["alpha"] == pytest.approx(want["alpha"], abs=1e-5)
+        assert math.isfinite(got["alpha"]) and set(got["corrections"]) >= {"dgm", "klinkenberg", "beskok_civan"}
+        solved.append(got)
+    assert len(solved) >= 2
+    assert CP.fit_bruggeman(solved) == pytest.approx(gold["bruggeman_alpha_fit"], abs=1e-5)

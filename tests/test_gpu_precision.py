@@ -10,13 +10,12 @@ one is stopped at that step, so that what is compared is the storage
 rounding alone and not where each run's stopping test happens to fire (near
 the threshold the two can stop some windows apart, and the result still
 moves by up to ~1e-6 per window there).  The FP32 solve must also meet the
-same test on its own.  16-bit diffusion (rebased deviations) 2e-3 (FP16) and
-1e-2 (BF16); 16-bit flow (deviations from the weights, FP16 scaled by 2^10)
-1e-2 (FP16) and 5e-2 (BF16: 8 mantissa bits; over the 400k steps the run
-may take, its rounding of updates far below an ulp of the stored deviation
-drifts the flow field by a few per cent), against the FP64 solve at 1e-10:
-16-bit runs may end on the step cap, their rounding noise flooring the
-relative-change test, and the field they reach is compared.  Run with -s to print the
+same test on its own.  16-bit storage, rebased on per-node references in
+both models (the diffusion on its concentration, the flow on its density),
+1e-4 (FP16) and 1e-3 (BF16, 8 mantissa bits) for k, 1e-3 and 5e-3 for D_eff
+(measured at most 1.1e-5, 3.1e-4, 3.7e-4 and 2.2e-3), against the FP64 solve
+at 1e-10: 16-bit runs may end on the step cap, their rounding noise flooring
+the relative-change test, and the field they reach is compared.  Run with -s to print the
 measured errors."""
 import pytest
 
@@ -24,7 +23,7 @@ import synthetic as S
 
 pytestmark = pytest.mark.gpu
 
-BOUNDS = {"OM_F32": (1e-5, 1e-5), "OM_F16DEV": (1e-2, 2e-3), "OM_BF16DEV": (5e-2, 1e-2)}  # (flow, diffusion)
+BOUNDS = {"OM_F32": (1e-5, 1e-5), "OM_F16DEV": (1e-4, 1e-3), "OM_BF16DEV": (1e-3, 5e-3)}  # (flow, diffusion)
 CASES = [S.small_structure(), S.sweep_structure(0.35, edge=64)]
 
 

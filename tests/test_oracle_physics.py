@@ -66,6 +66,19 @@ def test_kozeny_carman_and_bruggeman():
     assert P.kozeny_carman(1.0, 0.5) == pytest.approx(1 / 180 * 0.125 / 0.25)
     assert P.bruggeman_alpha(0.4 ** 1.5, 1.0, 0.4) == pytest.approx(1.5)
     assert P.tortuosity(0.4, 1.0, 0.4 / 2.0) == pytest.approx(2.0)
+    # Bruggeman's own law (alpha = 1.5, Sec. 4.2) is recovered exactly from
+    # structures that obey it, whatever their D; a second exponent from a
+    # set generated with it
+    eps = [0.15, 0.3, 0.55]
+    assert P.bruggeman_fit(eps, [2.0 * e ** 1.5 for e in eps], [2.0] * 3) == pytest.approx(1.5, rel=1e-13)
+    Dm = [1e-6, 3e-6, 7e-7]
+    assert P.bruggeman_fit(eps, [d * e ** 3.3 for d, e in zip(Dm, eps)], Dm) == pytest.approx(3.3, rel=1e-13)
+    # a least-squares line: scatter about the law averages out symmetrically
+    De = [2.0 * e ** 2.0 * f for e, f in zip(eps, (1.1, 1.0, 1.0))]
+    a = P.bruggeman_fit(eps, De, [2.0] * 3)
+    x = [math.log(e) for e in eps]
+    y = [math.log(d / 2.0) for d in De]
+    assert a == pytest.approx(sum(u * v for u, v in zip(x, y)) / sum(u * u for u in x), rel=1e-13)
 
 
 # ------------------------------------------------------------------ slip corrections (Sec. 4.4)
