@@ -476,8 +476,12 @@ om_status om_batch_destroy(om_batch* b);
  * start cold; the LB still runs to the same convergence test afterwards).
  * `levels` levels with channels ch[0..levels-1] (multiples of 16), two
  * 3x3x3 convolutions + ReLU per level, 2x average pooling down, nearest 2x
- * upsampling and skip concatenation up, a 1x1 head.  BF16 tensor-core
- * convolutions with FP32 accumulation; FP32 master weights and Adam.
+ * upsampling and skip concatenation up, a 1x1 head.  The 3x3x3
+ * convolutions (forward and data gradient) run on the 5th-generation tensor
+ * cores (tcgen05.mma, BF16 operands staged by TMA, FP32 accumulator in
+ * tensor memory); FP32 master weights and Adam.  om_unet_forward and
+ * om_unet_backward synchronise the stream and return OM_ETIMEOUT if a
+ * convolution's bounded wait gave up (the result is then not written).
  * Tensors are FP32 NDHWC on the device: x [B][D][H][W][in_ch] (in_ch <= 16),
  * targets/outputs [B][D][H][W][out_ch], mask [B][D][H][W] (loss over
  * voxels with mask != 0).  D, H, W must be multiples of 2^(levels-1).

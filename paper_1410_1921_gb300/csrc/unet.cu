@@ -12,9 +12,10 @@
 // 1x1 head without activation.  Masked mean-squared error; Adam.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
-#include "unet_kernels.cuh"
+#include "unet_tc.cuh"
 
 namespace om {
 namespace nn {
@@ -271,47 +272,113 @@ struct om_unet {
   // gradients (scratch)
   std::vector<Buf<bf16>> d1, d2, dcat, ds;
   Buf<double> loss;
+  Buf<int> tc_err;  // set by a tensor-core convolution whose wait ran out
 };
 
 namespace {
 
-om_status conv_forward(const om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
-                       bf16* y, const Grid& g, cudaStream_t s) {
-  ConvArgs a{};
-  a.x1 = x1, a.c1 = c.cin1, a.ld1 = ld1, a.o1 = o1;
-  a.x2 = x2, a.c2 = c.cin2, a.ld2 = ld2, a.o2 = o2;
-  a.wt = c.wt;
-  a.bias = U->w + c.b_off;
-  a.N = c.cout;
-  a.y = y, a.ldy = c.cout, a.oy = 0;
-  a.yf = nullptr;
-  a.relu = 1;
-  a.g = g;
-  const unsigned gx = (unsigned)((g.voxels() + kConvBM - 1) / kConvBM);
-  if (c.cout % 64 == 0) conv3d_igemm<64><<<dim3(gx, c.cout / 64), 128, 0, s>>>(a);
-  else if (c.cout % 32 == 0) conv3d_igemm<32><<<dim3(gx, c.cout / 32), 128, 0, s>>>(a);
-  else conv3d_igemm<16><<<dim3(gx, c.cout / 16), 128, 0, s>>>(a);
+// ------------------------------------------------------------------ tensor-core convolutions (unet_tc.cuh)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, fetched through the runtime (nothing links libcuda)
+om_status tensor_map_encoder(EncodeTiledFn* out) {
+  static std::mutex mu;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    OM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) return fail(OM_ECUDA, "U-Net: cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiledFn)p;
+  }
+  *out = fn;
+  return OM_OK;
+}
+
+// 5-D map of an NDHWC activation tensor: rows of ld BF16, c channels from o;
+// box {64 channels, 8 x, 8 y, 2 z, 1 batch}, 128-byte swizzle, zero fill
+om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, const Grid& g) {
+  EncodeTiledFn enc;
+  OM_TRY(tensor_map_encoder(&enc));
+  const cuuint64_t row = (cuuint64_t)ld * 2;
+  cuuint64_t dims[5] = {(cuuint64_t)c, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)g.D, (cuuint64_t)g.B};
+  cuuint64_t strides[4] = {row, row * g.W, row * g.W * g.H, row * g.W * g.H * g.D};
+  cuuint32_t box[5] = {(cuuint32_t)kTcKc, 8, 8, 2, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(x + o), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(OM_ECUDA, "U-Net: activation tensor map rejected (" + std::to_string((int)r) + ")");
+  return OM_OK;
+}
+
+// 2-D map of the operand WT[27 N][K]: box {64 columns, N rows}
+om_status weight_map(CUtensorMap* m, const bf16* wt, int K, int N) {
+  EncodeTiledFn enc;
+  OM_TRY(tensor_map_encoder(&enc));
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)27 * N};
+  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTcKc, (cuuint32_t)N};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wt, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(OM_ECUDA, "U-Net: weight tensor map rejected (" + std::to_string((int)r) + ")");
+  return OM_OK;
+}
+
+// stages + 1 KB alignment slack + barriers and the TMEM address slot
+size_t tc_smem_bytes(int N) { return 1024 + (size_t)kTcStages * (kTcATile + (size_t)N * 128) + 8 * (2 * kTcStages + 1) + 16; }
+
+// Y (rows of ldy, channels [oy, oy + N)) = conv of concat(x1, x2) with WT[27][N][c1 + c2]
+om_status conv_tc(const om_unet* U, const bf16* x1, int c1, int ld1, int o1, const bf16* x2, int c2, int ld2, int o2,
+                  const bf16* wt, int N, const float* bias, bf16* y, int ldy, int oy, float* yf, int relu, const Grid& g,
+                  cudaStream_t s) {
+  if (N % 16 || N < 16 || N > 256 || c1 < 8 || (c1 % 8) || (c2 % 8) || (ld1 % 8) || (o1 % 8) || (ldy % 8) || (oy % 8))
+    return fail(OM_EINVAL, "U-Net: convolution shape outside the tensor-core kernel's layout");
+  CUtensorMap m1, m2, mw;
+  OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g));
+  if (c2 > 0) {
+    if ((ld2 % 8) || (o2 % 8)) return fail(OM_EINVAL, "U-Net: second input not 16-byte aligned");
+    OM_TRY(activation_map(&m2, x2, c2, ld2, o2, g));
+  } else {
+    m2 = m1;
+  }
+  OM_TRY(weight_map(&mw, wt, c1 + c2, N));
+  TcConvArgs a{};
+  a.c1 = c1, a.c2 = c2, a.N = N, a.bias = bias, a.y = y, a.ldy = ldy, a.oy = oy, a.yf = yf, a.relu = relu, a.g = g;
+  a.tx = (g.W + 7) / 8, a.ty = (g.H + 7) / 8, a.tz = (g.D + 1) / 2;
+  a.err = U->tc_err.p;
+  OM_CUDA(cudaFuncSetAttribute(conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(N)));
+  const unsigned grid = (unsigned)((int64_t)g.B * a.tz * a.ty * a.tx);
+  conv3d_tc<<<grid, kTcThreads, tc_smem_bytes(N), s>>>(m1, m2, mw, a);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }
 
-// dX (rows of cin1 + cin2) = data gradient of conv c for the pre-activation gradient dyp
-om_status conv_dgrad(const Conv& c, const bf16* dyp, bf16* dx, const Grid& g, cudaStream_t s) {
-  ConvArgs a{};
-  a.x1 = dyp, a.c1 = c.cout, a.ld1 = c.cout, a.o1 = 0;
-  a.x2 = nullptr, a.c2 = 0;
-  a.wt = c.wd;
-  a.bias = nullptr;
-  a.N = c.cin1 + c.cin2;
-  a.y = dx, a.ldy = a.N, a.oy = 0;
-  a.relu = 0;
-  a.g = g;
-  const unsigned gx = (unsigned)((g.voxels() + kConvBM - 1) / kConvBM);
-  if (a.N % 64 == 0) conv3d_igemm<64><<<dim3(gx, a.N / 64), 128, 0, s>>>(a);
-  else if (a.N % 32 == 0) conv3d_igemm<32><<<dim3(gx, a.N / 32), 128, 0, s>>>(a);
-  else conv3d_igemm<16><<<dim3(gx, a.N / 16), 128, 0, s>>>(a);
-  OM_CUDA(cudaGetLastError());
+// a tensor-core convolution gave up a wait: report (synchronises)
+om_status check_tc(const om_unet* U, cudaStream_t s) {
+  int h = 0;
+  OM_CUDA(cudaMemcpyAsync(&h, U->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  OM_CUDA(cudaStreamSynchronize(s));
+  if (h) return fail(OM_ETIMEOUT, "U-Net: a tensor-core convolution's wait ran out");
   return OM_OK;
+}
+
+om_status conv_forward(const om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
+                       bf16* y, const Grid& g, cudaStream_t s) {
+  return conv_tc(U, x1, c.cin1, ld1, o1, x2, c.cin2, ld2, o2, c.wt, c.cout, U->w + c.b_off, y, c.cout, 0, nullptr, 1, g,
+                 s);
+}
+
+// dX (rows of cin1 + cin2) = data gradient of conv c for the pre-activation gradient dyp: the
+// forward convolution of dyp with the flipped, transposed weights WD[27][cin][cout]
+om_status conv_dgrad(const om_unet* U, const Conv& c, const bf16* dyp, bf16* dx, const Grid& g, cudaStream_t s) {
+  const int N = c.cin1 + c.cin2;
+  return conv_tc(U, dyp, c.cout, c.cout, 0, nullptr, 0, 0, 0, c.wd, N, nullptr, dx, N, 0, nullptr, 0, g, s);
 }
 
 template <int MT, int NT>
@@ -454,11 +521,11 @@ om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g,
     // h_l = relu(conv(b_l))
     relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d1[l].p, c, 0, U->h[l].p, c, Vl, U->d2[l].p);
     OM_TRY(conv_wgrad(U, U->dec2[l], U->b[l].p, c, 0, nullptr, 0, 0, U->d2[l].p, gl, s));
-    OM_TRY(conv_dgrad(U->dec2[l], U->d2[l].p, U->d1[l].p, gl, s));
+    OM_TRY(conv_dgrad(U, U->dec2[l], U->d2[l].p, U->d1[l].p, gl, s));
     // b_l = relu(conv(concat(u_l, s_l)))
     relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d1[l].p, c, 0, U->b[l].p, c, Vl, U->d2[l].p);
     OM_TRY(conv_wgrad(U, U->dec1[l], U->u[l].p, cb, 0, U->s[l].p, c, 0, U->d2[l].p, gl, s));
-    OM_TRY(conv_dgrad(U->dec1[l], U->d2[l].p, U->dcat[l].p, gl, s));
+    OM_TRY(conv_dgrad(U, U->dec1[l], U->d2[l].p, U->dcat[l].p, gl, s));
     // u_l = up(h_{l+1}) (or s_{L-1} at the bottom): gradient of the level below
     upsample2_bwd<<<blocks(level_grid(g, l + 1).voxels() * cb), kT, 0, s>>>(U->dcat[l].p, cb + c, 0, gl, cb,
                                                                             U->d1[l + 1].p);
@@ -479,17 +546,17 @@ om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g,
     // s_l = relu(conv(a_l))
     relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->ds[l].p, c, 0, U->s[l].p, c, Vl, U->d1[l].p);
     OM_TRY(conv_wgrad(U, U->enc2[l], U->a[l].p, c, 0, nullptr, 0, 0, U->d1[l].p, gl, s));
-    OM_TRY(conv_dgrad(U->enc2[l], U->d1[l].p, U->d2[l].p, gl, s));
+    OM_TRY(conv_dgrad(U, U->enc2[l], U->d1[l].p, U->d2[l].p, gl, s));
     // a_l = relu(conv(in_l))
     relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d2[l].p, c, 0, U->a[l].p, c, Vl, U->d1[l].p);
     const bf16* in = l == 0 ? U->x0.p : U->in[l].p;
     OM_TRY(conv_wgrad(U, U->enc1[l], in, cin, 0, nullptr, 0, 0, U->d1[l].p, gl, s));
     // d2[l] = gradient of in_l (pooled s_{l-1}); not needed at the input
-    if (l > 0) OM_TRY(conv_dgrad(U->enc1[l], U->d1[l].p, U->d2[l].p, gl, s));
+    if (l > 0) OM_TRY(conv_dgrad(U, U->enc1[l], U->d1[l].p, U->d2[l].p, gl, s));
   }
   double h = 0.0;
   OM_CUDA(cudaMemcpyAsync(&h, U->loss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  OM_CUDA(cudaStreamSynchronize(s));
+  OM_TRY(check_tc(U, s));
   if (loss_out) *loss_out = h;
   return OM_OK;
 }
@@ -518,7 +585,7 @@ extern "C" om_status om_unet_destroy(om_unet* U) {
   };
   drop(U->in), drop(U->a), drop(U->s), drop(U->u), drop(U->b), drop(U->h);
   drop(U->d1), drop(U->d2), drop(U->dcat), drop(U->ds);
-  U->x0.release(), U->out.release(), U->dout.release(), U->loss.release();
+  U->x0.release(), U->out.release(), U->dout.release(), U->loss.release(), U->tc_err.release();
   for (auto* v : {&U->enc1, &U->enc2, &U->dec1, &U->dec2})
     for (auto& c : *v) {
       cudaFree(c.wt);
@@ -601,11 +668,13 @@ extern "C" om_status om_unet_create(int32_t in_ch, int32_t out_ch, int32_t level
       const size_t n = 27ull * (c.cin1 + c.cin2) * c.cout;
       ok = ok && dal((void**)&c.wt, n * sizeof(bf16)) && dal((void**)&c.wd, n * sizeof(bf16));
     }
+  ok = ok && U->tc_err.ensure(1) == OM_OK;
   if (!ok) {
     om_unet_destroy(U);
     return fail(OM_ENOMEM, "om_unet_create: device allocation failed");
   }
   if (cudaMemcpy(U->w, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(U->tc_err.p, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(U->m, 0, sizeof(float) * off) != cudaSuccess || cudaMemset(U->v, 0, sizeof(float) * off) != cudaSuccess) {
     om_unet_destroy(U);
     return fail(OM_ECUDA, "om_unet_create: initialisation failed");
@@ -646,7 +715,7 @@ extern "C" om_status om_unet_forward(om_unet* U, const float* x, int32_t B, int3
   cudaStream_t s = as_stream(stream);
   OM_TRY(forward(U, x, g, s));
   OM_CUDA(cudaMemcpyAsync(y, U->out.p, sizeof(float) * g.voxels() * U->out_ch, cudaMemcpyDeviceToDevice, s));
-  return OM_OK;
+  return check_tc(U, s);
 }
 
 extern "C" om_status om_unet_backward(om_unet* U, const float* x, const float* t, const uint8_t* m, int32_t B,

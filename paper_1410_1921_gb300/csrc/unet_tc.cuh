@@ -1,0 +1,282 @@
+// unet_tc.cuh -- the U-Net's 3x3x3 convolutions (forward and data gradient)
+// on the 5th-generation tensor cores: tcgen05.mma with the accumulator in
+// tensor memory, operands staged in shared memory by TMA.
+//
+// Implicit GEMM  Y[v][n] = sum_k sum_c X[v + o_k][c] WT[k][n][c]  with a CTA
+// tile of M = 128 voxels (a box of 8 x 8 x 2 voxels in x, y, z) and all N
+// output channels (16..256).  For each of the 27 offsets o_k and each
+// 64-channel chunk of each input, TMA copies
+//   A: the voxel box shifted by o_k, 64 channels -- a 5-D box {64, 8, 8, 2, 1}
+//      of the NDHWC activation tensor (channels, x, y, z, batch); the box's
+//      part outside the grid (and channels past the input's count) is
+//      filled with zeros by the copy itself, which is the convolution's
+//      zero padding at the box faces;
+//   B: 64 columns of the N weight rows of offset k, a 2-D box {64, N} of
+//      WT[27 N][K];
+// both K-major with the 128-byte swizzle, into one of three stages.  One
+// thread (warp 0) issues the copies, another (warp 1) per stage four MMAs of
+// K = 16 (cta_group::1, kind::f16: BF16 x BF16 -> FP32, M = 128)
+// accumulating in TMEM; tcgen05.commit frees a stage when its MMAs have
+// read it.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// TMEM lanes = tile rows 32w..32w+31), adds the bias, applies ReLU and
+// stores BF16 (and an FP32 copy) for the rows inside the grid.
+//
+// Every wait on an mbarrier is bounded; a wait that runs out stops both
+// issuing threads, sets the error word, lets what was issued finish (again
+// bounded), frees the CTA's TMEM and returns without writing.
+#pragma once
+
+#include <cuda.h>  // CUtensorMap (the type only; the encoder is fetched through the runtime)
+
+#include "unet_kernels.cuh"
+
+namespace om {
+namespace nn {
+
+constexpr int kTcM = 128;            // voxels per CTA tile (8 x 8 x 2 box)
+constexpr int kTcKc = 64;            // channels per stage (128 bytes of BF16: one swizzle span)
+constexpr int kTcStages = 3;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTcATile = kTcM * kTcKc * 2;  // 16 KB
+constexpr unsigned long long kTcSpin = 1ull << 26;  // try_wait rounds before giving up
+
+struct TcConvArgs {
+  int c1, c2;         // channels of the two inputs (c2 = 0: one input)
+  int N;              // output channels (multiple of 16, <= 256)
+  const float* bias;  // [N] or null
+  bf16* y;            // output rows of ldy elements, channels [oy, oy + N)
+  int ldy, oy;
+  float* yf;          // optional FP32 copy, rows of N
+  int relu;
+  Grid g;
+  int tx, ty, tz;     // tiles along x, y, z (8, 8, 2 voxels each)
+  int* err;           // set when a wait ran out
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity to complete; false if it
+// ran out or (checked every 1024 rounds) another thread set *stop
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stop = nullptr) {
+  for (unsigned long long i = 0; i < kTcSpin; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (stop && (i & 1023) == 1023 && *stop) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile with the
+// 128-byte swizzle: rows of 128 bytes (64 BF16), 8-row atoms 1024 bytes
+// apart (stride byte offset), the leading byte offset unused for this
+// layout (encoded 1), descriptor version 1, layout type 2 (128-byte
+// swizzle).  The tile starts 1024-byte aligned; the k-th 16-element slice
+// of the 64 starts 32 k bytes further.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kTcThreads) conv3d_tc(const __grid_constant__ CUtensorMap map1,
+                                                        const __grid_constant__ CUtensorMap map2,
+                                                        const __grid_constant__ CUtensorMap mapw, TcConvArgs a) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  // stages 1024-byte aligned: [A 16 KB][B N x 128 B] x kTcStages, then the barriers
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = tc_smem_raw + (base - raw);
+  const uint32_t btile = (uint32_t)a.N * 128u;
+  const uint32_t stage_bytes = kTcATile + btile;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kTcStages * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
+  __shared__ volatile int stop;         // a wait ran out: issue nothing more
+  __shared__ int n_issued, n_consumed;  // copies issued / waited for by the MMA thread
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * kTcStages, done = full0 + 16u * kTcStages;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // tile coordinates
+  int t = blockIdx.x;
+  const int bx = t % a.tx;
+  t /= a.tx;
+  const int by = t % a.ty;
+  t /= a.ty;
+  const int bz = t % a.tz;
+  const int bb = t / a.tz;
+  const int x0 = bx * 8, y0 = by * 8, z0 = bz * 2;
+
+  const uint32_t ncols = a.N <= 32 ? 32u : (a.N <= 64 ? 64u : (a.N <= 128 ? 128u : 256u));
+  if (tid == 0) {
+    stop = 0;
+    n_issued = 0;
+    n_consumed = 0;
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(full0 + 8u * s, 1);
+      mbar_init(empty0 + 8u * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int n1 = (a.c1 + kTcKc - 1) / kTcKc, n2 = (a.c2 + kTcKc - 1) / kTcKc;
+  const int per_k = n1 + n2, nsteps = 27 * per_k;
+  if (tid == 0) {
+    // producer: step s = (offset k, chunk j) into stage s % kTcStages once
+    // the MMAs of step s - kTcStages have read that stage
+    int s = 0;
+    for (; s < nsteps; ++s) {
+      const int st = s % kTcStages;
+      if (s >= kTcStages && !mbar_wait(empty0 + 8u * st, (uint32_t)(s / kTcStages - 1) & 1u, &stop)) break;
+      if (stop) break;
+      const int k = s / per_k, j = s % per_k;
+      const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+      const uint32_t sa = base + (uint32_t)st * stage_bytes, sb = sa + kTcATile;
+      const uint32_t fb = full0 + 8u * st;
+      mbar_expect_tx(fb, kTcATile + btile);
+      int cw;  // column of WT's K dimension
+      if (j < n1) {
+        tma_load_5d(sa, &map1, j * kTcKc, x0 + dx, y0 + dy, z0 + dz, bb, fb);
+        cw = j * kTcKc;
+      } else {
+        tma_load_5d(sa, &map2, (j - n1) * kTcKc, x0 + dx, y0 + dy, z0 + dz, bb, fb);
+        cw = a.c1 + (j - n1) * kTcKc;
+      }
+      tma_load_2d(sb, &mapw, cw, k * a.N, fb);
+    }
+    n_issued = s;
+    if (s < nsteps) stop = 1;
+  } else if (tid == 32) {
+    // MMA issue: four K = 16 slices per stage, accumulating in TMEM
+    const uint32_t idesc = tc_idesc(kTcM, a.N);
+    int s = 0;
+    for (; s < nsteps; ++s) {
+      const int st = s % kTcStages;
+      if (!mbar_wait(full0 + 8u * st, (uint32_t)(s / kTcStages) & 1u, &stop)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + (uint32_t)st * stage_bytes, sb = sa + kTcATile;
+#pragma unroll
+      for (int kk = 0; kk < kTcKc / 16; ++kk) {
+        const uint64_t ad = sw128_desc(sa + 32u * kk), bd = sw128_desc(sb + 32u * kk);
+        const uint32_t acc = (s > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       empty0 + 8u * st)
+                   : "memory");
+    }
+    n_consumed = s;
+    if (s < nsteps) stop = 1;
+    // `done` fires when every MMA issued above has completed
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                 : "memory");
+  }
+  const bool fin = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // one decision for the whole CTA (the epilogue's TMEM loads are warp-collective)
+  const bool failed = __syncthreads_or(!fin || stop) != 0;
+  if (failed && tid == 0) {
+    atomicExch(a.err, 1);
+    // copies still in flight land in their stages: wait for them (bounded)
+    for (int s = n_consumed; s < n_issued; ++s)
+      (void)mbar_wait(full0 + 8u * (s % kTcStages), (uint32_t)(s / kTcStages) & 1u);
+  }
+
+  // epilogue: warp w reads TMEM lanes 32w..32w+31 = tile rows
+  if (!failed) {
+    const int r = warp * 32 + lane;
+    const int xx = x0 + (r & 7), yy = y0 + ((r >> 3) & 7), zz = z0 + (r >> 6);
+    const bool inside = xx < a.g.W && yy < a.g.H && zz < a.g.D;
+    const int64_t v = inside ? (((int64_t)bb * a.g.D + zz) * a.g.H + yy) * a.g.W + xx : 0;
+    for (int c0 = 0; c0 < a.N; c0 += 16) {
+      uint32_t q[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+            "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!inside) continue;
+      float f[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        f[i] = __uint_as_float(q[i]) + (a.bias ? a.bias[c0 + i] : 0.f);
+        if (a.relu) f[i] = fmaxf(f[i], 0.f);
+      }
+      if (a.y) {
+        uint32_t p[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+          p[i] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(a.y + v * a.ldy + a.oy + c0);
+        dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+      }
+      if (a.yf) {
+        float4* dst = reinterpret_cast<float4*>(a.yf + v * a.N + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+}  // namespace nn
+}  // namespace om
