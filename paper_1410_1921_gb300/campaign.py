@@ -73,3 +73,50 @@ def run(cfgs, fp=None, dp=None, drive=OM_DRIVE_PRESSURE, T_op=323.0, mu=1.73e-5,
             log(f"{row['seed']}: eps {eps:.3f} conn {row['connectivity']:.3f} k {row['k_m2']:.3e} m2 "
                 f"D_eff {row['D_eff_m2s']:.3e} m2/s tau {row['tortuosity']:.2f} alpha {row['alpha']:.2f}")
     return rows
+
+
+def main(argv=None):
+    """Command line: solve a sub-grid of the campaign and write one JSON
+    object (the rows, the fitted Bruggeman exponent, wall time).  Run from
+    the repository root, where the synthetic input generator lives:
+        python -m paper_1410_1921_gb300.campaign --means 45 --porosities 0.2,0.35,0.5 --seeds 2
+    """
+    import argparse
+    import json
+    import time
+
+    import synthetic
+
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--means", default="30,45,60", help="mean pore diameters <d> in nm")
+    ap.add_argument("--porosities", default=",".join(f"{0.10 + 0.05 * k:.2f}" for k in range(10)))
+    ap.add_argument("--xis", default="0.1,0.2,0.3", help="overlap tolerances")
+    ap.add_argument("--seeds", type=int, default=5, help="structures per configuration")
+    ap.add_argument("--edge", type=int, default=200, help="box edge in voxels (1.5 nm each)")
+    ap.add_argument("--drive", choices=("pressure", "force"), default="pressure")
+    ap.add_argument("--extrapolate", action="store_true", help="extrapolated restarts of the diffusion")
+    ap.add_argument("--out", default=None, help="JSON file (default: stdout)")
+    a = ap.parse_args(argv)
+    fl = lambda s: tuple(float(v) for v in s.split(","))
+    cfgs = synthetic.campaign_structures(means=fl(a.means), porosities=fl(a.porosities), xis=fl(a.xis),
+                                         seeds=a.seeds, edge=a.edge)
+    drive = OM_DRIVE_PRESSURE if a.drive == "pressure" else OM_DRIVE_FORCE
+    dp = diff_params(accel=1 if a.extrapolate else 0)
+    t0 = time.time()
+    rows = run(cfgs, flow_params(drive=drive), dp, drive=drive,
+               log=lambda m: print(f"[{time.time() - t0:7.1f} s] {m}", flush=True))
+    solved = [r for r in rows if r.get("D_eff_m2s", 0) > 0 and r.get("flow_status") == OM_OK]
+    out = {"structures": len(rows), "solved": len(solved), "wall_s": time.time() - t0, "edge": a.edge,
+           "drive": a.drive, "extrapolate": a.extrapolate,
+           "bruggeman_alpha_fit": fit_bruggeman(solved) if len(solved) >= 2 else None,
+           "rows": [{k: (list(v) if isinstance(v, tuple) else v) for k, v in r.items()} for r in rows]}
+    text = json.dumps(out, indent=1, default=float)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(text)
+    else:
+        print(text)
+
+
+if __name__ == "__main__":
+    main()
