@@ -48,13 +48,19 @@ def _args():
     ap.add_argument("--edge", type=int, default=256, help="structure edge (default: the 256^3 sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-converged-results leg")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "converge", "batch", "precision"],
+    ap.add_argument("--mode", default="throughput",
+                    choices=["throughput", "converge", "batch", "precision", "warmstart"],
                     help="converge: time to converged k and D_eff, plain vs batched + FP16 + warm start; "
                          "batch: the 150-structure set in one batch; precision: a 512^3 structure with "
-                         "FP32, FP16 and BF16 population storage")
+                         "FP32, FP16 and BF16 population storage; warmstart: the learned warm start "
+                         "trained on --n-train 96^3 structures, held-out 128^3 and 256^3 structures")
+    ap.add_argument("--train-edge", type=int, default=96, help="warmstart mode: training box edge")
+    ap.add_argument("--eval-edges", default="128,256", help="warmstart mode: held-out box edges")
     ap.add_argument("--n-struct", type=int, default=150, help="batch mode: structures")
     ap.add_argument("--batch-set", default="150", choices=["150", "small"],
                     help="batch mode: the 150-structure set, or 20 structures of 64^3 drawn like it")
+    ap.add_argument("--batch-split", action="store_true",
+                    help="batch mode: also time the structures of >= 2^19 nodes and the rest apart")
     ap.add_argument("--n-eval", type=int, default=24, help="converge mode: structures solved")
     ap.add_argument("--n-train", type=int, default=96, help="converge mode: training structures")
     ap.add_argument("--epochs", type=int, default=60, help="converge mode: U-Net epochs")
@@ -711,6 +717,46 @@ def _parity_us(model, nodes, bytes_per_node, peak, reps=20):
     return out
 
 
+def _batch_split(P, items, nodes):
+    """The set split at 2^19 nodes (structures that form groups of their
+    own, and the rest): each part as a batch (launch variant tuned, or forced
+    to 0, 1, 2 for the flow and 0, 1 for the diffusion) against one solver per
+    structure, MLUPS over 100-step windows."""
+    out = {}
+    for name, sub in (("large", [k for k in range(len(items)) if nodes[k] >= 1 << 19]),
+                      ("small", [k for k in range(len(items)) if nodes[k] < 1 << 19])):
+        total = sum(nodes[k] for k in sub)
+        part = {"structures": len(sub), "nodes": total}
+        for model, mname in ((0, "flow"), (1, "diffusion")):
+            res = {}
+            for var in ((-1, 0, 1, 2) if model == 0 else (-1, 0, 1)):
+                fp = P.flow_params(precision=P.OM_F32, check_every=WINDOW, variant=var)
+                dp = P.diff_params(precision=P.OM_F32, check_every=WINDOW, variant=var)
+                b = P.Batch([items[k][0] for k in sub], [items[k][1] for k in sub], [items[k][2] for k in sub],
+                            flow=fp if model == 0 else None, diff=dp if model == 1 else None)
+                res["tuned" if var < 0 else f"variant_{var}"] = _window_mlups(lambda: b.step(model, WINDOW), total,
+                                                                              WINDOW, 3)[0]
+                b.close()
+            solvers = []
+            for k in sub:
+                dom, tr, d = items[k]
+                ns = P.NodeSet(tr, dom)
+                solvers.append((ns, P.Flow(ns, P.flow_params(precision=P.OM_F32, check_every=WINDOW)) if model == 0
+                                else P.Diffusion(ns, d, P.diff_params(precision=P.OM_F32, check_every=WINDOW))))
+
+            def step_all():
+                for _, sv in solvers:
+                    sv.step(WINDOW)
+
+            res["plain"] = _window_mlups(step_all, total, WINDOW, 3)[0]
+            for ns, sv in solvers:
+                sv.close()
+                ns.close()
+            part[mname] = res
+        out[name] = part
+    return out
+
+
 def run_batch(a):
     """The 150-structure set (edges {64..200}^3, porosity U[0.10, 0.50], <d>
     U[10, 60] nm, tolerance U[0, 0.8], 1.5 nm voxels) advanced together: one
@@ -780,10 +826,11 @@ def run_batch(a):
         for ns, sv in solvers:
             sv.close()
             ns.close()
+    split = _batch_split(P, items, nodes) if a.batch_split else None
     line = {"metric": "aggregate fluid MLUPS, batched structures", "value": out["flow"]["mlups"],
             "unit": "MLUPS", "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
             "batched": out, "plain": plain, "window_modes": modes, "structures": len(items), "nodes": total,
-            "setup_s": t_setup, "batch_create_s": t_create,
+            "setup_s": t_setup, "batch_create_s": t_create, **({"split": split} if split else {}),
             "config": {"workload": ("150 structures, edges {64,96,128,160,200}^3 at 1.5 nm, porosity U[0.10,0.50]"
                                     if a.batch_set == "150" else
                                     "20 structures of 64^3 at 1.5 nm, porosity U[0.25,0.50]") +
@@ -839,8 +886,143 @@ def run_precision(a):
     return 0
 
 
+def _diff_solve(P, dom, tr, d, dp, init=None, from_linear=True):
+    """One diffusion solve on the transport set, optionally warm-started from
+    a device field; (status, D_lattice, steps, seconds)."""
+    import torch
+    ns = P.NodeSet(tr, dom)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    df = P.Diffusion(ns, d, dp)
+    if init is not None:
+        df.init_concentration(init, stride=1, from_linear=from_linear)
+    st, D, info = df.solve()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    df.close()
+    ns.close()
+    return st, D, info.steps, sec
+
+
+def run_warmstart(a):
+    """The learned warm start at the scale of its configuration: a 3-D U-Net
+    (4 levels, 16-32-64-128) trained on `--n-train` LB-solved 96^3
+    structures from the 256^3 sweep's generator (1 nm voxels, <d> 30 nm, sd
+    8, tolerance 0.3, porosity U[0.15, 0.45]; structures without transport
+    pores are redrawn), targets u_x and C from batched solves; then held-out
+    128^3 and 256^3 structures solved cold, warm-started by the network and
+    warm-started by a 2x-coarsened diffusion solve, every form with the same
+    solver and test (FP32, extrapolated restarts, relative change < 1e-6 over
+    1000 steps).  Per structure: diffusion steps and wall time of each form
+    (the network's inference and the coarse solve included in theirs), and
+    the D_eff of each against the cold one; at 128^3 against an FP64 solve
+    converged to 1e-11 too.  The flow is not warm-started (a predicted
+    velocity field excites slow pressure modes): its cold solve is reported
+    once per structure."""
+    import torch
+
+    from paper_1410_1921_gb300 import build as B
+    B.build()
+    import paper_1410_1921_gb300 as P
+    from paper_1410_1921_gb300 import warmstart as W
+
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    rng = np.random.default_rng(5)
+    fp = P.flow_params(precision=P.OM_F32, conv_tol=1e-6, check_every=1000, max_steps=3_000_000)
+    dp = P.diff_params(precision=P.OM_F32, conv_tol=1e-6, check_every=1000, max_steps=6_000_000,
+                       accel=P.OM_ACCEL_EXTRAPOLATE)
+    # training set: draw until n_train structures are solved
+    t0 = time.perf_counter()
+    data, tried, seed = [], 0, 500_000
+    while len(data) < a.n_train and tried < 4 * a.n_train:
+        want = a.n_train - len(data)
+        cfgs = []
+        for _ in range(min(64, int(want * 1.4) + 4)):
+            cfgs.append(S.sweep_structure(float(rng.uniform(0.15, 0.45)), seed=seed, edge=a.train_edge))
+            seed += 1
+        got, n = W.make_dataset_batched(cfgs, fp, dp, fields=("ux", "c"))
+        data += got[:want]
+        tried += n
+        log(f"training set: {len(data)} solved of {tried} drawn, {time.perf_counter() - t0:.0f} s")
+    t_data = time.perf_counter() - t0
+    net = P.UNet(2, 2, (16, 32, 64, 128), seed=3)
+    t0 = time.perf_counter()
+    hist = W.train(net, data, epochs=a.epochs, lr=1e-3, lr_end=1e-4, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n_train = len(data)
+    del data
+    torch.cuda.empty_cache()
+    # held-out structures
+    rows = []
+    dp64 = P.diff_params(precision=P.OM_F64, conv_tol=1e-11, check_every=1000, max_steps=20_000_000,
+                         accel=P.OM_ACCEL_EXTRAPOLATE)
+    edges = [int(e) for e in a.eval_edges.split(",")]
+    evals = [(e, p, 700_000 + 1000 * e + i) for e in edges
+             for i, p in enumerate((0.25, 0.35, 0.45) if e <= 128 else (0.30, 0.40))]
+    for edge, eps, sd in evals:
+        dom, mask, tr, d = W.structure(S.sweep_structure(eps, seed=sd, edge=edge))
+        if int(tr.sum().item()) == 0:
+            continue
+        row = {"edge": edge, "porosity_target": eps, "nodes": int(tr.sum().item())}
+        ns = P.NodeSet(tr, dom)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fl = P.Flow(ns, fp)
+        st, kl, info = fl.solve()
+        torch.cuda.synchronize()
+        row["flow"] = {"status": int(st), "k_lattice": kl, "steps": info.steps, "s": time.perf_counter() - t1}
+        fl.close()
+        ns.close()
+        st, Dc, sc, tc = _diff_solve(P, dom, tr, d, dp)
+        row["cold"] = {"status": int(st), "D_lattice": Dc, "steps": sc, "s": tc}
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        pred = W.predict(net, mask, d, dom)
+        c = pred.view(-1, 2)[:, 1].contiguous()
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t1
+        st, Dl, sl, tl = _diff_solve(P, dom, tr, d, dp, init=c)
+        row["learned"] = {"status": int(st), "D_lattice": Dl, "steps": sl, "s": tl + t_inf, "inference_s": t_inf,
+                          "rel_diff_D": abs(Dl - Dc) / abs(Dc)}
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        dep = W.coarse_departure(dom, tr, d, dp)
+        torch.cuda.synchronize()
+        t_c = time.perf_counter() - t1
+        st, D2, s2, t2 = _diff_solve(P, dom, tr, d, dp, init=dep)
+        row["two_level"] = {"status": int(st), "D_lattice": D2, "steps": s2, "s": t2 + t_c, "coarse_s": t_c,
+                            "rel_diff_D": abs(D2 - Dc) / abs(Dc)}
+        if edge <= 128:
+            st, D64, s64, t64 = _diff_solve(P, dom, tr, d, dp64)
+            row["fp64_reference"] = {"status": int(st), "D_lattice": D64, "steps": s64}
+            for k in ("cold", "learned", "two_level"):
+                row[k]["rel_err_D_vs_fp64"] = abs(row[k]["D_lattice"] - D64) / abs(D64)
+        rows.append(row)
+        log(json.dumps(row))
+    sums = {k: {"steps": sum(r[k]["steps"] for r in rows), "s": sum(r[k]["s"] for r in rows)}
+            for k in ("cold", "learned", "two_level")}
+    line = {"metric": "diffusion steps and wall time to the 1e-6 test, learned warm start vs cold start",
+            "value": sums["cold"]["s"] / sums["learned"]["s"] if sums["learned"]["s"] > 0 else None,
+            "unit": "x (cold wall time / learned wall time)", "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic", "dtype": "f32",
+            "training": {"structures": n_train, "edge": a.train_edge, "epochs": a.epochs,
+                         "loss_first": hist[0], "loss_last": hist[-1], "data_s": t_data, "train_s": t_train},
+            "totals": sums, "structures": rows,
+            "config": {"workload": f"U-Net 16-32-64-128 trained on {n_train} LB-solved {a.train_edge}^3 structures "
+                                   "(1 nm, <d> 30 nm sd 8, tolerance 0.3, porosity U[0.15,0.45]); held out "
+                                   "128^3 (porosity 0.25/0.35/0.45) and 256^3 (0.30/0.40)",
+                       "test": "relative change of the concentration field and the net flux < 1e-6 over 1000 "
+                               "steps, extrapolated restarts, FP32, in every form"}}
+    print(json.dumps(line))
+    return 0
+
+
 if __name__ == "__main__":
     args = _args()
+    if args.mode == "warmstart":
+        sys.exit(run_warmstart(args))
     if args.mode == "batch":
         sys.exit(run_batch(args))
     if args.mode == "precision":

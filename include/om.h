@@ -97,7 +97,12 @@ typedef struct {
    * prefetched, 6 even steps two consecutive nodes per thread with vector
    * loads and stores, odd steps as 0; 7/8/9 odd steps from the per-node
    * neighbour records, one thread per node / capped / on a resident grid,
-   * even steps as 6); larger values clamp to 9 */
+   * even steps as 6; 10/11/12 odd steps from the records holding only the
+   * populations across the collision, uncapped / capped / capped tighter,
+   * even steps as 6); larger values clamp to 12.  A batch (om_batch_create)
+   * takes 0..2: 0/1 one thread per node without/with a register cap, 2 as 1
+   * with each structure large enough for a group of its own in the forms
+   * of 2 (odd) and 6 (even) */
   int32_t variant;
   /* OM_DRIVE_FORCE: body_force along x, x periodic.  OM_DRIVE_PRESSURE
    * (Sec. 3.3): no force, x not periodic, densities 1 + delta_rho/2 and
@@ -412,8 +417,11 @@ om_status om_diff_load_state(om_diff* df, const void* host, int64_t bytes, void*
  * step advances a whole group over a work list of 256-node tiles, a check
  * window runs its steps group after group from a captured CUDA graph, and a
  * structure leaves the work list when it converges.  Launch shapes (register
- * cap; one CTA per tile or a resident grid of 2-8 CTAs per SM) are timed at
- * creation.  om_batch_step replays the window graph for whole windows from
+ * cap; one CTA per tile or a resident grid of 2-8 CTAs per SM; the large
+ * structures' forms) are timed at creation.  The flow of each structure
+ * enters the rebased mode (om_flow_solve) for its last decades: single
+ * precision once its relative change falls below 1e-4, 16-bit storage from
+ * the start.  om_batch_step replays the window graph for whole windows from
  * even times.  Both models share the parameters given; pass NULL for a
  * model that is not needed (d_nm_dev may then be NULL too).
  * nodes_dev[k]: uint8 N_k node mask (normally the transport set) of
@@ -458,6 +466,11 @@ om_status om_barrier_selftest(int32_t blocks, int32_t rounds, int32_t extra, int
  * om_diff_get_populations (double q*N_k, device) */
 om_status om_batch_get_populations(om_batch* b, int32_t model, int32_t item, double* dense_dev,
                                    void* stream);
+/* the field of structure `item` in its voxel layout (float N_item, device;
+ * 0 off the node set): model 0 u_x = sum_i e_ix f_i + g/2 (as
+ * om_flow_get_velocity's x component), model 1 the concentration C (as
+ * om_diff_get_fields) -- the solved fields a learned warm start trains on */
+om_status om_batch_get_field(om_batch* b, int32_t model, int32_t item, float* field_dev, void* stream);
 om_status om_batch_set_populations(om_batch* b, int32_t model, int32_t item,
                                    const double* dense_dev, void* stream);
 /* back to the initial state (rest / linear profile) at time 0 */

@@ -136,6 +136,7 @@ _SIGS = {
     "om_batch_set_window_mode": [_vp, C.c_int32, C.c_int32],
     "om_barrier_selftest": [C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.POINTER(C.c_int32), _vp],
     "om_batch_get_populations": [_vp, C.c_int32, C.c_int32, _vp, _vp],
+    "om_batch_get_field": [_vp, C.c_int32, C.c_int32, _vp, _vp],
     "om_batch_set_populations": [_vp, C.c_int32, C.c_int32, _vp, _vp],
     "om_batch_reset": [_vp, C.c_int32, _vp],
     "om_batch_init_fields": [_vp, C.c_int32, C.c_int32, _vp, C.c_int64, C.c_double, C.c_int32, _vp],
@@ -549,6 +550,9 @@ class Batch:
 
     def get_populations(self, model, item, out_dev, stream=None):
         _call("om_batch_get_populations", self.h, model, item, _ptr(out_dev), _stream(stream))
+
+    def get_field(self, model, item, out_dev, stream=None):
+        _call("om_batch_get_field", self.h, model, item, _ptr(out_dev), _stream(stream))
 
     def set_populations(self, model, item, f_dev, stream=None):
         _call("om_batch_set_populations", self.h, model, item, _ptr(f_dev), _stream(stream))

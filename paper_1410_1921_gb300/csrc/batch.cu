@@ -225,6 +225,39 @@ __global__ void __launch_bounds__(kTile, MINB) flow_solo_sweep(FlowArgs<T> a, ui
   flow_node<T, ODD>(a, off + ln, ln);
 }
 
+// The same item with the single-structure solver's fastest forms (launch
+// variant 2): odd steps on a resident grid whose threads stride over the
+// item's nodes, the next node's coordinates loaded ahead; even steps two
+// consecutive nodes per thread with 8-byte loads and stores (pairs from the
+// first even node number; a node before it is a single).
+template <class T>
+__global__ void __launch_bounds__(kTile) flow_solo_strided(FlowArgs<T> a, uint32_t off) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln >= a.nf) return;
+  uint32_t c = __ldg(a.coord + ln);
+  for (;;) {
+    const uint64_t nn = (uint64_t)ln + stride;
+    const bool more = nn < a.nf;
+    const uint32_t cn = more ? __ldg(a.coord + nn) : 0u;
+    flow_node_at<T, true>(a, off + ln, c);
+    if (!more) break;
+    ln = (uint32_t)nn;
+    c = cn;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTile) flow_solo_pair(FlowArgs<T> a, uint32_t off) {
+  const uint32_t head = off & 1u;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (head && t == 0) flow_node_at<T, false>(a, off, 0u);
+  const uint32_t ln = head + 2 * t;
+  if (ln >= a.nf) return;
+  if (ln + 1 == a.nf) flow_node_at<T, false>(a, off + ln, 0u);
+  else flow_pair_even<T>(a, off + ln);
+}
+
 template <class T, bool ODD, int MINB>
 __global__ void __launch_bounds__(kTile, MINB) diff_solo_sweep(DiffArgs<T> a, uint32_t off) {
   const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,8 +400,12 @@ __global__ void batch_omega(const int64_t* vox, const float* d_nm, uint32_t nf, 
   omega[n] = (C)(1.0 / tau);
 }
 
+// an item's populations (dense, FP64) and/or its field (dense, float: the
+// flow's u_x = sum_i e_ix f_i + g/2, as om_flow_get_velocity; the
+// diffusion's C = sum_i g_i, as om_diff_get_fields)
 template <class T, bool ODD>
-__global__ void flow_batch_export(FlowArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, double* out) {
+__global__ void flow_batch_export(FlowArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, double* out,
+                                  float* ux) {
   using C = typename Stg<T>::C;
   const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
   if (ln >= a.nf) return;
@@ -377,13 +414,22 @@ __global__ void flow_batch_export(FlowArgs<T> a, uint32_t off, const int64_t* vo
   C f[19];
   flow_load<T, ODD>(a, off + ln, nb, f);
   const int64_t v = vox[ln];
-  const double r1 = 1.0 + flow_ref(a, off + ln);
+  if (out) {
+    const double r1 = 1.0 + flow_ref(a, off + ln);
 #pragma unroll
-  for (int i = 0; i < 19; ++i) out[i * N + v] = (double)f[i] + q19_w(i) * r1;
+    for (int i = 0; i < 19; ++i) out[i * N + v] = (double)f[i] + q19_w(i) * r1;
+  }
+  if (ux) {
+    double jx = 0.0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) jx += (double)q19_e(i, 0) * (double)f[i];
+    ux[v] = (float)(jx + 0.5 * (double)a.g);
+  }
 }
 
 template <class T, bool ODD>
-__global__ void diff_batch_export(DiffArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, double* out) {
+__global__ void diff_batch_export(DiffArgs<T> a, uint32_t off, const int64_t* vox, int64_t N, double* out,
+                                  float* c) {
   using C = typename Stg<T>::C;
   const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
   if (ln >= a.nf) return;
@@ -395,8 +441,13 @@ __global__ void diff_batch_export(DiffArgs<T> a, uint32_t off, const int64_t* vo
   diff_load<T, D3Q7, ODD>(a, off + ln, nb, x, g);
   const int64_t v = vox[ln];
   const double cref = diff_ref(a, off + ln, x);
+  double dev = 0.0;
 #pragma unroll
-  for (int i = 0; i < 7; ++i) out[i * N + v] = (double)g[i] + q7_w(i) * cref;
+  for (int i = 0; i < 7; ++i) {
+    dev += (double)g[i];
+    if (out) out[i * N + v] = (double)g[i] + q7_w(i) * cref;
+  }
+  if (c) c[v] = (float)(dev + cref);
 }
 
 template <class T>
@@ -484,10 +535,22 @@ __global__ void batch_rebase(DiffArgs<T> a) {
   if (n < a.nf) diff_rebase_node<T>(a, n);
 }
 
+// the flow's rebased mode, per structure: every node of a group's items
+// (once per check window), or of one item (when it enters the mode)
 template <class T>
-__global__ void batch_flow_rebase(FlowArgs<T> a) {
-  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < a.nf) flow_rebase_node<T>(a, n);
+__global__ void batch_flow_rebase_group(FlowArgs<T> a, const __grid_constant__ GroupDesc g) {
+  const int nw = g.tile0[g.n];
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int k = group_item(g, w);
+    const uint32_t ln = (uint32_t)(w - g.tile0[k]) * kTile + threadIdx.x;
+    if (ln < g.it[k].nf) flow_rebase_node<T>(a, g.it[k].off + ln);
+  }
+}
+
+template <class T>
+__global__ void batch_flow_rebase_range(FlowArgs<T> a, uint32_t off, uint32_t nf) {
+  const uint32_t ln = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ln < nf) flow_rebase_node<T>(a, off + ln);
 }
 
 }  // namespace om
@@ -506,6 +569,9 @@ struct Model {
   void* pop = nullptr;   // arena [q][pitch]
   void* omega = nullptr; // diffusion only, compute type, [pitch]
   float* cr = nullptr;   // rebased storage: per-node reference concentration (diffusion) or density (flow)
+  // flow with cr: the items in the rebased mode (their sweeps take Reb<S>;
+  // every other item keeps cr = 0 on its nodes and takes the plain S sweeps)
+  std::vector<char> reb;
   double* prev = nullptr;
   double* dprev = nullptr;  // diffusion with OM_ACCEL_EXTRAPOLATE: each node's change over the last window
   int64_t t = 0;
@@ -545,6 +611,7 @@ struct om_batch {
   std::vector<int> gstart;
   std::vector<GroupDesc> gdesc;
   std::vector<int> gsolo;     // item of a solo group (one large item), else -1
+  std::vector<char> greb;     // flow: the group's items are in the rebased mode
   int ngroups = 0;
   int layout = 0;             // bumped whenever the work list is rebuilt
   int layout_model = -1;      // the model whose footprint sized the groups
@@ -593,18 +660,26 @@ int build_work(om_batch* b, const std::vector<int>& active, int model) {
   double fill = 0.0;
   b->gdesc.clear();
   b->gsolo.clear();
+  b->greb.clear();
   int in_group = 0;
+  // the flow's items in the plain mode first, then those in the rebased mode
+  const std::vector<char>& reb = b->m[0].reb;
+  const bool two = model == 0 && !reb.empty();
+  for (int pass = 0; pass < (two ? 2 : 1); ++pass)
   for (size_t a = 0; a < active.size(); ++a) {
     const int k = active[a];
+    const char mode = two ? reb[k] : 0;
+    if (mode != pass) continue;
     const BatchItem& bi = b->items_h[k];
     const double bytes = per * (double)bi.nf;
     const bool solo = bi.nf >= kSoloNodes;
-    if (b->ngroups == 0 || solo || b->gsolo.back() >= 0 || in_group == kGroupItems ||
+    if (b->ngroups == 0 || solo || b->gsolo.back() >= 0 || in_group == kGroupItems || b->greb.back() != mode ||
         (fill > 0.0 && fill + bytes > kGroupBytes)) {
       b->gstart.push_back(w);
       b->gcnt_h[b->ngroups] = 0;
       b->gdesc.push_back(GroupDesc{});
       b->gsolo.push_back(solo ? k : -1);
+      b->greb.push_back(mode);
       ++b->ngroups;
       fill = 0.0;
       in_group = 0;
@@ -667,7 +742,7 @@ DiffArgs<T> bdiff_args(const om_batch* b) {
 }
 
 template <class T, int MINB>
-void launch_flow(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
+void launch_flow_t(const om_batch* b, bool odd, int grid, int g, bool fast, cudaStream_t s) {
   FlowArgs<T> a = bflow_args<T>(b);
   const int solo = b->gsolo[g];
   if (solo >= 0) {
@@ -680,12 +755,31 @@ void launch_flow(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
     a.nz = it.nz;
     a.W = it.W;
     const unsigned nb = (it.nf + kTile - 1) / kTile;
+    if (fast) {
+      if (odd) {
+        flow_solo_strided<T><<<(unsigned)std::max(1, std::min<int>(grid, (int)nb)), kTile, 0, s>>>(a, it.off);
+      } else {
+        const uint32_t pairs = (it.nf - (it.off & 1u) + 1) / 2;
+        flow_solo_pair<T><<<std::max(1u, (pairs + kTile - 1) / kTile), kTile, 0, s>>>(a, it.off);
+      }
+      return;
+    }
     if (odd) flow_solo_sweep<T, true, MINB><<<nb, kTile, 0, s>>>(a, it.off);
     else flow_solo_sweep<T, false, MINB><<<nb, kTile, 0, s>>>(a, it.off);
     return;
   }
   if (odd) flow_batch_sweep<T, true, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
   else flow_batch_sweep<T, false, MINB><<<grid, kTile, 0, s>>>(a, b->gdesc[g]);
+}
+
+// the flow's sweeps of group g: rebased storage T = Reb<S> only for a group
+// in the rebased mode, the plain S sweeps (cr = 0 on its nodes) otherwise
+template <class T, int MINB>
+void launch_flow(const om_batch* b, bool odd, int grid, int g, bool fast, cudaStream_t s) {
+  if constexpr (kFlowRebased<T>) {
+    if (!b->greb[g]) return launch_flow_t<typename T::base, MINB>(b, odd, grid, g, fast, s);
+  }
+  launch_flow_t<T, MINB>(b, odd, grid, g, fast, s);
 }
 
 template <class T, int MINB>
@@ -712,13 +806,14 @@ void launch_diff(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
 }
 
 // variant 0: no residency hint; variant 1: capped for 4 (flow; 3 in FP64) / 8
-// (diffusion) CTAs per SM
+// (diffusion) CTAs per SM; variant 2 (flow): as 1, with the solo groups in
+// the single-structure solver's fastest forms (flow_solo_strided / _pair)
 // one step of group g
 template <class T>
 void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, int g, cudaStream_t s) {
   if (model == 0) {
-    if (variant == 0) launch_flow<T, 0>(b, odd, grid, g, s);
-    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, g, s);
+    if (variant == 0) launch_flow<T, 0>(b, odd, grid, g, false, s);
+    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, g, variant == 2, s);
   } else {
     if (variant == 0) launch_diff<T, 0>(b, odd, grid, g, s);
     else launch_diff<T, 8>(b, odd, grid, g, s);
@@ -782,6 +877,17 @@ om_status launch_window_persistent(om_batch* b, int model, int64_t t0, int K, cu
     OM_CUDA(cudaMemsetAsync(b->bar, 0, offsetof(GridBar, status), s));
     GridBar* bar = b->bar;
     if (model == 0) {
+      if constexpr (kFlowRebased<T>) {
+        if (!b->greb[g]) {
+          using S = typename T::base;
+          grid = (unsigned)std::min(tiles, window_grid<S>(b, model));
+          FlowArgs<S> a = bflow_args<S>(b);
+          void* args[] = {&a, &b->gdesc[g], &odd0, &K, &bar};
+          OM_CUDA(cudaLaunchCooperativeKernel((const void*)flow_batch_window<S, 0>, dim3(grid), dim3(kTile), args, 0,
+                                              s));
+          continue;
+        }
+      }
       FlowArgs<T> a = bflow_args<T>(b);
       void* args[] = {&a, &b->gdesc[g], &odd0, &K, &bar};
       OM_CUDA(cudaLaunchCooperativeKernel((const void*)flow_batch_window<T, 0>, dim3(grid), dim3(kTile), args, 0, s));
@@ -810,7 +916,10 @@ om_status window_t(om_batch* b, int model, int K, int mode, cudaStream_t s) {
   }
   m.t += K;
   if (model == 1 && m.cr) batch_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bdiff_args<T>(b));
-  if (model == 0 && m.cr) batch_flow_rebase<T><<<(b->total + 255) / 256, 256, 0, s>>>(bflow_args<T>(b));
+  if (model == 0 && m.cr)
+    for (int g = 0; g < b->ngroups; ++g)
+      if (b->greb[g] && b->gcnt_h[g] > 0)
+        batch_flow_rebase_group<T><<<std::min(b->gcnt_h[g], b->sms * 8), kTile, 0, s>>>(bflow_args<T>(b), b->gdesc[g]);
   return OM_OK;
 }
 
@@ -876,11 +985,15 @@ om_status tune_t(om_batch* b, int model, cudaStream_t s) {
   if (b->total == 0) return OM_OK;
   // {variant, CTAs per SM}; 0 CTAs per SM: one CTA per 256-node tile, the
   // hardware scheduler balancing the tiles, instead of a resident grid
-  const int shapes[6][2] = {{0, 0}, {1, 0}, {0, 2}, {0, 4}, {1, 4}, {1, 8}};
+  // (flow only) {2, 3}: solo groups in the single-structure forms, odd steps
+  // on 3 resident CTAs per SM
+  const int shapes[8][2] = {{0, 0}, {1, 0}, {0, 2}, {0, 4}, {1, 4}, {1, 8}, {2, 3}, {2, 4}};
+  const int nshapes = model == 0 ? 8 : 6;
   cudaEvent_t ev[3];
   for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
   float best[2] = {1e30f, 1e30f};
-  for (const auto& sh : shapes) {
+  for (int si = 0; si < nshapes; ++si) {
+    const int* sh = shapes[si];
     const int grid = sh[1] * b->sms;  // 0: one CTA per tile
     float tot[2] = {0.f, 0.f};
     for (int r = 0; r < 7; ++r) {
@@ -938,7 +1051,13 @@ om_status init_state_t(om_batch* b, int model, cudaStream_t s) {
   Model& m = b->m[model];
   OM_CUDA(cudaMemsetAsync(m.pop, 0, (size_t)m.q * b->pitch * stg_bytes(m.prec), s));  // rest / linear profile
   if (m.cr && model == 1) batch_cr_linear<<<b->sms * 4, kTile, 0, s>>>(b->items, b->work, b->nwork, b->dp.c_in, m.cr);
-  if (m.cr && model == 0) OM_CUDA(cudaMemsetAsync(m.cr, 0, sizeof(float) * b->pitch, s));  // rest density
+  if (m.cr && model == 0) {
+    OM_CUDA(cudaMemsetAsync(m.cr, 0, sizeof(float) * b->pitch, s));  // rest density
+    // as om_flow_solve: 16-bit storage rebased from the start, single
+    // precision from the last decades of each item's convergence
+    m.reb.assign(b->n, m.prec == OM_F32 ? 0 : 1);
+    b->layout_model = -1;  // groups follow the modes
+  }
   OM_CUDA(cudaGetLastError());
   m.t = 0;
   return OM_OK;
@@ -1006,6 +1125,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
       if (m.trial_ms[0] >= 0.f && m.trial_ms[1] >= 0.f) m.mode = m.trial_ms[1] < m.trial_ms[0] ? 1 : 0;
     }
     std::vector<int> keep;
+    bool switched = false;
     for (size_t a = 0; a < active.size(); ++a) {
       const int it = active[a];
       const double* o = b->obs_h + a * nv;
@@ -1033,6 +1153,15 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
       const bool diverged = !std::isfinite(o[0]) || !std::isfinite(o[2]);
       if (status) status[it] = done && !diverged ? OM_OK : OM_ENOTCONVERGED;
       if (!done && !diverged) keep.push_back(it);
+      // the flow: an item enters the rebased mode for its last decades, as
+      // om_flow_solve does (its group changes: the work list is rebuilt)
+      if (!done && !diverged && model == 0 && !m.reb.empty() && !m.reb[it] && rel < kRebaseBelow) {
+        if constexpr (kFlowRebased<T>)
+          batch_flow_rebase_range<T><<<(bi.nf + 255) / 256, 256, 0, s>>>(bflow_args<T>(b), bi.off, bi.nf);
+        OM_CUDA(cudaGetLastError());
+        m.reb[it] = 1;
+        switched = true;
+      }
       if (!done && !diverged && model == 1 && m.dprev) {
         const double f = track[it].observe(o[1]);
         if (f > 0.0) {
@@ -1042,7 +1171,7 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
         }
       }
     }
-    if (keep.size() != active.size()) {
+    if (keep.size() != active.size() || switched) {
       active.swap(keep);
       nw = build_work(b, active, model);
       OM_TRY(upload_work(b, nw, (int)active.size(), s));
@@ -1072,9 +1201,11 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
 }
 
 // The storage type of a model: the flow's single- and half-precision
-// populations are stored in the rebased mode (Reb<S>, flow_core.cuh) -- a
-// batch converges every structure to its test, so it takes the accurate
-// mode throughout; the diffusion's are rebased by its own scheme.
+// populations are handled as rebased storage (Reb<S>, flow_core.cuh) --
+// exact for every item, since an item not in the rebased mode keeps its
+// reference cr = 0 -- and the sweeps of the groups whose items are not in
+// that mode take the plain S (launch_flow).  The diffusion's storage is
+// rebased by its own scheme.
 #define OM_BATCH_DISPATCH(prec, fn, ...)                                      \
   switch (prec) {                                                             \
     case OM_F64: return fn<double>(__VA_ARGS__);                              \
@@ -1254,15 +1385,19 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     std::vector<int> all;
     for (int k = 0; k < n; ++k)
       if (b->items_h[k].nf > 0) all.push_back(k);
-    const int nw = build_work(b, all, model);
+    int nw = build_work(b, all, model);
     if ((st = upload_work(b, nw, (int)all.size(), s)) != OM_OK) return bail(st);
     if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
+    if (model == 0) {  // the flow's groups follow the modes its items start in
+      nw = build_work(b, all, model);
+      if ((st = upload_work(b, nw, (int)all.size(), s)) != OM_OK) return bail(st);
+    }
     const int variant = model == 0 ? fp->variant : dp->variant;
     if (variant < 0) {
       if ((st = dispatch_tune(b, model, s)) != OM_OK) return bail(st);
       if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
     } else {
-      m.var[0] = m.var[1] = std::min(variant, 1);
+      m.var[0] = m.var[1] = std::min(variant, model == 0 ? 2 : 1);
       m.grid[0] = m.grid[1] = 4 * b->sms;
     }
   }
@@ -1325,12 +1460,14 @@ extern "C" om_status om_batch_solve(om_batch* b, int32_t model, double* result, 
 
 namespace {
 template <class T>
-om_status exchange_t(om_batch* b, int model, int item, double* out, const double* in, cudaStream_t s) {
+om_status exchange_t(om_batch* b, int model, int item, double* out, const double* in, cudaStream_t s,
+                     float* field = nullptr) {
   const BatchItem& it = b->items_h[item];
   const om_nodeset* ns = b->ns[item];
   const int64_t N = ns->N;
   const Model& m = b->m[model];
   if (out) OM_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * m.q * N, s));
+  if (field) OM_CUDA(cudaMemsetAsync(field, 0, sizeof(float) * N, s));
   if (it.nf == 0) return OM_OK;
   const unsigned g = (it.nf + 255) / 256;
   if (model == 0) {
@@ -1343,8 +1480,8 @@ om_status exchange_t(om_batch* b, int model, int item, double* out, const double
     a.nz = it.nz;
     a.W = it.W;
     if (in) flow_batch_import<T><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, in);
-    else if (m.t & 1) flow_batch_export<T, true><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
-    else flow_batch_export<T, false><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
+    else if (m.t & 1) flow_batch_export<T, true><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out, field);
+    else flow_batch_export<T, false><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out, field);
   } else {
     DiffArgs<T> a = bdiff_args<T>(b);
     a.nf = it.nf;
@@ -1356,8 +1493,8 @@ om_status exchange_t(om_batch* b, int model, int item, double* out, const double
     a.W = it.W;
     a.s = (typename Stg<T>::C)it.slope;
     if (in) diff_batch_import<T><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, in);
-    else if (m.t & 1) diff_batch_export<T, true><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
-    else diff_batch_export<T, false><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out);
+    else if (m.t & 1) diff_batch_export<T, true><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out, field);
+    else diff_batch_export<T, false><<<g, 256, 0, s>>>(a, it.off, ns->vox, N, out, field);
   }
   OM_CUDA(cudaGetLastError());
   return OM_OK;
@@ -1369,6 +1506,12 @@ extern "C" om_status om_batch_get_populations(om_batch* b, int32_t model, int32_
   if (!b || model < 0 || model > 1 || !b->m[model].on || item < 0 || item >= b->n || !dense_dev)
     return fail(OM_EINVAL, "om_batch_get_populations: bad arguments");
   OM_BATCH_DISPATCH(b->m[model].prec, exchange_t, b, model, item, dense_dev, nullptr, as_stream(stream));
+}
+
+extern "C" om_status om_batch_get_field(om_batch* b, int32_t model, int32_t item, float* field_dev, void* stream) {
+  if (!b || model < 0 || model > 1 || !b->m[model].on || item < 0 || item >= b->n || !field_dev)
+    return fail(OM_EINVAL, "om_batch_get_field: bad arguments");
+  OM_BATCH_DISPATCH(b->m[model].prec, exchange_t, b, model, item, nullptr, nullptr, as_stream(stream), field_dev);
 }
 
 extern "C" om_status om_batch_set_populations(om_batch* b, int32_t model, int32_t item, const double* dense_dev,

@@ -74,12 +74,6 @@ namespace om {
 template <class T>
 constexpr int kMinBlocks1 = sizeof(T) == 8 ? 3 : 4;
 
-// om_flow_solve enters the rebased mode (flow_core.cuh) once the relative
-// change of the velocity field over a check window falls below this: two to
-// three decades before a tight test, and above the ~1e-5 floor that
-// single-precision rounding puts under that change in tight pores without
-// the rebase.
-constexpr double kRebaseBelow = 1e-4;
 constexpr int kSweepVariants = 13;
 
 template <class T, bool ODD, int MINB>

@@ -55,6 +55,13 @@ constexpr bool kFlowRebased = false;
 template <class S>
 constexpr bool kFlowRebased<Reb<S>> = true;
 
+// A solve (om_flow_solve, and per structure om_batch_solve) enters the
+// rebased mode once the relative change of the velocity field over a check
+// window falls below this: two to three decades before a tight test, and
+// above the ~1e-5 floor that single-precision rounding puts under that
+// change in tight pores without the rebase.
+constexpr double kRebaseBelow = 1e-4;
+
 // nb[i] = node number of x + e_i (kNoNode off the node set); periodic y, z,
 // and x unless a.px = 0 (no neighbour beyond the x faces)
 template <class T>

@@ -101,6 +101,7 @@ struct Pair<__nv_bfloat16> {
 // reference (kFlowRebased in flow_core.cuh).
 template <class S>
 struct Reb {
+  using base = S;
   S v;
 };
 template <class S>

@@ -20,7 +20,7 @@ import time
 import numpy as np
 import torch
 
-from . import (OM_ENOPERC, OM_F32, OM_OK, OM_PORE_CHORD13, Diffusion, Flow, NodeSet, UNet, diff_params, domain,
+from . import (OM_ENOPERC, OM_F32, OM_OK, OM_PORE_CHORD13, Batch, Diffusion, Flow, NodeSet, UNet, diff_params, domain,
                flow_params, om_coarsen2_dev, om_label_connectivity_dev, om_local_pore_diameter_dev,
                om_prolong2_dev, om_reconstruct_dev, om_unet_pack_structure, om_unet_pack_structure3, recon_params)
 
@@ -182,6 +182,49 @@ def make_dataset(cfgs, fp=None, dp=None, log=None, fields=FIELDS, coarse=False, 
             log(f"sample {len(data)}: {cfg.shape} eps={cfg.porosity:.2f} nodes={res['nodes']} "
                 f"flow {res.get('flow_steps', 0)} diff {res['diff_steps']} steps")
     return data
+
+
+def make_dataset_batched(cfgs, fp=None, dp=None, log=None, fields=FIELDS, chunk=64):
+    """make_dataset on the batched path: the structures are solved `chunk` at
+    a time in one om_batch (diffusion first, then the flow when "ux" is among
+    the fields), each to the same convergence test as a single solve, and
+    their fields taken with om_batch_get_field.  Returns the samples and the
+    count of structures reconstructed."""
+    fp = fp or flow_params(precision=OM_F32)
+    dp = dp or diff_params(precision=OM_F32)
+    flow = "ux" in fields
+    data, tried = [], 0
+    for c0 in range(0, len(cfgs), chunk):
+        group = []
+        for cfg in cfgs[c0:c0 + chunk]:
+            dom, mask, tr, d = structure(cfg)
+            tried += 1
+            if int(tr.sum().item()) > 0:
+                group.append((cfg, dom, mask, tr, d))
+        if not group:
+            continue
+        b = Batch([g[1] for g in group], [g[3] for g in group], [g[4] for g in group],
+                  flow=fp if flow else None, diff=dp)
+        _, _, info_d, st_d = b.solve(1)
+        st_f = info_f = None
+        if flow:
+            _, _, info_f, st_f = b.solve(0)
+        for j, (cfg, dom, mask, tr, d) in enumerate(group):
+            if st_d[j] != OM_OK or (flow and st_f[j] not in (OM_OK, OM_ENOPERC)):
+                continue
+            N = tr.numel()
+            res = {}
+            if flow:
+                res["ux"] = torch.empty(N, dtype=torch.float32, device="cuda")
+                b.get_field(0, j, res["ux"])
+            res["C"] = torch.empty(N, dtype=torch.float32, device="cuda")
+            b.get_field(1, j, res["C"])
+            data.append((net_input(mask, d, dom), targets(res, dom, fp, dp, fields), tr.view(1, dom.nx, dom.ny, dom.nz)))
+            if log:
+                log(f"sample {len(data)}: {cfg.shape} eps={cfg.porosity:.2f} nodes={int(tr.sum().item())} "
+                    f"flow {info_f[j].steps if flow else 0} diff {info_d[j].steps} steps")
+        b.close()
+    return data, tried
 
 
 def train(net, data, epochs, lr=1e-3, lr_end=1e-4, seed=0, log=None):

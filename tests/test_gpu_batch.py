@@ -320,3 +320,99 @@ def test_batch_extrapolated_restarts_match_oracle(orc, om):
                 assert dl[k] == pytest.approx(D, rel=rel), (P, accel, k)
             total[accel] = sum(i.steps for i in info[:-1])
         assert total[om.OM_ACCEL_EXTRAPOLATE] < 0.8 * total[om.OM_ACCEL_NONE], total
+
+
+# Launch variant 2 runs each structure large enough for a group of its own in
+# the single-structure solver's fastest forms (odd steps on a resident grid
+# striding over the nodes, even steps two nodes per thread, pairs from the
+# first even node number): the same per-node arithmetic as the one-thread-
+# per-node sweeps, so the same bits in every storage format, for an item
+# whose arena offset is odd and one whose offset is even.  In single
+# precision the solve enters each structure's rebased mode on the way (its
+# relative change passes 1e-4), as om_flow_solve does; the converged k
+# matches the single-structure solver's.
+def _variant_run(om, masks, prec, variant, K=100, windows=6):
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks],
+                 flow=om.flow_params(conv_tol=0.0, check_every=K, max_steps=K * windows, precision=prec,
+                                     variant=variant))
+    kl, _, _, st = b.solve(0)
+    b.step(0, 3)  # and an odd count of single steps
+    pops = []
+    for k, m in enumerate(masks):
+        out = torch.empty(19 * m.size, dtype=torch.float64, device="cuda")
+        b.get_populations(0, k, out)
+        pops.append(out.cpu().numpy())
+    b.close()
+    return kl, st, pops
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("prec", ["OM_F64", "OM_F32", "OM_BF16DEV"])
+def test_large_structure_forms_equal_plain_sweeps(om, prec):
+    # items 1 and 3 have > 2^19 nodes (groups of their own), at an even and
+    # an odd offset of the arena (the node counts before them)
+    masks = [S.random_mask((9, 33, 35), 0.7, 3), S.random_mask((72, 96, 96), 0.9, 41),
+             S.random_mask((5, 7, 9), 0.6, 1), S.random_mask((64, 96, 96), 0.9, 7)]
+    nf = [int(m.sum()) for m in masks]
+    assert nf[1] >= 1 << 19 and nf[3] >= 1 << 19
+    assert nf[0] % 2 == 0 and sum(nf[:3]) % 2 == 1
+    P = getattr(om, prec)
+    a = _variant_run(om, masks, P, 0)
+    b = _variant_run(om, masks, P, 2)
+    assert np.array_equal(a[0], b[0]) and list(a[1]) == list(b[1])
+    for x, y in zip(a[2], b[2]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.timeout(600)
+def test_batch_rebased_mode_per_structure_matches_single_solver(om):
+    masks = [S.random_mask((72, 96, 96), 0.9, 41), S.blob_mask((14, 19, 37), 11, n=7),
+             S.random_mask((9, 33, 35), 0.7, 3)]
+    doms = [om.domain(m.shape) for m in masks]
+    fp = om.flow_params(conv_tol=1e-6, precision=om.OM_F32)
+    b = om.Batch(doms, [_dev(m) for m in masks], flow=fp)
+    kl, _, info, status = b.solve(0)
+    b.close()
+    for k, m in enumerate(masks):
+        ns = om.NodeSet(_dev(m), doms[k])
+        fl = om.Flow(ns, fp)
+        s1, k1, i1 = fl.solve()
+        fl.close()
+        ns.close()
+        assert status[k] == om.OM_OK and s1 == om.OM_OK
+        assert kl[k] == pytest.approx(k1, rel=1e-6)
+        assert abs(info[k].steps - i1.steps) <= 100
+
+
+# om_batch_get_field: each item's u_x (flow) and C (diffusion) in its voxel
+# layout, the moments of the item's own populations (om_batch_get_populations)
+# at any time parity, zero off the node set.
+@pytest.mark.parametrize("prec", ["OM_F64", "OM_F32"])
+def test_batch_fields_are_the_moments_of_the_populations(orc, om, prec):
+    st = _structures(orc)
+    masks = [t for t, _ in st]
+    P = getattr(om, prec)
+    g = 1e-6
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks], [_dev(x) for _, x in st],
+                 flow=om.flow_params(body_force=g, precision=P), diff=om.diff_params(precision=P))
+    ex = np.array([e[0] for e in orc.velocities19()], np.float64)
+    for steps in (200, 1):
+        b.step(0, steps)
+        b.step(1, steps)
+        for k, m in enumerate(masks):
+            N = m.size
+            f = torch.empty(19 * N, dtype=torch.float64, device="cuda")
+            b.get_populations(0, k, f)
+            u = torch.empty(N, dtype=torch.float32, device="cuda")
+            b.get_field(0, k, u)
+            ux = (ex[:, None] * f.view(19, N).cpu().numpy()).sum(0) + 0.5 * g
+            on = m.reshape(-1) > 0
+            assert np.allclose(u.cpu().numpy()[on], ux[on], rtol=1e-6, atol=1e-12)
+            assert not u.cpu().numpy()[~on].any()
+            q = torch.empty(7 * N, dtype=torch.float64, device="cuda")
+            b.get_populations(1, k, q)
+            c = torch.empty(N, dtype=torch.float32, device="cuda")
+            b.get_field(1, k, c)
+            assert np.allclose(c.cpu().numpy()[on], q.view(7, N).cpu().numpy().sum(0)[on], rtol=1e-6, atol=1e-12)
+            assert not c.cpu().numpy()[~on].any()
+    b.close()
