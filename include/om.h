@@ -100,9 +100,11 @@ typedef struct {
    * even steps as 6; 10/11/12 odd steps from the records holding only the
    * populations across the collision, uncapped / capped / capped tighter,
    * even steps as 6); larger values clamp to 12.  A batch (om_batch_create)
-   * takes 0..2: 0/1 one thread per node without/with a register cap, 2 as 1
+   * takes 0..3: 0/1 one thread per node without/with a register cap, 2 as 1
    * with each structure large enough for a group of its own in the forms
-   * of 2 (odd) and 6 (even) */
+   * of 2 (odd) and 6 (even), 3 as 1 with each such structure in this
+   * solver's own sweeps, the variants tuned for its size (the diffusion
+   * takes 0, 1 and 3) */
   int32_t variant;
   /* OM_DRIVE_FORCE: body_force along x, x periodic.  OM_DRIVE_PRESSURE
    * (Sec. 3.3): no force, x not periodic, densities 1 + delta_rho/2 and

@@ -14,6 +14,7 @@
 // tile order (deterministic).  Launch shapes (residency cap, CTAs per SM) are
 // picked per parity by timing them on the batch itself.
 #include <algorithm>
+#include <array>
 #include <cstddef>
 #include <cmath>
 #include <vector>
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(kTile, MINB) flow_solo_sweep(FlowArgs<T> a, ui
 // variant 2): odd steps on a resident grid whose threads stride over the
 // item's nodes, the next node's coordinates loaded ahead; even steps two
 // consecutive nodes per thread with 8-byte loads and stores (pairs from the
-// first even node number; a node before it is a single).
+// first even node number; a node before it is a single -- never the case
+// for a solo item, whose arena offset is a multiple of 32).
 template <class T>
 __global__ void __launch_bounds__(kTile) flow_solo_strided(FlowArgs<T> a, uint32_t off) {
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -612,6 +614,13 @@ struct om_batch {
   std::vector<GroupDesc> gdesc;
   std::vector<int> gsolo;     // item of a solo group (one large item), else -1
   std::vector<char> greb;     // flow: the group's items are in the rebased mode
+  // items of >= kSoloNodes nodes: their arena offset is a multiple of 32, and
+  // they keep a copy of their column map in local node numbers (col_local)
+  // for the single-structure sweeps (flow launch variant 3), whose tuned
+  // variants svar[item][2 * rebased + odd] are picked at creation
+  std::vector<uint4*> col_local;
+  std::vector<std::array<int, 4>> svar;
+  std::vector<std::array<int, 2>> dvar;  // the same for the diffusion (diffusion launch variant 3)
   int ngroups = 0;
   int layout = 0;             // bumped whenever the work list is rebuilt
   int layout_model = -1;      // the model whose footprint sized the groups
@@ -741,10 +750,39 @@ DiffArgs<T> bdiff_args(const om_batch* b) {
   return a;
 }
 
+// the single-structure solver's view of solo item k: its slice of the arena
+// (pointers shifted by its offset, the slot pitch the arena's), its local
+// column map, coordinates and neighbour records
+template <class T>
+FlowArgs<T> solo_args(const om_batch* b, int k) {
+  FlowArgs<T> a = bflow_args<T>(b);
+  const BatchItem& it = b->items_h[k];
+  const om_nodeset* ns = b->ns[k];
+  for (int i = 0; i < 19; ++i) a.s[i] += it.off;
+  a.nf = it.nf;
+  a.col = b->col_local[k];
+  a.coord = it.coord;
+  a.rec7 = ns->rec7;
+  a.rec19 = ns->rec19;
+  a.slow = ns->slow;
+  a.nslow = (uint32_t)ns->n_slow;
+  if (a.rr) a.rr += it.off;
+  a.nx = it.nx;
+  a.ny = it.ny;
+  a.nz = it.nz;
+  a.W = it.W;
+  return a;
+}
+
 template <class T, int MINB>
-void launch_flow_t(const om_batch* b, bool odd, int grid, int g, bool fast, cudaStream_t s) {
+void launch_flow_t(const om_batch* b, bool odd, int grid, int g, int form, cudaStream_t s) {
   FlowArgs<T> a = bflow_args<T>(b);
   const int solo = b->gsolo[g];
+  if (solo >= 0 && form == 3 && b->col_local[solo]) {
+    flow_sweep_variant<T>(odd, b->svar[solo][2 * (int)kFlowRebased<T> + (int)odd], solo_args<T>(b, solo), s);
+    return;
+  }
+  const bool fast = form >= 2;
   if (solo >= 0) {
     const BatchItem& it = b->items_h[solo];
     a.nf = it.nf;
@@ -775,17 +813,49 @@ void launch_flow_t(const om_batch* b, bool odd, int grid, int g, bool fast, cuda
 // the flow's sweeps of group g: rebased storage T = Reb<S> only for a group
 // in the rebased mode, the plain S sweeps (cr = 0 on its nodes) otherwise
 template <class T, int MINB>
-void launch_flow(const om_batch* b, bool odd, int grid, int g, bool fast, cudaStream_t s) {
+void launch_flow(const om_batch* b, bool odd, int grid, int g, int form, cudaStream_t s) {
   if constexpr (kFlowRebased<T>) {
-    if (!b->greb[g]) return launch_flow_t<typename T::base, MINB>(b, odd, grid, g, fast, s);
+    if (!b->greb[g]) return launch_flow_t<typename T::base, MINB>(b, odd, grid, g, form, s);
   }
-  launch_flow_t<T, MINB>(b, odd, grid, g, fast, s);
+  launch_flow_t<T, MINB>(b, odd, grid, g, form, s);
+}
+
+// the single-structure solver's view of solo item k (as solo_args)
+template <class T>
+DiffArgs<T> solo_dargs(const om_batch* b, int k) {
+  DiffArgs<T> a = bdiff_args<T>(b);
+  const BatchItem& it = b->items_h[k];
+  const om_nodeset* ns = b->ns[k];
+  for (int i = 0; i < 7; ++i) a.q[i] += it.off;
+  a.omega += it.off;
+  if (a.cr) a.cr += it.off;
+  a.nf = it.nf;
+  a.col = b->col_local[k];
+  a.coord = it.coord;
+  a.rec7 = ns->rec7;
+  a.rec19 = ns->rec19;
+  a.slow = ns->slow;
+  a.nslow = (uint32_t)ns->n_slow;
+  a.nx = it.nx;
+  a.ny = it.ny;
+  a.nz = it.nz;
+  a.W = it.W;
+  a.s = (typename Stg<T>::C)it.slope;
+  return a;
 }
 
 template <class T, int MINB>
-void launch_diff(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
+void launch_diff(const om_batch* b, bool odd, int grid, int g, int form, cudaStream_t s) {
   DiffArgs<T> a = bdiff_args<T>(b);
   const int solo = b->gsolo[g];
+  // (the diffusion is never stored as Reb<S>: the batch's dispatch
+  // instantiates that type for both models, only the flow runs it)
+  if constexpr (!kFlowRebased<T>) {
+    if (solo >= 0 && form == 3 && b->col_local[solo]) {
+      diff_sweep_variant<T>(odd, b->dvar[solo][(int)odd], solo_dargs<T>(b, solo), s);
+      return;
+    }
+  }
   if (solo >= 0) {
     const BatchItem& it = b->items_h[solo];
     a.nf = it.nf;
@@ -807,16 +877,18 @@ void launch_diff(const om_batch* b, bool odd, int grid, int g, cudaStream_t s) {
 
 // variant 0: no residency hint; variant 1: capped for 4 (flow; 3 in FP64) / 8
 // (diffusion) CTAs per SM; variant 2 (flow): as 1, with the solo groups in
-// the single-structure solver's fastest forms (flow_solo_strided / _pair)
+// the single-structure solver's fastest forms (flow_solo_strided / _pair);
+// variant 3 (flow): as 1, with each solo group in the single-structure
+// solver's own sweeps, the variants tuned for its size
 // one step of group g
 template <class T>
 void launch_step(const om_batch* b, int model, bool odd, int variant, int grid, int g, cudaStream_t s) {
   if (model == 0) {
-    if (variant == 0) launch_flow<T, 0>(b, odd, grid, g, false, s);
-    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, g, variant == 2, s);
+    if (variant == 0) launch_flow<T, 0>(b, odd, grid, g, 0, s);
+    else launch_flow<T, (sizeof(T) == 8 ? 3 : 4)>(b, odd, grid, g, variant, s);
   } else {
-    if (variant == 0) launch_diff<T, 0>(b, odd, grid, g, s);
-    else launch_diff<T, 8>(b, odd, grid, g, s);
+    if (variant == 0) launch_diff<T, 0>(b, odd, grid, g, 0, s);
+    else launch_diff<T, 8>(b, odd, grid, g, variant, s);
   }
 }
 
@@ -976,6 +1048,39 @@ om_status observe_t(om_batch* b, int model, int nact, cudaStream_t s) {
   return OM_OK;
 }
 
+// the single-structure variants of every solo item, in both storage modes
+// of the flow (the populations change: the caller restores the state)
+template <class T>
+om_status tune_solo_t(om_batch* b, cudaStream_t s) {
+  using S = typename Plain<T>::type;
+  for (int k = 0; k < b->n; ++k) {
+    if (!b->col_local[k]) continue;
+    int V[2] = {0, 0};
+    OM_TRY(flow_tuned_variants<S>(solo_args<S>(b, k), b->m[0].prec, V, s, nullptr));
+    b->svar[k][0] = V[0], b->svar[k][1] = V[1];
+    if constexpr (kFlowRebased<T>) {
+      OM_TRY(flow_tuned_variants<T>(solo_args<T>(b, k), b->m[0].prec, V, s, nullptr));
+      b->svar[k][2] = V[0], b->svar[k][3] = V[1];
+    }
+  }
+  return OM_OK;
+}
+
+template <class T>
+om_status tune_solo_diff_t(om_batch* b, cudaStream_t s) {
+  if constexpr (kFlowRebased<T>) {
+    return fail(OM_EINVAL, "om_batch: rebased storage is the flow's");
+  } else {
+    for (int k = 0; k < b->n; ++k) {
+      if (!b->col_local[k]) continue;
+      int V[2] = {0, 0};
+      OM_TRY(diff_tuned_variants<T>(solo_dargs<T>(b, k), b->m[1].prec, V, s));
+      b->dvar[k][0] = V[0], b->dvar[k][1] = V[1];
+    }
+    return OM_OK;
+  }
+}
+
 // Autotuner: for each parity, time (variant, CTAs per SM) shapes over 6
 // steps after a warm-up step and keep the fastest.  Steps run from the
 // initial state, which the caller restores afterwards.
@@ -985,15 +1090,21 @@ om_status tune_t(om_batch* b, int model, cudaStream_t s) {
   if (b->total == 0) return OM_OK;
   // {variant, CTAs per SM}; 0 CTAs per SM: one CTA per 256-node tile, the
   // hardware scheduler balancing the tiles, instead of a resident grid
-  // (flow only) {2, 3}: solo groups in the single-structure forms, odd steps
-  // on 3 resident CTAs per SM
-  const int shapes[8][2] = {{0, 0}, {1, 0}, {0, 2}, {0, 4}, {1, 4}, {1, 8}, {2, 3}, {2, 4}};
-  const int nshapes = model == 0 ? 8 : 6;
+  // (flow only) {2, 3}: solo groups in the batch's forms of the single-
+  // structure sweeps, odd steps on 3 resident CTAs per SM; {3, .}: solo
+  // groups in the single-structure solver's own sweeps, their variants
+  // tuned per item (by size class) first
+  // (diffusion: {3, 0}, {3, 8} likewise, no variant 2)
+  const int shapes[10][2] = {{0, 0}, {1, 0}, {0, 2}, {0, 4}, {1, 4}, {1, 8}, {2, 3}, {2, 4}, {3, 0}, {3, 4}};
+  const int dshapes[8][2] = {{0, 0}, {1, 0}, {0, 2}, {0, 4}, {1, 4}, {1, 8}, {3, 0}, {3, 8}};
+  const int nshapes = model == 0 ? 10 : 8;
+  if (model == 0) OM_TRY(tune_solo_t<T>(b, s));
+  else OM_TRY(tune_solo_diff_t<T>(b, s));
   cudaEvent_t ev[3];
   for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
   float best[2] = {1e30f, 1e30f};
   for (int si = 0; si < nshapes; ++si) {
-    const int* sh = shapes[si];
+    const int* sh = model == 0 ? shapes[si] : dshapes[si];
     const int grid = sh[1] * b->sms;  // 0: one CTA per tile
     float tot[2] = {0.f, 0.f};
     for (int r = 0; r < 7; ++r) {
@@ -1217,6 +1328,12 @@ om_status solve_t(om_batch* b, int model, double* result, double* aux, om_run_in
   }
 
 om_status dispatch_tune(om_batch* b, int model, cudaStream_t s) { OM_BATCH_DISPATCH(b->m[model].prec, tune_t, b, model, s); }
+om_status dispatch_tune_solo(om_batch* b, int model, cudaStream_t s) {
+  if (model == 0) {
+    OM_BATCH_DISPATCH(b->m[0].prec, tune_solo_t, b, s);
+  }
+  OM_BATCH_DISPATCH(b->m[1].prec, tune_solo_diff_t, b, s);
+}
 om_status dispatch_init(om_batch* b, int model, cudaStream_t s) { OM_BATCH_DISPATCH(b->m[model].prec, init_state_t, b, model, s); }
 
 }  // namespace
@@ -1224,6 +1341,7 @@ om_status dispatch_init(om_batch* b, int model, cudaStream_t s) { OM_BATCH_DISPA
 extern "C" om_status om_batch_destroy(om_batch* b) {
   if (!b) return OM_OK;
   for (auto* ns : b->ns) om_nodeset_destroy(ns);
+  for (auto* c : b->col_local) cudaFree(c);
   for (auto& m : b->m) {
     if (m.exec) cudaGraphExecDestroy(m.exec);
     cudaFree(m.pop);
@@ -1288,6 +1406,22 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     BatchItem it{};
     it.col = ns->col;
     it.coord = ns->coord;
+    uint4* local = nullptr;
+    if ((uint32_t)ns->nf >= kSoloNodes) {
+      total = (total + 31) / 32 * 32;
+      const size_t bytes = sizeof(uint4) * (size_t)doms[k].nx * doms[k].ny * ns->W;
+      if (cudaMalloc((void**)&local, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bail(fail(OM_ENOMEM, "om_batch_create: device allocation failed"));
+      }
+      b->col_local.push_back(local);  // owned by the batch from here on
+      if (cudaMemcpyAsync(local, ns->col, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return bail(fail(OM_ECUDA, "om_batch_create: column map copy failed"));
+    } else {
+      b->col_local.push_back(nullptr);
+    }
+    b->svar.push_back({0, 0, 0, 0});
+    b->dvar.push_back({0, 0});
     it.off = (uint32_t)total;
     it.nf = (uint32_t)ns->nf;
     it.nx = doms[k].nx;
@@ -1354,13 +1488,16 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
     if ((st = dalloc((void**)&m.prev, sizeof(double) * b->pitch)) != OM_OK) return bail(st);
     if (model == 0 && stg_bytes(m.prec) <= 4 && (st = dalloc((void**)&m.cr, sizeof(float) * b->pitch)) != OM_OK)
       return bail(st);
+    if (m.cr) cudaMemsetAsync(m.cr, 0, sizeof(float) * b->pitch, s);
     if (model == 1 && dp->accel == OM_ACCEL_EXTRAPOLATE &&
         (st = dalloc((void**)&m.dprev, sizeof(double) * b->pitch)) != OM_OK)
       return bail(st);
     if (model == 1) {
       const size_t cb = m.prec == OM_F64 ? 8 : 4;
       if ((st = dalloc(&m.omega, cb * b->pitch)) != OM_OK) return bail(st);
+      cudaMemsetAsync(m.omega, 0, cb * b->pitch, s);  // the arena's gaps before aligned items
       if (stg_bytes(m.prec) <= 4 && (st = dalloc((void**)&m.cr, sizeof(float) * b->pitch)) != OM_OK) return bail(st);
+      if (m.cr) cudaMemsetAsync(m.cr, 0, sizeof(float) * b->pitch, s);
       int* bad = nullptr;
       if ((st = dalloc((void**)&bad, sizeof(int))) != OM_OK) return bail(st);
       cudaMemsetAsync(bad, 0, sizeof(int), s);
@@ -1397,7 +1534,12 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
       if ((st = dispatch_tune(b, model, s)) != OM_OK) return bail(st);
       if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
     } else {
-      m.var[0] = m.var[1] = std::min(variant, model == 0 ? 2 : 1);
+      m.var[0] = m.var[1] = std::min(variant, 3);
+      if (m.var[0] == 2 && model == 1) m.var[0] = m.var[1] = 1;
+      if (m.var[0] == 3) {
+        if ((st = dispatch_tune_solo(b, model, s)) != OM_OK) return bail(st);
+        if ((st = dispatch_init(b, model, s)) != OM_OK) return bail(st);
+      }
       m.grid[0] = m.grid[1] = 4 * b->sms;
     }
   }

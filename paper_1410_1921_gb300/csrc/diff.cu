@@ -332,6 +332,71 @@ void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const Diff
   else launch_sweep_p<T, L, false>(variant, nb, s, a);
 }
 
+}  // namespace
+
+namespace om {
+
+template <class T>
+void diff_sweep_variant(bool odd, int variant, const DiffArgs<T, D3Q7>& a, cudaStream_t s) {
+  launch_sweep<T, D3Q7>(odd, variant, blocks_for(a.nf), s, a);
+}
+
+// Time each launch variant of both sweeps on a (6 even/odd pairs after a
+// warm-up pair; the populations change) and keep the fastest per parity,
+// unless a node set of the same size class was tuned before in this process.
+template <class T, class L>
+om_status diff_tuned_variants_l(const DiffArgs<T, L>& a, int precision, int V[2], cudaStream_t s) {
+  const int kind = L::Q == 19 ? kTuneDiff19 : kTuneDiff7;
+  if (a.nf == 0 || tuned_lookup(kind, precision, a.nf, V)) return OM_OK;
+  const unsigned nb = blocks_for(a.nf);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
+  float best[2] = {1e30f, 1e30f};
+  for (int v = 0; v < kDiffVariants; ++v) {
+    float tot[2] = {0.f, 0.f};
+    for (int r = 0; r < 7; ++r) {
+      OM_CUDA(cudaEventRecord(ev[0], s));
+      launch_sweep<T, L>(false, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[1], s));
+      launch_sweep<T, L>(true, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[2], s));
+      OM_CUDA(cudaEventSynchronize(ev[2]));
+      if (r == 0) continue;
+      float m0 = 0.f, m1 = 0.f;
+      OM_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
+      OM_CUDA(cudaEventElapsedTime(&m1, ev[1], ev[2]));
+      tot[0] += m0;
+      tot[1] += m1;
+    }
+    for (int p = 0; p < 2; ++p)
+      if (tot[p] < best[p]) {
+        best[p] = tot[p];
+        V[p] = v;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  tuned_store(kind, precision, a.nf, V);
+  return OM_OK;
+}
+
+template <class T>
+om_status diff_tuned_variants(const DiffArgs<T, D3Q7>& a, int precision, int V[2], cudaStream_t s) {
+  return diff_tuned_variants_l<T, D3Q7>(a, precision, V, s);
+}
+
+#define OM_DIFF_SWEEP_API(T)                                                                      \
+  template void diff_sweep_variant<T>(bool, int, const DiffArgs<T, D3Q7>&, cudaStream_t);        \
+  template om_status diff_tuned_variants<T>(const DiffArgs<T, D3Q7>&, int, int*, cudaStream_t);
+OM_DIFF_SWEEP_API(double)
+OM_DIFF_SWEEP_API(float)
+OM_DIFF_SWEEP_API(__half)
+OM_DIFF_SWEEP_API(__nv_bfloat16)
+#undef OM_DIFF_SWEEP_API
+
+}  // namespace om
+
+namespace {
+
 // Capture K sweeps (K even, from an even time) into a CUDA graph once.
 template <class T, class L>
 om_status diff_capture_t(om_diff* df, int K) {
@@ -394,38 +459,7 @@ om_status diff_steps_t(om_diff* df, int64_t nsteps, cudaStream_t s) {
 template <class T, class L>
 om_status diff_tune_t(om_diff* df, cudaStream_t s) {
   if (df->ns->nf == 0) return OM_OK;
-  const int kind = L::Q == 19 ? kTuneDiff19 : kTuneDiff7;
-  if (tuned_lookup(kind, df->p.precision, df->ns->nf, df->var)) return OM_OK;
-  DiffArgs<T, L> a = diff_args<T, L>(df);
-  const unsigned nb = blocks_for(a.nf);
-  cudaEvent_t ev[3];
-  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
-  float best[2] = {1e30f, 1e30f};
-  for (int v = 0; v < kDiffVariants; ++v) {
-    float tot[2] = {0.f, 0.f};
-    for (int r = 0; r < 7; ++r) {
-      OM_CUDA(cudaEventRecord(ev[0], s));
-      launch_sweep<T, L>(false, v, nb, s, a);
-      OM_CUDA(cudaEventRecord(ev[1], s));
-      launch_sweep<T, L>(true, v, nb, s, a);
-      OM_CUDA(cudaEventRecord(ev[2], s));
-      OM_CUDA(cudaEventSynchronize(ev[2]));
-      if (r == 0) continue;
-      float m0 = 0.f, m1 = 0.f;
-      OM_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
-      OM_CUDA(cudaEventElapsedTime(&m1, ev[1], ev[2]));
-      tot[0] += m0;
-      tot[1] += m1;
-    }
-    for (int p = 0; p < 2; ++p)
-      if (tot[p] < best[p]) {
-        best[p] = tot[p];
-        df->var[p] = v;
-      }
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
-  tuned_store(kind, df->p.precision, df->ns->nf, df->var);
-  return OM_OK;
+  return diff_tuned_variants_l<T, L>(diff_args<T, L>(df), df->p.precision, df->var, s);
 }
 
 template <class T, class L>

@@ -290,6 +290,16 @@ __device__ __forceinline__ void diff_rebase_node(const DiffArgs<T, L>& a, uint32
   }
 }
 
+// The single-structure solver's D3Q7 sweeps (diff.cu), also run by batches
+// on their large structures: one sweep of launch variant `variant` over
+// nodes 0 .. a.nf of a's arrays; and the variants timed fastest per parity
+// on a node set of a's size class (cached per process; timing them changes
+// the populations).
+template <class T>
+void diff_sweep_variant(bool odd, int variant, const DiffArgs<T, D3Q7>& a, cudaStream_t s);
+template <class T>
+om_status diff_tuned_variants(const DiffArgs<T, D3Q7>& a, int precision, int V[2], cudaStream_t s);
+
 // Extrapolated restarts (om_diff_params.accel): the host side of the test
 // that the decay of the window-to-window change has settled on one mode.
 struct ExtrapolationTrack {

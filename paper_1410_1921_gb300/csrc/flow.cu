@@ -478,6 +478,72 @@ void launch_sweep(bool odd, int variant, unsigned nb, cudaStream_t s, const Flow
   else launch_sweep_p<T, false>(variant, nb, s, a);
 }
 
+}  // namespace
+
+namespace om {
+
+template <class T>
+void flow_sweep_variant(bool odd, int variant, const FlowArgs<T>& a, cudaStream_t s) {
+  launch_sweep<T>(odd, variant, blocks_for(a.nf), s, a);
+}
+
+// Time every launch variant of both sweeps on a (6 even/odd pairs each after
+// a warm-up pair; the populations change) and keep the fastest per parity,
+// unless a node set of the same size class was tuned before in this process.
+template <class T>
+om_status flow_tuned_variants(const FlowArgs<T>& a, int precision, int V[2], cudaStream_t s, bool* timed) {
+  const int kind = kFlowRebased<T> ? kTuneFlowReb : kTuneFlow;
+  if (timed) *timed = false;
+  if (a.nf == 0 || tuned_lookup(kind, precision, a.nf, V)) return OM_OK;
+  const unsigned nb = blocks_for(a.nf);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
+  float best[2] = {1e30f, 1e30f};
+  for (int v = 0; v < kSweepVariants; ++v) {
+    float tot[2] = {0.f, 0.f};
+    for (int r = 0; r < 7; ++r) {
+      OM_CUDA(cudaEventRecord(ev[0], s));
+      launch_sweep<T>(false, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[1], s));
+      launch_sweep<T>(true, v, nb, s, a);
+      OM_CUDA(cudaEventRecord(ev[2], s));
+      OM_CUDA(cudaEventSynchronize(ev[2]));
+      if (r == 0) continue;  // warm-up pair
+      float m0 = 0.f, m1 = 0.f;
+      OM_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
+      OM_CUDA(cudaEventElapsedTime(&m1, ev[1], ev[2]));
+      tot[0] += m0;
+      tot[1] += m1;
+    }
+    for (int p = 0; p < 2; ++p)
+      if (tot[p] < best[p]) {
+        best[p] = tot[p];
+        V[p] = v;
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  tuned_store(kind, precision, a.nf, V);
+  if (timed) *timed = true;
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+#define OM_FLOW_SWEEP_API(T)                                                                       \
+  template void flow_sweep_variant<T>(bool, int, const FlowArgs<T>&, cudaStream_t);               \
+  template om_status flow_tuned_variants<T>(const FlowArgs<T>&, int, int*, cudaStream_t, bool*);
+OM_FLOW_SWEEP_API(double)
+OM_FLOW_SWEEP_API(float)
+OM_FLOW_SWEEP_API(__half)
+OM_FLOW_SWEEP_API(__nv_bfloat16)
+OM_FLOW_SWEEP_API(Reb<float>)
+OM_FLOW_SWEEP_API(Reb<__half>)
+OM_FLOW_SWEEP_API(Reb<__nv_bfloat16>)
+#undef OM_FLOW_SWEEP_API
+
+}  // namespace om
+
+namespace {
+
 // One LB step: the pressure boundary kernel (pressure drive) and the sweep.
 template <class T>
 void launch_step(const om_flow* fl, bool odd, int variant, unsigned nb, cudaStream_t s, const FlowArgs<T>& a) {
@@ -563,39 +629,10 @@ om_status flow_steps_t(om_flow* fl, int64_t nsteps, cudaStream_t s) {
 template <class T>
 om_status flow_tune_t(om_flow* fl, cudaStream_t s) {
   if (fl->ns->nf == 0) return OM_OK;
-  const int kind = kFlowRebased<T> ? kTuneFlowReb : kTuneFlow;
-  int* V = flow_var<T>(fl);
-  if (tuned_lookup(kind, fl->p.precision, fl->ns->nf, V)) return OM_OK;
   FlowArgs<T> a = flow_args<T>(fl);
-  const unsigned nb = blocks_for(a.nf);
-  cudaEvent_t ev[3];
-  for (auto& e : ev) OM_CUDA(cudaEventCreate(&e));
-  float best[2] = {1e30f, 1e30f};
-  for (int v = 0; v < kSweepVariants; ++v) {
-    float tot[2] = {0.f, 0.f};
-    for (int r = 0; r < 7; ++r) {
-      OM_CUDA(cudaEventRecord(ev[0], s));
-      launch_sweep<T>(false, v, nb, s, a);
-      OM_CUDA(cudaEventRecord(ev[1], s));
-      launch_sweep<T>(true, v, nb, s, a);
-      OM_CUDA(cudaEventRecord(ev[2], s));
-      OM_CUDA(cudaEventSynchronize(ev[2]));
-      if (r == 0) continue;  // warm-up pair
-      float m0 = 0.f, m1 = 0.f;
-      OM_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
-      OM_CUDA(cudaEventElapsedTime(&m1, ev[1], ev[2]));
-      tot[0] += m0;
-      tot[1] += m1;
-    }
-    for (int p = 0; p < 2; ++p)
-      if (tot[p] < best[p]) {
-        best[p] = tot[p];
-        V[p] = v;
-      }
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
-  tuned_store(kind, fl->p.precision, fl->ns->nf, V);
-  d3q19_rest<T><<<nb, 256, 0, s>>>(a);
+  bool timed = false;
+  OM_TRY(flow_tuned_variants<T>(a, fl->p.precision, flow_var<T>(fl), s, &timed));
+  if (timed) d3q19_rest<T><<<blocks_for(a.nf), 256, 0, s>>>(a);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
 }

@@ -274,6 +274,16 @@ __device__ __forceinline__ double flow_ref(const FlowArgs<T>& a, uint32_t n) {
   else return 0.0;
 }
 
+// The single-structure solver's sweeps (flow.cu), also run by batches on
+// their large structures: one sweep of launch variant `variant` over nodes
+// 0 .. a.nf of a's arrays; and the variants timed fastest per parity on a
+// node set of a's size class (cached per process; *timed tells whether
+// this call timed them, which changes the populations).
+template <class T>
+void flow_sweep_variant(bool odd, int variant, const FlowArgs<T>& a, cudaStream_t s);
+template <class T>
+om_status flow_tuned_variants(const FlowArgs<T>& a, int precision, int V[2], cudaStream_t s, bool* timed);
+
 // flow_node_at for node n whose coordinates are coord[ln]
 template <class T, bool ODD>
 __device__ __forceinline__ void flow_node(const FlowArgs<T>& a, uint32_t n, uint32_t ln) {

@@ -104,6 +104,15 @@ struct Reb {
   using base = S;
   S v;
 };
+// the storage type without the rebased tag
+template <class T>
+struct Plain {
+  using type = T;
+};
+template <class S>
+struct Plain<Reb<S>> {
+  using type = S;
+};
 template <class S>
 struct Stg<Reb<S>> {
   using C = typename Stg<S>::C;

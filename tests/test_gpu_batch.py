@@ -322,35 +322,43 @@ def test_batch_extrapolated_restarts_match_oracle(orc, om):
         assert total[om.OM_ACCEL_EXTRAPOLATE] < 0.8 * total[om.OM_ACCEL_NONE], total
 
 
-# Launch variant 2 runs each structure large enough for a group of its own in
-# the single-structure solver's fastest forms (odd steps on a resident grid
-# striding over the nodes, even steps two nodes per thread, pairs from the
-# first even node number): the same per-node arithmetic as the one-thread-
-# per-node sweeps, so the same bits in every storage format, for an item
-# whose arena offset is odd and one whose offset is even.  In single
-# precision the solve enters each structure's rebased mode on the way (its
-# relative change passes 1e-4), as om_flow_solve does; the converged k
-# matches the single-structure solver's.
+# Launch variants 2 and 3 run each structure large enough for a group of its
+# own in the single-structure solver's forms: 2 (flow) in the batch's copies
+# of its fastest ones (odd steps on a resident grid striding over the nodes,
+# even steps two nodes per thread), 3 (flow and diffusion) in that solver's
+# own sweeps on the item's slice of the arena (its arena offset a multiple of
+# 32), with the launch variants tuned for the item's size.  All do the same per-node arithmetic
+# as the one-thread-per-node sweeps, so they give the same bits, in every
+# storage format.  In single precision the solve enters each structure's
+# rebased mode on the way (its relative change passes 1e-4), as
+# om_flow_solve does.
 def _variant_run(om, masks, prec, variant, K=100, windows=6):
-    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks],
+    rng = np.random.default_rng(9)
+    d = [(10 + 50 * rng.random(m.shape) * m).astype(np.float32) for m in masks]
+    b = om.Batch([om.domain(m.shape) for m in masks], [_dev(m) for m in masks], [_dev(x) for x in d],
                  flow=om.flow_params(conv_tol=0.0, check_every=K, max_steps=K * windows, precision=prec,
+                                     variant=variant),
+                 diff=om.diff_params(conv_tol=0.0, check_every=K, max_steps=K * windows, precision=prec,
                                      variant=variant))
     kl, _, _, st = b.solve(0)
+    dl, _, _, sd = b.solve(1)
     b.step(0, 3)  # and an odd count of single steps
+    b.step(1, 3)
     pops = []
-    for k, m in enumerate(masks):
-        out = torch.empty(19 * m.size, dtype=torch.float64, device="cuda")
-        b.get_populations(0, k, out)
-        pops.append(out.cpu().numpy())
+    for model, q in ((0, 19), (1, 7)):
+        for k, m in enumerate(masks):
+            out = torch.empty(q * m.size, dtype=torch.float64, device="cuda")
+            b.get_populations(model, k, out)
+            pops.append(out.cpu().numpy())
     b.close()
-    return kl, st, pops
+    return np.concatenate([kl, dl]), list(st) + list(sd), pops
 
 
 @pytest.mark.timeout(600)
 @pytest.mark.parametrize("prec", ["OM_F64", "OM_F32", "OM_BF16DEV"])
 def test_large_structure_forms_equal_plain_sweeps(om, prec):
-    # items 1 and 3 have > 2^19 nodes (groups of their own), at an even and
-    # an odd offset of the arena (the node counts before them)
+    # items 1 and 3 have > 2^19 nodes (groups of their own); the node counts
+    # before item 3 sum to an odd number (its offset is rounded up)
     masks = [S.random_mask((9, 33, 35), 0.7, 3), S.random_mask((72, 96, 96), 0.9, 41),
              S.random_mask((5, 7, 9), 0.6, 1), S.random_mask((64, 96, 96), 0.9, 7)]
     nf = [int(m.sum()) for m in masks]
@@ -358,10 +366,11 @@ def test_large_structure_forms_equal_plain_sweeps(om, prec):
     assert nf[0] % 2 == 0 and sum(nf[:3]) % 2 == 1
     P = getattr(om, prec)
     a = _variant_run(om, masks, P, 0)
-    b = _variant_run(om, masks, P, 2)
-    assert np.array_equal(a[0], b[0]) and list(a[1]) == list(b[1])
-    for x, y in zip(a[2], b[2]):
-        assert np.array_equal(x, y)
+    for v in (2, 3):
+        b = _variant_run(om, masks, P, v)
+        assert np.array_equal(a[0], b[0]) and list(a[1]) == list(b[1])
+        for x, y in zip(a[2], b[2]):
+            assert np.array_equal(x, y)
 
 
 @pytest.mark.timeout(600)
