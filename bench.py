@@ -49,11 +49,12 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-converged-results leg")
     ap.add_argument("--mode", default="throughput",
-                    choices=["throughput", "converge", "batch", "precision", "warmstart"],
+                    choices=["throughput", "converge", "batch", "precision", "warmstart", "layout"],
                     help="converge: time to converged k and D_eff, plain vs batched + FP16 + warm start; "
                          "batch: the 150-structure set in one batch; precision: a 512^3 structure with "
                          "FP32, FP16 and BF16 population storage; warmstart: the learned warm start "
-                         "trained on --n-train 96^3 structures, held-out 128^3 and 256^3 structures")
+                         "trained on --n-train 96^3 structures, held-out 128^3 and 256^3 structures; layout: "
+                         "the sparse and the dense population layouts on 128^3 structures of rising porosity")
     ap.add_argument("--train-edge", type=int, default=96, help="warmstart mode: training box edge")
     ap.add_argument("--eval-edges", default="128,256", help="warmstart mode: held-out box edges")
     ap.add_argument("--n-struct", type=int, default=150, help="batch mode: structures")
@@ -757,6 +758,48 @@ def _batch_split(P, items, nodes):
     return out
 
 
+def run_layout(a):
+    """The two population layouts of the host-level solves on structures of
+    rising porosity: the sweep workload's generator at 128^3 (porosity 0.35,
+    0.45) and body-centred cubic sphere arrays at 128^3 (0.5, 0.7, 0.9).
+    Per structure and model the fluid MLUPS of 2000 steps (20 windows with
+    their checks, no convergence) in the sparse and the dense layout (FP32),
+    and the layout OM_LAYOUT_AUTO picks."""
+    from paper_1410_1921_gb300 import build as B
+    B.build()
+    import paper_1410_1921_gb300 as P
+    from paper_1410_1921_gb300 import warmstart as W
+
+    cases = []
+    for eps in (0.35, 0.45):
+        dom, mask, tr, d = W.structure(S.sweep_structure(eps, seed=1, edge=128))
+        cases.append((f"sweep generator, porosity {eps}", dom, mask.cpu().numpy().reshape(128, 128, 128),
+                      d.cpu().numpy().reshape(128, 128, 128)))
+    for eps in (0.5, 0.7, 0.9):
+        m, _ = S.bcc_array(128, eps)
+        dom = P.domain(m.shape, 1.0)
+        d, _ = P.om_local_pore_diameter(m, dom, P.OM_PORE_CHORD13)
+        cases.append((f"bcc sphere array, porosity {eps}", dom, m, d))
+    rows = []
+    for name, dom, mask, d in cases:
+        row = {"structure": name, "pore_fraction": float(mask.mean())}
+        for model in ("flow", "diffusion"):
+            for lay, lname in ((P.OM_LAYOUT_SPARSE, "sparse"), (P.OM_LAYOUT_DENSE, "dense")):
+                if model == "flow":
+                    info = P.om_solve_permeability(mask, dom, P.flow_params(conv_tol=0.0, max_steps=2000,
+                                                                            layout=lay))[3]
+                else:
+                    info = P.om_solve_knudsen(mask, d, dom, P.diff_params(conv_tol=0.0, max_steps=2000,
+                                                                          layout=lay))[3]
+                row[f"{model}_{lname}_mlups"] = info.mlups
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "fluid MLUPS by population layout", "unit": "MLUPS", "n_gpus": 1, "dtype": "f32",
+                      "data": "synthetic", "structures": rows,
+                      "config": {"workload": "128^3 structures, porosity 0.35-0.9; 2000 steps in 100-step windows"}}))
+    return 0
+
+
 def run_batch(a):
     """The 150-structure set (edges {64..200}^3, porosity U[0.10, 0.50], <d>
     U[10, 60] nm, tolerance U[0, 0.8], 1.5 nm voxels) advanced together: one
@@ -1023,6 +1066,8 @@ if __name__ == "__main__":
     args = _args()
     if args.mode == "warmstart":
         sys.exit(run_warmstart(args))
+    if args.mode == "layout":
+        sys.exit(run_layout(args))
     if args.mode == "batch":
         sys.exit(run_batch(args))
     if args.mode == "precision":

@@ -117,9 +117,20 @@ typedef struct {
    * OM_DRIVE_FORCE. */
   int32_t drive;
   double delta_rho;
+  /* population layout of om_solve_permeability: OM_LAYOUT_SPARSE (the
+   * fluid-node-only storage of the node set), OM_LAYOUT_DENSE (every voxel of
+   * the box stored, neighbours by address arithmetic and the node mask;
+   * FP64 or FP32 with the body force), or OM_LAYOUT_AUTO: where the dense
+   * layout applies and the nodes fill at least half the box, the faster of
+   * the two over one even + odd pair on this structure, else sparse.  Both
+   * give the same update per node and step.  The solver objects
+   * (om_flow_create, batches) use the sparse layout and refuse
+   * OM_LAYOUT_DENSE. */
+  int32_t layout;
 } om_flow_params;
 
 enum { OM_DRIVE_FORCE = 0, OM_DRIVE_PRESSURE = 1 };
+enum { OM_LAYOUT_AUTO = 0, OM_LAYOUT_SPARSE = 1, OM_LAYOUT_DENSE = 2 };
 
 /* Knudsen diffusion (Sec. 3.2): temperature, molar mass, reference pore
  * size and relaxation time of Eq. 12, inlet/outlet concentrations.
@@ -144,6 +155,9 @@ typedef struct {
    * convergence test, so the fixed point and the test are those of the
    * plain solve.  OM_ACCEL_NONE: the plain iteration. */
   int32_t accel;
+  /* population layout of om_solve_knudsen (see om_flow_params.layout; the
+   * dense layout takes FP64 or FP32 and the D3Q7 lattice) */
+  int32_t layout;
 } om_diff_params;
 
 enum { OM_ACCEL_NONE = 0, OM_ACCEL_EXTRAPOLATE = 1 };

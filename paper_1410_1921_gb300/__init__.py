@@ -24,6 +24,7 @@ OM_F64, OM_F32, OM_F16DEV, OM_BF16DEV = range(4)
 OM_PORE_CHORD13, OM_PORE_MIS = 0, 1
 OM_DRIVE_FORCE, OM_DRIVE_PRESSURE = 0, 1
 OM_ACCEL_NONE, OM_ACCEL_EXTRAPOLATE = 0, 1
+OM_LAYOUT_AUTO, OM_LAYOUT_SPARSE, OM_LAYOUT_DENSE = 0, 1, 2
 STATUS_NAMES = ["OM_OK", "OM_EINVAL", "OM_ENOMEM", "OM_ECUDA", "OM_EINFEASIBLE", "OM_ENOPERC",
                 "OM_ENOTCONVERGED", "OM_ETIMEOUT"]
 
@@ -47,14 +48,15 @@ class om_recon_params(C.Structure):
 class om_flow_params(C.Structure):
     _fields_ = [("tau", C.c_double), ("body_force", C.c_double), ("conv_tol", C.c_double),
                 ("check_every", C.c_int32), ("max_steps", C.c_int64), ("precision", C.c_int32),
-                ("variant", C.c_int32), ("drive", C.c_int32), ("delta_rho", C.c_double)]
+                ("variant", C.c_int32), ("drive", C.c_int32), ("delta_rho", C.c_double), ("layout", C.c_int32)]
 
 
 class om_diff_params(C.Structure):
     _fields_ = [("T_K", C.c_double), ("M_kg_per_mol", C.c_double), ("d_ref_nm", C.c_double),
                 ("tau_ref", C.c_double), ("c_in", C.c_double), ("c_out", C.c_double),
                 ("conv_tol", C.c_double), ("check_every", C.c_int32), ("max_steps", C.c_int64),
-                ("precision", C.c_int32), ("variant", C.c_int32), ("lattice", C.c_int32), ("accel", C.c_int32)]
+                ("precision", C.c_int32), ("variant", C.c_int32), ("lattice", C.c_int32), ("accel", C.c_int32),
+                ("layout", C.c_int32)]
 
 
 class om_slip_corrections(C.Structure):
@@ -225,15 +227,16 @@ def recon_params(mean_d_nm, sd_d_nm, dmin_nm, dmax_nm, porosity, overlap_tol, p_
 
 
 def flow_params(tau=1.0, body_force=1e-6, conv_tol=1e-6, check_every=100, max_steps=10_000_000,
-                precision=OM_F32, variant=-1, drive=OM_DRIVE_FORCE, delta_rho=1e-4):
-    return om_flow_params(tau, body_force, conv_tol, check_every, max_steps, precision, variant, drive, delta_rho)
+                precision=OM_F32, variant=-1, drive=OM_DRIVE_FORCE, delta_rho=1e-4, layout=0):
+    return om_flow_params(tau, body_force, conv_tol, check_every, max_steps, precision, variant, drive, delta_rho,
+                          layout)
 
 
 def diff_params(T_K=300.0, M_kg_per_mol=0.016, d_ref_nm=60.0, tau_ref=1.0, c_in=1.0, c_out=0.0,
                 conv_tol=1e-6, check_every=100, max_steps=10_000_000, precision=OM_F32, variant=-1, lattice=7,
-                accel=0):
+                accel=0, layout=0):
     return om_diff_params(T_K, M_kg_per_mol, d_ref_nm, tau_ref, c_in, c_out, conv_tol, check_every,
-                          max_steps, precision, variant, lattice, accel)
+                          max_steps, precision, variant, lattice, accel, layout)
 
 
 # ------------------------------------------------------------------ host-buffer entry points

@@ -1377,6 +1377,8 @@ extern "C" om_status om_batch_create(int32_t n, const om_domain* doms, const uin
   if (dp && dp->accel != OM_ACCEL_NONE && dp->accel != OM_ACCEL_EXTRAPOLATE)
     return fail(OM_EINVAL, "om_batch_create: unknown accel");
   if (fp && !(fp->tau > 0.5)) return fail(OM_EINVAL, "om_batch_create: tau must exceed 1/2");
+  if ((fp && fp->layout == OM_LAYOUT_DENSE) || (dp && dp->layout == OM_LAYOUT_DENSE))
+    return fail(OM_EINVAL, "om_batch_create: batches use the sparse layout");
   if (fp && fp->drive != OM_DRIVE_FORCE) return fail(OM_EINVAL, "om_batch_create: batches take the body-force drive");
   if (dp && (!(dp->d_ref_nm > 0.0) || !(dp->tau_ref > 0.5) || !(dp->c_in != dp->c_out)))
     return fail(OM_EINVAL, "om_batch_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");

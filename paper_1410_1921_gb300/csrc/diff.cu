@@ -573,6 +573,8 @@ extern "C" om_status om_diff_create(const om_nodeset* ns, const float* d_nm_dev,
   if (!ns || !d_nm_dev || !p || !out) return fail(OM_EINVAL, "om_diff_create: null pointer");
   if (p->precision < OM_F64 || p->precision > OM_BF16DEV)
     return fail(OM_EINVAL, "om_diff_create: unknown precision");
+  if (p->layout == OM_LAYOUT_DENSE)
+    return fail(OM_EINVAL, "om_diff_create: solver objects use the sparse layout (the dense one is om_solve_knudsen's)");
   if (!(p->d_ref_nm > 0.0) || !(p->tau_ref > 0.5) || !(p->c_in != p->c_out))
     return fail(OM_EINVAL, "om_diff_create: need d_ref > 0, tau_ref > 1/2, c_in != c_out");
   if (p->lattice != 7 && p->lattice != 19) return fail(OM_EINVAL, "om_diff_create: lattice must be 7 or 19");

@@ -748,6 +748,8 @@ extern "C" om_status om_flow_create(const om_nodeset* ns, const om_flow_params* 
   if (19 * ns->pitch > (int64_t)UINT32_MAX)
     return fail(OM_EINVAL, "om_flow_create: more than 226 M nodes (slot offsets are 32-bit)");
   if (!(p->tau > 0.5)) return fail(OM_EINVAL, "om_flow_create: tau must exceed 1/2");
+  if (p->layout == OM_LAYOUT_DENSE)
+    return fail(OM_EINVAL, "om_flow_create: solver objects use the sparse layout (the dense one is om_solve_permeability's)");
   if (p->precision < OM_F64 || p->precision > OM_BF16DEV)
     return fail(OM_EINVAL, "om_flow_create: unknown precision");
   if (p->drive != OM_DRIVE_FORCE && p->drive != OM_DRIVE_PRESSURE)

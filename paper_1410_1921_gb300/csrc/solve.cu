@@ -10,6 +10,14 @@
 namespace om {
 om_status label_impl(const uint8_t* mask_dev, const om_domain& d, int* labels_dev, uint8_t* transport_dev,
                      int64_t* npore, int64_t* ntrans, cudaStream_t s);
+// dense.cu
+bool dense_flow_supported(const om_flow_params& p);
+bool dense_diff_supported(const om_diff_params& p);
+om_status dense_flow_solve(const uint8_t* node_dev, const om_domain& dom, int64_t nf, const om_flow_params& p,
+                           double* k_lattice, om_run_info* info, float* ux_dev, double* pair_ms, cudaStream_t s);
+om_status dense_diff_solve(const uint8_t* node_dev, const float* d_nm_dev, const om_domain& dom, int64_t nf,
+                           const om_diff_params& p, double* D_lattice, double* DL_sum, om_run_info* info, float* c_dev,
+                           double* pair_ms, cudaStream_t s);
 }
 
 using namespace om;
@@ -59,22 +67,76 @@ om_status transport_nodes(const uint8_t* mask, const om_domain& d, DevBuf<uint8_
   return OM_OK;
 }
 
+// OM_LAYOUT_AUTO times the layouts only where the nodes fill at least this
+// fraction of the box (below it the dense sweeps move more non-node lanes
+// than they save in lookups)
+constexpr double kDenseTryFraction = 0.5;
+
+// one even + odd pair of the sparse solver of this node set (after a warm-up pair)
+template <class Step>
+om_status pair_ms_of(Step step, cudaStream_t s, double* ms_out) {
+  cudaEvent_t e0, e1;
+  OM_CUDA(cudaEventCreate(&e0));
+  OM_CUDA(cudaEventCreate(&e1));
+  om_status st = step();
+  if (st == OM_OK) {
+    OM_CUDA(cudaEventRecord(e0, s));
+    st = step();
+    OM_CUDA(cudaEventRecord(e1, s));
+  }
+  if (st == OM_OK) {
+    OM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    OM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_out = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
 }  // namespace
 
 extern "C" om_status om_solve_permeability(const uint8_t* mask, om_domain d, const om_flow_params* params,
                                            double* k_m2, double* k_lattice, om_run_info* info, float* ux_out) {
   if (!mask || !params) return fail(OM_EINVAL, "om_solve_permeability: null pointer");
   OM_TRY(check_domain(d));
+  if (params->layout < OM_LAYOUT_AUTO || params->layout > OM_LAYOUT_DENSE)
+    return fail(OM_EINVAL, "om_solve_permeability: unknown layout");
+  if (params->layout == OM_LAYOUT_DENSE && !dense_flow_supported(*params))
+    return fail(OM_EINVAL, "om_solve_permeability: the dense layout takes FP64 or FP32 and the body force");
   Scope sc;
   OM_CUDA(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking));
   DevBuf<uint8_t> tr;
   int64_t np = 0, nt = 0;
   OM_TRY(transport_nodes(mask, d, tr, np, nt, sc.s));
   OM_TRY(om_nodeset_create(tr.p, d, sc.s, &sc.ns));
-  tr.release();
-  OM_TRY(om_flow_create(sc.ns, params, sc.s, &sc.fl));
+  const int64_t N = voxels(d);
+  om_flow_params ps = *params;  // the sparse solver's parameters
+  ps.layout = OM_LAYOUT_SPARSE;
+  // the layout: as asked, or for OM_LAYOUT_AUTO the faster one over an even + odd pair
+  bool dense = params->layout == OM_LAYOUT_DENSE && sc.ns->wrap_links > 0;
+  if (params->layout == OM_LAYOUT_AUTO && dense_flow_supported(*params) && sc.ns->wrap_links > 0 &&
+      (double)nt >= kDenseTryFraction * (double)N) {
+    double ms_dense = 0.0, ms_sparse = 0.0;
+    OM_TRY(dense_flow_solve(tr.p, d, nt, *params, nullptr, nullptr, nullptr, &ms_dense, sc.s));
+    OM_TRY(om_flow_create(sc.ns, &ps, sc.s, &sc.fl));
+    OM_TRY(pair_ms_of([&]() { return om_flow_step(sc.fl, 2, sc.s); }, sc.s, &ms_sparse));
+    om_flow_destroy(sc.fl);  // the solve starts from rest
+    sc.fl = nullptr;
+    dense = ms_dense < ms_sparse;
+  }
   double kl = 0.0;
-  om_status st = om_flow_solve(sc.fl, &kl, info, sc.s);
+  om_status st;
+  DevBuf<float> u;
+  if (dense) {
+    if (ux_out) OM_TRY(u.alloc(N));
+    st = dense_flow_solve(tr.p, d, nt, *params, &kl, info, ux_out ? u.p : nullptr, nullptr, sc.s);
+  } else {
+    tr.release();
+    OM_TRY(om_flow_create(sc.ns, &ps, sc.s, &sc.fl));
+    st = om_flow_solve(sc.fl, &kl, info, sc.s);
+  }
   if (st == OM_ENOPERC) {
     if (k_lattice) *k_lattice = 0.0;
     if (k_m2) *k_m2 = 0.0;
@@ -84,10 +146,10 @@ extern "C" om_status om_solve_permeability(const uint8_t* mask, om_domain d, con
   if (k_lattice) *k_lattice = kl;
   if (k_m2) *k_m2 = kl * dx * dx;  // Eq. 15
   if (ux_out) {
-    const int64_t N = voxels(d);
-    DevBuf<float> u;
-    OM_TRY(u.alloc(3 * N));
-    OM_TRY(om_flow_get_velocity(sc.fl, u.p, sc.s));
+    if (!dense) {
+      OM_TRY(u.alloc(3 * N));
+      OM_TRY(om_flow_get_velocity(sc.fl, u.p, sc.s));
+    }
     OM_CUDA(cudaMemcpyAsync(ux_out, u.p, N * sizeof(float), cudaMemcpyDeviceToHost, sc.s));
     OM_CUDA(cudaStreamSynchronize(sc.s));
   }
@@ -101,6 +163,10 @@ extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om
   OM_TRY(check_domain(d));
   if (!(params->T_K > 0.0) || !(params->M_kg_per_mol > 0.0))
     return fail(OM_EINVAL, "om_solve_knudsen: T_K and M_kg_per_mol must be positive");
+  if (params->layout < OM_LAYOUT_AUTO || params->layout > OM_LAYOUT_DENSE)
+    return fail(OM_EINVAL, "om_solve_knudsen: unknown layout");
+  if (params->layout == OM_LAYOUT_DENSE && !dense_diff_supported(*params))
+    return fail(OM_EINVAL, "om_solve_knudsen: the dense layout takes FP64 or FP32 and the D3Q7 lattice");
   const int64_t N = voxels(d);
   Scope sc;
   OM_CUDA(cudaStreamCreateWithFlags(&sc.s, cudaStreamNonBlocking));
@@ -108,27 +174,46 @@ extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om
   int64_t np = 0, nt = 0;
   OM_TRY(transport_nodes(mask, d, tr, np, nt, sc.s));
   OM_TRY(om_nodeset_create(tr.p, d, sc.s, &sc.ns));
-  tr.release();
   DevBuf<float> dd;
   OM_TRY(dd.alloc(N));
   OM_CUDA(cudaMemcpyAsync(dd.p, d_nm, N * sizeof(float), cudaMemcpyHostToDevice, sc.s));
-  OM_TRY(om_diff_create(sc.ns, dd.p, params, sc.s, &sc.df));
-  dd.release();
-  double Dl = 0.0;
-  om_status st = om_diff_solve(sc.df, &Dl, info, sc.s);
-  if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
-  double o[5];
-  OM_TRY(om_diff_observe(sc.df, o, sc.s));
+  om_diff_params ps = *params;  // the sparse solver's parameters
+  ps.layout = OM_LAYOUT_SPARSE;
+  // the layout: as asked, or for OM_LAYOUT_AUTO the faster one over an even + odd pair
+  bool dense = params->layout == OM_LAYOUT_DENSE;
+  if (params->layout == OM_LAYOUT_AUTO && dense_diff_supported(*params) && (double)nt >= kDenseTryFraction * (double)N) {
+    double ms_dense = 0.0, ms_sparse = 0.0;
+    OM_TRY(dense_diff_solve(tr.p, dd.p, d, nt, *params, nullptr, nullptr, nullptr, nullptr, &ms_dense, sc.s));
+    OM_TRY(om_diff_create(sc.ns, dd.p, &ps, sc.s, &sc.df));
+    OM_TRY(pair_ms_of([&]() { return om_diff_step(sc.df, 2, sc.s); }, sc.s, &ms_sparse));
+    om_diff_destroy(sc.df);  // the solve starts from the linear profile
+    sc.df = nullptr;
+    dense = ms_dense < ms_sparse;
+  }
+  double Dl = 0.0, DL_sum = 0.0;
+  om_status st;
+  DevBuf<float> c;
+  if (c_out) OM_TRY(c.alloc(N));
+  if (dense) {
+    st = dense_diff_solve(tr.p, dd.p, d, nt, *params, &Dl, &DL_sum, info, c_out ? c.p : nullptr, nullptr, sc.s);
+    if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
+  } else {
+    tr.release();
+    OM_TRY(om_diff_create(sc.ns, dd.p, &ps, sc.s, &sc.df));
+    st = om_diff_solve(sc.df, &Dl, info, sc.s);
+    if (st != OM_OK && st != OM_ENOTCONVERGED) return st;
+    double o[5];
+    OM_TRY(om_diff_observe(sc.df, o, sc.s));
+    DL_sum = o[4];
+    if (c_out) OM_TRY(om_diff_get_fields(sc.df, c.p, nullptr, sc.s));
+  }
   if (D_eff_m2s) *D_eff_m2s = diffusivity_to_si(Dl, *params);  // Eq. 15
   if (tortuosity) {
     const double porosity = (double)np / (double)N;
-    const double DL_mean = o[4] / (double)nt;
+    const double DL_mean = DL_sum / (double)nt;
     *tortuosity = porosity * DL_mean / Dl;  // Eq. 16
   }
   if (c_out) {
-    DevBuf<float> c;
-    OM_TRY(c.alloc(N));
-    OM_TRY(om_diff_get_fields(sc.df, c.p, nullptr, sc.s));
     OM_CUDA(cudaMemcpyAsync(c_out, c.p, N * sizeof(float), cudaMemcpyDeviceToHost, sc.s));
     OM_CUDA(cudaStreamSynchronize(sc.s));
   }
