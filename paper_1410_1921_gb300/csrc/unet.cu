@@ -299,33 +299,37 @@ om_status tensor_map_encoder(EncodeTiledFn* out) {
 }
 
 // 5-D map of an NDHWC activation tensor: rows of ld BF16, c channels from o;
-// box {64 channels, 8 x, 8 y, 2 z, 1 batch}, 128-byte swizzle, zero fill
-om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, const Grid& g) {
+// box {64 channels, 8 x, 8 y, 2 z, 1 batch}, 128-byte swizzle, zero fill (or,
+// halo = true, the resident-weight kernel's {32 channels, 10, 18, 3, 1} with
+// the 64-byte swizzle)
+om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, const Grid& g, bool halo = false) {
   EncodeTiledFn enc;
   OM_TRY(tensor_map_encoder(&enc));
   const cuuint64_t row = (cuuint64_t)ld * 2;
   cuuint64_t dims[5] = {(cuuint64_t)c, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)g.D, (cuuint64_t)g.B};
   cuuint64_t strides[4] = {row, row * g.W, row * g.W * g.H, row * g.W * g.H * g.D};
   cuuint32_t box[5] = {(cuuint32_t)kTcKc, 8, 8, 2, 1};
+  if (halo) box[0] = 32, box[1] = kTcHx, box[2] = kTcHy, box[3] = kTcHz;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(x + o), dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, halo ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(OM_ECUDA, "U-Net: activation tensor map rejected (" + std::to_string((int)r) + ")");
   return OM_OK;
 }
 
-// 2-D map of the operand WT[27 N][K]: box {64 columns, N rows}
-om_status weight_map(CUtensorMap* m, const bf16* wt, int K, int N) {
+// 2-D map of the operand WT[27 N][K]: box {64 columns, N rows}, 128-byte
+// swizzle (narrow = true: {32 columns, N rows}, 64-byte swizzle)
+om_status weight_map(CUtensorMap* m, const bf16* wt, int K, int N, bool narrow = false) {
   EncodeTiledFn enc;
   OM_TRY(tensor_map_encoder(&enc));
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)27 * N};
   cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kTcKc, (cuuint32_t)N};
+  cuuint32_t box[2] = {narrow ? 32u : (cuuint32_t)kTcKc, (cuuint32_t)N};
   cuuint32_t es[2] = {1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wt, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, narrow ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(OM_ECUDA, "U-Net: weight tensor map rejected (" + std::to_string((int)r) + ")");
   return OM_OK;
 }
@@ -340,6 +344,24 @@ om_status conv_tc(const om_unet* U, const bf16* x1, int c1, int ld1, int o1, con
   if (N % 16 || N < 16 || N > 256 || c1 < 8 || (c1 % 8) || (c2 % 8) || (ld1 % 8) || (o1 % 8) || (ldy % 8) || (oy % 8))
     return fail(OM_EINVAL, "U-Net: convolution shape outside the tensor-core kernel's layout");
   CUtensorMap m1, m2, mw;
+  if (c2 == 0 && c1 <= 32 && N <= 64) {
+    // resident weights: one persistent CTA per SM (conv3d_tc_res)
+    OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g, true));
+    OM_TRY(weight_map(&mw, wt, c1, N, true));
+    TcConvArgs a{};
+    a.c1 = c1, a.c2 = 0, a.N = N, a.bias = bias, a.y = y, a.ldy = ldy, a.oy = oy, a.yf = yf, a.relu = relu, a.g = g;
+    a.tx = (g.W + kTcTx - 1) / kTcTx, a.ty = (g.H + kTcTy - 1) / kTcTy;
+    a.err = U->tc_err.p;
+    int dev = 0, sms = 0;
+    OM_CUDA(cudaGetDevice(&dev));
+    OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = (int64_t)g.B * g.D * a.ty * a.tx;
+    const size_t smem = 1024 + 2 * (size_t)kTrHalo + 27 * (size_t)N * 64 + 8 * 10 + 16;
+    OM_CUDA(cudaFuncSetAttribute(conv3d_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv3d_tc_res<<<(unsigned)std::min<int64_t>(tiles, sms), kTrThreads, smem, s>>>(m1, mw, a);
+    OM_CUDA(cudaGetLastError());
+    return OM_OK;
+  }
   OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g));
   if (c2 > 0) {
     if ((ld2 % 8) || (o2 % 8)) return fail(OM_EINVAL, "U-Net: second input not 16-byte aligned");

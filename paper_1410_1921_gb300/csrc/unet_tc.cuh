@@ -39,6 +39,10 @@ constexpr int kTcStages = 3;
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTcATile = kTcM * kTcKc * 2;  // 16 KB
 constexpr unsigned long long kTcSpin = 1ull << 26;  // try_wait rounds before giving up
+// the resident-weight form's tile (8 x 16 voxels at one z) and its halo box
+constexpr int kTcTx = 8, kTcTy = 16;
+constexpr int kTcHx = kTcTx + 2, kTcHy = kTcTy + 2, kTcHz = 3;
+constexpr int kTcHRows = kTcHx * kTcHy * kTcHz;  // 540 rows
 
 struct TcConvArgs {
   int c1, c2;         // channels of the two inputs (c2 = 0: one input)
@@ -275,6 +279,206 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_tc(const __grid_constant__ 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// ------------------------------------------------------------------ resident-weight form
+// For a single input of at most 32 channels and at most 64 output channels
+// (the finest level's convolutions, which carry most of the voxels) the
+// whole operand WT[27][N][32] fits in shared memory next to two halo
+// buffers: a persistent CTA per SM loads the weights once and then walks its
+// tiles (8 x 16 voxels at one z).  Per tile TMA copies the halo -- 10 x 18 x
+// 3 voxels of 32 channels, rows of 64 bytes with the 64-byte swizzle -- and
+// the 27 filter offsets read it through shifted descriptors (the swizzle is
+// applied to the absolute shared-memory address, so a view shifted by whole
+// rows inside the TMA-written box is consistent).  Warp 0 issues the copies,
+// warp 1 the MMAs (2 per offset, K = 16) into one of two TMEM accumulators,
+// warps 2-5 drain the other accumulator (bias, ReLU, BF16 store) while the
+// next tile accumulates.  Channels past the input's count are the copy's
+// zero fill.  Waits are bounded as in conv3d_tc.
+constexpr int kTrThreads = 192;
+constexpr uint32_t kTrHBox = (uint32_t)kTcHRows * 64u;        // 34560 bytes
+constexpr uint32_t kTrHalo = (kTrHBox + 1023u) / 1024u * 1024u;  // 34816
+
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+__global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constant__ CUtensorMap map1,
+                                                            const __grid_constant__ CUtensorMap mapw, TcConvArgs a) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  // [halo x 2][weights 27 x N rows x 64 B][barriers][TMEM address], 1024-byte aligned
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = tc_smem_raw + (base - raw);
+  const uint32_t wbox = (uint32_t)a.N * 64u, wres = base + 2u * kTrHalo;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + 2 * kTrHalo + 27 * (size_t)wbox);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  const uint32_t b0 = smem_u32(bars);
+  const uint32_t wfull = b0, hfull0 = b0 + 8u, hempty0 = b0 + 24u, afull0 = b0 + 40u, aempty0 = b0 + 56u,
+                 done = b0 + 72u;
+  __shared__ volatile int stop;
+  __shared__ int h_issued, h_used;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = a.g.B * a.g.D * a.ty * a.tx;
+  const uint32_t ncols = a.N <= 16 ? 32u : (a.N <= 32 ? 64u : 128u);  // two accumulators of N columns
+
+  if (tid == 0) {
+    stop = 0;
+    h_issued = h_used = 0;
+    mbar_init(wfull, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(hfull0 + 8u * i, 1);
+      mbar_init(hempty0 + 8u * i, 1);
+      mbar_init(afull0 + 8u * i, 1);
+      mbar_init(aempty0 + 8u * i, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  auto tile_xyz = [&](int t, int& x0, int& y0, int& z0, int& bb) {
+    x0 = (t % a.tx) * kTcTx;
+    t /= a.tx;
+    y0 = (t % a.ty) * kTcTy;
+    t /= a.ty;
+    z0 = t % a.g.D;
+    bb = t / a.g.D;
+  };
+
+  if (tid == 0) {
+    // producer: the weights once, then each tile's halo into the buffer its
+    // tile two back has released
+    mbar_expect_tx(wfull, 27u * wbox);
+    for (int k = 0; k < 27; ++k) tma_load_2d(wres + (uint32_t)k * wbox, &mapw, 0, k * a.N, wfull);
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int hb = i & 1;
+      if (i >= 2 && !mbar_wait(hempty0 + 8u * hb, (uint32_t)((i >> 1) - 1) & 1u, &stop)) break;
+      if (stop) break;
+      int x0, y0, z0, bb;
+      tile_xyz(t, x0, y0, z0, bb);
+      mbar_expect_tx(hfull0 + 8u * hb, kTrHBox);
+      tma_load_5d(base + (uint32_t)hb * kTrHalo, &map1, 0, x0 - 1, y0 - 1, z0 - 1, bb, hfull0 + 8u * hb);
+      h_issued = i + 1;
+    }
+    if (blockIdx.x + (int64_t)h_issued * gridDim.x < ntiles) stop = 1;
+  } else if (tid == 32) {
+    // MMA issue
+    const uint32_t idesc = tc_idesc(kTcM, a.N);
+    bool ok = mbar_wait(wfull, 0, &stop);
+    int i = 0;
+    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+      const int hb = i & 1, ab = i & 1;
+      if (i >= 2 && !mbar_wait(aempty0 + 8u * ab, (uint32_t)((i >> 1) - 1) & 1u, &stop)) break;
+      if (!mbar_wait(hfull0 + 8u * hb, (uint32_t)(i >> 1) & 1u, &stop)) break;
+      h_used = i + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t hbase = base + (uint32_t)hb * kTrHalo, acc_addr = tmem + (uint32_t)(ab * a.N);
+      for (int k = 0; k < 27; ++k) {
+        const int dz = k / 9, dy = (k / 3) % 3, dx = k % 3;  // offset + 1
+        const uint32_t shift = (uint32_t)(((dz * kTcHy) + dy) * kTcHx + dx) * 64u;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint64_t ad = sw64_desc(hbase + shift + 32u * kk, kTcHx * 64u);
+          const uint64_t bd = sw64_desc(wres + (uint32_t)k * wbox + 32u * kk, 512u);
+          const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(acc_addr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       hempty0 + 8u * hb)
+                   : "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       afull0 + 8u * ab)
+                   : "memory");
+    }
+    if (!ok || blockIdx.x + (int64_t)h_used * gridDim.x < ntiles) stop = 1;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                 : "memory");
+  } else if (warp >= 2) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
+    const int q = warp & 3, r = q * 32 + lane;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int ab = i & 1;
+      if (!mbar_wait(afull0 + 8u * ab, (uint32_t)(i >> 1) & 1u, &stop)) {
+        if (lane == 0) stop = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int x0, y0, z0, bb;
+      tile_xyz(t, x0, y0, z0, bb);
+      const int xx = x0 + (r & 7), yy = y0 + (r >> 3);
+      const bool inside = xx < a.g.W && yy < a.g.H;
+      const int64_t v = inside ? (((int64_t)bb * a.g.D + z0) * a.g.H + yy) * a.g.W + xx : 0;
+      for (int c0 = 0; c0 < a.N; c0 += 16) {
+        uint32_t qv[16];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * a.N + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(qv[0]), "=r"(qv[1]), "=r"(qv[2]), "=r"(qv[3]), "=r"(qv[4]), "=r"(qv[5]), "=r"(qv[6]),
+              "=r"(qv[7]), "=r"(qv[8]), "=r"(qv[9]), "=r"(qv[10]), "=r"(qv[11]), "=r"(qv[12]), "=r"(qv[13]),
+              "=r"(qv[14]), "=r"(qv[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!inside) continue;
+        float f[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          f[j] = __uint_as_float(qv[j]) + (a.bias ? a.bias[c0 + j] : 0.f);
+          if (a.relu) f[j] = fmaxf(f[j], 0.f);
+        }
+        if (a.y) {
+          uint32_t p[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+            p[j] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(a.y + v * a.ldy + a.oy + c0);
+          dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
+          dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+        if (a.yf) {
+          float4* dst = reinterpret_cast<float4*>(a.yf + v * a.N + c0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dst[j] = make_float4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty0 + 8u * ab) : "memory");
+    }
+  }
+  const bool fin = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool failed = __syncthreads_or(!fin || stop) != 0;
+  if (failed && tid == 0) {
+    atomicExch(a.err, 1);
+    (void)mbar_wait(wfull, 0);  // the weight copies, if they never landed
+    for (int i = h_used; i < h_issued; ++i) (void)mbar_wait(hfull0 + 8u * (i & 1), (uint32_t)(i >> 1) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
