@@ -356,7 +356,13 @@ om_status conv_tc(const om_unet* U, const bf16* x1, int c1, int ld1, int o1, con
     OM_CUDA(cudaGetDevice(&dev));
     OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t tiles = (int64_t)g.B * g.D * a.ty * a.tx;
-    const size_t smem = 1024 + 2 * (size_t)kTrHalo + 27 * (size_t)N * 64 + 8 * 10 + 16;
+    // as many halo buffers (2..4) as 227 KB of shared memory hold next to the weights, and
+    // as many accumulators (2..4) as 256 TMEM columns
+    auto smem_for = [&](int nh) { return 1024 + (size_t)nh * kTrHalo + 27 * (size_t)N * 64 + 8 * 18 + 16; };
+    a.nhalo = 4;
+    while (a.nhalo > 2 && smem_for(a.nhalo) > 227 * 1024) --a.nhalo;
+    a.nacc = std::min(4, 256 / N);
+    const size_t smem = smem_for(a.nhalo);
     OM_CUDA(cudaFuncSetAttribute(conv3d_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conv3d_tc_res<<<(unsigned)std::min<int64_t>(tiles, sms), kTrThreads, smem, s>>>(m1, mw, a);
     OM_CUDA(cudaGetLastError());

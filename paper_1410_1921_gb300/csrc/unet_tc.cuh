@@ -53,7 +53,8 @@ struct TcConvArgs {
   float* yf;          // optional FP32 copy, rows of N
   int relu;
   Grid g;
-  int tx, ty, tz;     // tiles along x, y, z (8, 8, 2 voxels each)
+  int tx, ty, tz;     // tiles along x, y, z (8, 8, 2 voxels each; the resident form: 8, 16, 1)
+  int nhalo, nacc;    // the resident form's halo buffers and TMEM accumulators (2..4 each)
   int* err;           // set when a wait ran out
 };
 
@@ -295,7 +296,9 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_tc(const __grid_constant__ 
 // warp 1 the MMAs (2 per offset, K = 16) into one of two TMEM accumulators,
 // warps 2-5 drain the other accumulator (bias, ReLU, BF16 store) while the
 // next tile accumulates.  Channels past the input's count are the copy's
-// zero fill.  Waits are bounded as in conv3d_tc.
+// zero fill.  nhalo halo buffers and nacc accumulators (2..4 each, as the
+// shared memory and TMEM allow) keep that many tiles in flight.  Waits are
+// bounded as in conv3d_tc.
 constexpr int kTrThreads = 192;
 constexpr uint32_t kTrHBox = (uint32_t)kTcHRows * 64u;        // 34560 bytes
 constexpr uint32_t kTrHalo = (kTrHBox + 1023u) / 1024u * 1024u;  // 34816
@@ -308,27 +311,29 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr, uint32_t sbo) {
 __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constant__ CUtensorMap map1,
                                                             const __grid_constant__ CUtensorMap mapw, TcConvArgs a) {
   extern __shared__ uint8_t tc_smem_raw[];
-  // [halo x 2][weights 27 x N rows x 64 B][barriers][TMEM address], 1024-byte aligned
+  // [halo x nhalo][weights 27 x N rows x 64 B][barriers][TMEM address], 1024-byte aligned
   const uint32_t raw = smem_u32(tc_smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = tc_smem_raw + (base - raw);
-  const uint32_t wbox = (uint32_t)a.N * 64u, wres = base + 2u * kTrHalo;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + 2 * kTrHalo + 27 * (size_t)wbox);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  const int NH = a.nhalo, NA = a.nacc;
+  const uint32_t wbox = (uint32_t)a.N * 64u, wres = base + (uint32_t)NH * kTrHalo;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (size_t)NH * kTrHalo + 27 * (size_t)wbox);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 18);
   const uint32_t b0 = smem_u32(bars);
-  const uint32_t wfull = b0, hfull0 = b0 + 8u, hempty0 = b0 + 24u, afull0 = b0 + 40u, aempty0 = b0 + 56u,
-                 done = b0 + 72u;
+  const uint32_t wfull = b0, hfull0 = b0 + 8u, hempty0 = b0 + 40u, afull0 = b0 + 72u, aempty0 = b0 + 104u,
+                 done = b0 + 136u;
   __shared__ volatile int stop;
   __shared__ int h_issued, h_used;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = a.g.B * a.g.D * a.ty * a.tx;
-  const uint32_t ncols = a.N <= 16 ? 32u : (a.N <= 32 ? 64u : 128u);  // two accumulators of N columns
+  uint32_t ncols = 32u;  // NA accumulators of N columns, a power of two
+  while (ncols < (uint32_t)(NA * a.N)) ncols <<= 1;
 
   if (tid == 0) {
     stop = 0;
     h_issued = h_used = 0;
     mbar_init(wfull, 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(hfull0 + 8u * i, 1);
       mbar_init(hempty0 + 8u * i, 1);
       mbar_init(afull0 + 8u * i, 1);
@@ -365,8 +370,8 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
     for (int k = 0; k < 27; ++k) tma_load_2d(wres + (uint32_t)k * wbox, &mapw, 0, k * a.N, wfull);
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-      const int hb = i & 1;
-      if (i >= 2 && !mbar_wait(hempty0 + 8u * hb, (uint32_t)((i >> 1) - 1) & 1u, &stop)) break;
+      const int hb = i % NH;
+      if (i >= NH && !mbar_wait(hempty0 + 8u * hb, (uint32_t)(i / NH - 1) & 1u, &stop)) break;
       if (stop) break;
       int x0, y0, z0, bb;
       tile_xyz(t, x0, y0, z0, bb);
@@ -381,19 +386,24 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
     bool ok = mbar_wait(wfull, 0, &stop);
     int i = 0;
     for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
-      const int hb = i & 1, ab = i & 1;
-      if (i >= 2 && !mbar_wait(aempty0 + 8u * ab, (uint32_t)((i >> 1) - 1) & 1u, &stop)) break;
-      if (!mbar_wait(hfull0 + 8u * hb, (uint32_t)(i >> 1) & 1u, &stop)) break;
+      const int hb = i % NH, ab = i % NA;
+      if (i >= NA && !mbar_wait(aempty0 + 8u * ab, (uint32_t)(i / NA - 1) & 1u, &stop)) break;
+      if (!mbar_wait(hfull0 + 8u * hb, (uint32_t)(i / NH) & 1u, &stop)) break;
       h_used = i + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t hbase = base + (uint32_t)hb * kTrHalo, acc_addr = tmem + (uint32_t)(ab * a.N);
+      // descriptors of offset k, slice kk: the start-address field (address / 16)
+      // of the first ones advanced by the offset's row shift and the slice's 32 bytes
+      const uint64_t ad0 = sw64_desc(hbase, kTcHx * 64u), bd0 = sw64_desc(wres, 512u);
+      const uint64_t bstep = wbox >> 4;
+#pragma unroll
       for (int k = 0; k < 27; ++k) {
-        const int dz = k / 9, dy = (k / 3) % 3, dx = k % 3;  // offset + 1
-        const uint32_t shift = (uint32_t)(((dz * kTcHy) + dy) * kTcHx + dx) * 64u;
+        constexpr uint32_t kRow = 64u / 16u;  // a halo row in units of 16 bytes
+        const uint32_t shift = (uint32_t)((((k / 9) * kTcHy) + (k / 3) % 3) * kTcHx + k % 3) * kRow;
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-          const uint64_t ad = sw64_desc(hbase + shift + 32u * kk, kTcHx * 64u);
-          const uint64_t bd = sw64_desc(wres + (uint32_t)k * wbox + 32u * kk, 512u);
+          const uint64_t ad = ad0 + shift + 2u * kk;
+          const uint64_t bd = bd0 + (uint64_t)k * bstep + 2u * kk;
           const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
           asm volatile(
               "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -417,8 +427,8 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
     const int q = warp & 3, r = q * 32 + lane;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-      const int ab = i & 1;
-      if (!mbar_wait(afull0 + 8u * ab, (uint32_t)(i >> 1) & 1u, &stop)) {
+      const int ab = i % NA;
+      if (!mbar_wait(afull0 + 8u * ab, (uint32_t)(i / NA) & 1u, &stop)) {
         if (lane == 0) stop = 1;
         break;
       }
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
   if (failed && tid == 0) {
     atomicExch(a.err, 1);
     (void)mbar_wait(wfull, 0);  // the weight copies, if they never landed
-    for (int i = h_used; i < h_issued; ++i) (void)mbar_wait(hfull0 + 8u * (i & 1), (uint32_t)(i >> 1) & 1u);
+    for (int i = h_used; i < h_issued; ++i) (void)mbar_wait(hfull0 + 8u * (i % NH), (uint32_t)(i / NH) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
