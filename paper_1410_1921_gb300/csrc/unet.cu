@@ -52,63 +52,95 @@ __global__ void avgpool2(const bf16* in, Grid gf, int C, bf16* out) {
   }
 }
 
+// The element-wise kernels below move 8 channels (one 16-byte vector of
+// BF16) per thread: every channel count and row offset of the network is a
+// multiple of 16.
+union V8 {
+  uint4 u;
+  __nv_bfloat16 h[8];
+};
+
+__device__ __forceinline__ void fine_xyzb(int64_t v, const Grid& g, int& x, int& y, int& z, int& b) {
+  x = (int)(v % g.W);
+  v /= g.W;
+  y = (int)(v % g.H);
+  v /= g.H;
+  z = (int)(v % g.D);
+  b = (int)(v / g.D);
+}
+
+__device__ __forceinline__ int64_t coarse_of(const Grid& gf, int x, int y, int z, int b) {
+  return (((int64_t)b * (gf.D / 2) + z / 2) * (gf.H / 2) + y / 2) * (gf.W / 2) + x / 2;
+}
+
 // d(fine) = d(coarse parent) / 8
 __global__ void avgpool2_bwd(const bf16* dout, Grid gf, int C, bf16* din) {
-  const int64_t n = gf.voxels() * C;
+  const int C8 = C / 8;
+  const int64_t n = gf.voxels() * C8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int x = (int)(r % gf.W); r /= gf.W;
-    const int y = (int)(r % gf.H); r /= gf.H;
-    const int z = (int)(r % gf.D);
-    const int b = (int)(r / gf.D);
-    const int64_t vc = (((int64_t)b * (gf.D / 2) + z / 2) * (gf.H / 2) + y / 2) * (gf.W / 2) + x / 2;
-    din[i] = __float2bfloat16_rn(0.125f * __bfloat162float(dout[vc * C + c]));
+    const int c8 = (int)(i % C8);
+    const int64_t v = i / C8;
+    int x, y, z, b;
+    fine_xyzb(v, gf, x, y, z, b);
+    V8 a, o;
+    a.u = *reinterpret_cast<const uint4*>(dout + coarse_of(gf, x, y, z, b) * C + 8 * c8);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o.h[j] = __float2bfloat16_rn(0.125f * __bfloat162float(a.h[j]));
+    *reinterpret_cast<uint4*>(din + v * C + 8 * c8) = o.u;
   }
 }
 
 // nearest 2x: coarse [V_c x C] -> fine rows of ldo, channels [oo, oo + C)
 __global__ void upsample2(const bf16* in, Grid gf, int C, bf16* out, int ldo, int oo) {
-  const int64_t n = gf.voxels() * C;
+  const int C8 = C / 8;
+  const int64_t n = gf.voxels() * C8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const int64_t v = i / C;
-    int64_t r = v;
-    const int x = (int)(r % gf.W); r /= gf.W;
-    const int y = (int)(r % gf.H); r /= gf.H;
-    const int z = (int)(r % gf.D);
-    const int b = (int)(r / gf.D);
-    const int64_t vc = (((int64_t)b * (gf.D / 2) + z / 2) * (gf.H / 2) + y / 2) * (gf.W / 2) + x / 2;
-    out[v * ldo + oo + c] = in[vc * C + c];
+    const int c8 = (int)(i % C8);
+    const int64_t v = i / C8;
+    int x, y, z, b;
+    fine_xyzb(v, gf, x, y, z, b);
+    *reinterpret_cast<uint4*>(out + v * ldo + oo + 8 * c8) =
+        *reinterpret_cast<const uint4*>(in + coarse_of(gf, x, y, z, b) * C + 8 * c8);
   }
 }
 
 // d(coarse) = sum of the 8 fine children, read from rows of ldi at offset oi
 __global__ void upsample2_bwd(const bf16* dfine, int ldi, int oi, Grid gf, int C, bf16* dcoarse) {
   const Grid gc{gf.B, gf.D / 2, gf.H / 2, gf.W / 2};
-  const int64_t n = gc.voxels() * C;
+  const int C8 = C / 8;
+  const int64_t n = gc.voxels() * C8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int x = (int)(r % gc.W); r /= gc.W;
-    const int y = (int)(r % gc.H); r /= gc.H;
-    const int z = (int)(r % gc.D);
-    const int b = (int)(r / gc.D);
-    float s = 0.f;
+    const int c8 = (int)(i % C8);
+    const int64_t vcoarse = i / C8;
+    int x, y, z, b;
+    fine_xyzb(vcoarse, gc, x, y, z, b);
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int q = 0; q < 8; ++q) {
       const int64_t vf = (((int64_t)b * gf.D + 2 * z + (q >> 2)) * gf.H + 2 * y + ((q >> 1) & 1)) * gf.W + 2 * x + (q & 1);
-      s += __bfloat162float(dfine[vf * ldi + oi + c]);
+      V8 a;
+      a.u = *reinterpret_cast<const uint4*>(dfine + vf * ldi + oi + 8 * c8);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(a.h[j]);
     }
-    dcoarse[i] = __float2bfloat16_rn(s);
+    V8 o;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o.h[j] = __float2bfloat16_rn(acc[j]);
+    *reinterpret_cast<uint4*>(dcoarse + vcoarse * C + 8 * c8) = o.u;
   }
 }
 
 // gradient at the pre-activation: g * [y > 0]; g read from rows of ldg at og
 __global__ void relu_bwd(const bf16* g, int ldg, int og, const bf16* y, int N, int64_t V, bf16* out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = i / N;
-    const int c = (int)(i % N);
-    out[i] = __bfloat162float(y[i]) > 0.f ? g[v * ldg + og + c] : __float2bfloat16_rn(0.f);
+  const int N8 = N / 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N8; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / N8;
+    const int c8 = (int)(i % N8);
+    V8 yy, gg, o;
+    yy.u = *reinterpret_cast<const uint4*>(y + v * N + 8 * c8);
+    gg.u = *reinterpret_cast<const uint4*>(g + v * ldg + og + 8 * c8);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o.h[j] = __bfloat162float(yy.h[j]) > 0.f ? gg.h[j] : __float2bfloat16_rn(0.f);
+    *reinterpret_cast<uint4*>(out + v * N + 8 * c8) = o.u;
   }
 }
 
@@ -121,15 +153,23 @@ __global__ void add_into(bf16* a, int N, int64_t V, const bf16* b, int ldb, int 
   }
 }
 
-// db[c] += sum_v g[v][c] (per-block partial sums, then atomics)
+// db[c] += sum_v g[v][c]: thread t of a block sums channel t % N over the
+// block's voxels t / N, t / N + lanes, ... (coalesced rows), then the lanes
+// of a channel are reduced in shared memory and added to db
 __global__ void bias_grad(const bf16* g, int N, int64_t V, float* db) {
   extern __shared__ float sh[];
-  for (int c = threadIdx.x; c < N; c += blockDim.x) sh[c] = 0.f;
+  const int lanes = blockDim.x / N, c = threadIdx.x % N, lane = threadIdx.x / N;
+  float acc = 0.f;
+  if (lane < lanes)
+    for (int64_t v = (int64_t)blockIdx.x * lanes + lane; v < V; v += (int64_t)gridDim.x * lanes)
+      acc += __bfloat162float(g[v * N + c]);
+  sh[threadIdx.x] = lane < lanes ? acc : 0.f;
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N; i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&sh[i % N], __bfloat162float(g[i]));
-  __syncthreads();
-  for (int c = threadIdx.x; c < N; c += blockDim.x) atomicAdd(&db[c], sh[c]);
+  if (threadIdx.x < N) {
+    float t = 0.f;
+    for (int l = 0; l < lanes; ++l) t += sh[l * N + threadIdx.x];
+    atomicAdd(&db[threadIdx.x], t);
+  }
 }
 
 // 1x1 head: y[v][o] = b[o] + sum_c x[v][c] w[c][o]  (FP32 out)
@@ -437,7 +477,7 @@ om_status conv_wgrad(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1,
   else if (MT == 16 && NT == 64) launch_wgrad<16, 64>(a, K, s);
   else if (MT == 16 && NT == 32) launch_wgrad<16, 32>(a, K, s);
   else launch_wgrad<16, 16>(a, K, s);
-  bias_grad<<<std::min<int64_t>(blocks(g.voxels() * c.cout), 1216), kT, c.cout * sizeof(float), s>>>(
+  bias_grad<<<std::min<int64_t>(blocks(g.voxels() * c.cout), 1216), kT, kT * sizeof(float), s>>>(
       dyp, c.cout, g.voxels(), U->g + c.b_off);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
@@ -509,7 +549,7 @@ om_status forward(om_unet* U, const float* x, const Grid& g, cudaStream_t s) {
     const Grid gl = level_grid(g, l);
     const bf16* below = l + 1 == L - 1 ? U->s[L - 1].p : U->h[l + 1].p;
     const int cb = U->ch[l + 1];
-    upsample2<<<blocks(gl.voxels() * cb), kT, 0, s>>>(below, gl, cb, U->u[l].p, cb, 0);
+    upsample2<<<blocks(gl.voxels() * cb / 8), kT, 0, s>>>(below, gl, cb, U->u[l].p, cb, 0);
     OM_TRY(conv_forward(U, U->dec1[l], U->u[l].p, cb, 0, U->s[l].p, U->ch[l], 0, U->b[l].p, gl, s));
     OM_TRY(conv_forward(U, U->dec2[l], U->b[l].p, U->ch[l], 0, nullptr, 0, 0, U->h[l].p, gl, s));
   }
@@ -547,15 +587,15 @@ om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g,
     const int64_t Vl = gl.voxels();
     const int c = U->ch[l], cb = U->ch[l + 1];
     // h_l = relu(conv(b_l))
-    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d1[l].p, c, 0, U->h[l].p, c, Vl, U->d2[l].p);
+    relu_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->d1[l].p, c, 0, U->h[l].p, c, Vl, U->d2[l].p);
     OM_TRY(conv_wgrad(U, U->dec2[l], U->b[l].p, c, 0, nullptr, 0, 0, U->d2[l].p, gl, s));
     OM_TRY(conv_dgrad(U, U->dec2[l], U->d2[l].p, U->d1[l].p, gl, s));
     // b_l = relu(conv(concat(u_l, s_l)))
-    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d1[l].p, c, 0, U->b[l].p, c, Vl, U->d2[l].p);
+    relu_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->d1[l].p, c, 0, U->b[l].p, c, Vl, U->d2[l].p);
     OM_TRY(conv_wgrad(U, U->dec1[l], U->u[l].p, cb, 0, U->s[l].p, c, 0, U->d2[l].p, gl, s));
     OM_TRY(conv_dgrad(U, U->dec1[l], U->d2[l].p, U->dcat[l].p, gl, s));
     // u_l = up(h_{l+1}) (or s_{L-1} at the bottom): gradient of the level below
-    upsample2_bwd<<<blocks(level_grid(g, l + 1).voxels() * cb), kT, 0, s>>>(U->dcat[l].p, cb + c, 0, gl, cb,
+    upsample2_bwd<<<blocks(level_grid(g, l + 1).voxels() * cb / 8), kT, 0, s>>>(U->dcat[l].p, cb + c, 0, gl, cb,
                                                                             U->d1[l + 1].p);
   }
   // encoder, bottom level up: ds[l] = gradient of s_l
@@ -568,15 +608,15 @@ om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g,
     if (l == L - 1) {
       OM_CUDA(cudaMemcpyAsync(U->ds[l].p, U->d1[l].p, sizeof(bf16) * Vl * c, cudaMemcpyDeviceToDevice, s));
     } else {
-      avgpool2_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d2[l + 1].p, gl, c, U->ds[l].p);
+      avgpool2_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->d2[l + 1].p, gl, c, U->ds[l].p);
       add_into<<<blocks(Vl * c), kT, 0, s>>>(U->ds[l].p, c, Vl, U->dcat[l].p, U->ch[l + 1] + c, U->ch[l + 1]);
     }
     // s_l = relu(conv(a_l))
-    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->ds[l].p, c, 0, U->s[l].p, c, Vl, U->d1[l].p);
+    relu_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->ds[l].p, c, 0, U->s[l].p, c, Vl, U->d1[l].p);
     OM_TRY(conv_wgrad(U, U->enc2[l], U->a[l].p, c, 0, nullptr, 0, 0, U->d1[l].p, gl, s));
     OM_TRY(conv_dgrad(U, U->enc2[l], U->d1[l].p, U->d2[l].p, gl, s));
     // a_l = relu(conv(in_l))
-    relu_bwd<<<blocks(Vl * c), kT, 0, s>>>(U->d2[l].p, c, 0, U->a[l].p, c, Vl, U->d1[l].p);
+    relu_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->d2[l].p, c, 0, U->a[l].p, c, Vl, U->d1[l].p);
     const bf16* in = l == 0 ? U->x0.p : U->in[l].p;
     OM_TRY(conv_wgrad(U, U->enc1[l], in, cin, 0, nullptr, 0, 0, U->d1[l].p, gl, s));
     // d2[l] = gradient of in_l (pooled s_{l-1}); not needed at the input
