@@ -119,12 +119,14 @@ extern "C" om_status om_solve_permeability(const uint8_t* mask, om_domain d, con
   if (params->layout == OM_LAYOUT_AUTO && dense_flow_supported(*params) && sc.ns->wrap_links > 0 &&
       (double)nt >= kDenseTryFraction * (double)N) {
     double ms_dense = 0.0, ms_sparse = 0.0;
-    OM_TRY(dense_flow_solve(tr.p, d, nt, *params, nullptr, nullptr, nullptr, &ms_dense, sc.s));
-    OM_TRY(om_flow_create(sc.ns, &ps, sc.s, &sc.fl));
-    OM_TRY(pair_ms_of([&]() { return om_flow_step(sc.fl, 2, sc.s); }, sc.s, &ms_sparse));
-    om_flow_destroy(sc.fl);  // the solve starts from rest
-    sc.fl = nullptr;
-    dense = ms_dense < ms_sparse;
+    // a dense layout that does not fit in memory leaves the choice to the sparse one
+    if (dense_flow_solve(tr.p, d, nt, *params, nullptr, nullptr, nullptr, &ms_dense, sc.s) == OM_OK) {
+      OM_TRY(om_flow_create(sc.ns, &ps, sc.s, &sc.fl));
+      OM_TRY(pair_ms_of([&]() { return om_flow_step(sc.fl, 2, sc.s); }, sc.s, &ms_sparse));
+      om_flow_destroy(sc.fl);  // the solve starts from rest
+      sc.fl = nullptr;
+      dense = ms_dense < ms_sparse;
+    }
   }
   double kl = 0.0;
   om_status st;
@@ -183,12 +185,13 @@ extern "C" om_status om_solve_knudsen(const uint8_t* mask, const float* d_nm, om
   bool dense = params->layout == OM_LAYOUT_DENSE;
   if (params->layout == OM_LAYOUT_AUTO && dense_diff_supported(*params) && (double)nt >= kDenseTryFraction * (double)N) {
     double ms_dense = 0.0, ms_sparse = 0.0;
-    OM_TRY(dense_diff_solve(tr.p, dd.p, d, nt, *params, nullptr, nullptr, nullptr, nullptr, &ms_dense, sc.s));
-    OM_TRY(om_diff_create(sc.ns, dd.p, &ps, sc.s, &sc.df));
-    OM_TRY(pair_ms_of([&]() { return om_diff_step(sc.df, 2, sc.s); }, sc.s, &ms_sparse));
-    om_diff_destroy(sc.df);  // the solve starts from the linear profile
-    sc.df = nullptr;
-    dense = ms_dense < ms_sparse;
+    if (dense_diff_solve(tr.p, dd.p, d, nt, *params, nullptr, nullptr, nullptr, nullptr, &ms_dense, sc.s) == OM_OK) {
+      OM_TRY(om_diff_create(sc.ns, dd.p, &ps, sc.s, &sc.df));
+      OM_TRY(pair_ms_of([&]() { return om_diff_step(sc.df, 2, sc.s); }, sc.s, &ms_sparse));
+      om_diff_destroy(sc.df);  // the solve starts from the linear profile
+      sc.df = nullptr;
+      dense = ms_dense < ms_sparse;
+    }
   }
   double Dl = 0.0, DL_sum = 0.0;
   om_status st;
