@@ -144,12 +144,18 @@ __global__ void relu_bwd(const bf16* g, int ldg, int og, const bf16* y, int N, i
   }
 }
 
-// a[i] += b (rows of ldb at ob), BF16
+// a[i] += b (rows of ldb at ob), BF16; 8 channels per thread
 __global__ void add_into(bf16* a, int N, int64_t V, const bf16* b, int ldb, int ob) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = i / N;
-    const int c = (int)(i % N);
-    a[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[v * ldb + ob + c]));
+  const int N8 = N / 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * N8; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / N8;
+    const int c8 = (int)(i % N8);
+    V8 x, y;
+    x.u = *reinterpret_cast<const uint4*>(a + v * N + 8 * c8);
+    y.u = *reinterpret_cast<const uint4*>(b + v * ldb + ob + 8 * c8);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x.h[j] = __float2bfloat16_rn(__bfloat162float(x.h[j]) + __bfloat162float(y.h[j]));
+    *reinterpret_cast<uint4*>(a + v * N + 8 * c8) = x.u;
   }
 }
 
@@ -172,20 +178,39 @@ __global__ void bias_grad(const bf16* g, int N, int64_t V, float* db) {
   }
 }
 
-// 1x1 head: y[v][o] = b[o] + sum_c x[v][c] w[c][o]  (FP32 out)
+// 1x1 head: y[v][o] = b[o] + sum_c x[v][c] w[c][o]  (FP32 out); a thread per voxel reads its row
+// of C channels as 16-byte vectors
 __global__ void head_fwd(const bf16* x, int C, const float* w, const float* b, int O, int64_t V, float* y) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * O; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = i / O;
-    const int o = (int)(i % O);
-    float s = b[o];
-    for (int c = 0; c < C; ++c) s += __bfloat162float(x[v * C + c]) * w[c * O + o];
-    y[i] = s;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint4* row = reinterpret_cast<const uint4*>(x + v * C);
+    for (int o = 0; o < O; ++o) {
+      float acc = b[o];
+      for (int c8 = 0; c8 < C / 8; ++c8) {
+        V8 q;
+        q.u = row[c8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc += __bfloat162float(q.h[j]) * w[(8 * c8 + j) * O + o];
+      }
+      y[v * O + o] = acc;
+    }
   }
 }
 
-// masked MSE: loss = sum m (y - t)^2 * scale, dy = 2 m (y - t) * scale
-__global__ void mse_grad(const float* y, const float* t, const uint8_t* m, int O, int64_t V, float scale, float* dy,
-                         double* loss) {
+// the mask's nonzero count, added to *cnt (a double: exact below 2^53)
+__global__ void mask_count(const uint8_t* m, int64_t V, double* cnt) {
+  unsigned long long k = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+    k += m[v] != 0;
+  for (int o = 16; o > 0; o >>= 1) k += __shfl_down_sync(0xffffffffu, k, o);
+  if ((threadIdx.x & 31) == 0 && k) atomicAdd(cnt, (double)k);
+}
+
+// masked MSE: loss = sum m (y - t)^2 * scale, dy = 2 m (y - t) * scale, scale = 1 / (count O)
+// with the mask's count read from *cnt
+__global__ void mse_grad(const float* y, const float* t, const uint8_t* m, int O, int64_t V, const double* cnt,
+                         float* dy, double* loss) {
+  const int64_t nk = (int64_t)*cnt;
+  const float scale = nk > 0 ? 1.f / (float)(nk * O) : 0.f;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * O; i += (int64_t)gridDim.x * blockDim.x) {
     const float keep = m[i / O] ? 1.f : 0.f;
@@ -199,30 +224,56 @@ __global__ void mse_grad(const float* y, const float* t, const uint8_t* m, int O
 
 // head backward: dw[c][o] += sum_v x[v][c] dy[v][o]; db[o] += sum_v dy; dx[v][c] = sum_o dy w[c][o]
 __global__ void head_bwd_dx(const float* dy, const float* w, int C, int O, int64_t V, bf16* dx) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * C; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = i / C;
-    const int c = (int)(i % C);
-    float s = 0.f;
-    for (int o = 0; o < O; ++o) s += dy[v * O + o] * w[c * O + o];
-    dx[i] = __float2bfloat16_rn(s);
+  const int C8 = C / 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V * C8; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / C8;
+    const int c0 = (int)(i % C8) * 8;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int o = 0; o < O; ++o) {
+      const float d = dy[v * O + o];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] += d * w[(c0 + j) * O + o];
+    }
+    V8 q;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q.h[j] = __float2bfloat16_rn(acc[j]);
+    *reinterpret_cast<uint4*>(dx + v * C + c0) = q.u;
   }
 }
-__global__ void head_bwd_dw(const bf16* x, const float* dy, int C, int O, int64_t V, float* dw, float* db) {
-  // one block per (c, o) pair plus the bias row c == C
-  const int c = blockIdx.x / O, o = blockIdx.x % O;
-  float s = 0.f;
-  for (int64_t v = threadIdx.x; v < V; v += blockDim.x)
-    s += (c < C ? __bfloat162float(x[v * C + c]) : 1.f) * dy[v * O + o];
-  __shared__ float sh[kT];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
-    __syncthreads();
+// dw[c][o] and db[o] for o in [o0, o0 + 4): thread t of a block takes channel t % C of the
+// voxels t / C, t / C + lanes, ... (coalesced rows); the lanes are reduced in shared memory
+__global__ void head_bwd_dw(const bf16* x, const float* dy, int C, int O, int o0, int64_t V, float* dw, float* db) {
+  extern __shared__ float sh[];  // [8][blockDim.x]
+  const int lanes = blockDim.x / C, c = threadIdx.x % C, lane = threadIdx.x / C;
+  const int no = min(4, O - o0);
+  float aw[4] = {0, 0, 0, 0}, ab[4] = {0, 0, 0, 0};
+  if (lane < lanes)
+    for (int64_t v = (int64_t)blockIdx.x * lanes + lane; v < V; v += (int64_t)gridDim.x * lanes) {
+      const float xv = __bfloat162float(x[v * C + c]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < no) {
+          const float d = dy[v * O + o0 + j];
+          aw[j] += xv * d;
+          ab[j] += d;
+        }
+    }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    sh[j * blockDim.x + threadIdx.x] = lane < lanes ? aw[j] : 0.f;
+    sh[(4 + j) * blockDim.x + threadIdx.x] = lane < lanes ? ab[j] : 0.f;
   }
-  if (threadIdx.x == 0) {
-    if (c < C) dw[c * O + o] += sh[0];
-    else db[o] += sh[0];
+  __syncthreads();
+  if ((int)threadIdx.x < C) {
+    for (int j = 0; j < no; ++j) {
+      float tw = 0.f, tb = 0.f;
+      for (int l = 0; l < lanes; ++l) {
+        tw += sh[j * blockDim.x + l * C + threadIdx.x];
+        tb += sh[(4 + j) * blockDim.x + l * C + threadIdx.x];
+      }
+      atomicAdd(&dw[threadIdx.x * O + o0 + j], tw);
+      if (threadIdx.x == 0) atomicAdd(&db[o0 + j], tb);
+    }
   }
 }
 
@@ -338,18 +389,21 @@ om_status tensor_map_encoder(EncodeTiledFn* out) {
   return OM_OK;
 }
 
-// 5-D map of an NDHWC activation tensor: rows of ld BF16, c channels from o;
-// box {64 channels, 8 x, 8 y, 2 z, 1 batch}, 128-byte swizzle, zero fill (or,
-// halo = true, the resident-weight kernel's {32 channels, 10, 18, 3, 1} with
-// the 64-byte swizzle)
-om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, const Grid& g, bool halo = false) {
+// 5-D map of an NDHWC activation tensor: rows of ld BF16, c channels from o,
+// zero fill; box by mode: 0 = {64 channels, 8 x, 8 y, 2 z, 1 batch} with the
+// 128-byte swizzle, and with the 64-byte swizzle 1 = the {32, 10, 18, 3, 1}
+// halo, 2 = its one-plane form {32, 10, 18, 1, 1}, 3 = the 8 x 16 tile
+// {32, 8, 16, 1, 1}
+om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, const Grid& g, int mode = 0) {
+  const bool halo = mode != 0;
   EncodeTiledFn enc;
   OM_TRY(tensor_map_encoder(&enc));
   const cuuint64_t row = (cuuint64_t)ld * 2;
   cuuint64_t dims[5] = {(cuuint64_t)c, (cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)g.D, (cuuint64_t)g.B};
   cuuint64_t strides[4] = {row, row * g.W, row * g.W * g.H, row * g.W * g.H * g.D};
   cuuint32_t box[5] = {(cuuint32_t)kTcKc, 8, 8, 2, 1};
-  if (halo) box[0] = 32, box[1] = kTcHx, box[2] = kTcHy, box[3] = kTcHz;
+  if (mode == 1 || mode == 2) box[0] = 32, box[1] = kTcHx, box[2] = kTcHy, box[3] = mode == 1 ? kTcHz : 1;
+  if (mode == 3) box[0] = 32, box[1] = kTcTx, box[2] = kTcTy, box[3] = 1;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(x + o), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, halo ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
@@ -386,7 +440,7 @@ om_status conv_tc(const om_unet* U, const bf16* x1, int c1, int ld1, int o1, con
   CUtensorMap m1, m2, mw;
   if (c2 == 0 && c1 <= 32 && N <= 64) {
     // resident weights: one persistent CTA per SM (conv3d_tc_res)
-    OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g, true));
+    OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g, 1));
     OM_TRY(weight_map(&mw, wt, c1, N, true));
     TcConvArgs a{};
     a.c1 = c1, a.c2 = 0, a.N = N, a.bias = bias, a.y = y, a.ldy = ldy, a.oy = oy, a.yf = yf, a.relu = relu, a.g = g;
@@ -449,34 +503,48 @@ om_status conv_dgrad(const om_unet* U, const Conv& c, const bf16* dyp, bf16* dx,
   return conv_tc(U, dyp, c.cout, c.cout, 0, nullptr, 0, 0, 0, c.wd, N, nullptr, dx, N, 0, nullptr, 0, g, s);
 }
 
-template <int MT, int NT>
-void launch_wgrad(const WgradArgs& a, int K, cudaStream_t s) {
-  const unsigned gx = (unsigned)((a.g.voxels() + a.chunk - 1) / a.chunk);
-  conv3d_wgrad<MT, NT><<<dim3(gx, 27, (K / MT) * (a.N / NT)), MT * 2, 0, s>>>(a);
-}
-
-om_status conv_wgrad(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
-                     const bf16* dyp, const Grid& g, cudaStream_t s) {
-  WgradArgs a{};
-  a.x1 = x1, a.c1 = c.cin1, a.ld1 = ld1, a.o1 = o1;
-  a.x2 = x2, a.c2 = c.cin2, a.ld2 = ld2, a.o2 = o2;
-  a.dy = dyp;
-  a.N = c.cout;
+// dW += the weight gradient on tcgen05 (conv3d_wgrad_tc): one CTA per input chunk of 32
+// channels, (dz, dy) group and part of 128 output channels, gridDim.x of them over the tiles
+om_status wgrad_tc(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
+                   const bf16* dyp, const Grid& g, cudaStream_t s) {
+  TcWgradArgs a{};
+  a.c1 = c.cin1, a.c2 = c.cin2, a.nch1 = (c.cin1 + 31) / 32;
+  const int nch2 = (c.cin2 + 31) / 32;
+  a.N = c.cout, a.Nm = (std::min(c.cout, 128) + 31) / 32 * 32;
+  a.npart = (c.cout + 127) / 128;
+  a.npair = a.Nm == 32 ? 9 : 3;
   a.dw = U->g + c.w_off;
   a.g = g;
-  a.chunk = 1024;
-  const int K = c.cin1 + c.cin2;
-  const int MT = K % 64 == 0 ? 64 : (K % 32 == 0 ? 32 : 16);
-  const int NT = c.cout % 64 == 0 ? 64 : (c.cout % 32 == 0 ? 32 : 16);
-  if (MT == 64 && NT == 64) launch_wgrad<64, 64>(a, K, s);
-  else if (MT == 64 && NT == 32) launch_wgrad<64, 32>(a, K, s);
-  else if (MT == 64 && NT == 16) launch_wgrad<64, 16>(a, K, s);
-  else if (MT == 32 && NT == 64) launch_wgrad<32, 64>(a, K, s);
-  else if (MT == 32 && NT == 32) launch_wgrad<32, 32>(a, K, s);
-  else if (MT == 32 && NT == 16) launch_wgrad<32, 16>(a, K, s);
-  else if (MT == 16 && NT == 64) launch_wgrad<16, 64>(a, K, s);
-  else if (MT == 16 && NT == 32) launch_wgrad<16, 32>(a, K, s);
-  else launch_wgrad<16, 16>(a, K, s);
+  a.tx = (g.W + kTcTx - 1) / kTcTx, a.ty = (g.H + kTcTy - 1) / kTcTy;
+  a.err = U->tc_err.p;
+  const int hmode = a.npair == 9 ? 1 : 2;
+  CUtensorMap m1, m2, md;
+  OM_TRY(activation_map(&m1, x1, c.cin1, ld1, o1, g, hmode));
+  if (c.cin2 > 0) OM_TRY(activation_map(&m2, x2, c.cin2, ld2, o2, g, hmode));
+  else m2 = m1;
+  OM_TRY(activation_map(&md, dyp, c.cout, c.cout, 0, g, 3));
+  const size_t stage = wg_stage_bytes(a.npair, a.Nm);
+  a.nstage = (int)std::min<size_t>(4, (227 * 1024 - 2048) / stage);
+  const size_t smem = 1024 + (size_t)a.nstage * stage + 8 * (2 * a.nstage + 1) + 16;
+  int dev = 0, sms = 0;
+  OM_CUDA(cudaGetDevice(&dev));
+  OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int gy = (a.nch1 + nch2) * (9 / a.npair) * a.npart;
+  const int64_t ntiles = (int64_t)g.B * g.D * a.ty * a.tx;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (sms + gy - 1) / gy));
+  OM_CUDA(cudaFuncSetAttribute(conv3d_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  conv3d_wgrad_tc<<<dim3(gx, (unsigned)gy), kTcThreads, smem, s>>>(m1, m2, md, a);
+  OM_CUDA(cudaGetLastError());
+  return OM_OK;
+}
+
+// dW += the weight gradient of conv c, db += its bias gradient, for the pre-activation gradient dyp
+om_status conv_wgrad(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
+                     const bf16* dyp, const Grid& g, cudaStream_t s) {
+  if (c.cout % 16 || c.cout > 256 || c.cin1 % 8 || c.cin2 % 8 || ld1 % 8 || o1 % 8 ||
+      (c.cin2 > 0 && (ld2 % 8 || o2 % 8)))
+    return fail(OM_EINVAL, "U-Net: weight-gradient shape outside the tensor-core kernel's layout");
+  OM_TRY(wgrad_tc(U, c, x1, ld1, o1, x2, ld2, o2, dyp, g, s));
   bias_grad<<<std::min<int64_t>(blocks(g.voxels() * c.cout), 1216), kT, kT * sizeof(float), s>>>(
       dyp, c.cout, g.voxels(), U->g + c.b_off);
   OM_CUDA(cudaGetLastError());
@@ -554,7 +622,7 @@ om_status forward(om_unet* U, const float* x, const Grid& g, cudaStream_t s) {
     OM_TRY(conv_forward(U, U->dec2[l], U->b[l].p, U->ch[l], 0, nullptr, 0, 0, U->h[l].p, gl, s));
   }
   const bf16* top = L > 1 ? U->h[0].p : U->s[0].p;
-  head_fwd<<<blocks(g.voxels() * U->out_ch), kT, 0, s>>>(top, U->ch[0], U->w + U->head_w, U->w + U->head_b, U->out_ch,
+  head_fwd<<<blocks(g.voxels()), kT, 0, s>>>(top, U->ch[0], U->w + U->head_w, U->w + U->head_b, U->out_ch,
                                                          g.voxels(), U->out.p);
   OM_CUDA(cudaGetLastError());
   return OM_OK;
@@ -565,22 +633,19 @@ om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g,
   const int L = U->L;
   const int64_t V = g.voxels();
   OM_CUDA(cudaMemsetAsync(U->g, 0, sizeof(float) * U->nparam, s));
-  OM_TRY(U->loss.ensure(1));
-  OM_CUDA(cudaMemsetAsync(U->loss.p, 0, sizeof(double), s));
-  // masked mean over pore voxels and output channels: the count is taken on the host
-  std::vector<uint8_t> hm((size_t)V);
-  OM_CUDA(cudaMemcpyAsync(hm.data(), mk, (size_t)V, cudaMemcpyDeviceToHost, s));
-  OM_CUDA(cudaStreamSynchronize(s));
-  int64_t cnt = 0;
-  for (uint8_t q : hm) cnt += q != 0;
-  const float scale = cnt > 0 ? 1.f / (float)(cnt * U->out_ch) : 0.f;
-  mse_grad<<<std::min<unsigned>(blocks(V * U->out_ch), 1216), kT, 0, s>>>(U->out.p, t, mk, U->out_ch, V, scale, U->dout.p,
-                                                                           U->loss.p);
+  OM_TRY(U->loss.ensure(2));
+  OM_CUDA(cudaMemsetAsync(U->loss.p, 0, 2 * sizeof(double), s));
+  // masked mean over pore voxels and output channels: the count in loss[1]
+  mask_count<<<std::min<unsigned>(blocks(V), 1216), kT, 0, s>>>(mk, V, U->loss.p + 1);
+  mse_grad<<<std::min<unsigned>(blocks(V * U->out_ch), 1216), kT, 0, s>>>(U->out.p, t, mk, U->out_ch, V, U->loss.p + 1,
+                                                                           U->dout.p, U->loss.p);
   // head
   const int c0 = U->ch[0];
   const bf16* top = L > 1 ? U->h[0].p : U->s[0].p;
-  head_bwd_dw<<<(c0 + 1) * U->out_ch, kT, 0, s>>>(top, U->dout.p, c0, U->out_ch, V, U->g + U->head_w, U->g + U->head_b);
-  head_bwd_dx<<<blocks(V * c0), kT, 0, s>>>(U->dout.p, U->w + U->head_w, c0, U->out_ch, V, U->d1[0].p);
+  for (int o0 = 0; o0 < U->out_ch; o0 += 4)
+    head_bwd_dw<<<1216, kT, 8 * kT * sizeof(float), s>>>(top, U->dout.p, c0, U->out_ch, o0, V, U->g + U->head_w,
+                                                         U->g + U->head_b);
+  head_bwd_dx<<<blocks(V * c0 / 8), kT, 0, s>>>(U->dout.p, U->w + U->head_w, c0, U->out_ch, V, U->d1[0].p);
   // decoder, top level down: d1[l] holds the gradient of the level's output h_l
   for (int l = 0; l + 1 < L; ++l) {
     const Grid gl = level_grid(g, l);
@@ -609,7 +674,7 @@ om_status backward(om_unet* U, const float* t, const uint8_t* mk, const Grid& g,
       OM_CUDA(cudaMemcpyAsync(U->ds[l].p, U->d1[l].p, sizeof(bf16) * Vl * c, cudaMemcpyDeviceToDevice, s));
     } else {
       avgpool2_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->d2[l + 1].p, gl, c, U->ds[l].p);
-      add_into<<<blocks(Vl * c), kT, 0, s>>>(U->ds[l].p, c, Vl, U->dcat[l].p, U->ch[l + 1] + c, U->ch[l + 1]);
+      add_into<<<blocks(Vl * c / 8), kT, 0, s>>>(U->ds[l].p, c, Vl, U->dcat[l].p, U->ch[l + 1] + c, U->ch[l + 1]);
     }
     // s_l = relu(conv(a_l))
     relu_bwd<<<blocks(Vl * c / 8), kT, 0, s>>>(U->ds[l].p, c, 0, U->s[l].p, c, Vl, U->d1[l].p);

@@ -1,8 +1,19 @@
-// unet_tc.cuh -- the U-Net's 3x3x3 convolutions (forward and data gradient)
+// unet_tc.cuh -- the 3x3x3 convolutions of the learned warm start's U-Net (it
+// predicts the steady velocity and concentration fields from the structure)
 // on the 5th-generation tensor cores: tcgen05.mma with the accumulator in
 // tensor memory, operands staged in shared memory by TMA.
 //
-// Implicit GEMM  Y[v][n] = sum_k sum_c X[v + o_k][c] WT[k][n][c]  with a CTA
+// Activations are BF16 in NDHWC layout (channels last); weights are kept in
+// FP32 (master copy for Adam) and converted to BF16 operand layouts before
+// each pass.  With o_k = (k/9 - 1, k/3 % 3 - 1, k % 3 - 1) over (z, y, x) and
+// zero padding at the box faces:
+//   forward    Y[v][n] = sum_k sum_c X[v + o_k][c] WT[k][n][c]
+//   data grad  the forward kernels on dY with WT[k][ci][co] = W[26-k][ci][co]
+//   weight grad  dW[k][ci][co] = sum_v X[v + o_k][ci] dY[v][co]
+// Three kernels: conv3d_tc (below), conv3d_tc_res (the forward with resident
+// weights, for narrow layers) and conv3d_wgrad_tc (the weight gradient).
+//
+// conv3d_tc: implicit GEMM  Y[v][n] = sum_k sum_c X[v + o_k][c] WT[k][n][c]  with a CTA
 // tile of M = 128 voxels (a box of 8 x 8 x 2 voxels in x, y, z) and all N
 // output channels (16..256).  For each of the 27 offsets o_k and each
 // 64-channel chunk of each input, TMA copies
@@ -28,10 +39,19 @@
 
 #include <cuda.h>  // CUtensorMap (the type only; the encoder is fetched through the runtime)
 
-#include "unet_kernels.cuh"
+#include <cuda_bf16.h>
+
+#include "common.cuh"
 
 namespace om {
 namespace nn {
+
+typedef __nv_bfloat16 bf16;
+
+struct Grid {
+  int B, D, H, W;
+  __host__ __device__ int64_t voxels() const { return (int64_t)B * D * H * W; }
+};
 
 constexpr int kTcM = 128;            // voxels per CTA tile (8 x 8 x 2 box)
 constexpr int kTcKc = 64;            // channels per stage (128 bytes of BF16: one swizzle span)
@@ -485,6 +505,193 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
     atomicExch(a.err, 1);
     (void)mbar_wait(wfull, 0);  // the weight copies, if they never landed
     for (int i = h_used; i < h_issued; ++i) (void)mbar_wait(hfull0 + 8u * (i % NH), (uint32_t)(i / NH) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// ------------------------------------------------------------------ weight gradient
+// dW[k][ci][co] = sum over voxels v of X[v + o_k][ci] dY[v][co], read in
+// place: no transposed copies.  Both operands are "MN-major" (channels
+// contiguous, voxels along K) views of TMA copies with the 64-byte swizzle:
+// A of the input's halo (rows of 32 channels, as conv3d_tc_res loads it), B
+// of the 8 x 16-voxel tile of dY (one 32-channel atom per 8 KB).  An MN atom
+// of A is 32 channels; its four atoms sit one halo row (64 bytes) apart, so
+// one MMA's 128 rows of D are the channels of the offsets dx = -1, 0, +1 (and
+// a fourth, discarded).  A K-group of 8 voxels is one x row of the tile (10
+// halo rows apart in A, 8 in B); one K = 16 MMA covers two y rows.  A CTA
+// takes one 32-channel chunk of the input, a group of (dz, dy) pairs (all
+// nine, or for more than 32 output columns the three of one dz) and up to 128
+// output channels, keeps one TMEM accumulator per pair over every gridDim.x-th
+// tile and adds them to dW with FP32 atomics at the end.  Waits are bounded as in conv3d_tc.
+struct TcWgradArgs {
+  int c1, c2;     // input channels of the two concatenated parts
+  int nch1;       // 32-channel chunks of the first part
+  int N, Nm;      // output channels, and the MMA's N (min(N, 128) rounded up to 32)
+  int npart;      // parts of Nm output channels (N / 128 rounded up)
+  int npair;      // (dz, dy) pairs per CTA: 9, or 3 (one dz, a one-plane halo)
+  int nstage;     // pipeline stages
+  float* dw;      // [27][c1 + c2][N], accumulated
+  Grid g;
+  int tx, ty;     // tiles along x (8) and y (16); one z plane per tile
+  int* err;
+};
+
+constexpr uint32_t kWgPlane = (uint32_t)(kTcHx * kTcHy) * 64u;  // 11520: one z plane of the halo
+constexpr uint32_t kWgAtom = 128u * 64u;                         // 8192: 32 channels of the dY tile
+
+__host__ __device__ constexpr uint32_t wg_halo_bytes(int npair) { return npair == 9 ? kTrHalo : 12288u; }
+__host__ __device__ constexpr uint32_t wg_stage_bytes(int npair, int Nm) {
+  return wg_halo_bytes(npair) + (uint32_t)(Nm / 32) * kWgAtom;
+}
+
+// MN-major shared-memory descriptor, 64-byte swizzle: MN atoms of 32
+// elements `lbo` bytes apart, K-groups of 8 rows (64 bytes each) `sbo` apart
+__device__ __forceinline__ uint64_t mn_sw64_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+__global__ void __launch_bounds__(kTcThreads) conv3d_wgrad_tc(const __grid_constant__ CUtensorMap xm1,
+                                                              const __grid_constant__ CUtensorMap xm2,
+                                                              const __grid_constant__ CUtensorMap dym, TcWgradArgs a) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  // [halo + dY atoms] x nstage (1024-byte aligned), then the barriers and the TMEM address
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = tc_smem_raw + (base - raw);
+  const int S = a.nstage;
+  const uint32_t hbytes = wg_halo_bytes(a.npair), stage_bytes = wg_stage_bytes(a.npair, a.Nm);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (size_t)S * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * S, done = full0 + 16u * S;
+  __shared__ volatile int stop;
+  __shared__ int n_issued, n_used;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = a.g.B * a.g.D * a.ty * a.tx;
+  // this CTA's input chunk and (dz, dy) group
+  const int ngroup = 9 / a.npair;
+  const int part = (int)blockIdx.y % a.npart, n0 = part * a.Nm;
+  const int chunk = (int)blockIdx.y / a.npart / ngroup, grp = (int)blockIdx.y / a.npart % ngroup;
+  const bool second = chunk >= a.nch1;
+  const int ch0 = second ? (chunk - a.nch1) * 32 : chunk * 32;            // channel coordinate in its part
+  const int cnt = min(32, (second ? a.c2 : a.c1) - ch0);                  // real channels of the chunk
+  const int row0 = second ? a.c1 + ch0 : ch0;                             // its first row of dW
+  const int pair0 = grp * a.npair;                                        // first (dz, dy) pair: dz * 3 + dy
+  const CUtensorMap* xm = second ? &xm2 : &xm1;
+  const uint32_t tx_bytes = (a.npair == 9 ? 3u : 1u) * kWgPlane + (uint32_t)(a.Nm / 32) * kWgAtom;
+  uint32_t ncols = 32u;
+  while (ncols < (uint32_t)(a.npair * a.Nm)) ncols <<= 1;
+  int mytiles = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) ++mytiles;
+
+  if (tid == 0) {
+    stop = 0;
+    n_issued = n_used = 0;
+    for (int i = 0; i < S; ++i) {
+      mbar_init(full0 + 8u * i, 1);
+      mbar_init(empty0 + 8u * i, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (tid == 0) {
+    // producer: per tile the input halo (three planes, or plane z + dz) and the dY atoms
+    int i = 0;
+    for (; i < mytiles; ++i) {
+      const int st = i % S;
+      if (i >= S && !mbar_wait(empty0 + 8u * st, (uint32_t)(i / S - 1) & 1u, &stop)) break;
+      if (stop) break;
+      int t = blockIdx.x + i * gridDim.x;
+      const int x0 = (t % a.tx) * kTcTx;
+      t /= a.tx;
+      const int y0 = (t % a.ty) * kTcTy;
+      t /= a.ty;
+      const int z0 = t % a.g.D, bb = t / a.g.D;
+      const uint32_t sa = base + (uint32_t)st * stage_bytes, fb = full0 + 8u * st;
+      mbar_expect_tx(fb, tx_bytes);
+      tma_load_5d(sa, xm, ch0, x0 - 1, y0 - 1, a.npair == 9 ? z0 - 1 : z0 + grp - 1, bb, fb);
+      for (int j = 0; j < a.Nm / 32; ++j)
+        tma_load_5d(sa + hbytes + (uint32_t)j * kWgAtom, &dym, n0 + 32 * j, x0, y0, z0, bb, fb);
+      n_issued = i + 1;
+    }
+    if (i < mytiles) stop = 1;
+  } else if (tid == 32) {
+    // MMA issue: per pair and two y rows, A = halo rows (plane, y + dy, x + dx) for dx = 0..3
+    const uint32_t idesc = tc_idesc(kTcM, a.Nm) | (1u << 15) | (1u << 16);
+    int i = 0;
+    for (; i < mytiles; ++i) {
+      const int st = i % S;
+      if (!mbar_wait(full0 + 8u * st, (uint32_t)(i / S) & 1u, &stop)) break;
+      n_used = i + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + (uint32_t)st * stage_bytes;
+      const uint64_t ad0 = mn_sw64_desc(sa, 64u, kTcHx * 64u), bd0 = mn_sw64_desc(sa + hbytes, kWgAtom, 512u);
+      for (int p = 0; p < a.npair; ++p) {
+        const int pr = pair0 + p, dz = pr / 3, dy = pr % 3;
+        const uint32_t row = (uint32_t)((a.npair == 9 ? dz * kTcHy : 0) + dy) * kTcHx;  // first halo row
+        const uint32_t acc_addr = tmem + (uint32_t)(p * a.Nm);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint64_t ad = ad0 + (row + (uint32_t)kk * 2u * kTcHx) * 4u;  // 64-byte rows in units of 16 bytes
+          const uint64_t bd = bd0 + (uint32_t)kk * 64u;                      // 1024 bytes: two rows of 8 voxels
+          const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(acc_addr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       empty0 + 8u * st)
+                   : "memory");
+    }
+    if (i < mytiles) stop = 1;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                 : "memory");
+  }
+  const bool fin = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool failed = __syncthreads_or(!fin || stop) != 0;
+  if (failed && tid == 0) {
+    atomicExch(a.err, 1);
+    for (int j = n_used; j < n_issued; ++j) (void)mbar_wait(full0 + 8u * (j % S), (uint32_t)(j / S) & 1u);
+  }
+  // epilogue: warp w < 3 holds TMEM lanes 32 w .. + 31 = offset dx = w - 1, channel ch0 + lane
+  if (!failed && mytiles > 0 && warp < 3) {
+    for (int p = 0; p < a.npair; ++p) {
+      const int k = (pair0 + p) * 3 + warp;
+      float* dst = a.dw + ((int64_t)k * (a.c1 + a.c2) + row0 + lane) * a.N + n0;
+      for (int c0 = 0; c0 < a.Nm && n0 + c0 < a.N; c0 += 16) {
+        uint32_t q[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * a.Nm + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+              "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (lane >= cnt) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) atomicAdd(dst + c0 + j, __uint_as_float(q[j]));
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -28,8 +28,9 @@ def _case(shape, in_ch, out_ch, seed):
     return x.contiguous(), t.contiguous(), m.contiguous()
 
 
+# (16, 144): 144 output channels take two parts of the weight gradient's output columns
 @pytest.mark.parametrize("ch,shape", [((16, 32), (1, 16, 16, 16)), ((16, 32, 64, 128), (1, 16, 24, 32)),
-                                      ((32, 48), (2, 8, 12, 16))])
+                                      ((32, 48), (2, 8, 12, 16)), ((16, 144), (1, 8, 12, 16))])
 def test_unet_forward_and_gradients_match_reference(om, ch, shape):
     from oracle import unet as R
     in_ch, out_ch = 2, 2
