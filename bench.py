@@ -49,7 +49,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-converged-results leg")
     ap.add_argument("--mode", default="throughput",
-                    choices=["throughput", "converge", "batch", "precision", "warmstart", "layout"],
+                    choices=["throughput", "converge", "batch", "precision", "warmstart", "layout", "unet"],
                     help="converge: time to converged k and D_eff, plain vs batched + FP16 + warm start; "
                          "batch: the 150-structure set in one batch; precision: a 512^3 structure with "
                          "FP32, FP16 and BF16 population storage; warmstart: the learned warm start "
@@ -57,6 +57,8 @@ def _args():
                          "the sparse and the dense population layouts on 128^3 structures of rising porosity")
     ap.add_argument("--train-edge", type=int, default=96, help="warmstart mode: training box edge")
     ap.add_argument("--eval-edges", default="128,256", help="warmstart mode: held-out box edges")
+    ap.add_argument("--unet-shape", default="4,64,32-64-128",
+                    help="unet mode: batch, box edge and channels per level")
     ap.add_argument("--n-struct", type=int, default=150, help="batch mode: structures")
     ap.add_argument("--batch-set", default="150", choices=["150", "small"],
                     help="batch mode: the 150-structure set, or 20 structures of 64^3 drawn like it")
@@ -800,6 +802,61 @@ def run_layout(a):
     return 0
 
 
+def run_unet(a):
+    """The warm start's U-Net alone: forward and training step (forward, backward,
+    Adam) of a B x E^3 batch with 2 input and 1 output channel, random inputs,
+    CUDA events around 20 forwards and 10 steps after 3 warm-up passes.  The
+    convolution FLOPs of a forward are 2 x voxels x 27 x K x N per layer, K
+    counted as stored (the first layer's 2 input channels are padded to 16)."""
+    import torch
+
+    from paper_1410_1921_gb300 import build as B
+    B.build()
+    import paper_1410_1921_gb300 as P
+
+    nb, edge, chs = a.unet_shape.split(",")
+    nb, edge = int(nb), int(edge)
+    ch = tuple(int(c) for c in chs.split("-"))
+    torch.cuda.set_device(0)
+    net = P.UNet(2, 1, ch, seed=3)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.rand(nb, edge, edge, edge, 2, device="cuda", generator=g)
+    t = torch.rand(nb, edge, edge, edge, 1, device="cuda", generator=g)
+    y = torch.empty(nb, edge, edge, edge, 1, device="cuda")
+    m = torch.ones(nb, edge, edge, edge, dtype=torch.uint8, device="cuda")
+    flops = 0
+    for lv in range(len(ch)):
+        v = nb * (edge >> lv) ** 3
+        cin = 16 if lv == 0 else ch[lv - 1]
+        flops += 2 * v * 27 * (cin * ch[lv] + ch[lv] * ch[lv])
+        if lv + 1 < len(ch):
+            flops += 2 * v * 27 * ((ch[lv + 1] + ch[lv]) * ch[lv] + ch[lv] * ch[lv])
+    for _ in range(3):
+        net.forward(x, y)
+        net.train_step(x, t, m, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        net.forward(x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / 20
+    e0.record()
+    for _ in range(10):
+        net.train_step(x, t, m, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    step = e0.elapsed_time(e1) / 10
+    print(json.dumps({"metric": "U-Net training step", "value": round(step, 3), "unit": "ms", "higher_is_better": False,
+                      "n_gpus": 1, "dtype": "bf16", "data": "synthetic", "forward_ms": round(fwd, 3),
+                      "forward_conv_gflop": round(flops / 1e9, 2),
+                      "forward_conv_tflops": round(flops / fwd / 1e9, 1),
+                      "config": {"workload": f"U-Net {a.unet_shape.split(',')[2]}, {nb} x {edge}^3, 2 -> 1 channels",
+                                 "l2": "activations larger than L2"}}))
+    return 0
+
+
 def run_batch(a):
     """The 150-structure set (edges {64..200}^3, porosity U[0.10, 0.50], <d>
     U[10, 60] nm, tolerance U[0, 0.8], 1.5 nm voxels) advanced together: one
@@ -1068,6 +1125,8 @@ if __name__ == "__main__":
         sys.exit(run_warmstart(args))
     if args.mode == "layout":
         sys.exit(run_layout(args))
+    if args.mode == "unet":
+        sys.exit(run_unet(args))
     if args.mode == "batch":
         sys.exit(run_batch(args))
     if args.mode == "precision":

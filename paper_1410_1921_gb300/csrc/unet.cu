@@ -516,6 +516,7 @@ om_status wgrad_tc(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, c
   a.dw = U->g + c.w_off;
   a.g = g;
   a.tx = (g.W + kTcTx - 1) / kTcTx, a.ty = (g.H + kTcTy - 1) / kTcTy;
+  a.vec4 = reinterpret_cast<uintptr_t>(a.dw) % 16 == 0;
   a.err = U->tc_err.p;
   const int hmode = a.npair == 9 ? 1 : 2;
   CUtensorMap m1, m2, md;

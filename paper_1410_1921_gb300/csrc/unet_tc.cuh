@@ -525,7 +525,8 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
 // takes one 32-channel chunk of the input, a group of (dz, dy) pairs (all
 // nine, or for more than 32 output columns the three of one dz) and up to 128
 // output channels, keeps one TMEM accumulator per pair over every gridDim.x-th
-// tile and adds them to dW with FP32 atomics at the end.  Waits are bounded as in conv3d_tc.
+// tile and adds them to dW with FP32 atomics (four columns each) at the end.
+// Waits are bounded as in conv3d_tc.
 struct TcWgradArgs {
   int c1, c2;     // input channels of the two concatenated parts
   int nch1;       // 32-channel chunks of the first part
@@ -536,6 +537,7 @@ struct TcWgradArgs {
   float* dw;      // [27][c1 + c2][N], accumulated
   Grid g;
   int tx, ty;     // tiles along x (8) and y (16); one z plane per tile
+  int vec4;       // dw 16-byte aligned: add four columns per atomic
   int* err;
 };
 
@@ -688,8 +690,16 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_wgrad_tc(const __grid_const
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (lane >= cnt) continue;
+        if (a.vec4) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) atomicAdd(dst + c0 + j, __uint_as_float(q[j]));
+          for (int j = 0; j < 16; j += 4)
+            atomicAdd(reinterpret_cast<float4*>(dst + c0 + j),
+                      make_float4(__uint_as_float(q[j]), __uint_as_float(q[j + 1]), __uint_as_float(q[j + 2]),
+                                  __uint_as_float(q[j + 3])));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) atomicAdd(dst + c0 + j, __uint_as_float(q[j]));
+        }
       }
     }
   }
