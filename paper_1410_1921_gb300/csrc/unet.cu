@@ -532,7 +532,8 @@ om_status wgrad_tc(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, c
   OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int gy = (a.nch1 + nch2) * (9 / a.npair) * a.npart;
   const int64_t ntiles = (int64_t)g.B * g.D * a.ty * a.tx;
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (sms + gy - 1) / gy));
+  // one CTA per SM fits (shared memory); at most one wave, or the last CTAs run as a second
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms / gy));
   OM_CUDA(cudaFuncSetAttribute(conv3d_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   conv3d_wgrad_tc<<<dim3(gx, (unsigned)gy), kTcThreads, smem, s>>>(m1, m2, md, a);
   OM_CUDA(cudaGetLastError());
