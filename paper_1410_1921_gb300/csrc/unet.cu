@@ -413,13 +413,13 @@ om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, co
 }
 
 // 2-D map of the operand WT[27 N][K]: box {64 columns, N rows}, 128-byte
-// swizzle (narrow = true: {32 columns, N rows}, 64-byte swizzle)
-om_status weight_map(CUtensorMap* m, const bf16* wt, int K, int N, bool narrow = false) {
+// swizzle (narrow = true: {32 columns, rows (default N) rows}, 64-byte swizzle)
+om_status weight_map(CUtensorMap* m, const bf16* wt, int K, int N, bool narrow = false, int rows = 0) {
   EncodeTiledFn enc;
   OM_TRY(tensor_map_encoder(&enc));
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)27 * N};
   cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {narrow ? 32u : (cuuint32_t)kTcKc, (cuuint32_t)N};
+  cuuint32_t box[2] = {narrow ? 32u : (cuuint32_t)kTcKc, (cuuint32_t)(rows > 0 ? rows : N)};
   cuuint32_t es[2] = {1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wt, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, narrow ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
@@ -438,28 +438,34 @@ om_status conv_tc(const om_unet* U, const bf16* x1, int c1, int ld1, int o1, con
   if (N % 16 || N < 16 || N > 256 || c1 < 8 || (c1 % 8) || (c2 % 8) || (ld1 % 8) || (o1 % 8) || (ldy % 8) || (oy % 8))
     return fail(OM_EINVAL, "U-Net: convolution shape outside the tensor-core kernel's layout");
   CUtensorMap m1, m2, mw;
-  if (c2 == 0 && c1 <= 32 && N <= 64) {
-    // resident weights: one persistent CTA per SM (conv3d_tc_res)
+  if (c2 == 0 && c1 <= 32 && (N <= 64 || !yf)) {
+    // resident weights: one persistent CTA per SM (conv3d_tc_res); wider outputs in parts
+    // of at most 64 channels (multiples of 16), one launch each
     OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g, 1));
-    OM_TRY(weight_map(&mw, wt, c1, N, true));
-    TcConvArgs a{};
-    a.c1 = c1, a.c2 = 0, a.N = N, a.bias = bias, a.y = y, a.ldy = ldy, a.oy = oy, a.yf = yf, a.relu = relu, a.g = g;
-    a.tx = (g.W + kTcTx - 1) / kTcTx, a.ty = (g.H + kTcTy - 1) / kTcTy;
-    a.err = U->tc_err.p;
+    const int nparts = (N + 63) / 64, width = ((N + nparts - 1) / nparts + 15) / 16 * 16;
     int dev = 0, sms = 0;
     OM_CUDA(cudaGetDevice(&dev));
     OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t tiles = (int64_t)g.B * g.D * a.ty * a.tx;
-    // as many halo buffers (2..4) as 227 KB of shared memory hold next to the weights, and
-    // as many accumulators (2..4) as 256 TMEM columns
-    auto smem_for = [&](int nh) { return 1024 + (size_t)nh * kTrHalo + 27 * (size_t)N * 64 + 8 * 18 + 16; };
-    a.nhalo = 4;
-    while (a.nhalo > 2 && smem_for(a.nhalo) > 227 * 1024) --a.nhalo;
-    a.nacc = std::min(4, 256 / N);
-    const size_t smem = smem_for(a.nhalo);
-    OM_CUDA(cudaFuncSetAttribute(conv3d_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv3d_tc_res<<<(unsigned)std::min<int64_t>(tiles, sms), kTrThreads, smem, s>>>(m1, mw, a);
-    OM_CUDA(cudaGetLastError());
+    for (int n0 = 0; n0 < N; n0 += width) {
+      const int np = std::min(width, N - n0);
+      OM_TRY(weight_map(&mw, wt, c1, N, true, np));
+      TcConvArgs a{};
+      a.c1 = c1, a.c2 = 0, a.N = np, a.bias = bias ? bias + n0 : nullptr, a.y = y, a.ldy = ldy, a.oy = oy + n0;
+      a.yf = yf, a.relu = relu, a.g = g, a.nw = N, a.n0 = n0;
+      a.tx = (g.W + kTcTx - 1) / kTcTx, a.ty = (g.H + kTcTy - 1) / kTcTy;
+      a.err = U->tc_err.p;
+      const int64_t tiles = (int64_t)g.B * g.D * a.ty * a.tx;
+      // as many halo buffers (2..4) as 227 KB of shared memory hold next to the weights, and
+      // as many accumulators (2..4) as 256 TMEM columns
+      auto smem_for = [&](int nh) { return 1024 + (size_t)nh * kTrHalo + 27 * (size_t)np * 64 + 8 * 18 + 16; };
+      a.nhalo = 4;
+      while (a.nhalo > 2 && smem_for(a.nhalo) > 227 * 1024) --a.nhalo;
+      a.nacc = std::min(4, 256 / np);
+      const size_t smem = smem_for(a.nhalo);
+      OM_CUDA(cudaFuncSetAttribute(conv3d_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      conv3d_tc_res<<<(unsigned)std::min<int64_t>(tiles, sms), kTrThreads, smem, s>>>(m1, mw, a);
+      OM_CUDA(cudaGetLastError());
+    }
     return OM_OK;
   }
   OM_TRY(activation_map(&m1, x1, c1, ld1, o1, g));

@@ -75,6 +75,7 @@ struct TcConvArgs {
   Grid g;
   int tx, ty, tz;     // tiles along x, y, z (8, 8, 2 voxels each; the resident form: 8, 16, 1)
   int nhalo, nacc;    // the resident form's halo buffers and TMEM accumulators (2..4 each)
+  int nw, n0;         // the resident form: weight rows per offset in WT, and this launch's first
   int* err;           // set when a wait ran out
 };
 
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
     // producer: the weights once, then each tile's halo into the buffer its
     // tile two back has released
     mbar_expect_tx(wfull, 27u * wbox);
-    for (int k = 0; k < 27; ++k) tma_load_2d(wres + (uint32_t)k * wbox, &mapw, 0, k * a.N, wfull);
+    for (int k = 0; k < 27; ++k) tma_load_2d(wres + (uint32_t)k * wbox, &mapw, 0, k * a.nw + a.n0, wfull);
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int hb = i % NH;
