@@ -393,7 +393,7 @@ om_status tensor_map_encoder(EncodeTiledFn* out) {
 // zero fill; box by mode: 0 = {64 channels, 8 x, 8 y, 2 z, 1 batch} with the
 // 128-byte swizzle, and with the 64-byte swizzle 1 = the {32, 10, 18, 3, 1}
 // halo, 2 = its one-plane form {32, 10, 18, 1, 1}, 3 = the 8 x 16 tile
-// {32, 8, 16, 1, 1}
+// {32, 8, 16, 1, 1}, 4 = {32, 10, 16, 3, 1}, 5 = {32, 8, 18, 1, 1}
 om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, const Grid& g, int mode = 0) {
   const bool halo = mode != 0;
   EncodeTiledFn enc;
@@ -404,6 +404,8 @@ om_status activation_map(CUtensorMap* m, const bf16* x, int c, int ld, int o, co
   cuuint32_t box[5] = {(cuuint32_t)kTcKc, 8, 8, 2, 1};
   if (mode == 1 || mode == 2) box[0] = 32, box[1] = kTcHx, box[2] = kTcHy, box[3] = mode == 1 ? kTcHz : 1;
   if (mode == 3) box[0] = 32, box[1] = kTcTx, box[2] = kTcTy, box[3] = 1;
+  if (mode == 4) box[0] = 32, box[1] = kTcHx, box[2] = kTcTy, box[3] = 3;
+  if (mode == 5) box[0] = 32, box[1] = kTcTx, box[2] = kTcTy + 2, box[3] = 1;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(x + o), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, halo ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
@@ -509,8 +511,9 @@ om_status conv_dgrad(const om_unet* U, const Conv& c, const bf16* dyp, bf16* dx,
   return conv_tc(U, dyp, c.cout, c.cout, 0, nullptr, 0, 0, 0, c.wd, N, nullptr, dx, N, 0, nullptr, 0, g, s);
 }
 
-// dW += the weight gradient on tcgen05 (conv3d_wgrad_tc): one CTA per input chunk of 32
-// channels, (dz, dy) group and part of 128 output channels, gridDim.x of them over the tiles
+// dW += the weight gradient on tcgen05: conv3d_wgrad_tc32 for at most 32 output channels
+// (one CTA per input chunk of 32 channels), else conv3d_wgrad_tc (one CTA per chunk, dz and
+// part of 128 output channels); gridDim.x of them over the tiles
 om_status wgrad_tc(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, const bf16* x2, int ld2, int o2,
                    const bf16* dyp, const Grid& g, cudaStream_t s) {
   TcWgradArgs a{};
@@ -518,13 +521,34 @@ om_status wgrad_tc(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, c
   const int nch2 = (c.cin2 + 31) / 32;
   a.N = c.cout, a.Nm = (std::min(c.cout, 128) + 31) / 32 * 32;
   a.npart = (c.cout + 127) / 128;
-  a.npair = a.Nm == 32 ? 9 : 3;
   a.dw = U->g + c.w_off;
   a.g = g;
   a.tx = (g.W + kTcTx - 1) / kTcTx, a.ty = (g.H + kTcTy - 1) / kTcTy;
   a.vec4 = reinterpret_cast<uintptr_t>(a.dw) % 16 == 0;
   a.err = U->tc_err.p;
-  const int hmode = a.npair == 9 ? 1 : 2;
+  int dev = 0, sms = 0;
+  OM_CUDA(cudaGetDevice(&dev));
+  OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (a.Nm == 32) {
+    // at most 32 output channels: the swapped form (conv3d_wgrad_tc32), all 27 offsets per CTA
+    CUtensorMap m1, m2, md;
+    OM_TRY(activation_map(&m1, x1, c.cin1, ld1, o1, g, 4));
+    if (c.cin2 > 0) OM_TRY(activation_map(&m2, x2, c.cin2, ld2, o2, g, 4));
+    else m2 = m1;
+    OM_TRY(activation_map(&md, dyp, c.cout, c.cout, 0, g, 5));
+    a.nstage = (int)std::min<size_t>(4, (227 * 1024 - 2048) / kWnStage);
+    const size_t smem = 1024 + (size_t)a.nstage * kWnStage + 8 * (2 * a.nstage + 1) + 16;
+    const int gy = a.nch1 + nch2;
+    const int64_t ntiles = (int64_t)g.B * g.D * (a.ty + 1) * a.tx;
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms / gy));
+    OM_CUDA(cudaFuncSetAttribute(conv3d_wgrad_tc32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv3d_wgrad_tc32<<<dim3(gx, (unsigned)gy), kTcThreads, smem, s>>>(m1, m2, md, a);
+    OM_CUDA(cudaGetLastError());
+    return OM_OK;
+  }
+  // wider outputs: conv3d_wgrad_tc, the three (dz, dy) pairs of one dz per CTA
+  a.npair = 3;
+  const int hmode = 2;
   CUtensorMap m1, m2, md;
   OM_TRY(activation_map(&m1, x1, c.cin1, ld1, o1, g, hmode));
   if (c.cin2 > 0) OM_TRY(activation_map(&m2, x2, c.cin2, ld2, o2, g, hmode));
@@ -533,9 +557,6 @@ om_status wgrad_tc(om_unet* U, const Conv& c, const bf16* x1, int ld1, int o1, c
   const size_t stage = wg_stage_bytes(a.npair, a.Nm);
   a.nstage = (int)std::min<size_t>(4, (227 * 1024 - 2048) / stage);
   const size_t smem = 1024 + (size_t)a.nstage * stage + 8 * (2 * a.nstage + 1) + 16;
-  int dev = 0, sms = 0;
-  OM_CUDA(cudaGetDevice(&dev));
-  OM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int gy = (a.nch1 + nch2) * (9 / a.npair) * a.npart;
   const int64_t ntiles = (int64_t)g.B * g.D * a.ty * a.tx;
   // one CTA per SM fits (shared memory); at most one wave, or the last CTAs run as a second

@@ -10,8 +10,9 @@
 //   forward    Y[v][n] = sum_k sum_c X[v + o_k][c] WT[k][n][c]
 //   data grad  the forward kernels on dY with WT[k][ci][co] = W[26-k][ci][co]
 //   weight grad  dW[k][ci][co] = sum_v X[v + o_k][ci] dY[v][co]
-// Three kernels: conv3d_tc (below), conv3d_tc_res (the forward with resident
-// weights, for narrow layers) and conv3d_wgrad_tc (the weight gradient).
+// Kernels: conv3d_tc (below), conv3d_tc_res (the forward with resident
+// weights, for narrow inputs), conv3d_wgrad_tc and conv3d_wgrad_tc32 (the
+// weight gradient; the second for at most 32 output channels).
 //
 // conv3d_tc: implicit GEMM  Y[v][n] = sum_k sum_c X[v + o_k][c] WT[k][n][c]  with a CTA
 // tile of M = 128 voxels (a box of 8 x 8 x 2 voxels in x, y, z) and all N
@@ -524,8 +525,8 @@ __global__ void __launch_bounds__(kTrThreads) conv3d_tc_res(const __grid_constan
 // a fourth, discarded).  A K-group of 8 voxels is one x row of the tile (10
 // halo rows apart in A, 8 in B); one K = 16 MMA covers two y rows.  A CTA
 // takes one 32-channel chunk of the input, a group of (dz, dy) pairs (all
-// nine, or for more than 32 output columns the three of one dz) and up to 128
-// output channels, keeps one TMEM accumulator per pair over every gridDim.x-th
+// nine when 9 x N columns fit TMEM; the host launches it with the three of
+// one dz, for more than 32 output channels) and up to 128 output channels, keeps one TMEM accumulator per pair over every gridDim.x-th
 // tile and adds them to dW with FP32 atomics (four columns each) at the end.
 // Waits are bounded as in conv3d_tc.
 struct TcWgradArgs {
@@ -703,6 +704,165 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_wgrad_tc(const __grid_const
         }
       }
     }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// Weight gradient for at most 32 output channels: the roles swapped, so that
+// one MMA is 128 x 96 x 16 instead of 128 x 32 x 16.  A = dY from a copy of
+// the tile's rows y0 - 2 .. y0 + 15 (box {32, 8, 18, 1, 1}); its four 32-channel
+// atoms are those rows shifted by a = 0..3 in y (one tile row, 512 bytes,
+// apart).  B = the input's rows y0 - 1 .. y0 + 14 of planes z0 - 1 .. z0 + 1
+// (box {32, 10, 16, 3, 1}); its three atoms are shifted by b = 0..2 in x (one
+// halo row apart).  For the dY voxel u the product pairs dY[u] with
+// X[u + (b - 1, 1 - a, dz)]: D row (a, co), column (b, ci) of the accumulator
+// of plane dz is the gradient of offset (dz, dy = 1 - a, dx = b - 1), and
+// a = 3 is discarded.  Tile row j sums u over y0 - 2 + a + [0, 16); one more
+// tile row (j = ty) with only its first two rows closes the gap this leaves
+// at the far face for a < 2.  A CTA takes one 32-channel input chunk and all
+// 27 offsets (3 accumulators of 96 columns).
+constexpr uint32_t kWnB = 3u * 160u * 64u;  // 30720: B, three planes of 16 x 10 rows
+constexpr uint32_t kWnA = 10240u;           // A: 18 x 8 rows (9216 bytes) and the discarded atom's overrun
+constexpr uint32_t kWnStage = kWnB + kWnA;
+constexpr uint32_t kWnTx = kWnB + 144u * 64u;
+
+__global__ void __launch_bounds__(kTcThreads) conv3d_wgrad_tc32(const __grid_constant__ CUtensorMap xm1,
+                                                                const __grid_constant__ CUtensorMap xm2,
+                                                                const __grid_constant__ CUtensorMap dym, TcWgradArgs a) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = tc_smem_raw + (base - raw);
+  const int S = a.nstage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (size_t)S * kWnStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * S, done = full0 + 16u * S;
+  __shared__ volatile int stop;
+  __shared__ int n_issued, n_used;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tyx = a.ty + 1;  // tile rows, the last one two rows high
+  const int ntiles = a.g.B * a.g.D * tyx * a.tx;
+  const int chunk = (int)blockIdx.y;
+  const bool second = chunk >= a.nch1;
+  const int ch0 = second ? (chunk - a.nch1) * 32 : chunk * 32;
+  const int cnt = min(32, (second ? a.c2 : a.c1) - ch0);
+  const int row0 = second ? a.c1 + ch0 : ch0;
+  const CUtensorMap* xm = second ? &xm2 : &xm1;
+  constexpr uint32_t ncols = 512u;  // 3 x 96
+  int mytiles = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) ++mytiles;
+
+  if (tid == 0) {
+    stop = 0;
+    n_issued = n_used = 0;
+    for (int i = 0; i < S; ++i) {
+      mbar_init(full0 + 8u * i, 1);
+      mbar_init(empty0 + 8u * i, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (tid == 0) {
+    int i = 0;
+    for (; i < mytiles; ++i) {
+      const int st = i % S;
+      if (i >= S && !mbar_wait(empty0 + 8u * st, (uint32_t)(i / S - 1) & 1u, &stop)) break;
+      if (stop) break;
+      int t = blockIdx.x + i * gridDim.x;
+      const int x0 = (t % a.tx) * kTcTx;
+      t /= a.tx;
+      const int y0 = (t % tyx) * kTcTy;
+      t /= tyx;
+      const int z0 = t % a.g.D, bb = t / a.g.D;
+      const uint32_t sa = base + (uint32_t)st * kWnStage, fb = full0 + 8u * st;
+      mbar_expect_tx(fb, kWnTx);
+      tma_load_5d(sa, xm, ch0, x0 - 1, y0 - 1, z0 - 1, bb, fb);
+      tma_load_5d(sa + kWnB, &dym, 0, x0, y0 - 2, z0, bb, fb);
+      n_issued = i + 1;
+    }
+    if (i < mytiles) stop = 1;
+  } else if (tid == 32) {
+    const uint32_t idesc = tc_idesc(kTcM, 96) | (1u << 15) | (1u << 16);
+    int i = 0;
+    for (; i < mytiles; ++i) {
+      const int st = i % S;
+      if (!mbar_wait(full0 + 8u * st, (uint32_t)(i / S) & 1u, &stop)) break;
+      n_used = i + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int yt = (blockIdx.x + i * gridDim.x) / a.tx % tyx;
+      const int nk = yt == a.ty ? 1 : 8;  // the last tile row: its first two rows only
+      const uint32_t sa = base + (uint32_t)st * kWnStage;
+      // A: dY, atoms one tile row (512 bytes) apart, K-groups one tile row apart;
+      // B: the planes, atoms one halo row (64 bytes) apart, K-groups 10 rows apart
+      const uint64_t ad0 = mn_sw64_desc(sa + kWnB, 512u, 512u), bd0 = mn_sw64_desc(sa, 64u, kTcHx * 64u);
+      for (int dz = 0; dz < 3; ++dz) {
+        const uint32_t acc_addr = tmem + (uint32_t)(dz * 96);
+        for (int kk = 0; kk < nk; ++kk) {
+          const uint64_t ad = ad0 + (uint32_t)kk * 64u;                                    // 1024 bytes
+          const uint64_t bd = bd0 + ((uint32_t)dz * 160u + (uint32_t)kk * 2u * kTcHx) * 4u;  // 64-byte rows
+          const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(acc_addr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       empty0 + 8u * st)
+                   : "memory");
+    }
+    if (i < mytiles) stop = 1;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                 : "memory");
+  }
+  const bool fin = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool failed = __syncthreads_or(!fin || stop) != 0;
+  if (failed && tid == 0) {
+    atomicExch(a.err, 1);
+    for (int j = n_used; j < n_issued; ++j) (void)mbar_wait(full0 + 8u * (j % S), (uint32_t)(j / S) & 1u);
+  }
+  // epilogue: warp w < 3 holds TMEM lanes 32 w .. + 31 = dy = 1 - w, output channel lane;
+  // columns dz * 96 + b * 32 + ci
+  if (!failed && mytiles > 0 && warp < 3) {
+    const bool live = lane < a.N;
+    for (int dz = 0; dz < 3; ++dz)
+      for (int b = 0; b < 3; ++b) {
+        const int k = dz * 9 + (2 - warp) * 3 + b;
+        float* dst = a.dw + ((int64_t)k * (a.c1 + a.c2) + row0) * a.N + lane;
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+          uint32_t q[16];
+          const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dz * 96 + b * 32 + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+                "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]),
+                "=r"(q[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (!live) continue;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < cnt) atomicAdd(dst + (int64_t)(c0 + j) * a.N, __uint_as_float(q[j]));
+        }
+      }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
