@@ -59,6 +59,7 @@ def test_unet_forward_and_gradients_match_reference(om, ch, shape):
     assert loss == pytest.approx(ref_loss, rel=2e-2)
     gg = grads.cpu().double()
     off = 0
+    rels = {}
     for name, shp in R.layout(in_ch, out_ch, ch):
         k = int(np.prod(shp))
         a, b = gg[off:off + k], ref_grad[off:off + k]
@@ -70,7 +71,15 @@ def test_unet_forward_and_gradients_match_reference(om, ch, shape):
             b = b.reshape(27, 16, -1)[:, :in_ch].reshape(-1)
         rel = ((a - b).norm() / b.norm()).item()
         cos = (torch.dot(a, b) / (a.norm() * b.norm())).item()
-        assert rel <= 5e-2 and cos >= 0.995, (name, rel, cos)
+        # BF16 activations and gradients on both sides: measured at most 2.6e-2 and at least 0.9996
+        assert rel <= 4e-2 and cos >= 0.999, (name, rel, cos)
+        rels[name] = rel
+    # a convolution's weight and bias gradients contract the same pre-activation gradient, so the
+    # weight gradient's deviation follows the bias gradient's; more than that would be its own
+    # kernel's error (measured: at most 0.87 of this bound)
+    for name, rel in rels.items():
+        if name.endswith(".w") and not name.startswith("head") and name[:-2] + ".b" in rels:
+            assert rel <= 1.5 * rels[name[:-2] + ".b"] + 3e-3, (name, rel, rels[name[:-2] + ".b"])
 
 
 def test_unet_training_reduces_loss(om):
